@@ -1,0 +1,164 @@
+"""CPU oracle of geometry-TSDF + asymmetric colour-volume integration.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` are the only callers.  The CUDA path in
+``paper_1602_06645_gb300`` shares no code with it and never imports it.
+
+``oracle.c`` is the plain per-voxel definition (Section IV.B, Eq. 5-7, 9 and
+the inherited KinectFusion TSDF update; Eq. 8-10 as colour mode 1) in binary32
+with a fixed operation order; ``adjoint.c`` is the binary64 photometric loss
+and its analytic gradient (the calibration-refinement extension).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRCS = [os.path.join(_HERE, "oracle.c"), os.path.join(_HERE, "adjoint.c")]
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+# -ffp-contract=off: no implicit fused multiply-adds; the operation order in the
+# source is the definition.  No fast-math.
+CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-shared", "-fPIC"]
+
+
+def build(force: bool = False) -> str:
+    srcs = [s for s in _SRCS if os.path.exists(s)]
+    newest = max(os.path.getmtime(s) for s in srcs)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", *CFLAGS, *srcs, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("ng", ctypes.c_int32 * 3),
+        ("nc", ctypes.c_int32 * 3),
+        ("s_g", ctypes.c_float),
+        ("s_c", ctypes.c_float),
+        ("origin", ctypes.c_float * 3),
+        ("mu", ctypes.c_float),
+        ("max_weight", ctypes.c_int32),
+        ("sigma", ctypes.c_float),
+        ("band", ctypes.c_float),
+        ("colour_mode", ctypes.c_int32),
+        ("sample_mode", ctypes.c_int32),
+        ("update_free_space", ctypes.c_int32),
+        ("n_threads", ctypes.c_int32),
+    ]
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        vp = ctypes.c_void_p
+        lib.orc_integrate.argtypes = [ctypes.POINTER(Params), vp, vp, vp, vp, ctypes.c_int, ctypes.c_int, vp,
+                                      ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp]
+        lib.orc_integrate.restype = ctypes.c_int
+        lib.orc_integrate_geometry.argtypes = [ctypes.POINTER(Params), vp, vp, vp, ctypes.c_int, ctypes.c_int,
+                                               vp, vp]
+        lib.orc_integrate_geometry.restype = ctypes.c_longlong
+        lib.orc_frame_constants.argtypes = [ctypes.POINTER(Params), vp, vp, vp, vp, vp, vp, vp]
+        lib.orc_params_size.restype = ctypes.c_int
+        assert lib.orc_params_size() == ctypes.sizeof(Params)
+        if hasattr(lib, "orc_adj_loss_grad"):
+            lib.orc_adj_loss_grad.restype = ctypes.c_double
+        _lib = lib
+    return _lib
+
+
+def _f32(a, shape):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    assert a.shape == shape, (a.shape, shape)
+    return a
+
+
+def volume_geometry(dims_geo, voxel_size):
+    """(s_g, s_c-independent) extent and default origin: the cube of
+    dims_geo * voxel_size centred on the world origin."""
+    return tuple(float(np.float32(-0.5 * float(n) * float(voxel_size))) for n in dims_geo)
+
+
+def colour_voxel(dims_geo, dims_col, voxel_size):
+    """Colour voxel size: the same physical extent split into dims_col voxels
+    (Section IV.B: same size, more voxels), binary64 then rounded to binary32."""
+    return float(np.float32(float(dims_geo[0]) * float(voxel_size) / float(dims_col[0])))
+
+
+class Oracle:
+    """Holds the two volumes (linear, x fastest) and integrates frames on the CPU."""
+
+    def __init__(self, dims_geo, dims_col, voxel_size, mu, max_weight, sigma=0.020, band=None,
+                 colour_mode=0, sample_mode=0, update_free_space=1, origin=None, n_threads=1):
+        self.lib = _load()
+        p = Params()
+        p.ng[:] = [int(v) for v in dims_geo]
+        p.nc[:] = [int(v) for v in dims_col]
+        p.s_g = float(voxel_size)
+        p.s_c = colour_voxel(dims_geo, dims_col, voxel_size)
+        o = volume_geometry(dims_geo, voxel_size) if origin is None else origin
+        p.origin[:] = [float(v) for v in o]
+        p.mu = float(mu)
+        p.max_weight = int(max_weight)
+        p.sigma = float(sigma)
+        # default band: one colour voxel either side of the zero crossing, in
+        # normalised TSDF units (binary32 quotient)
+        p.band = float(np.float32(p.s_c) / np.float32(p.mu)) if band is None else float(band)
+        p.colour_mode, p.sample_mode = int(colour_mode), int(sample_mode)
+        p.update_free_space, p.n_threads = int(update_free_space), int(n_threads)
+        self.p = p
+        gx, gy, gz = dims_geo
+        cx, cy, cz = dims_col
+        self.F = np.zeros((gz, gy, gx), dtype=np.float32)
+        self.W = np.zeros((gz, gy, gx), dtype=np.uint8)
+        self.C = np.zeros((cz, cy, cx), dtype=np.uint32)
+        self.counts = np.zeros(2, dtype=np.int64)
+
+    def integrate(self, depth, rgb, K_depth, K_rgb, T_world_depth, T_depth_rgb):
+        depth = np.ascontiguousarray(depth, dtype=np.uint16)
+        rgb = np.ascontiguousarray(rgb, dtype=np.uint8)
+        dh, dw = depth.shape
+        ch, cw, _ = rgb.shape
+        Kd, Kr = _f32(K_depth, (3, 3)), _f32(K_rgb, (3, 3))
+        Twd, Tdr = _f32(T_world_depth, (4, 4)), _f32(T_depth_rgb, (4, 4))
+        self.lib.orc_integrate(ctypes.byref(self.p), self.F.ctypes.data, self.W.ctypes.data, self.C.ctypes.data,
+                               depth.ctypes.data, dw, dh, rgb.ctypes.data, cw, ch, Kd.ctypes.data, Kr.ctypes.data,
+                               Twd.ctypes.data, Tdr.ctypes.data, self.counts.ctypes.data)
+        return int(self.counts[0]), int(self.counts[1])
+
+    def integrate_geometry(self, depth, K_depth, T_world_depth):
+        depth = np.ascontiguousarray(depth, dtype=np.uint16)
+        dh, dw = depth.shape
+        Kd, Twd = _f32(K_depth, (3, 3)), _f32(T_world_depth, (4, 4))
+        return int(self.lib.orc_integrate_geometry(ctypes.byref(self.p), self.F.ctypes.data, self.W.ctypes.data,
+                                                   depth.ctypes.data, dw, dh, Kd.ctypes.data, Twd.ctypes.data))
+
+    def frame_constants(self, K_depth, K_rgb, T_world_depth, T_depth_rgb):
+        R = np.zeros(9, np.float32)
+        t = np.zeros(3, np.float32)
+        Kdi = np.zeros(9, np.float32)
+        args = [_f32(K_depth, (3, 3)), _f32(K_rgb, (3, 3)), _f32(T_world_depth, (4, 4)), _f32(T_depth_rgb, (4, 4))]
+        self.lib.orc_frame_constants(ctypes.byref(self.p), *[a.ctypes.data for a in args], R.ctypes.data,
+                                     t.ctypes.data, Kdi.ctypes.data)
+        return R.reshape(3, 3), t, Kdi.reshape(3, 3)
+
+    @property
+    def colour_rgb(self):
+        """(Nz, Ny, Nx, 3) uint8 colours."""
+        c = self.C
+        return np.stack([(c >> (8 * k)) & 0xFF for k in range(3)], axis=-1).astype(np.uint8)
+
+    @property
+    def colour_weight(self):
+        return (self.C >> 24).astype(np.uint8)

@@ -1,0 +1,66 @@
+"""The oracle pins must catch plausible slips in the oracle.
+
+Each case copies the oracle to a temporary directory, plants one mistake in
+its C source (a transposed pose, a swapped u/v, a dropped gate, a wrong
+rounding, ...), rebuilds it there and runs the pin suite against the planted
+copy on the CPU.  The pin suite must fail for every mutant.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTANTS = {
+    "pose_not_transposed": ("f->R[r * 3 + c] = Twd[c * 4 + r];", "f->R[r * 3 + c] = Twd[r * 4 + c];"),
+    "translation_sign": ("f->t[i] = (float)(-s);", "f->t[i] = (float)(s);"),
+    "u_v_swapped": ("*u = xh * rz;\n    *v = yh * rz;", "*v = xh * rz;\n    *u = yh * rz;"),
+    "pixel_floor_not_round": ("float fu = floorf(u + 0.5f), fv = floorf(v + 0.5f);",
+                              "float fu = floorf(u), fv = floorf(v);"),
+    "sdf_sign": ("float sdf = d - P[2];", "float sdf = P[2] - d;"),
+    "hidden_not_skipped": ("if (sdf < -p->mu) continue;", ""),
+    "no_truncation": ("float t = fminf(1.0f, sdf * fr->inv_mu);", "float t = sdf * fr->inv_mu;"),
+    "plain_mean": ("F[idx] = fmaf(F[idx], wf, t) / (wf + 1.0f);", "F[idx] = (F[idx] + t) * 0.5f;"),
+    "weight_uncapped": ("W[idx] = (uint8_t)(w + 1 < p->max_weight ? w + 1 : p->max_weight);",
+                        "W[idx] = (uint8_t)(w + 1);"),
+    "depth_in_cm": ("float d = (float)D * 0.001f;\n                float sdf",
+                    "float d = (float)D * 0.01f;\n                float sdf"),
+    "no_sigma_gate": ("if (dist2 > fr->sigma2) continue;", ""),
+    "no_band_gate": ("if (!(fabsf(Ft) <= p->band)) continue;", ""),
+    "extrinsic_translation_flipped": ("rigid(fr->Rc, fr->tc, Pc[0], Pc[1], Pc[2], Ph);",
+                                      "rigid(fr->Rc, fr->tc, Pc[0], Pc[1], Pc[2], Ph); Ph[0] -= 2 * fr->tc[0];"),
+    "trilinear_axis_mixed": ("float c0 = lerpf(c00, c10, fr[1]);", "float c0 = lerpf(c00, c10, fr[0]);"),
+    "colour_rounds_down": ("uint32_t nc = (cc * w + s[c] + ((w + 1u) >> 1)) / (w + 1u);",
+                           "uint32_t nc = (cc * w + s[c]) / (w + 1u);"),
+    "bilinear_weights_swapped": ("float top = fmaf(ax, p10 - p00, p00);", "float top = fmaf(ay, p10 - p00, p00);"),
+    "colour_before_geometry": (
+        "long long g = orc_geometry(p, &fr, F, W, depth);\n    long long c = orc_colour(p, &fr, F, W, C, depth, rgb);",
+        "long long c = orc_colour(p, &fr, F, W, C, depth, rgb);\n    long long g = orc_geometry(p, &fr, F, W, depth);"),
+    "normal_weight_sign": ("float dot = fmaf(n[0], Pc[0], fmaf(n[1], Pc[1], n[2] * Pc[2]));",
+                           "float dot = -fmaf(n[0], Pc[0], fmaf(n[1], Pc[1], n[2] * Pc[2]));"),
+    "eq10_additive": ("uint32_t wn = wp + (wq * (255u - wp) + 127u) / 255u;",
+                      "uint32_t wn = wp + wq > 255u ? 255u : wp + wq;"),
+    "no_08_gate": ("if (!(5u * wq > 4u * wp)) return 0;", ""),
+    "unobserved_corner_used": ("if (W[idx] == 0) return 0;", ""),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(tmp_path, name):
+    before, after = MUTANTS[name]
+    src = open(os.path.join(ROOT, "oracle", "oracle.c")).read()
+    assert src.count(before) == 1, "mutation site not found: " + name
+    d = tmp_path / "repo"
+    shutil.copytree(os.path.join(ROOT, "oracle"), d / "oracle",
+                    ignore=shutil.ignore_patterns("*.so", "*.tmp*", "__pycache__"))
+    (d / "oracle" / "oracle.c").write_text(src.replace(before, after))
+    shutil.copytree(os.path.join(ROOT, "tests"), d / "tests", ignore=shutil.ignore_patterns("__pycache__"))
+    os.symlink(os.path.join(ROOT, "paper_1602_06645_gb300"), d / "paper_1602_06645_gb300")
+    shutil.copy(os.path.join(ROOT, "pytest.ini"), d / "pytest.ini")
+    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-q", "-x",
+                        "-p", "no:cacheprovider", "-m", "not gpu"],
+                       cwd=d, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1, "pins did not catch mutant %s:\n%s" % (name, r.stdout[-2000:])
