@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""Throughput of per-frame geometry-TSDF + asymmetric colour-volume fusion.
+
+One step = one frame of the whole fusion path (depth tiles, brick culling,
+TSDF update, colour work list, colour update) through libtsdf.so, on the
+scan-scale workload: 512^3 binary32 TSDF + uint8 weights and a 1024^3 RGBA8
+colour volume over a 2 m cube, a seeded 300-frame orbit of a 20-primitive
+scene (640x480 uint16 depth, 1920x1080 uint8 RGB).  Frames are integrated in
+sequence: W warm-up frames, then K timed frames.
+
+Prints one JSON line (rank 0).  `value` is nominal voxel-updates/s
+((N_geo + N_col) x frames / device time, the usual KinectFusion figure) with
+frames already resident in HBM; `e2e` is the same metric through the public
+API with page-locked host frames (host->device copies and a read-back of the
+frame's counters inside the timed region).
+
+--impl reference times the CPU oracle on the host cores on a bounded sample
+of the same workload (the central 1/64 of both volumes), same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=295)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="scan",
+                    help="scan (512^3/1024^3) | small (128^3/256^3) | sweep256 | sweep512 | sweep768 | sweep1024")
+    ap.add_argument("--dense", action="store_true", help="culling off (dense sweep of every brick)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-frames", type=int, default=12, help="frames of the oracle CPU-baseline sample")
+    return ap.parse_args()
+
+
+def make_sequence(workload, n_frames, rank):
+    from paper_1602_06645_gb300 import synth
+    if workload == "scan":
+        return synth.sequence_scan(n_frames=n_frames, seed=2 + 1000 * rank)
+    if workload == "small":
+        return synth.sequence_small(n_frames=n_frames, seed=1 + 1000 * rank)
+    if workload.startswith("sweep"):
+        return synth.sequence_sweep(int(workload[5:]), n_frames=n_frames, seed=3 + 1000 * rank)
+    raise SystemExit("unknown workload " + workload)
+
+
+def render_frames(seq, n):
+    out = []
+    for f in range(n):
+        out.append(seq.frame(f))
+    return out
+
+
+def nominal_voxels(seq):
+    return int(np.prod(seq.dims_geo)) + int(np.prod(seq.dims_col))
+
+
+# ----------------------------------------------------------- clocks -----
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.gpu_id, "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.12)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_uuid(dev):
+    import torch
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(dev)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+# ------------------------------------------------------- CPU oracle -----
+def oracle_sample(seq, frames, n_threads):
+    """Time the oracle on the central 1/64 of both volumes (1/4 of each edge)
+    over `frames`.  Returns (nominal voxel-updates/s of the sample, seconds,
+    description)."""
+    import oracle
+
+    g = [d // 4 for d in seq.dims_geo]
+    r = seq.dims_col[0] // seq.dims_geo[0]
+    full_origin = oracle.volume_geometry(seq.dims_geo, seq.voxel_size)
+    start = [(d - s) // 2 for d, s in zip(seq.dims_geo, g)]
+    origin = tuple(float(np.float32(o + st * np.float64(seq.voxel_size))) for o, st in zip(full_origin, start))
+    o = oracle.Oracle(g, [x * r for x in g], seq.voxel_size, seq.mu, seq.max_weight, origin=origin,
+                      n_threads=n_threads)
+    t0 = time.perf_counter()
+    for f, (d, c) in frames:
+        o.integrate(d, c, seq.K_depth, seq.K_rgb, seq.poses[f], seq.T_depth_rgb)
+    dt = time.perf_counter() - t0
+    nvox = int(np.prod(g)) + int(np.prod([x * r for x in g]))
+    desc = ("oracle (binary32, OpenMP) on the central %s geometry / %s colour block (1/64 of each volume), "
+            "%d frames" % ("x".join(map(str, g)), "x".join(str(x * r) for x in g), len(frames)))
+    return nvox * len(frames) / dt, dt, desc
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n = args.warmup + args.steps
+    seq = make_sequence(args.workload, n, 0)
+    frames = render_frames(seq, n)
+    cores = os.cpu_count() or 1
+    import oracle
+    oracle.build()
+    # warm-up steps (untimed), then K timed steps of one frame each
+    _, _, _ = oracle_sample(seq, list(enumerate(frames[:args.warmup])), cores) if args.warmup else (0, 0, "")
+    v, dt, desc = oracle_sample(seq, [(args.warmup + i, frames[args.warmup + i]) for i in range(args.steps)], cores)
+    line = {
+        "impl": "reference", "metric": "voxel-updates/s (nominal, geo+colour)", "value": v,
+        "unit": "voxel-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / max(args.steps, 1), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+u8", "data": "synthetic",
+        "config": {"workload": seq.name, "dims_geo": list(seq.dims_geo), "dims_col": list(seq.dims_col),
+                   "sample": "central 1/64 of both volumes"},
+        "cpu_baseline": {"value": v, "unit": "voxel-updates/s", "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": v, "unit": "voxel-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------- GPU -----
+def run_ours(args):
+    import torch
+    import paper_1602_06645_gb300 as T
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if not os.path.exists(T.LIB_PATH):
+        from paper_1602_06645_gb300 import build as b
+        b.build()
+    T.load()
+
+    n = args.warmup + args.steps
+    seq = make_sequence(args.workload, n, rank)
+    t0 = time.perf_counter()
+    frames = render_frames(seq, n)
+    gen_s = time.perf_counter() - t0
+    dev_frames = [(torch.from_numpy(d.view(np.int16)).cuda(), torch.from_numpy(c).cuda()) for d, c in frames]
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    vol = T.Volume(seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, seq.max_weight, culling=not args.dense,
+                   stream=stream.cuda_stream)
+    for f in range(args.warmup):
+        d, c = dev_frames[f]
+        vol.integrate(d, c, seq.K_depth, seq.K_rgb, seq.poses[f], seq.T_depth_rgb)
+    vol.synchronize()
+    vol.profile(True)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(gpu_uuid(local)) if rank == 0 else None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+        time.sleep(0.15)
+    for i in range(args.steps):
+        f = args.warmup + i
+        flush.zero_()  # evict L2 between steps (outside the timed events)
+        d, c = dev_frames[f]
+        ev[i][0].record(stream)
+        vol.integrate(d, c, seq.K_depth, seq.K_rgb, seq.poses[f], seq.T_depth_rgb)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    vol.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = float(sum(step_ms))
+    phases, pframes = vol.profile_read()
+    st = vol.stats()
+    vol.close()
+    del flush
+
+    nominal = nominal_voxels(seq)
+    units = nominal * args.steps
+    if dist:
+        t = torch.tensor([total_ms, float(units)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        total_ms, units = float(tmax[0]), float(t[1])
+    value = units / (total_ms / 1e3)
+
+    # ---- roofline of the dominant kernel (algorithmic bytes / event time)
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    K = max(args.steps, 1)
+    geo_bytes = 10.0 * st.total_geo_updated / K            # F (4 B) + w (1 B), read and written
+    col_bytes = (8.0 * st.total_col_updated                 # packed RGBW, read and written
+                 + 5.0 * 1000 * st.total_col_bricks) / K    # geometry tile (10^3 F + w) per colour brick
+    kern = {"geometry": (phases["geometry"] / K, geo_bytes), "colour": (phases["colour"] / K, col_bytes)}
+    dom = max(kern, key=lambda k: kern[k][0])
+    ms_launch, bytes_launch = kern[dom]
+    achieved = bytes_launch / (ms_launch / 1e3) / 1e9 if ms_launch > 0 else 0.0
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tr = json.load(f)
+        if tr.get("workload") == seq.name and tr.get("kernel") == dom and not args.dense:
+            traffic = tr.get("bytes_per_launch")
+    except Exception:
+        pass
+
+    result = {
+        "metric": "voxel-updates/s (nominal, geo+colour)", "value": value, "unit": "voxel-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / K,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+u8", "data": "synthetic",
+        "config": {"workload": seq.name, "dims_geo": list(seq.dims_geo), "dims_col": list(seq.dims_col),
+                   "depth": "%dx%d" % seq.depth_size, "rgb": "%dx%d" % seq.rgb_size, "frames": args.steps,
+                   "culling": not args.dense, "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": "independent scan per GPU" if world > 1 else "single GPU"},
+        "frames_per_s": args.steps * world / (total_ms / 1e3),
+        "updated_voxels_per_s": (st.total_geo_updated + st.total_col_updated) * world / (total_ms / 1e3),
+        "per_frame": {"geo_updated": st.total_geo_updated / K, "col_updated": st.total_col_updated / K,
+                      "geo_bricks": st.total_geo_bricks / K, "col_bricks": st.total_col_bricks / K,
+                      "visible_bricks": st.total_visible_bricks / K, "total_bricks": st.total_bricks},
+        "phase_ms_per_frame": {k: v / max(pframes, 1) for k, v in phases.items()},
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": traffic, "bytes_per_launch": bytes_launch,
+                     "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                     else "fallback 6.8 TB/s"},
+        "gpu_launches": 5 * args.steps,
+        "clocks": clocks,
+        "frame_generation_s": gen_s,
+    }
+
+    # ---- end to end through the public API, page-locked host frames
+    if not args.no_e2e:
+        host = [(torch.from_numpy(d.view(np.int16)).pin_memory(), torch.from_numpy(c).pin_memory()) for d, c in frames]
+        vol2 = T.Volume(seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, seq.max_weight, culling=not args.dense,
+                        stream=stream.cuda_stream)
+        for f in range(args.warmup):
+            vol2.integrate(host[f][0], host[f][1], seq.K_depth, seq.K_rgb, seq.poses[f], seq.T_depth_rgb)
+            vol2.stats()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            f = args.warmup + i
+            vol2.integrate(host[f][0], host[f][1], seq.K_depth, seq.K_rgb, seq.poses[f], seq.T_depth_rgb)
+            vol2.stats()  # device -> host read of the frame's counters (synchronising)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t[0])
+        vol2.close()
+        h2d = frames[0][0].nbytes + frames[0][1].nbytes
+        result["e2e"] = {"value": units / e2e_s, "unit": "voxel-updates/s", "h2d_bytes_per_step": int(h2d),
+                         "d2h_bytes_per_step": 88, "frames_per_s": args.steps * world / e2e_s}
+
+    # ---- CPU baseline: the oracle on the host cores, bounded sample
+    if world == 1 and rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        cores = os.cpu_count() or 1
+        nf = min(args.cpu_frames, len(frames))
+        v, dt, desc = oracle_sample(seq, list(enumerate(frames[:nf])), cores)
+        result["cpu_baseline"] = {"value": v, "unit": "voxel-updates/s", "cores": cores, "kind": "oracle",
+                                  "sample": desc, "seconds": dt}
+
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * tsdf.h — C ABI of the GB300 geometry-TSDF + asymmetric colour-volume fusion
+ * library (libtsdf.so).
+ *
+ * The library fuses RGB-D frames into two volumes over the same cube:
+ *   - a geometry volume: truncated signed distance F (binary32, normalised to
+ *     [-1, 1] by the truncation distance mu) and an 8-bit weight w, the
+ *     KinectFusion TSDF the paper builds on (Section III);
+ *   - a colour volume with more voxels over the same extent (Section IV.B, the
+ *     "asymmetric" colour volume), each voxel an 8-bit RGB colour C and an
+ *     8-bit weight W packed as R | G<<8 | B<<16 | W<<24.
+ * Each frame is a depth image (Kinect depth camera) and an HD RGB image from a
+ * rigidly attached, calibrated camera (Section IV.A).
+ *
+ * Units and conventions
+ *   - lengths in metres; depth images in uint16 millimetres, 0 = no measurement;
+ *   - RGB images uint8, height x width x 3, R first, rows contiguous;
+ *   - cameras: x right, y down, z forward; pixel (i, j) has its centre at
+ *     image coordinates (i, j);
+ *   - K: row-major 3x3 intrinsics (Eq. 1); T: row-major 4x4 rigid transforms;
+ *   - T_world_depth maps depth-camera coordinates to world coordinates (the
+ *     inverse of the motion (R_n, t_n) of Eq. 5); T_depth_rgb maps depth-camera
+ *     coordinates to RGB-camera coordinates ([R_calib | t_calib], Eq. 3);
+ *   - the volumes are axis-aligned in world coordinates; voxel (x, y, z) has
+ *     its centre at origin + (index + 0.5) * voxel_size;
+ *   - volumes returned by tsdf_read are linear, x fastest:
+ *     index = (z * Ny + y) * Nx + x.
+ *
+ * Errors: every call returns a tsdf_status; no call aborts, throws across the
+ * ABI or traps the device.  Kernel-side problems are recorded in a device
+ * status word and reported by the next synchronising call (tsdf_read,
+ * tsdf_synchronize, tsdf_save).
+ *
+ * Threading: one handle is used from one host thread at a time; work on a
+ * handle is ordered on its CUDA stream.
+ */
+#ifndef TSDF_H
+#define TSDF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tsdf_volume tsdf_volume; /* opaque; owned by the library */
+
+typedef enum {
+    TSDF_OK = 0,
+    TSDF_ERR_INVALID_ARG = -1,  /* an argument failed validation; nothing was done */
+    TSDF_ERR_OOM = -2,          /* device memory could not be allocated */
+    TSDF_ERR_CUDA = -3,         /* a CUDA runtime call failed (see tsdf_last_error) */
+    TSDF_ERR_TIMEOUT = -4,      /* a bounded device-side wait gave up */
+    TSDF_ERR_DEVICE_FAULT = -5, /* a kernel recorded an internal inconsistency */
+    TSDF_ERR_IO = -6            /* checkpoint file could not be read or written */
+} tsdf_status;
+
+typedef struct {
+    int32_t width, height;
+} tsdf_image_size;
+
+/* Device-memory provider.  alloc returns a device pointer (NULL on failure)
+ * for `bytes` bytes, usable on `stream`; free releases it.  NULL alloc/free
+ * select cudaMalloc/cudaFree.  The Python binding passes PyTorch's caching
+ * allocator here. */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* stream, void* ctx);
+    void (*free)(void* ptr, size_t bytes, void* stream, void* ctx);
+    void* ctx;
+} tsdf_allocator;
+
+enum { TSDF_COLOUR_COUNT = 0, TSDF_COLOUR_PAPER_NORMAL = 1 };
+enum { TSDF_SAMPLE_NEAREST = 0, TSDF_SAMPLE_BILINEAR = 1 };
+
+/* Options of tsdf_create_ex.  Fill with tsdf_params_default first. */
+typedef struct {
+    float origin[3];           /* world position of the volumes' minimum corner;
+                                  NaN = the cube centred on the world origin */
+    float sigma;               /* depth-distance gate of Eq. 7, metres [0.020, the paper's 20 mm] */
+    float band;                /* TSDF band gate on colour voxels, normalised units;
+                                  NaN = one colour voxel: s_c / mu */
+    int32_t colour_mode;       /* TSDF_COLOUR_COUNT: Eq. 9 with sample weight 1 (the
+                                  weight counts observing frames, capped at max_weight);
+                                  TSDF_COLOUR_PAPER_NORMAL: Eq. 8-10 */
+    int32_t sample_mode;       /* TSDF_SAMPLE_NEAREST (the HD pixel of Eq. 9) or BILINEAR */
+    int32_t culling;           /* 1: skip bricks that provably change nothing (results
+                                  are identical either way); 0: sweep every brick */
+    int32_t update_free_space; /* 1: voxels in front of the surface (sdf > mu) are
+                                  updated with F = 1; 0: only |sdf| <= mu */
+    void* stream;              /* cudaStream_t for all work on the handle; NULL = legacy default */
+    tsdf_allocator allocator;
+} tsdf_params;
+
+/* Fill *p with the defaults listed above. */
+void tsdf_params_default(tsdf_params* p);
+
+/* Create the two volumes, zero-initialised (F = 0, all weights 0).
+ *   dims_geo    geometry voxels per axis (x, y, z), each 1..4096
+ *   dims_col    colour voxels per axis; the same cube is split into more (or
+ *               fewer) voxels: dims_col[i] * dims_geo[0] == dims_col[0] * dims_geo[i]
+ *               (Section IV.B: "same size, higher dimension")
+ *   voxel_size  geometry voxel edge s_g (m) > 0; the cube edge is dims_geo * s_g
+ *               and the colour voxel edge s_c = dims_geo[0] * s_g / dims_col[0]
+ *   mu          truncation distance (m) > 0
+ *   max_weight  weight cap, 1..255 (weights count observing frames up to it)
+ *   out         receives the handle (owned by the caller until tsdf_destroy)
+ * Errors: INVALID_ARG (bad dims, ratio, sizes or NULL out), OOM, CUDA. */
+tsdf_status tsdf_create(const int32_t dims_geo[3], const int32_t dims_col[3], float voxel_size, float mu,
+                        int32_t max_weight, tsdf_volume** out);
+tsdf_status tsdf_create_ex(const int32_t dims_geo[3], const int32_t dims_col[3], float voxel_size, float mu,
+                           int32_t max_weight, const tsdf_params* params, tsdf_volume** out);
+
+/* Fuse one frame (Section IV.B): the geometry (TSDF) update of every geometry
+ * voxel, then the colour update of every colour voxel against the updated
+ * geometry:
+ *   Eq. 5   voxel -> current depth camera with the inverse of T_world_depth
+ *   Eq. 6   projection with K_depth; outside the image or D = 0 -> skipped
+ *   TSDF    sdf = D/1000 - Z; sdf < -mu -> skipped; F <- (F w + min(1, sdf/mu)) / (w+1),
+ *           w <- min(w+1, max_weight)
+ *   Eq. 7   colour voxels farther than sigma from the back-projected depth pixel are skipped
+ *   band    colour voxels whose trilinear TSDF has |F| > band are skipped
+ *   Eq. 3-4 projection through T_depth_rgb and K_rgb into the HD image
+ *   Eq. 9   C <- (C W + HD + floor((W+1)/2)) div (W+1) per channel, W <- min(W+1, max_weight)
+ *           (colour_mode TSDF_COLOUR_PAPER_NORMAL: Eq. 8-10 instead)
+ *   depth_mm  dsz.height x dsz.width uint16, host or device pointer
+ *   rgb_hwc   csz.height x csz.width x 3 uint8, host or device pointer
+ *   K_depth, K_rgb, T_world_depth, T_depth_rgb: host pointers, read before return
+ * Host images are copied with cudaMemcpyAsync on the handle's stream:
+ * pageable memory is consumed before the call returns, page-locked memory when
+ * the stream reaches the copy.  Device images are read in place by kernels
+ * queued on the stream.  In both asynchronous cases the caller must not
+ * overwrite the buffer until the stream has passed that point.  The call is
+ * asynchronous with respect to the host.
+ * Errors: INVALID_ARG (NULL pointers, sizes outside 1..16384, non-finite or
+ * singular K, non-finite or non-rigid T with |R^T R - I| > 1e-4), OOM, CUDA. */
+tsdf_status tsdf_integrate(tsdf_volume* vol, const uint16_t* depth_mm, tsdf_image_size dsz, const uint8_t* rgb_hwc,
+                           tsdf_image_size csz, const float K_depth[9], const float K_rgb[9],
+                           const float T_world_depth[16], const float T_depth_rgb[16]);
+
+/* Copy the volumes out, linear x-fastest (Section IV.B: "the new RGB value and
+ * weight are saved in the colour voxel").  Each destination may be NULL (not
+ * read) or a host or device pointer of dims_geo product floats (tsdf), bytes
+ * (w_geo) or dims_col product uint32 (rgbw).  Synchronous: returns after the
+ * copies are complete, and reports any recorded device-side error. */
+tsdf_status tsdf_read(tsdf_volume* vol, float* tsdf, uint8_t* w_geo, uint32_t* rgbw);
+
+/* Overwrite the volumes from linear x-fastest arrays (host or device), e.g. to
+ * resume from a previous state.  Any argument may be NULL (left unchanged). */
+tsdf_status tsdf_write(tsdf_volume* vol, const float* tsdf, const uint8_t* w_geo, const uint32_t* rgbw);
+
+/* Wait for all queued work on the handle and report recorded device errors. */
+tsdf_status tsdf_synchronize(tsdf_volume* vol);
+
+/* Checkpoint: a little-endian file holding a header (magic "TSDFVOL1",
+ * version, dims, voxel size, mu, max_weight, origin, sigma, band, modes, frame
+ * count) then F, w and the packed colours, linear x-fastest.  tsdf_load needs
+ * a handle created with the same dims; it restores the arrays and the frame
+ * count.  Errors: IO, INVALID_ARG (header mismatch). */
+tsdf_status tsdf_save(tsdf_volume* vol, const char* path);
+tsdf_status tsdf_load(tsdf_volume* vol, const char* path);
+
+/* Release the volumes and the handle.  NULL is ignored. */
+void tsdf_destroy(tsdf_volume* vol);
+
+/* Change the stream used by later calls on the handle. */
+tsdf_status tsdf_set_stream(tsdf_volume* vol, void* stream);
+
+/* Read-only description of a handle. */
+typedef struct {
+    int32_t dims_geo[3], dims_col[3];
+    float voxel_geo, voxel_col;  /* s_g, s_c (m) */
+    float origin[3];
+    float mu, sigma, band;
+    int32_t max_weight, colour_mode, sample_mode, culling, update_free_space;
+    int64_t frames;              /* frames integrated so far */
+    int64_t device_bytes;        /* bytes of device memory the handle holds */
+} tsdf_info;
+tsdf_status tsdf_get_info(const tsdf_volume* vol, tsdf_info* out);
+
+/* Work counters (read synchronously).  The first group covers the most
+ * recent tsdf_integrate: voxels whose geometry / colour was updated, and the
+ * bricks (8^3 geometry voxels) the geometry and colour kernels processed.
+ * The totals cover every frame since creation or the last
+ * tsdf_profile_enable. */
+typedef struct {
+    int64_t geo_updated, col_updated;
+    int64_t geo_bricks, col_bricks, visible_bricks, total_bricks;
+    int64_t frames_counted;
+    int64_t total_geo_updated, total_col_updated, total_geo_bricks, total_col_bricks, total_visible_bricks;
+} tsdf_stats;
+tsdf_status tsdf_get_stats(tsdf_volume* vol, tsdf_stats* out);
+
+/* Phase timing.  While enabled, tsdf_integrate records CUDA events on the
+ * handle's stream around each phase of a frame; tsdf_profile_read waits for
+ * them and returns the accumulated device time per phase (milliseconds) and
+ * the number of frames timed.  Enabling resets the accumulators and the
+ * stats totals.  Timing adds event records between kernels and nothing else. */
+enum {
+    TSDF_PHASE_UPLOAD = 0,      /* host -> device copies of the frame */
+    TSDF_PHASE_DEPTH_TILES = 1, /* per-tile depth range */
+    TSDF_PHASE_BRICKS = 2,      /* brick culling and work lists */
+    TSDF_PHASE_GEOMETRY = 3,    /* TSDF update */
+    TSDF_PHASE_COLOUR_LIST = 4, /* colour work list */
+    TSDF_PHASE_COLOUR = 5,      /* colour update */
+    TSDF_PHASE_COUNT = 6
+};
+typedef struct {
+    int64_t frames;
+    double ms[TSDF_PHASE_COUNT];
+} tsdf_profile_report;
+tsdf_status tsdf_profile_enable(tsdf_volume* vol, int32_t enable);
+tsdf_status tsdf_profile_read(tsdf_volume* vol, tsdf_profile_report* out);
+
+/* Human-readable text of a status, and the last error message of a handle
+ * (empty if none).  The strings are owned by the library. */
+const char* tsdf_status_string(tsdf_status s);
+const char* tsdf_last_error(const tsdf_volume* vol);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TSDF_H */

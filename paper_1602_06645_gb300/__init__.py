@@ -1,0 +1,392 @@
+"""GB300-native geometry-TSDF + asymmetric colour-volume fusion.
+
+Thin Python binding of the C ABI in ``include/tsdf.h`` (``libtsdf.so``): the
+functions below carry the C names and only marshal arguments; every step of
+fusion runs in the library's CUDA kernels.  PyTorch provides device memory
+(through its caching allocator) and streams.
+
+The library is loaded on first use; calling into it without the built
+``libtsdf.so`` raises an error (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtsdf.so")
+
+TSDF_OK = 0
+TSDF_ERR_INVALID_ARG = -1
+TSDF_ERR_OOM = -2
+TSDF_ERR_CUDA = -3
+TSDF_ERR_TIMEOUT = -4
+TSDF_ERR_DEVICE_FAULT = -5
+TSDF_ERR_IO = -6
+TSDF_COLOUR_COUNT, TSDF_COLOUR_PAPER_NORMAL = 0, 1
+TSDF_SAMPLE_NEAREST, TSDF_SAMPLE_BILINEAR = 0, 1
+
+# symbols include/tsdf.h declares (checked by the tests)
+EXPORTS = [
+    "tsdf_params_default", "tsdf_create", "tsdf_create_ex", "tsdf_integrate", "tsdf_read", "tsdf_write",
+    "tsdf_synchronize", "tsdf_save", "tsdf_load", "tsdf_destroy", "tsdf_set_stream", "tsdf_get_info",
+    "tsdf_get_stats", "tsdf_status_string", "tsdf_last_error", "tsdf_profile_enable", "tsdf_profile_read",
+]
+PHASES = ["upload", "depth_tiles", "bricks", "geometry", "colour_list", "colour"]
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class tsdf_allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
+class tsdf_params(ctypes.Structure):
+    _fields_ = [
+        ("origin", ctypes.c_float * 3),
+        ("sigma", ctypes.c_float),
+        ("band", ctypes.c_float),
+        ("colour_mode", ctypes.c_int32),
+        ("sample_mode", ctypes.c_int32),
+        ("culling", ctypes.c_int32),
+        ("update_free_space", ctypes.c_int32),
+        ("stream", ctypes.c_void_p),
+        ("allocator", tsdf_allocator),
+    ]
+
+
+class tsdf_image_size(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32)]
+
+
+class tsdf_info(ctypes.Structure):
+    _fields_ = [
+        ("dims_geo", ctypes.c_int32 * 3), ("dims_col", ctypes.c_int32 * 3),
+        ("voxel_geo", ctypes.c_float), ("voxel_col", ctypes.c_float), ("origin", ctypes.c_float * 3),
+        ("mu", ctypes.c_float), ("sigma", ctypes.c_float), ("band", ctypes.c_float),
+        ("max_weight", ctypes.c_int32), ("colour_mode", ctypes.c_int32), ("sample_mode", ctypes.c_int32),
+        ("culling", ctypes.c_int32), ("update_free_space", ctypes.c_int32),
+        ("frames", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+    ]
+
+
+class tsdf_stats(ctypes.Structure):
+    _fields_ = [
+        ("geo_updated", ctypes.c_int64), ("col_updated", ctypes.c_int64), ("geo_bricks", ctypes.c_int64),
+        ("col_bricks", ctypes.c_int64), ("visible_bricks", ctypes.c_int64), ("total_bricks", ctypes.c_int64),
+        ("frames_counted", ctypes.c_int64), ("total_geo_updated", ctypes.c_int64),
+        ("total_col_updated", ctypes.c_int64), ("total_geo_bricks", ctypes.c_int64),
+        ("total_col_bricks", ctypes.c_int64), ("total_visible_bricks", ctypes.c_int64),
+    ]
+
+
+class tsdf_profile_report(ctypes.Structure):
+    _fields_ = [("frames", ctypes.c_int64), ("ms", ctypes.c_double * 6)]
+
+
+class TsdfError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__("%s (%d)%s" % (_status_text(status), status, (": " + msg) if msg else ""))
+
+
+_lib = None
+
+
+def _status_text(s):
+    try:
+        return load().tsdf_status_string(s).decode()
+    except Exception:
+        return "status"
+
+
+def load():
+    """Load libtsdf.so (built by ``__graft_entry__.build()``); raises if missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libtsdf.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i32p, fp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)
+    H = ctypes.POINTER(ctypes.c_void_p)
+    lib.tsdf_params_default.argtypes = [ctypes.POINTER(tsdf_params)]
+    lib.tsdf_params_default.restype = None
+    lib.tsdf_create.argtypes = [i32p, i32p, ctypes.c_float, ctypes.c_float, ctypes.c_int32, H]
+    lib.tsdf_create_ex.argtypes = [i32p, i32p, ctypes.c_float, ctypes.c_float, ctypes.c_int32,
+                                   ctypes.POINTER(tsdf_params), H]
+    lib.tsdf_integrate.argtypes = [vp, vp, tsdf_image_size, vp, tsdf_image_size, fp, fp, fp, fp]
+    lib.tsdf_read.argtypes = [vp, vp, vp, vp]
+    lib.tsdf_write.argtypes = [vp, vp, vp, vp]
+    lib.tsdf_synchronize.argtypes = [vp]
+    lib.tsdf_save.argtypes = [vp, ctypes.c_char_p]
+    lib.tsdf_load.argtypes = [vp, ctypes.c_char_p]
+    lib.tsdf_destroy.argtypes = [vp]
+    lib.tsdf_destroy.restype = None
+    lib.tsdf_set_stream.argtypes = [vp, vp]
+    lib.tsdf_get_info.argtypes = [vp, ctypes.POINTER(tsdf_info)]
+    lib.tsdf_get_stats.argtypes = [vp, ctypes.POINTER(tsdf_stats)]
+    lib.tsdf_status_string.argtypes = [ctypes.c_int]
+    lib.tsdf_status_string.restype = ctypes.c_char_p
+    lib.tsdf_last_error.argtypes = [vp]
+    lib.tsdf_last_error.restype = ctypes.c_char_p
+    lib.tsdf_profile_enable.argtypes = [vp, ctypes.c_int32]
+    lib.tsdf_profile_read.argtypes = [vp, ctypes.POINTER(tsdf_profile_report)]
+    for name in ("tsdf_create", "tsdf_create_ex", "tsdf_integrate", "tsdf_read", "tsdf_write", "tsdf_synchronize",
+                 "tsdf_save", "tsdf_load", "tsdf_set_stream", "tsdf_get_info", "tsdf_get_stats",
+                 "tsdf_profile_enable", "tsdf_profile_read"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+# ------------------------------------------------------------ marshalling --
+def _check(status, handle=None):
+    if status != TSDF_OK:
+        msg = ""
+        if handle:
+            msg = load().tsdf_last_error(handle).decode()
+        raise TsdfError(status, msg)
+
+
+def _i32x3(v):
+    return (ctypes.c_int32 * 3)(*[int(x) for x in v])
+
+
+def _mat(a, n):
+    arr = np.ascontiguousarray(np.asarray(a, dtype=np.float32).reshape(-1))
+    if arr.size != n:
+        raise ValueError("expected %d values, got %d" % (n, arr.size))
+    return arr, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def _ptr(x, dtype, keep):
+    """Host or device pointer of an image/volume argument (numpy array or torch tensor)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):  # torch tensor (CPU or CUDA)
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        keep.append(x)
+        return ctypes.c_void_p(x.data_ptr())
+    arr = np.ascontiguousarray(x, dtype=dtype)
+    keep.append(arr)
+    return ctypes.c_void_p(arr.ctypes.data)
+
+
+def _hw(x):
+    s = tuple(x.shape)
+    return s[0], s[1]
+
+
+def torch_allocator(device=None):
+    """A tsdf_allocator drawing from PyTorch's CUDA caching allocator."""
+    import torch
+
+    dev = torch.cuda.current_device() if device is None else device
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream or 0)
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a = tsdf_allocator(ALLOC_FN(_alloc), FREE_FN(_free), None)
+    return a
+
+
+# ------------------------------------------------------------- C names ----
+def tsdf_params_default():
+    p = tsdf_params()
+    load().tsdf_params_default(ctypes.byref(p))
+    return p
+
+
+def tsdf_create(dims_geo, dims_col, voxel_size, mu, max_weight):
+    h = ctypes.c_void_p()
+    _check(load().tsdf_create(_i32x3(dims_geo), _i32x3(dims_col), float(voxel_size), float(mu), int(max_weight),
+                              ctypes.byref(h)))
+    return h
+
+
+def tsdf_create_ex(dims_geo, dims_col, voxel_size, mu, max_weight, params):
+    h = ctypes.c_void_p()
+    _check(load().tsdf_create_ex(_i32x3(dims_geo), _i32x3(dims_col), float(voxel_size), float(mu), int(max_weight),
+                                 ctypes.byref(params), ctypes.byref(h)))
+    return h
+
+
+def tsdf_integrate(h, depth_mm, rgb_hwc, K_depth, K_rgb, T_world_depth, T_depth_rgb):
+    keep = []
+    dh, dw = _hw(depth_mm)
+    ch, cw = _hw(rgb_hwc)
+    dp = _ptr(depth_mm, np.uint16, keep)
+    cp = _ptr(rgb_hwc, np.uint8, keep)
+    mats = [_mat(K_depth, 9), _mat(K_rgb, 9), _mat(T_world_depth, 16), _mat(T_depth_rgb, 16)]
+    _check(load().tsdf_integrate(h, dp, tsdf_image_size(dw, dh), cp, tsdf_image_size(cw, ch),
+                                 *[m[1] for m in mats]), h)
+
+
+def tsdf_read(h, tsdf=None, w_geo=None, rgbw=None):
+    keep = []
+    _check(load().tsdf_read(h, _ptr(tsdf, np.float32, keep), _ptr(w_geo, np.uint8, keep),
+                            _ptr(rgbw, np.uint32, keep)), h)
+
+
+def tsdf_write(h, tsdf=None, w_geo=None, rgbw=None):
+    keep = []
+    _check(load().tsdf_write(h, _ptr(tsdf, np.float32, keep), _ptr(w_geo, np.uint8, keep),
+                             _ptr(rgbw, np.uint32, keep)), h)
+
+
+def tsdf_synchronize(h):
+    _check(load().tsdf_synchronize(h), h)
+
+
+def tsdf_save(h, path):
+    _check(load().tsdf_save(h, str(path).encode()), h)
+
+
+def tsdf_load(h, path):
+    _check(load().tsdf_load(h, str(path).encode()), h)
+
+
+def tsdf_destroy(h):
+    if h:
+        load().tsdf_destroy(h)
+
+
+def tsdf_set_stream(h, stream):
+    _check(load().tsdf_set_stream(h, ctypes.c_void_p(int(stream or 0))), h)
+
+
+def tsdf_get_info(h):
+    o = tsdf_info()
+    _check(load().tsdf_get_info(h, ctypes.byref(o)), h)
+    return o
+
+
+def tsdf_get_stats(h):
+    o = tsdf_stats()
+    _check(load().tsdf_get_stats(h, ctypes.byref(o)), h)
+    return o
+
+
+def tsdf_profile_enable(h, enable=True):
+    _check(load().tsdf_profile_enable(h, int(bool(enable))), h)
+
+
+def tsdf_profile_read(h):
+    """{phase name: accumulated device ms} and the number of frames timed."""
+    o = tsdf_profile_report()
+    _check(load().tsdf_profile_read(h, ctypes.byref(o)), h)
+    return {n: float(o.ms[i]) for i, n in enumerate(PHASES)}, int(o.frames)
+
+
+def tsdf_status_string(s):
+    return load().tsdf_status_string(int(s)).decode()
+
+
+def tsdf_last_error(h):
+    return load().tsdf_last_error(h).decode()
+
+
+# ------------------------------------------------------------- Volume -----
+class Volume:
+    """A fusion handle with PyTorch-backed device memory on the current stream."""
+
+    def __init__(self, dims_geo, dims_col, voxel_size, mu, max_weight, *, origin=None, sigma=0.020, band=None,
+                 colour_mode=TSDF_COLOUR_COUNT, sample_mode=TSDF_SAMPLE_NEAREST, culling=True,
+                 update_free_space=True, stream=None, torch_memory=True):
+        import torch
+
+        self.dims_geo = tuple(int(v) for v in dims_geo)
+        self.dims_col = tuple(int(v) for v in dims_col)
+        p = tsdf_params_default()
+        if origin is not None:
+            p.origin[:] = [float(v) for v in origin]
+        p.sigma = float(sigma)
+        if band is not None:
+            p.band = float(band)
+        p.colour_mode, p.sample_mode = int(colour_mode), int(sample_mode)
+        p.culling, p.update_free_space = int(bool(culling)), int(bool(update_free_space))
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        p.stream = ctypes.c_void_p(int(stream))
+        self.stream = int(stream)
+        if torch_memory:
+            self._alloc = torch_allocator()
+            p.allocator = self._alloc
+        self.h = tsdf_create_ex(self.dims_geo, self.dims_col, voxel_size, mu, max_weight, p)
+
+    def integrate(self, depth_mm, rgb_hwc, K_depth, K_rgb, T_world_depth, T_depth_rgb):
+        tsdf_integrate(self.h, depth_mm, rgb_hwc, K_depth, K_rgb, T_world_depth, T_depth_rgb)
+
+    def read(self):
+        """(F, w, rgbw) as numpy arrays shaped (Nz, Ny, Nx), linear x-fastest."""
+        gx, gy, gz = self.dims_geo
+        cx, cy, cz = self.dims_col
+        F = np.empty((gz, gy, gx), np.float32)
+        W = np.empty((gz, gy, gx), np.uint8)
+        C = np.empty((cz, cy, cx), np.uint32)
+        tsdf_read(self.h, F, W, C)
+        return F, W, C
+
+    def read_torch(self, device="cuda"):
+        """(F, w, rgbw) as device tensors (rgbw as int32 holding the packed bits)."""
+        import torch
+
+        gx, gy, gz = self.dims_geo
+        cx, cy, cz = self.dims_col
+        F = torch.empty((gz, gy, gx), dtype=torch.float32, device=device)
+        W = torch.empty((gz, gy, gx), dtype=torch.uint8, device=device)
+        C = torch.empty((cz, cy, cx), dtype=torch.int32, device=device)
+        tsdf_read(self.h, F, W, C)
+        return F, W, C
+
+    def write(self, F=None, W=None, C=None):
+        tsdf_write(self.h, F, W, C)
+
+    def synchronize(self):
+        tsdf_synchronize(self.h)
+
+    def stats(self):
+        return tsdf_get_stats(self.h)
+
+    def info(self):
+        return tsdf_get_info(self.h)
+
+    def profile(self, enable=True):
+        tsdf_profile_enable(self.h, enable)
+
+    def profile_read(self):
+        return tsdf_profile_read(self.h)
+
+    def save(self, path):
+        tsdf_save(self.h, path)
+
+    def load(self, path):
+        tsdf_load(self.h, path)
+
+    def close(self):
+        if getattr(self, "h", None):
+            tsdf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

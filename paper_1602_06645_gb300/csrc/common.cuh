@@ -1,0 +1,123 @@
+// Internal declarations shared by the CUDA translation units of libtsdf.so.
+//
+// Numerics: every kernel is compiled with --fmad=false, so a product and a sum
+// are rounded separately unless written as fmaf(); reciprocals, quotients and
+// square roots use the correctly rounded __frcp_rn / __fdiv_rn / __fsqrt_rn.
+// The operation order of each step is the one written in the comments; it is
+// what makes the integer decisions (pixel choice, gates, weights and colours)
+// reproducible bit for bit on any IEEE binary32 implementation.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tsdf {
+
+// Volumes are stored brick-major: 8x8x8 voxel bricks, each brick contiguous
+// (voxel (x,y,z) of a brick at ((z*8)+y)*8+x), bricks ordered x fastest.  A
+// brick of F is 2 KB, of w 512 B, of colour 2 KB: whole DRAM sectors.
+constexpr int BRICK = 8;
+constexpr int BRICK_VOX = BRICK * BRICK * BRICK;
+constexpr int TILE_PX = 16;  // depth-culling tiles are 16x16 pixels
+
+// Per-frame constants, passed by value as a kernel parameter.
+struct FrameConst {
+    float R[9], t[3];      // world -> depth camera: the motion (R_n, t_n) of Eq. 5
+    float Kd[9], Kdi[9];   // K_c and K_c^-1 (Eq. 6, Eq. 7)
+    float Kr[9];           // K_hd (Eq. 4)
+    float Rc[9], tc[3];    // (R_calib, t_calib), Eq. 3
+    float origin[3];       // volume minimum corner (world)
+    float s_g, s_c;        // geometry / colour voxel edge
+    float inv_sg;          // 1/s_g (binary32 quotient)
+    float mu, inv_mu;      // truncation distance and 1/mu
+    float sigma2;          // sigma * sigma (Eq. 7)
+    float band;            // TSDF band gate
+    float cull_behind;     // metres beyond the farthest depth where nothing can change
+    int32_t ng[3], nc[3];  // geometry / colour dims
+    int32_t nb[3], ncb[3]; // bricks per axis (geometry / colour)
+    int32_t dw, dh, cw, ch;
+    int32_t tiles_x, tiles_y;
+    int32_t kd_pinhole, kr_pinhole, kdi_pinhole;
+    int32_t max_weight, free_space, sample_mode, colour_mode, culling;
+};
+
+// Min/max of F over observed voxels (w > 0) and min of w over the in-volume
+// voxels of one geometry brick.  No observed voxel: fmin = +inf, fmax = -inf.
+struct BrickSummary {
+    float fmin, fmax;
+    uint32_t wmin;
+    uint32_t pad;
+};
+
+struct Counters {
+    uint32_t n_geo;      // geometry work list length
+    uint32_t n_vis;      // visible brick list length
+    uint32_t n_col;      // colour work list length
+    uint32_t geo_next;   // persistent-loop work counters
+    uint32_t col_next;
+    uint32_t pad;
+    unsigned long long geo_updated;
+    unsigned long long col_updated;
+    // running totals over frames, folded in by the first kernel of each frame
+    unsigned long long frames;
+    unsigned long long tot_geo_updated, tot_col_updated;
+    unsigned long long tot_geo_bricks, tot_col_bricks, tot_vis_bricks;
+};
+
+// Device error word bits.
+enum : uint32_t {
+    ERR_TILE_RANGE = 1u,   // a colour voxel fell outside its brick's geometry tile
+};
+
+// Device scratch for one frame.
+struct Scratch {
+    Counters* ctr;
+    uint32_t* geo_list;
+    uint32_t* vis_list;
+    uint32_t* col_list;
+    uint32_t* depth_tiles;  // per 16x16 tile: min valid depth | max valid depth << 16
+    uint32_t* err;
+};
+
+struct Volumes {
+    float* F;
+    uint8_t* W;
+    uint32_t* C;
+    BrickSummary* summ;
+};
+
+// ------------------------------------------------------------- launchers --
+// All launchers queue work on `stream` and return cudaGetLastError().
+cudaError_t launch_init_summaries(BrickSummary* summ, int64_t n, cudaStream_t stream);
+// Queue the five kernels of one frame.  `ev` (nullable) holds 6 events:
+// ev[0] is recorded before the first kernel and ev[k] after the k-th.
+cudaError_t launch_frame(const FrameConst& c, const Volumes& v, const Scratch& s, const uint16_t* depth,
+                         const uint8_t* rgb, int grid_geo, int grid_col, cudaStream_t stream,
+                         cudaEvent_t* ev = nullptr);
+int geometry_blocks_per_sm();
+int colour_blocks_per_sm();
+
+// Layout conversion between brick-major storage and linear x-fastest arrays,
+// for z in [z0, z1).  `dst`/`src` point at the slab's first element.
+cudaError_t launch_to_linear_f32(const float* brick, float* lin, const int32_t dims[3], int z0, int z1,
+                                 cudaStream_t stream);
+cudaError_t launch_to_linear_u8(const uint8_t* brick, uint8_t* lin, const int32_t dims[3], int z0, int z1,
+                                cudaStream_t stream);
+cudaError_t launch_to_linear_u32(const uint32_t* brick, uint32_t* lin, const int32_t dims[3], int z0, int z1,
+                                 cudaStream_t stream);
+cudaError_t launch_from_linear_f32(float* brick, const float* lin, const int32_t dims[3], int z0, int z1,
+                                   cudaStream_t stream);
+cudaError_t launch_from_linear_u8(uint8_t* brick, const uint8_t* lin, const int32_t dims[3], int z0, int z1,
+                                  cudaStream_t stream);
+cudaError_t launch_from_linear_u32(uint32_t* brick, const uint32_t* lin, const int32_t dims[3], int z0, int z1,
+                                   cudaStream_t stream);
+cudaError_t launch_recompute_summaries(const float* F, const uint8_t* W, BrickSummary* summ, const int32_t ng[3],
+                                       cudaStream_t stream);
+
+// ------------------------------------------------------------ addressing --
+__host__ __device__ __forceinline__ int64_t brick_offset(int x, int y, int z, const int32_t nb[3]) {
+    int64_t b = ((int64_t)(z >> 3) * nb[1] + (y >> 3)) * nb[0] + (x >> 3);
+    return b * BRICK_VOX + (((z & 7) * BRICK + (y & 7)) * BRICK + (x & 7));
+}
+
+}  // namespace tsdf
