@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--dense", action="store_true", help="culling off (dense sweep of every brick)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-frames", type=int, default=12, help="frames of the oracle CPU-baseline sample")
+    ap.add_argument("--cpu-frames", type=int, default=120, help="frames of the oracle CPU-baseline sample")
     return ap.parse_args()
 
 
