@@ -15,7 +15,7 @@ API with page-locked host frames (host->device copies and a read-back of the
 frame's counters inside the timed region).
 
 --impl reference times the CPU oracle on the host cores on a bounded sample
-of the same workload (the central 1/64 of both volumes), same metric.
+of the same workload (the central 1/8 of both volumes), same metric.
 """
 from __future__ import annotations
 
@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--dense", action="store_true", help="culling off (dense sweep of every brick)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-frames", type=int, default=120, help="frames of the oracle CPU-baseline sample")
+    ap.add_argument("--cpu-frames", type=int, default=100, help="frames of the oracle CPU-baseline sample")
     return ap.parse_args()
 
 
@@ -55,6 +55,8 @@ def make_sequence(workload, n_frames, rank):
     from paper_1602_06645_gb300 import synth
     if workload == "scan":
         return synth.sequence_scan(n_frames=n_frames, seed=2 + 1000 * rank)
+    if workload == "scan_r1":  # same scan, colour volume at the geometry resolution (profiling size)
+        return synth.sequence_scan(n_frames=n_frames, seed=2 + 1000 * rank, ratio=1)
     if workload == "small":
         return synth.sequence_small(n_frames=n_frames, seed=1 + 1000 * rank)
     if workload.startswith("sweep"):
@@ -149,12 +151,12 @@ def measured_peaks():
 
 # ------------------------------------------------------- CPU oracle -----
 def oracle_sample(seq, frames, n_threads):
-    """Time the oracle on the central 1/64 of both volumes (1/4 of each edge)
+    """Time the oracle on the central 1/8 of both volumes (half of each edge)
     over `frames`.  Returns (nominal voxel-updates/s of the sample, seconds,
     description)."""
     import oracle
 
-    g = [d // 4 for d in seq.dims_geo]
+    g = [d // 2 for d in seq.dims_geo]
     r = seq.dims_col[0] // seq.dims_geo[0]
     full_origin = oracle.volume_geometry(seq.dims_geo, seq.voxel_size)
     start = [(d - s) // 2 for d, s in zip(seq.dims_geo, g)]
@@ -166,7 +168,7 @@ def oracle_sample(seq, frames, n_threads):
         o.integrate(d, c, seq.K_depth, seq.K_rgb, seq.poses[f], seq.T_depth_rgb)
     dt = time.perf_counter() - t0
     nvox = int(np.prod(g)) + int(np.prod([x * r for x in g]))
-    desc = ("oracle (binary32, OpenMP) on the central %s geometry / %s colour block (1/64 of each volume), "
+    desc = ("oracle (binary32, OpenMP) on the central %s geometry / %s colour block (1/8 of each volume), "
             "%d frames" % ("x".join(map(str, g)), "x".join(str(x * r) for x in g), len(frames)))
     return nvox * len(frames) / dt, dt, desc
 
@@ -190,7 +192,7 @@ def run_reference(args):
         "ms_per_step": 1e3 * dt / max(args.steps, 1), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+u8", "data": "synthetic",
         "config": {"workload": seq.name, "dims_geo": list(seq.dims_geo), "dims_col": list(seq.dims_col),
-                   "sample": "central 1/64 of both volumes"},
+                   "sample": "central 1/8 of both volumes"},
         "cpu_baseline": {"value": v, "unit": "voxel-updates/s", "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": v, "unit": "voxel-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -276,7 +278,8 @@ def run_ours(args):
     geo_bytes = 10.0 * st.total_geo_updated / K            # F (4 B) + w (1 B), read and written
     col_bytes = (8.0 * st.total_col_updated                 # packed RGBW, read and written
                  + 5.0 * 1000 * st.total_col_bricks) / K    # geometry tile (10^3 F + w) per colour brick
-    kern = {"geometry": (phases["geometry"] / K, geo_bytes), "colour": (phases["colour"] / K, col_bytes)}
+    kern = {"geometry": (phases["geometry"] / K, geo_bytes),
+            "colour": ((phases["colour_cells"] + phases["colour"]) / K, col_bytes)}
     dom = max(kern, key=lambda k: kern[k][0])
     ms_launch, bytes_launch = kern[dom]
     achieved = bytes_launch / (ms_launch / 1e3) / 1e9 if ms_launch > 0 else 0.0
@@ -301,13 +304,15 @@ def run_ours(args):
         "updated_voxels_per_s": (st.total_geo_updated + st.total_col_updated) * world / (total_ms / 1e3),
         "per_frame": {"geo_updated": st.total_geo_updated / K, "col_updated": st.total_col_updated / K,
                       "geo_bricks": st.total_geo_bricks / K, "col_bricks": st.total_col_bricks / K,
-                      "visible_bricks": st.total_visible_bricks / K, "total_bricks": st.total_bricks},
+                      "visible_bricks": st.total_visible_bricks / K, "total_bricks": st.total_bricks,
+                      "col_active_bricks": st.total_col_active_bricks / K, "cells": st.total_cells / K,
+                      "geo_changed_bricks": st.total_geo_changed_bricks / K},
         "phase_ms_per_frame": {k: v / max(pframes, 1) for k, v in phases.items()},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "bytes_per_launch": bytes_launch,
                      "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                      else "fallback 6.8 TB/s"},
-        "gpu_launches": 5 * args.steps,
+        "gpu_launches": 6 * args.steps,  # depth tiles, bricks, geometry, colour list, colour cells, colour voxels
         "clocks": clocks,
         "frame_generation_s": gen_s,
     }

@@ -99,7 +99,8 @@ void tsdf_params_default(tsdf_params* p);
  *   dims_geo    geometry voxels per axis (x, y, z), each 1..4096
  *   dims_col    colour voxels per axis; the same cube is split into more (or
  *               fewer) voxels: dims_col[i] * dims_geo[0] == dims_col[0] * dims_geo[i]
- *               (Section IV.B: "same size, higher dimension")
+ *               and dims_col[i] <= 8 * dims_geo[i] (Section IV.B: same size,
+ *               higher dimension; the paper uses a ratio of 2)
  *   voxel_size  geometry voxel edge s_g (m) > 0; the cube edge is dims_geo * s_g
  *               and the colour voxel edge s_c = dims_geo[0] * s_g / dims_col[0]
  *   mu          truncation distance (m) > 0
@@ -188,6 +189,10 @@ typedef struct {
     int64_t geo_bricks, col_bricks, visible_bricks, total_bricks;
     int64_t frames_counted;
     int64_t total_geo_updated, total_col_updated, total_geo_bricks, total_col_bricks, total_visible_bricks;
+    /* totals of: colour candidate bricks holding at least one trilinear cell
+     * that can pass the band gate, such cells, and geometry bricks in which
+     * at least one voxel was updated */
+    int64_t total_col_active_bricks, total_cells, total_geo_changed_bricks;
 } tsdf_stats;
 tsdf_status tsdf_get_stats(tsdf_volume* vol, tsdf_stats* out);
 
@@ -201,9 +206,10 @@ enum {
     TSDF_PHASE_DEPTH_TILES = 1, /* per-tile depth range */
     TSDF_PHASE_BRICKS = 2,      /* brick culling and work lists */
     TSDF_PHASE_GEOMETRY = 3,    /* TSDF update */
-    TSDF_PHASE_COLOUR_LIST = 4, /* colour work list */
-    TSDF_PHASE_COLOUR = 5,      /* colour update */
-    TSDF_PHASE_COUNT = 6
+    TSDF_PHASE_COLOUR_LIST = 4, /* colour candidate list */
+    TSDF_PHASE_COLOUR_CELLS = 5, /* active trilinear cells of the candidates */
+    TSDF_PHASE_COLOUR = 6,      /* colour update of the cells' colour voxels */
+    TSDF_PHASE_COUNT = 7
 };
 typedef struct {
     int64_t frames;

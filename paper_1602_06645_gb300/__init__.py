@@ -34,7 +34,7 @@ EXPORTS = [
     "tsdf_synchronize", "tsdf_save", "tsdf_load", "tsdf_destroy", "tsdf_set_stream", "tsdf_get_info",
     "tsdf_get_stats", "tsdf_status_string", "tsdf_last_error", "tsdf_profile_enable", "tsdf_profile_read",
 ]
-PHASES = ["upload", "depth_tiles", "bricks", "geometry", "colour_list", "colour"]
+PHASES = ["upload", "depth_tiles", "bricks", "geometry", "colour_list", "colour_cells", "colour"]
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -80,11 +80,13 @@ class tsdf_stats(ctypes.Structure):
         ("frames_counted", ctypes.c_int64), ("total_geo_updated", ctypes.c_int64),
         ("total_col_updated", ctypes.c_int64), ("total_geo_bricks", ctypes.c_int64),
         ("total_col_bricks", ctypes.c_int64), ("total_visible_bricks", ctypes.c_int64),
+        ("total_col_active_bricks", ctypes.c_int64), ("total_cells", ctypes.c_int64),
+        ("total_geo_changed_bricks", ctypes.c_int64),
     ]
 
 
 class tsdf_profile_report(ctypes.Structure):
-    _fields_ = [("frames", ctypes.c_int64), ("ms", ctypes.c_double * 6)]
+    _fields_ = [("frames", ctypes.c_int64), ("ms", ctypes.c_double * 7)]
 
 
 class TsdfError(RuntimeError):

@@ -43,11 +43,28 @@ struct FrameConst {
 
 // Min/max of F over observed voxels (w > 0) and min of w over the in-volume
 // voxels of one geometry brick.  No observed voxel: fmin = +inf, fmax = -inf.
+// flags: bit 0 / 1 = some observed voxel has F <= band + eps / F >= -band - eps;
+// bits 2 + 2f / 3 + 2f = the same over face layer f (-x, +x, -y, +y, -z, +z).
 struct BrickSummary {
     float fmin, fmax;
     uint32_t wmin;
-    uint32_t pad;
+    uint32_t flags;
 };
+
+// Band flags of one voxel at local brick position (x, y, z).
+__host__ __device__ __forceinline__ uint32_t band_flags(bool observed, float f, float lo_thr, float hi_thr, int x,
+                                                        int y, int z) {
+    if (!observed) return 0u;
+    const uint32_t b = (f <= lo_thr ? 1u : 0u) | (f >= hi_thr ? 2u : 0u);
+    uint32_t m = b;
+    if (x == 0) m |= b << 2;
+    if (x == 7) m |= b << 4;
+    if (y == 0) m |= b << 6;
+    if (y == 7) m |= b << 8;
+    if (z == 0) m |= b << 10;
+    if (z == 7) m |= b << 12;
+    return m;
+}
 
 struct Counters {
     uint32_t n_geo;      // geometry work list length
@@ -55,6 +72,10 @@ struct Counters {
     uint32_t n_col;      // colour work list length
     uint32_t geo_next;   // persistent-loop work counters
     uint32_t col_next;
+    uint32_t n_vox;      // band-gate voxel records (may exceed the buffer's capacity)
+    uint32_t n_cells;    // trilinear cells that can pass the band gate
+    uint32_t n_col_active;   // colour candidates with at least one such cell
+    uint32_t n_geo_changed;  // geometry bricks with at least one updated voxel
     uint32_t pad;
     unsigned long long geo_updated;
     unsigned long long col_updated;
@@ -62,6 +83,7 @@ struct Counters {
     unsigned long long frames;
     unsigned long long tot_geo_updated, tot_col_updated;
     unsigned long long tot_geo_bricks, tot_col_bricks, tot_vis_bricks;
+    unsigned long long tot_cells, tot_col_active, tot_geo_changed;
 };
 
 // Device error word bits.
@@ -77,6 +99,8 @@ struct Scratch {
     uint32_t* col_list;
     uint32_t* depth_tiles;  // per 16x16 tile: min valid depth | max valid depth << 16
     uint32_t* err;
+    uint2* vox;           // colour voxels that passed the band gate this frame: x | y << 16, z
+    uint32_t vox_cap;
 };
 
 struct Volumes {
@@ -89,13 +113,17 @@ struct Volumes {
 // ------------------------------------------------------------- launchers --
 // All launchers queue work on `stream` and return cudaGetLastError().
 cudaError_t launch_init_summaries(BrickSummary* summ, int64_t n, cudaStream_t stream);
-// Queue the five kernels of one frame.  `ev` (nullable) holds 6 events:
-// ev[0] is recorded before the first kernel and ev[k] after the k-th.
+// Queue the kernels of one frame.  `ev` (nullable) holds 7 events: ev[0] is
+// recorded before the first kernel, then one after each of depth tiles, brick
+// culling, geometry, colour list, colour band and colour voxels.
+struct LaunchGrids {
+    int geo, col, vox;  // persistent grid sizes (blocks) of the geometry and two colour kernels
+};
 cudaError_t launch_frame(const FrameConst& c, const Volumes& v, const Scratch& s, const uint16_t* depth,
-                         const uint8_t* rgb, int grid_geo, int grid_col, cudaStream_t stream,
-                         cudaEvent_t* ev = nullptr);
+                         const uint8_t* rgb, const LaunchGrids& g, cudaStream_t stream, cudaEvent_t* ev = nullptr);
 int geometry_blocks_per_sm();
 int colour_blocks_per_sm();
+int voxel_blocks_per_sm();
 
 // Layout conversion between brick-major storage and linear x-fastest arrays,
 // for z in [z0, z1).  `dst`/`src` point at the slab's first element.
@@ -112,7 +140,8 @@ cudaError_t launch_from_linear_u8(uint8_t* brick, const uint8_t* lin, const int3
 cudaError_t launch_from_linear_u32(uint32_t* brick, const uint32_t* lin, const int32_t dims[3], int z0, int z1,
                                    cudaStream_t stream);
 cudaError_t launch_recompute_summaries(const float* F, const uint8_t* W, BrickSummary* summ, const int32_t ng[3],
-                                       cudaStream_t stream);
+                                       float band, cudaStream_t stream);
+constexpr float CELL_EPS = 1e-5f;  // bound on trilinear overshoot of the corner range
 
 // ------------------------------------------------------------ addressing --
 __host__ __device__ __forceinline__ int64_t brick_offset(int x, int y, int z, const int32_t nb[3]) {

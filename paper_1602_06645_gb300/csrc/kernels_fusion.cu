@@ -6,8 +6,10 @@
 //   k_bricks        conservative per-brick visibility -> geometry and visible lists
 //   k_geometry      persistent: TSDF update of each listed brick, brick summaries
 //   k_colour_list   visible bricks whose 3x3x3 neighbourhood can hold |F| <= band
-//   k_colour        persistent: colour update of the colour voxels each listed
-//                   geometry brick owns, against a shared-memory geometry tile
+//   k_colour_band   one warp per listed brick: stages its geometry tile, finds
+//                   the trilinear cells that can pass the band gate and records
+//                   the colour voxels whose trilinear TSDF passes it
+//   k_colour_voxels one thread per recorded colour voxel: the rest of the update
 // Culling only removes work whose every voxel the per-voxel logic would skip
 // or leave unchanged, so results do not depend on it.
 #include <cfloat>
@@ -19,12 +21,11 @@ namespace tsdf {
 namespace {
 
 constexpr int GEO_THREADS = 128;  // 4 voxels per thread, one brick per block iteration
-constexpr int COL_THREADS = 256;
+constexpr int COL_THREADS = 128;  // 4 warps, one colour work item per warp
 constexpr int TILE_G = BRICK + 2;          // geometry tile edge: brick + 1-voxel halo each side
 constexpr int TILE_G3 = TILE_G * TILE_G * TILE_G;
 constexpr int CELLS = BRICK + 1;           // trilinear cells whose corners lie in the tile
 constexpr int CELLS3 = CELLS * CELLS * CELLS;
-constexpr float CELL_EPS = 1e-5f;          // bound on trilinear overshoot of the corner range
 
 // ------------------------------------------------------------- helpers ---
 // Eq. 1 / 4 / 6: (xh, yh, zh) = K (X, Y, Z), u = xh * (1/zh), v = yh * (1/zh).
@@ -49,12 +50,14 @@ __device__ __forceinline__ bool project(const float* K, int pinhole, float X, fl
     return true;
 }
 
-// Nearest pixel, half-up, bounds tested in float before conversion.
+// Nearest pixel, half-up: floor(u + 1/2).  With t = u + 1/2, the bounds
+// 0 <= floor(t) <= W - 1 are tested in float as 0 <= t < W (NaN fails), and
+// only then is t converted with rounding toward minus infinity.
 __device__ __forceinline__ bool nearest_pixel(float u, float v, int W, int H, int& iu, int& iv) {
-    float fu = floorf(u + 0.5f), fv = floorf(v + 0.5f);
-    if (!(fu >= 0.0f && fu <= (float)(W - 1) && fv >= 0.0f && fv <= (float)(H - 1))) return false;
-    iu = (int)fu;
-    iv = (int)fv;
+    const float tu = u + 0.5f, tv = v + 0.5f;
+    if (!(tu >= 0.0f && tu < (float)W && tv >= 0.0f && tv < (float)H)) return false;
+    iu = __float2int_rd(tu);
+    iv = __float2int_rd(tv);
     return true;
 }
 
@@ -118,9 +121,14 @@ __global__ void __launch_bounds__(256) k_depth_tiles(FrameConst c, const uint16_
             ctr->tot_geo_bricks += ctr->n_geo;
             ctr->tot_col_bricks += ctr->n_col;
             ctr->tot_vis_bricks += ctr->n_vis;
+            ctr->tot_cells += ctr->n_cells;
+            ctr->tot_col_active += ctr->n_col_active;
+            ctr->tot_geo_changed += ctr->n_geo_changed;
+            ctr->n_col_active = ctr->n_geo_changed = 0;
             ctr->frames += 1ull;
             ctr->n_geo = ctr->n_vis = ctr->n_col = 0;
             ctr->geo_next = ctr->col_next = 0;
+            ctr->n_cells = ctr->n_vox = 0;
             ctr->geo_updated = ctr->col_updated = 0ull;
         }
     }
@@ -136,7 +144,9 @@ __global__ void __launch_bounds__(256) k_depth_tiles(FrameConst c, const uint16_
 // A visible brick needs no geometry work when every voxel it holds would be
 // left unchanged: it lies in front of the nearest depth by more than mu and
 // either free-space updates are off or the brick is saturated free space
-// (all F = 1, all w = max_weight), where (1 * w + 1) / (w + 1) = 1.
+// (all F = 1, all w = max_weight), where (1 * w + 1) / (w + 1) = 1.  The
+// visible list (the colour candidates) also drops bricks lying in front of
+// the nearest depth by more than sigma + margin.
 __global__ void __launch_bounds__(256) k_bricks(FrameConst c, const BrickSummary* __restrict__ summ,
                                                 const uint32_t* __restrict__ tiles, Counters* __restrict__ ctr,
                                                 uint32_t* __restrict__ geo_list, uint32_t* __restrict__ vis_list) {
@@ -205,6 +215,10 @@ __global__ void __launch_bounds__(256) k_bricks(FrameConst c, const BrickSummary
             const BrickSummary s = summ[b];
             bool sat = c.free_space == 0 || (s.fmin == 1.0f && s.wmin == (uint32_t)c.max_weight);
             if (sat && zmax < (float)dmin * 0.001f - c.mu - 2e-3f) geo = false;
+            // colour: Eq. 7 needs |Z - d| <= sigma (pinhole K_c: the back-projected
+            // point has Z = d), so a brick wholly nearer than the nearest depth
+            // minus sigma holds no colour voxel that can pass
+            if (c.kdi_pinhole && zmax < (float)dmin * 0.001f - c.cull_behind) vis = false;
         }
     }
     append(geo, b, &ctr->n_geo, geo_list);
@@ -216,119 +230,165 @@ __global__ void __launch_bounds__(256) k_bricks(FrameConst c, const BrickSummary
 //   D = depth at the nearest pixel of the voxel centre (Eq. 6); D = 0 skipped
 //   sdf = D * 0.001 - Z; sdf < -mu skipped; (free space off: sdf > mu skipped)
 //   t = min(1, sdf * (1/mu)); F <- fmaf(F, w, t) / (w + 1); w <- min(w+1, max_w)
-// Thread t of a block owns voxels 4t..4t+3 of the brick (same y and z), so the
-// y/z part of Eq. 5 is computed once per thread; F and w move as one float4
-// and one 32-bit word, a warp covering 512 + 128 contiguous bytes.
-__global__ void __launch_bounds__(GEO_THREADS) k_geometry(FrameConst c, Volumes vol, const uint16_t* __restrict__ depth,
+// One warp per brick, taken round-robin from the list.  Lane l owns the four
+// float4 groups q = l + 32 j (j = 0..3) of the brick: voxels 4q..4q+3, i.e.
+// x in {0..3} or {4..7}, y = (l >> 1) & 7, z = (l >> 4) + 2 j.  Each group of
+// the warp is 512 contiguous bytes of F and 128 of w.  The brick's F and w are
+// requested before the projections so their latency overlaps the arithmetic;
+// all 16 depth fetches of a lane are issued together.  The warp then writes
+// the brick summary (min/max F over observed voxels, min w).
+template <bool PINHOLE, bool FREE_SPACE>
+__global__ void __launch_bounds__(GEO_THREADS, 7) k_geometry(FrameConst c, Volumes vol, const uint16_t* __restrict__ depth,
                                                           Counters* __restrict__ ctr,
                                                           const uint32_t* __restrict__ list) {
-    __shared__ uint32_t s_item;
-    __shared__ float s_fmin[GEO_THREADS / 32], s_fmax[GEO_THREADS / 32];
-    __shared__ uint32_t s_wmin[GEO_THREADS / 32];
-    const int tid = threadIdx.x;
-    const int lx = (tid & 1) * 4, ly = (tid >> 1) & 7, lz = tid >> 4;
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t n = ctr->n_geo;
-    for (;;) {
-        if (tid == 0) s_item = atomicAdd(&ctr->geo_next, 1u);
-        __syncthreads();
-        const uint32_t item = s_item;
-        if (item >= n) break;
+    const int lx = (lane & 1) * 4, ly = (lane >> 1) & 7, lz = lane >> 4;
+    uint32_t count = 0, changed = 0;
+    for (uint32_t item = warp; item < n; item += nwarps) {
         const uint32_t b = list[item];
         const int bx = b % c.nb[0], by = (b / c.nb[0]) % c.nb[1], bz = b / (c.nb[0] * c.nb[1]);
-        const int gx0 = bx * BRICK + lx, gy = by * BRICK + ly, gz = bz * BRICK + lz;
-        const float py = fmaf((float)gy + 0.5f, c.s_g, c.origin[1]);
-        const float pz = fmaf((float)gz + 0.5f, c.s_g, c.origin[2]);
-        const float B0 = fmaf(c.R[1], py, fmaf(c.R[2], pz, c.t[0]));
-        const float B1 = fmaf(c.R[4], py, fmaf(c.R[5], pz, c.t[1]));
-        const float B2 = fmaf(c.R[7], py, fmaf(c.R[8], pz, c.t[2]));
-        const bool yz_in = gy < c.ng[1] && gz < c.ng[2];
-        float tv[4];
-        uint32_t upd = 0, inb = 0;
+        float* Fb = vol.F + (size_t)b * BRICK_VOX + lane * 4;
+        uint8_t* Wb = vol.W + (size_t)b * BRICK_VOX + lane * 4;
+        float4 f[4];
+        uint32_t wv[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            tv[j] = 0.0f;
-            const int gx = gx0 + j;
-            if (!(yz_in && gx < c.ng[0])) continue;
-            inb |= 1u << j;
-            const float px = fmaf((float)gx + 0.5f, c.s_g, c.origin[0]);
-            const float X = fmaf(c.R[0], px, B0), Y = fmaf(c.R[3], px, B1), Z = fmaf(c.R[6], px, B2);
-            float u, v;
-            int iu, iv;
-            if (!project(c.Kd, c.kd_pinhole, X, Y, Z, u, v)) continue;
-            if (!nearest_pixel(u, v, c.dw, c.dh, iu, iv)) continue;
-            const uint32_t D = __ldg(depth + (size_t)iv * c.dw + iu);
-            if (D == 0u) continue;
-            const float d = (float)D * 0.001f;
-            const float sdf = d - Z;
-            if (sdf < -c.mu) continue;
-            if (!c.free_space && sdf > c.mu) continue;
-            tv[j] = fminf(1.0f, sdf * c.inv_mu);
-            upd |= 1u << j;
+            f[j] = *reinterpret_cast<const float4*>(Fb + 128 * j);
+            wv[j] = *reinterpret_cast<const uint32_t*>(Wb + 128 * j);
         }
-        if (__syncthreads_or(upd != 0u)) {
-            const size_t base = (size_t)b * BRICK_VOX + (size_t)tid * 4;
-            float4 f = *reinterpret_cast<const float4*>(vol.F + base);
-            uint32_t wv = *reinterpret_cast<const uint32_t*>(vol.W + base);
-            float fv[4] = {f.x, f.y, f.z, f.w};
-            uint32_t wn = wv;
-            float fmn = FLT_MAX, fmx = -FLT_MAX;
-            uint32_t wmn = 0xFFFFFFFFu;
+        const int gy = by * BRICK + ly;
+        const float py = fmaf((float)gy + 0.5f, c.s_g, c.origin[1]);
+        float px[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                uint32_t w = (wv >> (8 * j)) & 0xFFu;
-                if (upd & (1u << j)) {
-                    const float wf = (float)w;
-                    fv[j] = __fdiv_rn(fmaf(fv[j], wf, tv[j]), wf + 1.0f);
-                    w = min(w + 1u, (uint32_t)c.max_weight);
-                    wn = (wn & ~(0xFFu << (8 * j))) | (w << (8 * j));
-                }
-                if (inb & (1u << j)) {
-                    wmn = min(wmn, w);
-                    if (w) { fmn = fminf(fmn, fv[j]); fmx = fmaxf(fmx, fv[j]); }
-                }
-            }
-            if (upd) {
-                *reinterpret_cast<float4*>(vol.F + base) = make_float4(fv[0], fv[1], fv[2], fv[3]);
-                *reinterpret_cast<uint32_t*>(vol.W + base) = wn;
-            }
-            // brick summary: block reduction of min/max
+        for (int i = 0; i < 4; ++i) px[i] = fmaf((float)(bx * BRICK + lx + i) + 0.5f, c.s_g, c.origin[0]);
+        float fmn = FLT_MAX, fmx = -FLT_MAX;
+        uint32_t wmn = 0xFFFFFFFFu, upd_all = 0, lom = 0, him = 0;
+        const float lo_thr = c.band + CELL_EPS, hi_thr = -c.band - CELL_EPS;
+        // two halves of 8 voxels (groups j = 2h, 2h + 1) keep the live set small
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                fmn = fminf(fmn, __shfl_xor_sync(0xffffffffu, fmn, o));
-                fmx = fmaxf(fmx, __shfl_xor_sync(0xffffffffu, fmx, o));
-            }
-            wmn = __reduce_min_sync(0xffffffffu, wmn);
-            const uint32_t cnt = __reduce_add_sync(0xffffffffu, (uint32_t)__popc(upd));
-            if ((tid & 31) == 0) {
-                s_fmin[tid >> 5] = fmn;
-                s_fmax[tid >> 5] = fmx;
-                s_wmin[tid >> 5] = wmn;
-                if (cnt) atomicAdd(&ctr->geo_updated, (unsigned long long)cnt);
-            }
-            __syncthreads();
-            if (tid == 0) {
-                for (int i = 1; i < GEO_THREADS / 32; ++i) {
-                    fmn = fminf(fmn, s_fmin[i]);
-                    fmx = fmaxf(fmx, s_fmax[i]);
-                    wmn = min(wmn, s_wmin[i]);
+        for (int h = 0; h < 2; ++h) {
+            int pix[8];
+            float Zc[8];
+            uint32_t inb = 0;
+#pragma unroll
+            for (int jj = 0; jj < 2; ++jj) {
+                const int gz = bz * BRICK + lz + 2 * (2 * h + jj);
+                const float pz = fmaf((float)gz + 0.5f, c.s_g, c.origin[2]);
+                const float B0 = fmaf(c.R[1], py, fmaf(c.R[2], pz, c.t[0]));
+                const float B1 = fmaf(c.R[4], py, fmaf(c.R[5], pz, c.t[1]));
+                const float B2 = fmaf(c.R[7], py, fmaf(c.R[8], pz, c.t[2]));
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int k = 4 * jj + i;
+                    pix[k] = -1;
+                    Zc[k] = 0.0f;
+                    if (!(gy < c.ng[1] && gz < c.ng[2] && bx * BRICK + lx + i < c.ng[0])) continue;
+                    inb |= 1u << k;
+                    const float X = fmaf(c.R[0], px[i], B0), Y = fmaf(c.R[3], px[i], B1), Z = fmaf(c.R[6], px[i], B2);
+                    float u, v;
+                    int iu, iv;
+                    if (!project(c.Kd, PINHOLE, X, Y, Z, u, v)) continue;
+                    if (!nearest_pixel(u, v, c.dw, c.dh, iu, iv)) continue;
+                    pix[k] = iv * c.dw + iu;
+                    Zc[k] = Z;
                 }
-                BrickSummary s;
-                s.fmin = fmn == FLT_MAX ? __int_as_float(0x7f800000) : fmn;
-                s.fmax = fmx == -FLT_MAX ? __int_as_float(0xff800000) : fmx;
-                s.wmin = wmn == 0xFFFFFFFFu ? 0u : wmn;
-                s.pad = 0;
-                vol.summ[b] = s;
+            }
+            uint32_t D[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) D[k] = pix[k] >= 0 ? (uint32_t)__ldg(depth + pix[k]) : 0u;
+            uint32_t upd = 0;
+            float tv[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                tv[k] = 0.0f;
+                if (D[k] == 0u) continue;
+                const float d = (float)D[k] * 0.001f;
+                const float sdf = d - Zc[k];
+                if (sdf < -c.mu) continue;
+                if (!FREE_SPACE && sdf > c.mu) continue;
+                tv[k] = fminf(1.0f, sdf * c.inv_mu);
+                upd |= 1u << k;
+            }
+            upd_all |= upd << (8 * h);
+#pragma unroll
+            for (int jj = 0; jj < 2; ++jj) {
+                const int j = 2 * h + jj;
+                float fv[4] = {f[j].x, f[j].y, f[j].z, f[j].w};
+                uint32_t wn = wv[j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int k = 4 * jj + i;
+                    uint32_t w = (wv[j] >> (8 * i)) & 0xFFu;
+                    if (upd & (1u << k)) {
+                        const float wf = (float)w;
+                        fv[i] = __fdiv_rn(fmaf(fv[i], wf, tv[k]), wf + 1.0f);
+                        w = min(w + 1u, (uint32_t)c.max_weight);
+                        wn = (wn & ~(0xFFu << (8 * i))) | (w << (8 * i));
+                    }
+                    if (inb & (1u << k)) {
+                        wmn = min(wmn, w);
+                        if (w) {
+                            fmn = fminf(fmn, fv[i]);
+                            fmx = fmaxf(fmx, fv[i]);
+                        }
+                        lom |= (w != 0u && fv[i] <= lo_thr ? 1u : 0u) << (4 * j + i);
+                        him |= (w != 0u && fv[i] >= hi_thr ? 1u : 0u) << (4 * j + i);
+                    }
+                }
+                if ((upd >> (4 * jj)) & 0xFu) {
+                    *reinterpret_cast<float4*>(Fb + 128 * j) = make_float4(fv[0], fv[1], fv[2], fv[3]);
+                    *reinterpret_cast<uint32_t*>(Wb + 128 * j) = wn;
+                }
             }
         }
-        __syncthreads();
+        count += __popc(upd_all);
+        // bricks where nothing changed keep their summary
+        if (!__any_sync(0xffffffffu, upd_all != 0u)) continue;
+        ++changed;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            fmn = fminf(fmn, __shfl_xor_sync(0xffffffffu, fmn, o));
+            fmx = fmaxf(fmx, __shfl_xor_sync(0xffffffffu, fmx, o));
+        }
+        wmn = __reduce_min_sync(0xffffffffu, wmn);
+        // band flags (see BrickSummary): voxel 4 j + i of this lane sits at
+        // x = lx + i, y = ly, z = lz + 2 j
+        uint32_t bflags = 0;
+        {
+            const uint32_t fm[6] = {lx == 0 ? 0x1111u : 0u, lx == 4 ? 0x8888u : 0u, ly == 0 ? 0xFFFFu : 0u,
+                                    ly == 7 ? 0xFFFFu : 0u, lz == 0 ? 0x000Fu : 0u, lz == 1 ? 0xF000u : 0u};
+            bflags = (lom ? 1u : 0u) | (him ? 2u : 0u);
+#pragma unroll
+            for (int f = 0; f < 6; ++f)
+                bflags |= ((lom & fm[f]) ? 1u : 0u) << (2 + 2 * f) | ((him & fm[f]) ? 1u : 0u) << (3 + 2 * f);
+        }
+        bflags = __reduce_or_sync(0xffffffffu, bflags);
+        if (lane == 0) {
+            BrickSummary sm;
+            sm.fmin = fmn == FLT_MAX ? __int_as_float(0x7f800000) : fmn;
+            sm.fmax = fmx == -FLT_MAX ? __int_as_float(0xff800000) : fmx;
+            sm.wmin = wmn == 0xFFFFFFFFu ? 0u : wmn;
+            sm.flags = bflags;
+            vol.summ[b] = sm;
+        }
     }
+    count = __reduce_add_sync(0xffffffffu, count);
+    if (lane == 0 && count) atomicAdd(&ctr->geo_updated, (unsigned long long)count);
+    if (lane == 0 && changed) atomicAdd(&ctr->n_geo_changed, changed);
 }
 
 // ------------------------------------------------------- colour list ----
-// A visible geometry brick goes to the colour list when the F range of its
-// 3x3x3 brick neighbourhood (observed voxels only) meets [-band, band]: the
-// trilinear TSDF of any colour voxel it owns is a convex combination of
-// corner values from that neighbourhood, up to CELL_EPS of rounding.
+// A visible geometry brick goes to the colour list when some trilinear cell
+// of the colour voxels it owns can have corners on both sides of the band:
+// the cells' corners lie in the brick and in the one-voxel layers of its 26
+// neighbours that touch it, so the brick needs an observed voxel with
+// F <= band + eps and one with F >= -band - eps among its own voxels and
+// those layers.  A face neighbour contributes its touching face layer; an
+// edge or corner neighbour contributes only voxels on all of its touching
+// faces, so the AND of those faces' flags is still a necessary condition.
 __global__ void __launch_bounds__(256) k_colour_list(FrameConst c, const BrickSummary* __restrict__ summ,
                                                      Counters* __restrict__ ctr, const uint32_t* __restrict__ vis_list,
                                                      uint32_t* __restrict__ col_list) {
@@ -342,8 +402,8 @@ __global__ void __launch_bounds__(256) k_colour_list(FrameConst c, const BrickSu
             act = true;
             if (c.culling) {
                 const int bx = b % c.nb[0], by = (b / c.nb[0]) % c.nb[1], bz = b / (c.nb[0] * c.nb[1]);
-                float mn = FLT_MAX, mx = -FLT_MAX;
-                for (int dz = -1; dz <= 1; ++dz) {
+                uint32_t acc = summ[b].flags & 3u;
+                for (int dz = -1; dz <= 1 && acc != 3u; ++dz) {
                     const int z = bz + dz;
                     if (z < 0 || z >= c.nb[2]) continue;
                     for (int dy = -1; dy <= 1; ++dy) {
@@ -351,14 +411,18 @@ __global__ void __launch_bounds__(256) k_colour_list(FrameConst c, const BrickSu
                         if (y < 0 || y >= c.nb[1]) continue;
                         for (int dx = -1; dx <= 1; ++dx) {
                             const int x = bx + dx;
-                            if (x < 0 || x >= c.nb[0]) continue;
-                            const BrickSummary s = summ[((size_t)z * c.nb[1] + y) * c.nb[0] + x];
-                            mn = fminf(mn, s.fmin);
-                            mx = fmaxf(mx, s.fmax);
+                            if (x < 0 || x >= c.nb[0] || (dx == 0 && dy == 0 && dz == 0)) continue;
+                            const uint32_t f = summ[((size_t)z * c.nb[1] + y) * c.nb[0] + x].flags;
+                            // the neighbour at -x touches with its +x face (bits 4-5), etc.
+                            uint32_t m = 3u;
+                            if (dx) m &= f >> (dx < 0 ? 4 : 2);
+                            if (dy) m &= f >> (dy < 0 ? 8 : 6);
+                            if (dz) m &= f >> (dz < 0 ? 12 : 10);
+                            acc |= m & 3u;
                         }
                     }
                 }
-                act = mn <= c.band + CELL_EPS && mx >= -c.band - CELL_EPS;
+                act = acc == 3u;
             }
         }
         append(act, b, &ctr->n_col, col_list);
@@ -448,138 +512,406 @@ __device__ __forceinline__ bool paper_normal_update(const FrameConst& c, const u
     return true;
 }
 
-// Colour update (Section IV.B) of the colour voxels a geometry brick owns.
-// The block stages the brick's geometry plus a one-voxel halo (10^3 F and w,
-// post-update) in shared memory, marks which of the 9^3 trilinear cells can
-// pass the band gate (all 8 corners observed and the corner range meets
-// [-band, band]), and then runs, per colour voxel whose cell is marked:
-//   Eq. 5 -> Eq. 6 -> D > 0 -> Eq. 7 sigma gate -> trilinear band gate
-//   -> Eq. 3-4 -> HD sample -> Eq. 9 (integer, half-up) or Eq. 8-10.
-// The cell test is conservative, so the gates decide exactly as written.
-__global__ void __launch_bounds__(COL_THREADS) k_colour(FrameConst c, Volumes vol, const uint16_t* __restrict__ depth,
-                                                        const uint8_t* __restrict__ rgb, Counters* __restrict__ ctr,
-                                                        const uint32_t* __restrict__ list, uint32_t* __restrict__ err) {
-    __shared__ float sF[TILE_G3];
-    __shared__ uint8_t sW[TILE_G3];
-    __shared__ uint8_t sCell[CELLS3];
-    __shared__ uint32_t s_item;
-    const int tid = threadIdx.x;
-    const uint32_t n = ctr->n_col;
-    for (;;) {
-        if (tid == 0) s_item = atomicAdd(&ctr->col_next, 1u);
-        __syncthreads();
-        const uint32_t item = s_item;
-        if (item >= n) break;
-        const uint32_t b = list[item];
-        const int bb[3] = {(int)(b % c.nb[0]), (int)((b / c.nb[0]) % c.nb[1]), (int)(b / (c.nb[0] * c.nb[1]))};
-        const int t0[3] = {bb[0] * BRICK - 1, bb[1] * BRICK - 1, bb[2] * BRICK - 1};
-        for (int i = tid; i < TILE_G3; i += COL_THREADS) {
-            const int x = t0[0] + i % TILE_G, y = t0[1] + (i / TILE_G) % TILE_G, z = t0[2] + i / (TILE_G * TILE_G);
-            float f = 0.0f;
-            uint8_t w = 0;
-            if (x >= 0 && y >= 0 && z >= 0 && x < c.ng[0] && y < c.ng[1] && z < c.ng[2]) {
-                const int64_t o = brick_offset(x, y, z, c.nb);
-                f = vol.F[o];
-                w = vol.W[o];
-            }
-            sF[i] = f;
-            sW[i] = w;
-        }
-        __syncthreads();
-        for (int i = tid; i < CELLS3; i += COL_THREADS) {
-            const int x = i % CELLS, y = (i / CELLS) % CELLS, z = i / (CELLS * CELLS);
-            const int o = (z * TILE_G + y) * TILE_G + x;
-            bool allw = true;
-            float mn = FLT_MAX, mx = -FLT_MAX;
+// Colour update of one colour voxel (Section IV.B) that has passed the
+// trilinear band gate, given its indices k:
+//   Eq. 5 -> Eq. 6 -> D > 0 -> Eq. 7 sigma gate -> Eq. 3-4 -> HD sample
+//   -> Eq. 9 (integer, half-up) or Eq. 8-10.
+// (The gates are independent predicates, so testing the band first changes
+// nothing.)  Returns whether the voxel was updated.
+__device__ __forceinline__ bool colour_after_band(const FrameConst& c, uint32_t* __restrict__ C,
+                                                  const uint16_t* __restrict__ depth, const uint8_t* __restrict__ rgb,
+                                                  int kx, int ky, int kz) {
+    const float pwx = fmaf((float)kx + 0.5f, c.s_c, c.origin[0]);
+    const float pwy = fmaf((float)ky + 0.5f, c.s_c, c.origin[1]);
+    const float pwz = fmaf((float)kz + 0.5f, c.s_c, c.origin[2]);
+    float X, Y, Z;
+    rigid(c.R, c.t, pwx, pwy, pwz, X, Y, Z);
+    float u, v;
+    int iu, iv;
+    if (!project(c.Kd, c.kd_pinhole, X, Y, Z, u, v)) return false;
+    if (!nearest_pixel(u, v, c.dw, c.dh, iu, iv)) return false;
+    const uint32_t D = __ldg(depth + (size_t)iv * c.dw + iu);
+    if (D == 0u) return false;
+    const float d = (float)D * 0.001f;
+    float PdX, PdY, PdZ;
+    back_project(c, iu, iv, d, PdX, PdY, PdZ);
+    const float ex = X - PdX, ey = Y - PdY, ez = Z - PdZ;
+    const float dist2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+    if (dist2 > c.sigma2) return false;
+    float Xh, Yh, Zh;
+    rigid(c.Rc, c.tc, X, Y, Z, Xh, Yh, Zh);
+    float uh, vh;
+    if (!project(c.Kr, c.kr_pinhole, Xh, Yh, Zh, uh, vh)) return false;
+    uint32_t smp[3];
+    if (!sample_rgb(c, rgb, uh, vh, smp)) return false;
+    const int64_t co = brick_offset(kx, ky, kz, c.ncb);
+    uint32_t vox = C[co];
+    if (c.colour_mode == 1) {
+        if (!paper_normal_update(c, depth, iu, iv, PdX, PdY, PdZ, X, Y, Z, vox, smp)) return false;
+    } else {
+        const uint32_t w = vox >> 24;
+        uint32_t out = 0;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int oo = o + (k & 1) + ((k >> 1) & 1) * TILE_G + (k >> 2) * TILE_G * TILE_G;
-                allw = allw && sW[oo] != 0;
-                mn = fminf(mn, sF[oo]);
-                mx = fmaxf(mx, sF[oo]);
-            }
-            bool act = allw;
-            if (c.culling) act = act && mn <= c.band + CELL_EPS && mx >= -c.band - CELL_EPS;
-            sCell[i] = act ? 1 : 0;
+        for (int k = 0; k < 3; ++k) {
+            const uint32_t cc = (vox >> (8 * k)) & 0xFFu;
+            out |= ((cc * w + smp[k] + ((w + 1u) >> 1)) / (w + 1u)) << (8 * k);
         }
-        __syncthreads();
-        int k0[3], k1[3];
-        for (int a = 0; a < 3; ++a) owned_range(bb[a], c.ng[a], c.nc[a], k0[a], k1[a]);
-        const int ex = k1[0] - k0[0], ey = k1[1] - k0[1], ez = k1[2] - k0[2];
-        const int nvox = ex * ey * ez;
-        uint32_t cnt = 0;
-        for (int i = tid; i < nvox; i += COL_THREADS) {
-            const int kx = k0[0] + i % ex, ky = k0[1] + (i / ex) % ey, kz = k0[2] + i / (ex * ey);
-            const float pw[3] = {fmaf((float)kx + 0.5f, c.s_c, c.origin[0]), fmaf((float)ky + 0.5f, c.s_c, c.origin[1]),
-                                 fmaf((float)kz + 0.5f, c.s_c, c.origin[2])};
-            float g[3], i0[3];
-            int cell[3];
-            bool range_ok = true;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                g[a] = fmaf(pw[a] - c.origin[a], c.inv_sg, -0.5f);
-                i0[a] = floorf(g[a]);
-                cell[a] = (int)i0[a] - t0[a];
-                range_ok = range_ok && cell[a] >= 0 && cell[a] < CELLS;
-            }
-            if (!range_ok) {
-                atomicOr(err, ERR_TILE_RANGE);
-                continue;
-            }
-            if (!sCell[(cell[2] * CELLS + cell[1]) * CELLS + cell[0]]) continue;
-            float X, Y, Z;
-            rigid(c.R, c.t, pw[0], pw[1], pw[2], X, Y, Z);
-            float u, v;
-            int iu, iv;
-            if (!project(c.Kd, c.kd_pinhole, X, Y, Z, u, v)) continue;
-            if (!nearest_pixel(u, v, c.dw, c.dh, iu, iv)) continue;
-            const uint32_t D = __ldg(depth + (size_t)iv * c.dw + iu);
-            if (D == 0u) continue;
-            const float d = (float)D * 0.001f;
-            float PdX, PdY, PdZ;
-            back_project(c, iu, iv, d, PdX, PdY, PdZ);
-            const float ex_ = X - PdX, ey_ = Y - PdY, ez_ = Z - PdZ;
-            const float dist2 = fmaf(ex_, ex_, fmaf(ey_, ey_, ez_ * ez_));
-            if (dist2 > c.sigma2) continue;
-            // trilinear TSDF: lerp along x, then y, then z
-            const int o = (cell[2] * TILE_G + cell[1]) * TILE_G + cell[0];
-            const float fx = g[0] - i0[0], fy = g[1] - i0[1], fz = g[2] - i0[2];
-            const float c00 = lerp(sF[o], sF[o + 1], fx);
-            const float c10 = lerp(sF[o + TILE_G], sF[o + TILE_G + 1], fx);
-            const float c01 = lerp(sF[o + TILE_G * TILE_G], sF[o + TILE_G * TILE_G + 1], fx);
-            const float c11 = lerp(sF[o + TILE_G * TILE_G + TILE_G], sF[o + TILE_G * TILE_G + TILE_G + 1], fx);
-            const float c0 = lerp(c00, c10, fy);
-            const float c1 = lerp(c01, c11, fy);
-            const float Ft = lerp(c0, c1, fz);
-            if (!(fabsf(Ft) <= c.band)) continue;
-            float Xh, Yh, Zh;
-            rigid(c.Rc, c.tc, X, Y, Z, Xh, Yh, Zh);
-            float uh, vh;
-            if (!project(c.Kr, c.kr_pinhole, Xh, Yh, Zh, uh, vh)) continue;
-            uint32_t s[3];
-            if (!sample_rgb(c, rgb, uh, vh, s)) continue;
-            const int64_t co = brick_offset(kx, ky, kz, c.ncb);
-            uint32_t vox = vol.C[co];
-            if (c.colour_mode == 1) {
-                if (!paper_normal_update(c, depth, iu, iv, PdX, PdY, PdZ, X, Y, Z, vox, s)) continue;
-            } else {
-                const uint32_t w = vox >> 24;
-                uint32_t out = 0;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const uint32_t cc = (vox >> (8 * k)) & 0xFFu;
-                    out |= ((cc * w + s[k] + ((w + 1u) >> 1)) / (w + 1u)) << (8 * k);
-                }
-                const uint32_t wn = min(w + 1u, (uint32_t)c.max_weight);
-                vox = out | (wn << 24);
-            }
-            vol.C[co] = vox;
-            ++cnt;
-        }
-        cnt = __reduce_add_sync(0xffffffffu, cnt);
-        if ((tid & 31) == 0 && cnt) atomicAdd(&ctr->col_updated, (unsigned long long)cnt);
-        __syncthreads();
+        const uint32_t wn = min(w + 1u, (uint32_t)c.max_weight);
+        vox = out | (wn << 24);
     }
+    C[co] = vox;
+    return true;
+}
+
+// Band gate of the colour voxels a geometry brick owns (first colour
+// kernel).  One warp per listed brick, taken with an atomic counter.  The warp
+//   1. stages the brick's post-update geometry plus a one-voxel halo (10^3 F
+//      and w: the centre brick as float4, the halo as its 6 faces, 12 edges
+//      and 8 corners) in its shared-memory slot with three flag bits per
+//      voxel: observed (w > 0), F <= band + eps, F >= -band - eps; and
+//      tabulates, per axis, the owned colour indices' centres, trilinear
+//      cell and cell fraction;
+//   2. packs the flags into 10-bit row masks;
+//   3. marks the 9^3 trilinear cells that can pass the band gate (all eight
+//      corners observed, the corner range meets [-band, band]) as 9-bit masks
+//      (AND / OR of four rows, then of neighbouring bits) and compacts them;
+//   4. evaluates the trilinear TSDF (lerp along x, then y, then z) of every
+//      colour voxel of a marked cell and records those with |F| <= band for
+//      the colour-voxel kernel, through a shared staging buffer (one atomic
+//      per 256 records).  Records that do not fit the global buffer are
+//      finished by the warp itself (same arithmetic).
+// The cell marks are conservative (eps bounds the trilinear rounding); the
+// band gate itself is evaluated exactly as written.
+constexpr int MAXK = 66;    // owned colour indices per axis (colour/geometry ratio <= 8)
+constexpr int STAGE = 256;  // per-warp record staging entries
+
+struct ColourSlot {  // one warp's shared-memory working set (~11 KB)
+    float F[TILE_G3];
+    uint8_t flag[TILE_G3];
+    uint16_t row[3][TILE_G * TILE_G];
+    uint16_t cells[CELLS3];
+    float frac[3][MAXK];
+    int8_t cellof[3][MAXK];
+    uint8_t start[3][CELLS], end[3][CELLS];
+    int32_t nbr[27];  // neighbour brick indices, -1 outside the volume
+    uint2 out[STAGE];
+};
+
+// Store one staged geometry voxel with its flags.
+__device__ __forceinline__ void stage(ColourSlot& S, int tx, int ty, int tz, float f, uint32_t w, float lo_thr,
+                                      float hi_thr) {
+    const int i = (tz * TILE_G + ty) * TILE_G + tx;
+    S.F[i] = f;
+    S.flag[i] = (uint8_t)((w != 0u ? 1u : 0u) | (f <= lo_thr ? 2u : 0u) | (f >= hi_thr ? 4u : 0u));
+}
+
+// Offset of tile voxel (tx, ty, tz) in the brick-major volume, or -1.  Tile
+// coordinate 0 is local 7 of the previous brick, 1..8 are locals 0..7 of the
+// centre brick, 9 is local 0 of the next brick.
+__device__ __forceinline__ int64_t tile_offset(const ColourSlot& S, int tx, int ty, int tz) {
+    const int sx = tx == 0 ? 0 : (tx == TILE_G - 1 ? 2 : 1);
+    const int sy = ty == 0 ? 0 : (ty == TILE_G - 1 ? 2 : 1);
+    const int sz = tz == 0 ? 0 : (tz == TILE_G - 1 ? 2 : 1);
+    const int nb = S.nbr[(sz * 3 + sy) * 3 + sx];
+    if (nb < 0) return -1;
+    const int lx = (tx + 7) & 7, ly = (ty + 7) & 7, lz = (tz + 7) & 7;
+    return (int64_t)nb * BRICK_VOX + (lz * BRICK + ly) * BRICK + lx;
+}
+
+__device__ __forceinline__ int ceil_log2(int v) {
+    int s = 0;
+    while ((1 << s) < v) ++s;
+    return s;
+}
+
+// Move n staged records to the global list; those beyond its capacity are
+// finished here.  Returns the number of colour voxels updated here.
+__device__ uint32_t flush_records(const FrameConst& c, Volumes& vol, const uint16_t* __restrict__ depth,
+                                  const uint8_t* __restrict__ rgb, const Scratch& scr, ColourSlot& S, uint32_t n,
+                                  int lane) {
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&scr.ctr->n_vox, n);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    uint32_t done = 0;
+    for (uint32_t i = lane; i < n; i += 32) {
+        const uint2 r = S.out[i];
+        if ((uint64_t)base + i < scr.vox_cap)
+            scr.vox[base + i] = r;
+        else if (colour_after_band(c, vol.C, depth, rgb, (int)(r.x & 0xFFFFu), (int)(r.x >> 16), (int)r.y))
+            ++done;
+    }
+    __syncwarp();
+    return done;
+}
+
+__global__ void __launch_bounds__(COL_THREADS, 5) k_colour_band(FrameConst c, Volumes vol,
+                                                                const uint16_t* __restrict__ depth,
+                                                                const uint8_t* __restrict__ rgb, Scratch scr) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ColourSlot& S = reinterpret_cast<ColourSlot*>(smem_raw)[threadIdx.x >> 5];
+    Counters* __restrict__ ctr = scr.ctr;
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    const uint32_t n = ctr->n_col;
+    const float lo_thr = c.band + CELL_EPS, hi_thr = -c.band - CELL_EPS;
+    uint32_t count = 0, n_active = 0, n_cells = 0;
+    for (;;) {
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(&ctr->col_next, 1u);
+        item = __shfl_sync(full, item, 0);
+        if (item >= n) break;
+        const uint32_t b = scr.col_list[item];
+        const int bb[3] = {(int)(b % c.nb[0]), (int)((b / c.nb[0]) % c.nb[1]), (int)(b / (c.nb[0] * c.nb[1]))};
+        int k0[3], k1[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) owned_range(bb[a], c.ng[a], c.nc[a], k0[a], k1[a]);
+        if (lane < 27) {
+            const int x = bb[0] + lane % 3 - 1, y = bb[1] + (lane / 3) % 3 - 1, z = bb[2] + lane / 9 - 1;
+            S.nbr[lane] = (x >= 0 && y >= 0 && z >= 0 && x < c.nb[0] && y < c.nb[1] && z < c.nb[2])
+                              ? (int32_t)(((int64_t)z * c.nb[1] + y) * c.nb[0] + x)
+                              : -1;
+            S.start[lane / 9][lane % 9] = 0;
+            S.end[lane / 9][lane % 9] = 0;
+        }
+        __syncwarp();
+
+        // 1a. centre brick: four float4 of F and four words of w per lane
+        {
+            const float* Fb = vol.F + (size_t)b * BRICK_VOX + lane * 4;
+            const uint8_t* Wb = vol.W + (size_t)b * BRICK_VOX + lane * 4;
+            float4 f[4];
+            uint32_t wv[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                f[j] = *reinterpret_cast<const float4*>(Fb + 128 * j);
+                wv[j] = *reinterpret_cast<const uint32_t*>(Wb + 128 * j);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int q = lane + 32 * j;
+                const int x0 = (q & 1) * 4 + 1, y = ((q >> 1) & 7) + 1, z = (q >> 4) + 1;
+                stage(S, x0 + 0, y, z, f[j].x, wv[j] & 0xFFu, lo_thr, hi_thr);
+                stage(S, x0 + 1, y, z, f[j].y, (wv[j] >> 8) & 0xFFu, lo_thr, hi_thr);
+                stage(S, x0 + 2, y, z, f[j].z, (wv[j] >> 16) & 0xFFu, lo_thr, hi_thr);
+                stage(S, x0 + 3, y, z, f[j].w, wv[j] >> 24, lo_thr, hi_thr);
+            }
+        }
+        // 1b. halo: 6 faces x 64, 12 edges x 8, 8 corners = 488 voxels
+        {
+            int txs[16], tys[16], tzs[16];
+#pragma unroll
+            for (int i = 0; i < 12; ++i) {  // faces: i = 2 * face + half
+                const int face = i >> 1, q = lane + 32 * (i & 1);
+                const int axis = face >> 1, side = (face & 1) ? TILE_G - 1 : 0;
+                const int a = (q & 7) + 1, bq = (q >> 3) + 1;
+                txs[i] = axis == 0 ? side : a;
+                tys[i] = axis == 1 ? side : (axis == 0 ? a : bq);
+                tzs[i] = axis == 2 ? side : bq;
+            }
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {  // edges
+                const int q = lane + 32 * i, e = q >> 3, m = (q & 7) + 1;
+                const int axis = e >> 2, s1 = (e & 1) ? TILE_G - 1 : 0, s2 = (e & 2) ? TILE_G - 1 : 0;
+                txs[12 + i] = axis == 0 ? m : s1;
+                tys[12 + i] = axis == 1 ? m : (axis == 0 ? s1 : s2);
+                tzs[12 + i] = axis == 2 ? m : s2;
+            }
+            txs[15] = (lane & 1) ? TILE_G - 1 : 0;  // corners (lanes 0..7)
+            tys[15] = (lane & 2) ? TILE_G - 1 : 0;
+            tzs[15] = (lane & 4) ? TILE_G - 1 : 0;
+            float hf[16];
+            uint32_t hw[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int64_t off = (i < 15 || lane < 8) ? tile_offset(S, txs[i], tys[i], tzs[i]) : -1;
+                hf[i] = off >= 0 ? vol.F[off] : 0.0f;
+                hw[i] = off >= 0 ? (uint32_t)vol.W[off] : 0u;
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+                if (i < 15 || lane < 8) stage(S, txs[i], tys[i], tzs[i], hf[i], hw[i], lo_thr, hi_thr);
+        }
+        // 1c. per-axis colour tables: trilinear cell and fraction of each owned index
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int ka = a == 0 ? k0[0] : (a == 1 ? k0[1] : k0[2]);
+            const int nk = (a == 0 ? k1[0] : (a == 1 ? k1[1] : k1[2])) - ka;
+            const int ta = (a == 0 ? bb[0] : (a == 1 ? bb[1] : bb[2])) * BRICK - 1;
+            const float oa = a == 0 ? c.origin[0] : (a == 1 ? c.origin[1] : c.origin[2]);
+            for (int j = lane; j < nk; j += 32) {
+                const float p = fmaf((float)(ka + j) + 0.5f, c.s_c, oa);
+                const float g = fmaf(p - oa, c.inv_sg, -0.5f);
+                const float i0 = floorf(g);
+                int cell = (int)i0 - ta;
+                if (cell < 0 || cell >= CELLS) {
+                    atomicOr(scr.err, ERR_TILE_RANGE);
+                    cell = -1;
+                }
+                S.frac[a][j] = g - i0;
+                S.cellof[a][j] = (int8_t)cell;
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int nk = a == 0 ? k1[0] - k0[0] : (a == 1 ? k1[1] - k0[1] : k1[2] - k0[2]);
+            for (int j = lane; j < nk; j += 32) {
+                const int cell = S.cellof[a][j];
+                if (cell < 0) continue;
+                if (j == 0 || S.cellof[a][j - 1] != cell) S.start[a][cell] = (uint8_t)j;
+                if (j == nk - 1 || S.cellof[a][j + 1] != cell) S.end[a][cell] = (uint8_t)(j + 1);
+            }
+        }
+        __syncwarp();
+
+        // 2. row masks (row = z * 10 + y, bit = x)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = lane + 32 * i;
+            if (r < TILE_G * TILE_G) {
+                uint32_t mo = 0, ml = 0, mh = 0;
+#pragma unroll
+                for (int x = 0; x < TILE_G; ++x) {
+                    const uint32_t fl = S.flag[r * TILE_G + x];
+                    mo |= (fl & 1u) << x;
+                    ml |= ((fl >> 1) & 1u) << x;
+                    mh |= ((fl >> 2) & 1u) << x;
+                }
+                S.row[0][r] = (uint16_t)mo;
+                S.row[1][r] = (uint16_t)ml;
+                S.row[2][r] = (uint16_t)mh;
+            }
+        }
+        __syncwarp();
+
+        // 3. active cells, compacted
+        uint32_t xmask = 0;
+        int shx, shy, shz;
+        {
+            int mx = 0, my = 0, mz = 0;
+#pragma unroll
+            for (int cell = 0; cell < CELLS; ++cell) {
+                const int nx = S.end[0][cell] - S.start[0][cell];
+                xmask |= (nx > 0 ? 1u : 0u) << cell;
+                mx = max(mx, nx);
+                my = max(my, S.end[1][cell] - S.start[1][cell]);
+                mz = max(mz, S.end[2][cell] - S.start[2][cell]);
+            }
+            shx = ceil_log2(mx);
+            shy = ceil_log2(my);
+            shz = ceil_log2(mz);
+        }
+        uint32_t act[3];
+        uint32_t total = 0;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const int yz = lane + 32 * r;
+            act[r] = 0;
+            if (yz < CELLS * CELLS) {
+                const int cy = yz % CELLS, cz = yz / CELLS;
+                if (S.end[1][cy] > S.start[1][cy] && S.end[2][cz] > S.start[2][cz]) {
+                    const int r00 = cz * TILE_G + cy, r10 = r00 + 1, r01 = r00 + TILE_G, r11 = r01 + 1;
+                    uint32_t o = S.row[0][r00] & S.row[0][r10] & S.row[0][r01] & S.row[0][r11];
+                    o &= o >> 1;
+                    uint32_t a = o & xmask;
+                    if (c.culling) {
+                        uint32_t l = S.row[1][r00] | S.row[1][r10] | S.row[1][r01] | S.row[1][r11];
+                        uint32_t h = S.row[2][r00] | S.row[2][r10] | S.row[2][r01] | S.row[2][r11];
+                        a &= (l | (l >> 1)) & (h | (h >> 1));
+                    }
+                    act[r] = a & 0x1FFu;
+                }
+            }
+            total += __popc(act[r]);
+        }
+        uint32_t incl = total;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(full, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const uint32_t nact = __shfl_sync(full, incl, 31);
+        if (nact == 0) continue;  // no colour voxel of this brick can pass the band gate
+        ++n_active;
+        n_cells += nact;
+        uint32_t pos = incl - total;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            uint32_t a = act[r];
+            const int yz = lane + 32 * r;
+            while (a) {
+                const int cx = __ffs(a) - 1;
+                a &= a - 1;
+                S.cells[pos++] = (uint16_t)(yz * CELLS + cx);
+            }
+        }
+        __syncwarp();
+
+        // 4. band gate of each colour voxel of the active cells; records
+        const uint32_t sh = shx + shy + shz;
+        const uint32_t units = nact << sh;
+        const uint32_t lanemask_lt = (1u << lane) - 1u;
+        uint32_t nstage = 0;
+        for (uint32_t ub = 0; ub < units; ub += 32) {
+            const uint32_t u = ub + lane;
+            bool pass = false;
+            uint2 rec = make_uint2(0u, 0u);
+            if (u < units) {
+                const uint32_t cellid = S.cells[u >> sh];
+                const uint32_t sub = u & ((1u << sh) - 1u);
+                const int cx = cellid % CELLS, cy = (cellid / CELLS) % CELLS, cz = cellid / (CELLS * CELLS);
+                const int jx = S.start[0][cx] + (int)(sub & ((1u << shx) - 1u));
+                const int jy = S.start[1][cy] + (int)((sub >> shx) & ((1u << shy) - 1u));
+                const int jz = S.start[2][cz] + (int)(sub >> (shx + shy));
+                if (jx < S.end[0][cx] && jy < S.end[1][cy] && jz < S.end[2][cz]) {
+                    const int o = (cz * TILE_G + cy) * TILE_G + cx;
+                    const float fx = S.frac[0][jx], fy = S.frac[1][jy], fz = S.frac[2][jz];
+                    const float c00 = lerp(S.F[o], S.F[o + 1], fx);
+                    const float c10 = lerp(S.F[o + TILE_G], S.F[o + TILE_G + 1], fx);
+                    const float c01 = lerp(S.F[o + TILE_G * TILE_G], S.F[o + TILE_G * TILE_G + 1], fx);
+                    const float c11 =
+                        lerp(S.F[o + TILE_G * TILE_G + TILE_G], S.F[o + TILE_G * TILE_G + TILE_G + 1], fx);
+                    const float c0 = lerp(c00, c10, fy);
+                    const float c1 = lerp(c01, c11, fy);
+                    const float Ft = lerp(c0, c1, fz);
+                    pass = fabsf(Ft) <= c.band;
+                    rec = make_uint2((uint32_t)(k0[0] + jx) | ((uint32_t)(k0[1] + jy) << 16), (uint32_t)(k0[2] + jz));
+                }
+            }
+            const uint32_t m = __ballot_sync(full, pass);
+            if (pass) S.out[nstage + __popc(m & lanemask_lt)] = rec;
+            nstage += __popc(m);
+            if (nstage > STAGE - 32) {
+                __syncwarp();
+                count += flush_records(c, vol, depth, rgb, scr, S, nstage, lane);
+                nstage = 0;
+            }
+        }
+        __syncwarp();
+        if (nstage) count += flush_records(c, vol, depth, rgb, scr, S, nstage, lane);
+    }
+    count = __reduce_add_sync(full, count);
+    if (lane == 0) {  // n_active and n_cells are the same in every lane
+        if (count) atomicAdd(&ctr->col_updated, (unsigned long long)count);
+        if (n_active) atomicAdd(&ctr->n_col_active, n_active);
+        if (n_cells) atomicAdd(&ctr->n_cells, n_cells);
+    }
+}
+
+// Colour voxels that passed the band gate (second colour kernel): one thread
+// per record, so the work is balanced however the surface is spread over
+// bricks.
+__global__ void __launch_bounds__(256) k_colour_voxels(FrameConst c, Volumes vol, const uint16_t* __restrict__ depth,
+                                                       const uint8_t* __restrict__ rgb, Scratch scr) {
+    Counters* __restrict__ ctr = scr.ctr;
+    const uint32_t nv = min(ctr->n_vox, scr.vox_cap);
+    uint32_t count = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x) {
+        const uint2 r = scr.vox[i];
+        if (colour_after_band(c, vol.C, depth, rgb, (int)(r.x & 0xFFFFu), (int)(r.x >> 16), (int)r.y)) ++count;
+    }
+    count = __reduce_add_sync(0xffffffffu, count);
+    if ((threadIdx.x & 31) == 0 && count) atomicAdd(&ctr->col_updated, (unsigned long long)count);
 }
 
 __global__ void k_init_summaries(BrickSummary* summ, int64_t n) {
@@ -589,7 +921,7 @@ __global__ void k_init_summaries(BrickSummary* summ, int64_t n) {
         s.fmin = __int_as_float(0x7f800000);
         s.fmax = __int_as_float(0xff800000);
         s.wmin = 0;
-        s.pad = 0;
+        s.flags = 0;
         summ[i] = s;
     }
 }
@@ -604,18 +936,27 @@ cudaError_t launch_init_summaries(BrickSummary* summ, int64_t n, cudaStream_t st
 
 int geometry_blocks_per_sm() {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_geometry, GEO_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_geometry<true, true>, GEO_THREADS, 0);
     return n > 0 ? n : 1;
 }
 
+size_t colour_smem_bytes() { return sizeof(ColourSlot) * (COL_THREADS / 32); }
+
 int colour_blocks_per_sm() {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_colour, COL_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_colour_band, COL_THREADS, colour_smem_bytes());
+    return n > 0 ? n : 1;
+}
+
+int voxel_blocks_per_sm() {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_colour_voxels, 256, 0);
     return n > 0 ? n : 1;
 }
 
 cudaError_t launch_frame(const FrameConst& c, const Volumes& v, const Scratch& s, const uint16_t* depth,
-                         const uint8_t* rgb, int grid_geo, int grid_col, cudaStream_t stream, cudaEvent_t* ev) {
+                         const uint8_t* rgb, const LaunchGrids& g, cudaStream_t stream, cudaEvent_t* ev) {
+    const int grid_geo = g.geo, grid_col = g.col;
     auto mark = [&](int i) {
         if (ev) cudaEventRecord(ev[i], stream);
     };
@@ -626,14 +967,23 @@ cudaError_t launch_frame(const FrameConst& c, const Volumes& v, const Scratch& s
     const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
     k_bricks<<<(nbt + 255) / 256, 256, 0, stream>>>(c, v.summ, s.depth_tiles, s.ctr, s.geo_list, s.vis_list);
     mark(2);
-    k_geometry<<<grid_geo, GEO_THREADS, 0, stream>>>(c, v, depth, s.ctr, s.geo_list);
+    if (c.kd_pinhole && c.free_space)
+        k_geometry<true, true><<<grid_geo, GEO_THREADS, 0, stream>>>(c, v, depth, s.ctr, s.geo_list);
+    else if (c.kd_pinhole)
+        k_geometry<true, false><<<grid_geo, GEO_THREADS, 0, stream>>>(c, v, depth, s.ctr, s.geo_list);
+    else if (c.free_space)
+        k_geometry<false, true><<<grid_geo, GEO_THREADS, 0, stream>>>(c, v, depth, s.ctr, s.geo_list);
+    else
+        k_geometry<false, false><<<grid_geo, GEO_THREADS, 0, stream>>>(c, v, depth, s.ctr, s.geo_list);
     mark(3);
     unsigned gl = (nbt + 255) / 256;
     if (gl > 1024u) gl = 1024u;
     k_colour_list<<<gl, 256, 0, stream>>>(c, v.summ, s.ctr, s.vis_list, s.col_list);
     mark(4);
-    k_colour<<<grid_col, COL_THREADS, 0, stream>>>(c, v, depth, rgb, s.ctr, s.col_list, s.err);
+    k_colour_band<<<grid_col, COL_THREADS, colour_smem_bytes(), stream>>>(c, v, depth, rgb, s);
     mark(5);
+    k_colour_voxels<<<g.vox, 256, 0, stream>>>(c, v, depth, rgb, s);
+    mark(6);
     return cudaGetLastError();
 }
 

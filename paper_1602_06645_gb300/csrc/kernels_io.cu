@@ -40,16 +40,17 @@ cudaError_t convert(T* brick, T* lin, const int32_t dims[3], int z0, int z1, cud
 // in-volume voxels (the same summary the geometry kernel maintains).
 __global__ void __launch_bounds__(128) k_summaries(const float* __restrict__ F, const uint8_t* __restrict__ W,
                                                    BrickSummary* __restrict__ summ, int nx, int ny, int nz, int nbx,
-                                                   int nby) {
+                                                   int nby, float band) {
     __shared__ float s_fmin[4], s_fmax[4];
-    __shared__ uint32_t s_wmin[4];
+    __shared__ uint32_t s_wmin[4], s_flags[4];
     const uint32_t b = blockIdx.x;
     const int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
     const int tid = threadIdx.x;
     const int lx = (tid & 1) * 4, ly = (tid >> 1) & 7, lz = tid >> 4;
     const size_t base = (size_t)b * BRICK_VOX + (size_t)tid * 4;
     float fmn = FLT_MAX, fmx = -FLT_MAX;
-    uint32_t wmn = 0xFFFFFFFFu;
+    uint32_t wmn = 0xFFFFFFFFu, flags = 0;
+    const float lo_thr = band + CELL_EPS, hi_thr = -band - CELL_EPS;
     for (int j = 0; j < 4; ++j) {
         const int x = bx * BRICK + lx + j, y = by * BRICK + ly, z = bz * BRICK + lz;
         if (x >= nx || y >= ny || z >= nz) continue;
@@ -57,21 +58,33 @@ __global__ void __launch_bounds__(128) k_summaries(const float* __restrict__ F, 
         const float f = F[base + j];
         wmn = min(wmn, w);
         if (w) { fmn = fminf(fmn, f); fmx = fmaxf(fmx, f); }
+        flags |= band_flags(w != 0u, f, lo_thr, hi_thr, lx + j, ly, lz);
     }
+    flags = __reduce_or_sync(0xffffffffu, flags);
     for (int o = 16; o > 0; o >>= 1) {
         fmn = fminf(fmn, __shfl_xor_sync(0xffffffffu, fmn, o));
         fmx = fmaxf(fmx, __shfl_xor_sync(0xffffffffu, fmx, o));
     }
     wmn = __reduce_min_sync(0xffffffffu, wmn);
-    if ((tid & 31) == 0) { s_fmin[tid >> 5] = fmn; s_fmax[tid >> 5] = fmx; s_wmin[tid >> 5] = wmn; }
+    if ((tid & 31) == 0) {
+        s_fmin[tid >> 5] = fmn;
+        s_fmax[tid >> 5] = fmx;
+        s_wmin[tid >> 5] = wmn;
+        s_flags[tid >> 5] = flags;
+    }
     __syncthreads();
     if (tid == 0) {
-        for (int i = 1; i < 4; ++i) { fmn = fminf(fmn, s_fmin[i]); fmx = fmaxf(fmx, s_fmax[i]); wmn = min(wmn, s_wmin[i]); }
+        for (int i = 1; i < 4; ++i) {
+            fmn = fminf(fmn, s_fmin[i]);
+            fmx = fmaxf(fmx, s_fmax[i]);
+            wmn = min(wmn, s_wmin[i]);
+            flags |= s_flags[i];
+        }
         BrickSummary s;
         s.fmin = fmn == FLT_MAX ? __int_as_float(0x7f800000) : fmn;
         s.fmax = fmx == -FLT_MAX ? __int_as_float(0xff800000) : fmx;
         s.wmin = wmn == 0xFFFFFFFFu ? 0u : wmn;
-        s.pad = 0;
+        s.flags = flags;
         summ[b] = s;
     }
 }
@@ -99,10 +112,10 @@ cudaError_t launch_from_linear_u32(uint32_t* b, const uint32_t* l, const int32_t
 }
 
 cudaError_t launch_recompute_summaries(const float* F, const uint8_t* W, BrickSummary* summ, const int32_t ng[3],
-                                       cudaStream_t stream) {
+                                       float band, cudaStream_t stream) {
     const int nbx = (ng[0] + BRICK - 1) / BRICK, nby = (ng[1] + BRICK - 1) / BRICK, nbz = (ng[2] + BRICK - 1) / BRICK;
     const int64_t nbt = (int64_t)nbx * nby * nbz;
-    if (nbt > 0) k_summaries<<<(unsigned)nbt, 128, 0, stream>>>(F, W, summ, ng[0], ng[1], ng[2], nbx, nby);
+    if (nbt > 0) k_summaries<<<(unsigned)nbt, 128, 0, stream>>>(F, W, summ, ng[0], ng[1], ng[2], nbx, nby, band);
     return cudaGetLastError();
 }
 

@@ -27,7 +27,7 @@ struct tsdf_volume {
     cudaStream_t stream;
     tsdf_allocator alloc;
     int device;
-    int grid_geo, grid_col;
+    LaunchGrids grids;
     Volumes vol;
     Scratch scr;
     uint32_t* depth_tiles;
@@ -98,6 +98,11 @@ void dev_free(tsdf_volume* v, void* p) {
             return;
         }
     }
+}
+
+// Band-gate voxel record capacity for a volume of nbt geometry bricks.
+int64_t vox_capacity(int64_t nbt) {
+    return std::min<int64_t>(std::max<int64_t>(int64_t(1) << 22, nbt * 64), int64_t(1) << 28);
 }
 
 bool finite_all(const float* a, int n) {
@@ -302,6 +307,7 @@ tsdf_status tsdf_create_ex(const int32_t dims_geo[3], const int32_t dims_col[3],
         if (dims_geo[a] < 1 || dims_geo[a] > MAX_DIM || dims_col[a] < 1 || dims_col[a] > MAX_DIM)
             return TSDF_ERR_INVALID_ARG;
         if ((int64_t)dims_col[a] * dims_geo[0] != (int64_t)dims_col[0] * dims_geo[a]) return TSDF_ERR_INVALID_ARG;
+        if (dims_col[a] > 8 * dims_geo[a]) return TSDF_ERR_INVALID_ARG;  // colour/geometry ratio <= 8
     }
     if (!(voxel_size > 0.0f) || !std::isfinite(voxel_size) || !(mu > 0.0f) || !std::isfinite(mu))
         return TSDF_ERR_INVALID_ARG;
@@ -351,12 +357,14 @@ tsdf_status tsdf_create_ex(const int32_t dims_geo[3], const int32_t dims_col[3],
         delete v;
         return TSDF_ERR_CUDA;
     }
-    v->grid_geo = sms * geometry_blocks_per_sm();
-    v->grid_col = sms * colour_blocks_per_sm();
+    v->grids.geo = sms * geometry_blocks_per_sm();
+    v->grids.col = sms * colour_blocks_per_sm();
+    v->grids.vox = sms * voxel_blocks_per_sm();
 
     const int64_t nbt = (int64_t)v->nb[0] * v->nb[1] * v->nb[2];
     const int64_t ncbt = (int64_t)v->ncb[0] * v->ncb[1] * v->ncb[2];
-    const size_t need = (size_t)nbt * BRICK_VOX * 5 + (size_t)ncbt * BRICK_VOX * 4 + (size_t)nbt * (sizeof(BrickSummary) + 12);
+    const size_t need = (size_t)nbt * BRICK_VOX * 5 + (size_t)ncbt * BRICK_VOX * 4 + (size_t)nbt * (sizeof(BrickSummary) + 12) +
+                        (size_t)vox_capacity(nbt) * sizeof(uint2);
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && need > free_b) {
         delete v;
@@ -372,8 +380,16 @@ tsdf_status tsdf_create_ex(const int32_t dims_geo[3], const int32_t dims_col[3],
     v->scr.vis_list = (uint32_t*)dev_alloc(v, (size_t)nbt * sizeof(uint32_t));
     v->scr.col_list = (uint32_t*)dev_alloc(v, (size_t)nbt * sizeof(uint32_t));
     v->scr.err = (uint32_t*)dev_alloc(v, sizeof(uint32_t));
+    // band-gate voxel records of one frame; records that do not fit are
+    // finished by the band kernel itself, so the capacity only bounds memory
+    v->scr.vox_cap = (uint32_t)vox_capacity(nbt);
+    if (const char* cap = std::getenv("TSDF_VOXEL_RECORD_CAPACITY")) {  // test / tuning override
+        const long long n = std::atoll(cap);
+        if (n >= 1 && n < (long long)v->scr.vox_cap) v->scr.vox_cap = (uint32_t)n;
+    }
+    v->scr.vox = (uint2*)dev_alloc(v, (size_t)v->scr.vox_cap * sizeof(uint2));
     if (!v->vol.F || !v->vol.W || !v->vol.C || !v->vol.summ || !v->scr.ctr || !v->scr.geo_list || !v->scr.vis_list ||
-        !v->scr.col_list || !v->scr.err) {
+        !v->scr.col_list || !v->scr.err || !v->scr.vox) {
         tsdf_destroy(v);
         return TSDF_ERR_OOM;
     }
@@ -480,7 +496,7 @@ tsdf_status tsdf_integrate(tsdf_volume* v, const uint16_t* depth_mm, tsdf_image_
         if (!v->depth_tiles) return fail(v, TSDF_ERR_OOM, "depth tile buffer");
     }
     v->scr.depth_tiles = v->depth_tiles;
-    e = launch_frame(c, v->vol, v->scr, d_depth, d_rgb, v->grid_geo, v->grid_col, v->stream, evs ? evs->e + 1 : nullptr);
+    e = launch_frame(c, v->vol, v->scr, d_depth, d_rgb, v->grids, v->stream, evs ? evs->e + 1 : nullptr);
     if (e != cudaSuccess) return cuda_fail(v, e, "integrate launch");
     ++v->frames;
     return TSDF_OK;
@@ -506,7 +522,7 @@ tsdf_status tsdf_write(tsdf_volume* v, const float* tsdf, const uint8_t* w_geo, 
     if (s == TSDF_OK) s = write_volume<uint8_t>(v, v->vol.W, w_geo, v->ng, launch_from_linear_u8);
     if (s == TSDF_OK) s = write_volume<uint32_t>(v, v->vol.C, rgbw, v->nc, launch_from_linear_u32);
     if (s != TSDF_OK) return s;
-    cudaError_t e = launch_recompute_summaries(v->vol.F, v->vol.W, v->vol.summ, v->ng, v->stream);
+    cudaError_t e = launch_recompute_summaries(v->vol.F, v->vol.W, v->vol.summ, v->ng, v->band, v->stream);
     if (e != cudaSuccess) return cuda_fail(v, e, "summaries");
     return check_device_error(v);
 }
@@ -552,6 +568,9 @@ tsdf_status tsdf_get_stats(tsdf_volume* v, tsdf_stats* o) {
     o->total_geo_bricks = (int64_t)(h.tot_geo_bricks + h.n_geo);
     o->total_col_bricks = (int64_t)(h.tot_col_bricks + h.n_col);
     o->total_visible_bricks = (int64_t)(h.tot_vis_bricks + h.n_vis);
+    o->total_col_active_bricks = (int64_t)(h.tot_col_active + h.n_col_active);
+    o->total_cells = (int64_t)(h.tot_cells + h.n_cells);
+    o->total_geo_changed_bricks = (int64_t)(h.tot_geo_changed + h.n_geo_changed);
     return TSDF_OK;
 }
 

@@ -64,6 +64,7 @@ def test_params_default(T):
 @pytest.mark.parametrize("dims_geo,dims_col,vs,mu,mw", [
     ((0, 8, 8), (16, 16, 16), 0.01, 0.03, 64),        # dims <= 0
     ((8, 8, 8), (16, 16, 17), 0.01, 0.03, 64),        # anisotropic ratio
+    ((8, 8, 8), (72, 72, 72), 0.01, 0.03, 64),        # colour/geometry ratio above 8
     ((8, 8, 5000), (8, 8, 5000), 0.01, 0.03, 64),     # dims > 4096
     ((8, 8, 8), (16, 16, 16), 0.0, 0.03, 64),         # voxel size <= 0
     ((8, 8, 8), (16, 16, 16), 0.01, -1.0, 64),        # mu <= 0

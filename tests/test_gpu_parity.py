@@ -115,6 +115,17 @@ def test_modes(mode):
     assert_parity(o, F, W, C, mode)
 
 
+def test_record_buffer_overflow_path_is_exact(monkeypatch):
+    """With a voxel-record buffer of 5 entries almost every band-passing voxel
+    is finished by the band kernel itself; the volumes still equal the
+    oracle's."""
+    monkeypatch.setenv("TSDF_VOXEL_RECORD_CAPACITY", "5")
+    seq = synth.sequence_small(n_frames=4, dims_geo=64, seed=17)
+    o, F, W, C, _ = run_sequence(seq, range(4))
+    assert_parity(o, F, W, C, "overflow")
+    assert ((C >> 24) > 0).sum() > 1000
+
+
 def test_device_and_host_inputs_agree():
     seq = synth.sequence_small(n_frames=3, dims_geo=48, seed=9)
     o1, F1, W1, C1, _ = run_sequence(seq, range(3))
@@ -221,7 +232,7 @@ def test_invalid_frame_arguments_are_rejected():
     v = T.Volume(seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, seq.max_weight)
     d, c = seq.frame(0)
     bad_T = seq.poses[0].copy()
-    bad_T[0, 0] *= 1.1  # not a rotation
+    bad_T[:3, 0] *= 1.1  # not a rotation (column norm 1.1)
     for args in [(d, c, seq.K_depth, seq.K_rgb, bad_T, seq.T_depth_rgb),
                  (d, c, np.zeros((3, 3)), seq.K_rgb, seq.poses[0], seq.T_depth_rgb),
                  (d, c, seq.K_depth, seq.K_rgb, np.full((4, 4), np.nan), seq.T_depth_rgb)]:
