@@ -218,6 +218,42 @@ typedef struct {
 tsdf_status tsdf_profile_enable(tsdf_volume* vol, int32_t enable);
 tsdf_status tsdf_profile_read(tsdf_volume* vol, tsdf_profile_report* out);
 
+/* Allocation-free geometry fusion.  (The paper has no counterpart: this is an
+ * interface for callers that cannot allocate device memory, for example code
+ * running while another framework owns the device allocator, or a host with a
+ * device-memory budget fixed in advance.)
+ *
+ * Fuses one depth frame into a caller-owned TSDF volume with the same
+ * arithmetic and the same results as the geometry step of tsdf_integrate
+ * (culling only skips bricks that cannot change).  It needs no handle and
+ * calls no cudaMalloc, cudaFree or other allocating routine: its scratch
+ * (work counters, depth tiles, brick work list) is one fixed device array of
+ * about 4.3 MB that every GPU loading the library holds until the process
+ * exits.
+ *   dims            voxels per axis (x, y, z), 1..4096, with at most
+ *                   TSDF_STATIC_MAX_BRICKS bricks of 8^3 voxels
+ *   voxel_size, mu, max_weight, origin   as in tsdf_create_ex
+ *   tsdf_dev, w_dev device arrays of dims[0]*dims[1]*dims[2] floats / bytes,
+ *                   linear x-fastest, read and updated in place (start from
+ *                   zeros for an empty volume)
+ *   depth_dev       device uint16 millimetre depth image of dsz, at most
+ *                   TSDF_STATIC_MAX_DEPTH_TILES tiles of 16x16 pixels
+ *   K_depth, T_world_depth  host pointers, as in tsdf_integrate
+ *   stream          cudaStream_t the kernels are queued on (NULL = legacy default)
+ * Sizes beyond the maxima, NULL pointers and invalid K / T are rejected with
+ * TSDF_ERR_INVALID_ARG before any work is queued.  The first call on a device
+ * looks up the scratch array's device address there (cudaGetSymbolAddress),
+ * so make it before any stream capture.  Every call shares the one scratch
+ * array, which keeps the previous call's contents (the call clears what must
+ * start at zero): calls whose work overlaps on the GPU race, so queue them on
+ * one stream or wait between them.  Asynchronous with respect to the host. */
+#define TSDF_STATIC_MAX_BRICKS (1 << 20)     /* e.g. 512^3 voxels use 262,144 bricks */
+#define TSDF_STATIC_MAX_DEPTH_TILES 65536    /* e.g. 4096 x 4096 pixels use 65,536 tiles */
+tsdf_status tsdf_integrate_geometry_static(const int32_t dims[3], float voxel_size, float mu, int32_t max_weight,
+                                           const float origin[3], float* tsdf_dev, uint8_t* w_dev,
+                                           const uint16_t* depth_dev, tsdf_image_size dsz, const float K_depth[9],
+                                           const float T_world_depth[16], void* stream);
+
 /* Human-readable text of a status, and the last error message of a handle
  * (empty if none).  The strings are owned by the library. */
 const char* tsdf_status_string(tsdf_status s);

@@ -33,6 +33,7 @@ EXPORTS = [
     "tsdf_params_default", "tsdf_create", "tsdf_create_ex", "tsdf_integrate", "tsdf_read", "tsdf_write",
     "tsdf_synchronize", "tsdf_save", "tsdf_load", "tsdf_destroy", "tsdf_set_stream", "tsdf_get_info",
     "tsdf_get_stats", "tsdf_status_string", "tsdf_last_error", "tsdf_profile_enable", "tsdf_profile_read",
+    "tsdf_integrate_geometry_static",
 ]
 PHASES = ["upload", "depth_tiles", "bricks", "geometry", "colour_list", "colour_cells", "colour"]
 
@@ -135,6 +136,9 @@ def load():
     lib.tsdf_status_string.restype = ctypes.c_char_p
     lib.tsdf_last_error.argtypes = [vp]
     lib.tsdf_last_error.restype = ctypes.c_char_p
+    lib.tsdf_integrate_geometry_static.argtypes = [i32p, ctypes.c_float, ctypes.c_float, ctypes.c_int32, fp, vp, vp,
+                                                   vp, tsdf_image_size, fp, fp, vp]
+    lib.tsdf_integrate_geometry_static.restype = ctypes.c_int
     lib.tsdf_profile_enable.argtypes = [vp, ctypes.c_int32]
     lib.tsdf_profile_read.argtypes = [vp, ctypes.POINTER(tsdf_profile_report)]
     for name in ("tsdf_create", "tsdf_create_ex", "tsdf_integrate", "tsdf_read", "tsdf_write", "tsdf_synchronize",
@@ -278,6 +282,22 @@ def tsdf_get_stats(h):
     o = tsdf_stats()
     _check(load().tsdf_get_stats(h, ctypes.byref(o)), h)
     return o
+
+
+def tsdf_integrate_geometry_static(dims, voxel_size, mu, max_weight, origin, tsdf, w, depth_mm, K_depth,
+                                   T_world_depth, stream=None):
+    """Allocation-free geometry fusion into caller-owned device arrays (see
+    include/tsdf.h): `tsdf` / `w` are CUDA tensors of dims[2] x dims[1] x
+    dims[0] float32 / uint8, `depth_mm` a CUDA tensor of the depth image."""
+    keep = []
+    dh, dw = _hw(depth_mm)
+    org = np.ascontiguousarray(np.asarray(origin, dtype=np.float32).reshape(3))
+    Kd, Twd = _mat(K_depth, 9), _mat(T_world_depth, 16)
+    _check(load().tsdf_integrate_geometry_static(_i32x3(dims), float(voxel_size), float(mu), int(max_weight),
+                                                 org.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                 _ptr(tsdf, np.float32, keep), _ptr(w, np.uint8, keep),
+                                                 _ptr(depth_mm, np.uint16, keep), tsdf_image_size(dw, dh), Kd[1],
+                                                 Twd[1], ctypes.c_void_p(int(stream or 0))))
 
 
 def tsdf_profile_enable(h, enable=True):

@@ -143,6 +143,19 @@ cudaError_t launch_recompute_summaries(const float* F, const uint8_t* W, BrickSu
                                        float band, cudaStream_t stream);
 constexpr float CELL_EPS = 1e-5f;  // bound on trilinear overshoot of the corner range
 
+// Geometry-only fusion of one frame into caller-owned linear x-fastest F / w
+// arrays, with caller-provided scratch (counters, depth tiles, brick list).
+cudaError_t launch_geometry_static(const FrameConst& c, float* F, uint8_t* W, const uint16_t* depth, Counters* ctr,
+                                   uint32_t* tiles, uint32_t* geo_list, int grid_geo, cudaStream_t stream);
+// Frame constants of a volume description, by the same rules as tsdf_integrate.
+struct VolumeDesc {
+    int32_t ng[3];
+    float s_g, origin[3], mu;
+    int32_t max_weight;
+};
+void geometry_frame_constants(const VolumeDesc& d, const float Kd[9], const float Twd[16], int dw, int dh,
+                              FrameConst& c);
+
 // ------------------------------------------------------------ addressing --
 __host__ __device__ __forceinline__ int64_t brick_offset(int x, int y, int z, const int32_t nb[3]) {
     int64_t b = ((int64_t)(z >> 3) * nb[1] + (y >> 3)) * nb[0] + (x >> 3);

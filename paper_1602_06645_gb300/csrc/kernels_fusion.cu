@@ -914,6 +914,126 @@ __global__ void __launch_bounds__(256) k_colour_voxels(FrameConst c, Volumes vol
     if ((threadIdx.x & 31) == 0 && count) atomicAdd(&ctr->col_updated, (unsigned long long)count);
 }
 
+// ------------------------------------------ caller-owned geometry volume ----
+// Culling for the allocation-free geometry entry point: the frustum, empty
+// footprint and hidden-behind tests of k_bricks, without the saturated
+// free-space skip (that needs per-brick summaries, which this path does not
+// keep).  Appends to the geometry work list only.
+__global__ void __launch_bounds__(256) k_bricks_static(FrameConst c, const uint32_t* __restrict__ tiles,
+                                                       Counters* __restrict__ ctr, uint32_t* __restrict__ geo_list) {
+    const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
+    uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    bool vis = b < nbt;
+    if (vis && c.culling) {
+        int bx = b % c.nb[0], by = (b / c.nb[0]) % c.nb[1], bz = b / (c.nb[0] * c.nb[1]);
+        float lo[3], hi[3];
+        int bc[3] = {bx, by, bz};
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = c.origin[a] + ((float)(bc[a] * BRICK) - 0.5f) * c.s_g;
+            hi[a] = c.origin[a] + ((float)(bc[a] * BRICK + BRICK) + 0.5f) * c.s_g;
+        }
+        float umin = FLT_MAX, umax = -FLT_MAX, vmin = FLT_MAX, vmax = -FLT_MAX, zmin = FLT_MAX;
+        bool straddle = false;
+        for (int k = 0; k < 8; ++k) {
+            float x = (k & 1) ? hi[0] : lo[0], y = (k & 2) ? hi[1] : lo[1], z = (k & 4) ? hi[2] : lo[2];
+            float X = c.R[0] * x + c.R[1] * y + c.R[2] * z + c.t[0];
+            float Y = c.R[3] * x + c.R[4] * y + c.R[5] * z + c.t[1];
+            float Z = c.R[6] * x + c.R[7] * y + c.R[8] * z + c.t[2];
+            float xh = c.Kd[0] * X + c.Kd[1] * Y + c.Kd[2] * Z;
+            float yh = c.Kd[3] * X + c.Kd[4] * Y + c.Kd[5] * Z;
+            float zh = c.Kd[6] * X + c.Kd[7] * Y + c.Kd[8] * Z;
+            zmin = fminf(zmin, Z);
+            if (zh <= 1e-4f) { straddle = true; continue; }
+            float u = xh / zh, v = yh / zh;
+            umin = fminf(umin, u); umax = fmaxf(umax, u);
+            vmin = fminf(vmin, v); vmax = fmaxf(vmax, v);
+        }
+        int px0 = 0, px1 = c.dw - 1, py0 = 0, py1 = c.dh - 1;
+        if (!straddle) {
+            if (umax < -2.0f || vmax < -2.0f || umin > (float)c.dw + 1.0f || vmin > (float)c.dh + 1.0f) {
+                vis = false;
+            } else {
+                umin = fmaxf(umin, -4.0f); umax = fminf(umax, (float)c.dw + 4.0f);
+                vmin = fmaxf(vmin, -4.0f); vmax = fminf(vmax, (float)c.dh + 4.0f);
+                px0 = max(0, (int)floorf(umin) - 2); px1 = min(c.dw - 1, (int)ceilf(umax) + 2);
+                py0 = max(0, (int)floorf(vmin) - 2); py1 = min(c.dh - 1, (int)ceilf(vmax) + 2);
+            }
+        }
+        if (vis) {
+            uint32_t dmax = 0u;
+            int tx0 = px0 / TILE_PX, tx1 = px1 / TILE_PX, ty0 = py0 / TILE_PX, ty1 = py1 / TILE_PX;
+            if ((tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= 64) {
+                for (int ty = ty0; ty <= ty1; ++ty)
+                    for (int tx = tx0; tx <= tx1; ++tx) dmax = max(dmax, tiles[ty * c.tiles_x + tx] >> 16);
+            } else {
+                dmax = 0xFFFFu;
+            }
+            if (dmax == 0u) vis = false;
+            else if (zmin > (float)dmax * 0.001f + c.cull_behind) vis = false;
+        }
+    }
+    append(vis, b, &ctr->n_geo, geo_list);
+}
+
+// TSDF update of a caller-owned volume in linear x-fastest layout: the same
+// per-voxel arithmetic as k_geometry (one warp per 8^3 brick of the work
+// list, lane l owning x in {0..3} or {4..7}, y = (l >> 1) & 7,
+// z = (l >> 4) + 2 j), with scalar loads and stores of the linear arrays and
+// no brick summary.
+template <bool PINHOLE, bool FREE_SPACE>
+__global__ void __launch_bounds__(GEO_THREADS, 7) k_geometry_linear(FrameConst c, float* __restrict__ F,
+                                                                 uint8_t* __restrict__ W,
+                                                                 const uint16_t* __restrict__ depth,
+                                                                 Counters* __restrict__ ctr,
+                                                                 const uint32_t* __restrict__ list) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t n = ctr->n_geo;
+    const int lx = (lane & 1) * 4, ly = (lane >> 1) & 7, lz = lane >> 4;
+    uint32_t count = 0;
+    for (uint32_t item = warp; item < n; item += nwarps) {
+        const uint32_t b = list[item];
+        const int bx = b % c.nb[0], by = (b / c.nb[0]) % c.nb[1], bz = b / (c.nb[0] * c.nb[1]);
+        const int gy = by * BRICK + ly;
+        const float py = fmaf((float)gy + 0.5f, c.s_g, c.origin[1]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gz = bz * BRICK + lz + 2 * j;
+            const float pz = fmaf((float)gz + 0.5f, c.s_g, c.origin[2]);
+            const float B0 = fmaf(c.R[1], py, fmaf(c.R[2], pz, c.t[0]));
+            const float B1 = fmaf(c.R[4], py, fmaf(c.R[5], pz, c.t[1]));
+            const float B2 = fmaf(c.R[7], py, fmaf(c.R[8], pz, c.t[2]));
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int gx = bx * BRICK + lx + i;
+                if (!(gx < c.ng[0] && gy < c.ng[1] && gz < c.ng[2])) continue;
+                const float px = fmaf((float)gx + 0.5f, c.s_g, c.origin[0]);
+                const float X = fmaf(c.R[0], px, B0), Y = fmaf(c.R[3], px, B1), Z = fmaf(c.R[6], px, B2);
+                float u, v;
+                int iu, iv;
+                if (!project(c.Kd, PINHOLE, X, Y, Z, u, v)) continue;
+                if (!nearest_pixel(u, v, c.dw, c.dh, iu, iv)) continue;
+                const uint32_t D = __ldg(depth + (size_t)iv * c.dw + iu);
+                if (D == 0u) continue;
+                const float d = (float)D * 0.001f;
+                const float sdf = d - Z;
+                if (sdf < -c.mu) continue;
+                if (!FREE_SPACE && sdf > c.mu) continue;
+                const float t = fminf(1.0f, sdf * c.inv_mu);
+                const size_t o = ((size_t)gz * c.ng[1] + gy) * c.ng[0] + gx;
+                const uint32_t w = W[o];
+                const float wf = (float)w;
+                F[o] = __fdiv_rn(fmaf(F[o], wf, t), wf + 1.0f);
+                W[o] = (uint8_t)min(w + 1u, (uint32_t)c.max_weight);
+                ++count;
+            }
+        }
+    }
+    count = __reduce_add_sync(0xffffffffu, count);
+    if (lane == 0 && count) atomicAdd(&ctr->geo_updated, (unsigned long long)count);
+}
+
 __global__ void k_init_summaries(BrickSummary* summ, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
@@ -984,6 +1104,23 @@ cudaError_t launch_frame(const FrameConst& c, const Volumes& v, const Scratch& s
     mark(5);
     k_colour_voxels<<<g.vox, 256, 0, stream>>>(c, v, depth, rgb, s);
     mark(6);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_geometry_static(const FrameConst& c, float* F, uint8_t* W, const uint16_t* depth, Counters* ctr,
+                                   uint32_t* tiles, uint32_t* geo_list, int grid_geo, cudaStream_t stream) {
+    dim3 tg(c.tiles_x, c.tiles_y);
+    k_depth_tiles<<<tg, dim3(TILE_PX, TILE_PX), 0, stream>>>(c, depth, tiles, ctr);
+    const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
+    k_bricks_static<<<(nbt + 255) / 256, 256, 0, stream>>>(c, tiles, ctr, geo_list);
+    if (c.kd_pinhole && c.free_space)
+        k_geometry_linear<true, true><<<grid_geo, GEO_THREADS, 0, stream>>>(c, F, W, depth, ctr, geo_list);
+    else if (c.kd_pinhole)
+        k_geometry_linear<true, false><<<grid_geo, GEO_THREADS, 0, stream>>>(c, F, W, depth, ctr, geo_list);
+    else if (c.free_space)
+        k_geometry_linear<false, true><<<grid_geo, GEO_THREADS, 0, stream>>>(c, F, W, depth, ctr, geo_list);
+    else
+        k_geometry_linear<false, false><<<grid_geo, GEO_THREADS, 0, stream>>>(c, F, W, depth, ctr, geo_list);
     return cudaGetLastError();
 }
 

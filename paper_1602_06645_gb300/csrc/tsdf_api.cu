@@ -265,6 +265,37 @@ tsdf_status write_volume(tsdf_volume* v, T* brick, const T* src, const int32_t d
 
 }  // namespace
 
+
+namespace tsdf {
+// Frame constants for the allocation-free geometry entry point: a volume
+// description filled into a temporary handle and passed to the same
+// frame_constants() as tsdf_integrate (geometry fields only; the colour
+// fields are unused on that path).
+void geometry_frame_constants(const VolumeDesc& d, const float Kd[9], const float Twd[16], int dw, int dh,
+                              FrameConst& c) {
+    tsdf_volume v;
+    for (int a = 0; a < 3; ++a) {
+        v.ng[a] = d.ng[a];
+        v.nc[a] = d.ng[a];
+        v.nb[a] = (d.ng[a] + BRICK - 1) / BRICK;
+        v.ncb[a] = v.nb[a];
+        v.origin[a] = d.origin[a];
+    }
+    v.s_g = d.s_g;
+    v.s_c = d.s_g;
+    v.mu = d.mu;
+    v.sigma = d.mu;  // the cull margin then reduces to mu, the geometry bound
+    v.band = 0.0f;
+    v.max_weight = d.max_weight;
+    v.colour_mode = 0;
+    v.sample_mode = 0;
+    v.culling = 1;
+    v.free_space = 1;
+    const float I[16] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1};
+    frame_constants(&v, Kd, Kd, Twd, I, dw, dh, dw, dh, c);
+}
+}  // namespace tsdf
+
 // =================================================================== API ==
 extern "C" {
 
