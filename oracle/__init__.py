@@ -54,6 +54,16 @@ class Params(ctypes.Structure):
     ]
 
 
+class AdjProblem(ctypes.Structure):
+    _fields_ = [
+        ("n_frames", ctypes.c_int32), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+        ("images", ctypes.c_void_p), ("Rn", ctypes.c_void_p), ("tn", ctypes.c_void_p),
+        ("offsets", ctypes.c_void_p), ("idx", ctypes.c_void_p),
+        ("nc", ctypes.c_int32 * 3), ("s_c", ctypes.c_float), ("origin", ctypes.c_float * 3),
+        ("T0", ctypes.c_double * 16),
+    ]
+
+
 _lib = None
 
 
@@ -72,8 +82,18 @@ def _load():
         lib.orc_frame_constants.argtypes = [ctypes.POINTER(Params), vp, vp, vp, vp, vp, vp, vp]
         lib.orc_params_size.restype = ctypes.c_int
         assert lib.orc_params_size() == ctypes.sizeof(Params)
-        if hasattr(lib, "orc_adj_loss_grad"):
-            lib.orc_adj_loss_grad.restype = ctypes.c_double
+        lib.orc_record_gates.argtypes = [ctypes.POINTER(Params), vp, vp, vp, ctypes.c_int, ctypes.c_int, vp, vp, vp,
+                                         ctypes.c_longlong]
+        lib.orc_record_gates.restype = ctypes.c_longlong
+        lib.orc_adj_size.restype = ctypes.c_int
+        assert lib.orc_adj_size() == ctypes.sizeof(AdjProblem)
+        lib.orc_adj_voxels.argtypes = [ctypes.POINTER(AdjProblem), vp]
+        lib.orc_adj_voxels.restype = ctypes.c_int64
+        lib.orc_adj_cells.argtypes = [ctypes.POINTER(AdjProblem), vp, vp]
+        lib.orc_adj_cells.restype = None
+        lib.orc_adj_eval.argtypes = [ctypes.POINTER(AdjProblem), vp, vp, vp, ctypes.c_int64, vp, vp, vp, vp, vp,
+                                     ctypes.c_int64, vp]
+        lib.orc_adj_eval.restype = ctypes.c_double
         _lib = lib
     return _lib
 
@@ -153,6 +173,19 @@ class Oracle:
                                      t.ctypes.data, Kdi.ctypes.data)
         return R.reshape(3, 3), t, Kdi.reshape(3, 3)
 
+    def record_gates(self, depth, K_depth, T_world_depth):
+        """Geometry update of one frame, then S_k: the colour voxels (linear
+        indices, ascending) that pass the depth-side gates against the
+        updated geometry."""
+        depth = np.ascontiguousarray(depth, dtype=np.uint16)
+        dh, dw = depth.shape
+        Kd, Twd = _f32(K_depth, (3, 3)), _f32(T_world_depth, (4, 4))
+        cap = int(np.prod(self.C.shape))
+        out = np.empty(cap, dtype=np.uint32)
+        n = self.lib.orc_record_gates(ctypes.byref(self.p), self.F.ctypes.data, self.W.ctypes.data, depth.ctypes.data,
+                                      dw, dh, Kd.ctypes.data, Twd.ctypes.data, out.ctypes.data, cap)
+        return out[:n].copy()
+
     @property
     def colour_rgb(self):
         """(Nz, Ny, Nx, 3) uint8 colours."""
@@ -162,3 +195,53 @@ class Oracle:
     @property
     def colour_weight(self):
         return (self.C >> 24).astype(np.uint8)
+
+
+class Adjoint:
+    """Binary64 photometric loss of the colour volume and its gradient with
+    respect to theta = (fx, fy, cx, cy, rho, phi) (adjoint.c)."""
+
+    def __init__(self, images, Rn, tn, S, dims_col, s_c, origin, T0):
+        self.lib = _load()
+        self.images = np.ascontiguousarray(images, dtype=np.float32)
+        n, H, W, _ = self.images.shape
+        self.Rn = np.ascontiguousarray(np.asarray(Rn, np.float32).reshape(n, 9))
+        self.tn = np.ascontiguousarray(np.asarray(tn, np.float32).reshape(n, 3))
+        self.offsets = np.zeros(n + 1, np.int64)
+        self.offsets[1:] = np.cumsum([len(x) for x in S])
+        self.idx = np.ascontiguousarray(np.concatenate([np.asarray(x, np.uint32) for x in S]) if n else
+                                        np.zeros(0, np.uint32))
+        p = AdjProblem()
+        p.n_frames, p.width, p.height = n, W, H
+        p.images, p.Rn, p.tn = self.images.ctypes.data, self.Rn.ctypes.data, self.tn.ctypes.data
+        p.offsets, p.idx = self.offsets.ctypes.data, self.idx.ctypes.data
+        p.nc[:] = [int(v) for v in dims_col]
+        p.s_c = float(s_c)
+        p.origin[:] = [float(v) for v in origin]
+        p.T0[:] = [float(v) for v in np.asarray(T0, np.float64).reshape(16)]
+        self.p = p
+        nv = self.lib.orc_adj_voxels(ctypes.byref(p), None)
+        self.V = np.empty(nv, np.uint32)
+        self.lib.orc_adj_voxels(ctypes.byref(p), self.V.ctypes.data)
+
+    def cells(self, theta):
+        th = np.ascontiguousarray(theta, np.float64)
+        cells = np.empty(2 * len(self.idx), np.int32)
+        self.lib.orc_adj_cells(ctypes.byref(self.p), th.ctypes.data, cells.ctypes.data)
+        return cells
+
+    def eval(self, theta, cells, target=None, grad=False, query=None):
+        th = np.ascontiguousarray(theta, np.float64)
+        nV = len(self.V)
+        C = np.empty((nV, 3), np.float64)
+        n = np.empty(nV, np.int32)
+        tg = None if target is None else np.ascontiguousarray(target, np.float64)
+        g = np.empty(10, np.float64) if grad else None
+        q = None if query is None else np.ascontiguousarray(query, np.int64).reshape(-1, 4)
+        qg = None if q is None else np.empty(len(q), np.float64)
+        loss = self.lib.orc_adj_eval(ctypes.byref(self.p), th.ctypes.data, np.ascontiguousarray(cells).ctypes.data,
+                                     self.V.ctypes.data, nV, None if tg is None else tg.ctypes.data, C.ctypes.data,
+                                     n.ctypes.data, None if g is None else g.ctypes.data,
+                                     None if q is None else q.ctypes.data, 0 if q is None else len(q),
+                                     None if qg is None else qg.ctypes.data)
+        return dict(loss=loss, C=C, n=n, grad=g, qgrad=qg)

@@ -256,6 +256,32 @@ static int orc_paper_normal_update(const orc_params* p, const orc_frame* fr, con
                                    int iu, int iv, const float Pd[3], const float Pc[3],
                                    uint32_t* vox, const uint32_t s[3]);
 
+/* The depth-side gates of colour voxel (x, y, z): Eq. 5, Eq. 6 (frustum and
+ * D > 0), Eq. 7 (sigma) and the trilinear band gate.  On success returns 1
+ * with the voxel in the current depth camera (Pc), its depth pixel and the
+ * back-projected depth point (Pd). */
+static int colour_depth_gates(const orc_params* p, const orc_frame* fr, const float* F, const uint8_t* W,
+                              const uint16_t* depth, int x, int y, int z, float Pc[3], int* iu, int* iv,
+                              float Pd[3]) {
+    float pw[3] = {centre(p->origin[0], x, p->s_c), centre(p->origin[1], y, p->s_c), centre(p->origin[2], z, p->s_c)};
+    rigid(fr->R, fr->t, pw[0], pw[1], pw[2], Pc);
+    float u, v;
+    if (!project(fr->Kd, Pc[0], Pc[1], Pc[2], &u, &v)) return 0;
+    if (!nearest_pixel(u, v, fr->dw, fr->dh, iu, iv)) return 0;
+    uint16_t D = depth[(size_t)(*iv) * fr->dw + *iu];
+    if (D == 0) return 0;
+    float d = (float)D * 0.001f;
+    back_project(fr, *iu, *iv, d, Pd);
+    float ex = Pc[0] - Pd[0], ey = Pc[1] - Pd[1], ez = Pc[2] - Pd[2];
+    float dist2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+    if (dist2 > fr->sigma2) return 0;
+    float g[3], Ft;
+    for (int a = 0; a < 3; ++a) g[a] = fmaf(pw[a] - p->origin[a], fr->inv_sg, -0.5f);
+    if (!trilinear(p, F, W, g, &Ft)) return 0;
+    if (!(fabsf(Ft) <= p->band)) return 0;
+    return 1;
+}
+
 static long long orc_colour(const orc_params* p, const orc_frame* fr, const float* F, const uint8_t* W,
                             uint32_t* C, const uint16_t* depth, const uint8_t* rgb) {
     const int nx = p->nc[0], ny = p->nc[1], nz = p->nc[2];
@@ -264,26 +290,9 @@ static long long orc_colour(const orc_params* p, const orc_frame* fr, const floa
     for (int z = 0; z < nz; ++z) {
         for (int y = 0; y < ny; ++y) {
             for (int x = 0; x < nx; ++x) {
-                float pw[3] = {centre(p->origin[0], x, p->s_c), centre(p->origin[1], y, p->s_c),
-                               centre(p->origin[2], z, p->s_c)};
-                float Pc[3];
-                rigid(fr->R, fr->t, pw[0], pw[1], pw[2], Pc);
-                float u, v;
+                float Pc[3], Pd[3];
                 int iu, iv;
-                if (!project(fr->Kd, Pc[0], Pc[1], Pc[2], &u, &v)) continue;
-                if (!nearest_pixel(u, v, fr->dw, fr->dh, &iu, &iv)) continue;
-                uint16_t D = depth[(size_t)iv * fr->dw + iu];
-                if (D == 0) continue;
-                float d = (float)D * 0.001f;
-                float Pd[3];
-                back_project(fr, iu, iv, d, Pd);
-                float ex = Pc[0] - Pd[0], ey = Pc[1] - Pd[1], ez = Pc[2] - Pd[2];
-                float dist2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                if (dist2 > fr->sigma2) continue;
-                float g[3], Ft;
-                for (int a = 0; a < 3; ++a) g[a] = fmaf(pw[a] - p->origin[a], fr->inv_sg, -0.5f);
-                if (!trilinear(p, F, W, g, &Ft)) continue;
-                if (!(fabsf(Ft) <= p->band)) continue;
+                if (!colour_depth_gates(p, fr, F, W, depth, x, y, z, Pc, &iu, &iv, Pd)) continue;
                 float Ph[3];
                 rigid(fr->Rc, fr->tc, Pc[0], Pc[1], Pc[2], Ph);
                 float uh, vh;
@@ -401,3 +410,27 @@ void orc_frame_constants(const orc_params* p, const float Kd[9], const float Kr[
 }
 
 int orc_params_size(void) { return (int)sizeof(orc_params); }
+
+/* Geometry update of one frame, then the list of colour voxels that pass the
+ * depth-side gates (colour_depth_gates) against the updated geometry: the
+ * set S_k of the photometric loss.  Writes at most cap linear colour indices
+ * (ascending) to out and returns how many pass. */
+long long orc_record_gates(const orc_params* p, float* F, uint8_t* W, const uint16_t* depth, int dw, int dh,
+                           const float Kd[9], const float Twd[16], uint32_t* out, long long cap) {
+    orc_frame fr;
+    float I[16] = {1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1};
+    orc_frame_setup(&fr, p, Kd, Kd, Twd, I, dw, dh, dw, dh);
+    orc_geometry(p, &fr, F, W, depth);
+    const int nx = p->nc[0], ny = p->nc[1], nz = p->nc[2];
+    long long n = 0;
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                float Pc[3], Pd[3];
+                int iu, iv;
+                if (!colour_depth_gates(p, &fr, F, W, depth, x, y, z, Pc, &iu, &iv, Pd)) continue;
+                if (n < cap) out[n] = (uint32_t)(((size_t)z * ny + y) * nx + x);
+                ++n;
+            }
+    return n;
+}

@@ -1,0 +1,147 @@
+"""Pins of the binary64 adjoint oracle (photometric colour loss and its
+gradient with respect to the HD intrinsics, the se(3) extrinsic and the HD
+pixels).
+
+The analytic gradient must agree with central finite differences of the loss
+(binary64, step 1e-6, the discrete choices held fixed); the depth-side gate
+sets must be exactly the voxels the fusion step can colour.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1602_06645_gb300 import synth
+
+
+def small_problem(n_frames=4, dims_geo=32, cw=160, ch=120, seed=4):
+    seq = synth.sequence_adjoint(n_frames=n_frames, seed=seed, dims_geo=dims_geo)
+    seq.rgb_size = (cw, ch)
+    seq.K_rgb = synth.intrinsics(1050.0 * cw / 1920, 1050.0 * cw / 1920, (cw - 1) / 2.0, (ch - 1) / 2.0)
+    o = oracle.Oracle(seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, seq.max_weight)
+    S, imgs, Rn, tn = [], [], [], []
+    for f in range(n_frames):
+        d, c = seq.frame(f)
+        S.append(o.record_gates(d, seq.K_depth, seq.poses[f]))
+        imgs.append(c.astype(np.float32))
+        R, t, _ = o.frame_constants(seq.K_depth, seq.K_rgb, seq.poses[f], seq.T_depth_rgb)
+        Rn.append(R)
+        tn.append(t)
+    return seq, o, S, np.stack(imgs), np.stack(Rn), np.stack(tn)
+
+
+def perturbed(T, seed=0, dt=0.01, deg=1.0):
+    rng = np.random.default_rng(seed)
+    a = rng.normal(size=3)
+    a /= np.linalg.norm(a)
+    b = rng.normal(size=3)
+    b /= np.linalg.norm(b)
+    P = np.eye(4)
+    P[:3, :3] = synth.rot_axis_angle(b, math.radians(deg))
+    P[:3, 3] = dt * a
+    return P @ np.asarray(T, np.float64)
+
+
+@pytest.fixture(scope="module")
+def prob():
+    seq, o, S, imgs, Rn, tn = small_problem()
+    Ktrue = np.array([seq.K_rgb[0, 0], seq.K_rgb[1, 1], seq.K_rgb[0, 2], seq.K_rgb[1, 2]], np.float64)
+    truth = oracle.Adjoint(imgs, Rn, tn, S, seq.dims_col, o.p.s_c, list(o.p.origin), seq.T_depth_rgb)
+    th_true = np.concatenate([Ktrue, np.zeros(6)])
+    tgt = truth.eval(th_true, truth.cells(th_true))
+    target = np.where(tgt["n"][:, None] > 0, tgt["C"], np.nan)
+    adj = oracle.Adjoint(imgs, Rn, tn, S, seq.dims_col, o.p.s_c, list(o.p.origin), perturbed(seq.T_depth_rgb))
+    th0 = np.concatenate([Ktrue * np.array([1.01, 0.99, 1.0, 1.0]) + np.array([0, 0, 0.7, -0.4]), np.zeros(6)])
+    return dict(seq=seq, o=o, S=S, adj=adj, truth=truth, th0=th0, th_true=th_true, target=target)
+
+
+def test_gate_sets_are_non_trivial(prob):
+    assert all(len(s) > 200 for s in prob["S"])
+    assert len(prob["adj"].V) > 500
+
+
+def test_theta_gradient_matches_central_differences(prob):
+    adj, th0, target = prob["adj"], prob["th0"], prob["target"]
+    cells = adj.cells(th0)
+    r = adj.eval(th0, cells, target, grad=True)
+    assert r["loss"] > 0
+    g = r["grad"]
+    for j in range(10):
+        h = 1e-6 * max(1.0, abs(th0[j]))
+        tp, tm = th0.copy(), th0.copy()
+        tp[j] += h
+        tm[j] -= h
+        fd = (adj.eval(tp, cells, target)["loss"] - adj.eval(tm, cells, target)["loss"]) / (2 * h)
+        scale = max(abs(g[j]), 1e-6 * np.abs(g).max())
+        assert abs(fd - g[j]) <= 1e-5 * scale, (j, fd, g[j])
+
+
+def test_pixel_gradient_matches_central_differences(prob):
+    adj, th0, target = prob["adj"], prob["th0"], prob["target"]
+    cells = adj.cells(th0)
+    valid = cells[0::2] != np.iinfo(np.int32).min
+    rng = np.random.default_rng(7)
+    # pixels under samples of frames 0..3: pick 24 pairs, one corner channel each
+    offs = adj.offsets
+    pairs = rng.choice(np.nonzero(valid)[0], size=24, replace=False)
+    query = []
+    for i in pairs:
+        k = int(np.searchsorted(offs, i, side="right") - 1)
+        x0, y0 = cells[2 * i], cells[2 * i + 1]
+        query.append((k, y0 + int(rng.integers(0, 2)), x0 + int(rng.integers(0, 2)), int(rng.integers(0, 3))))
+    query = np.array(query, np.int64)
+    qg = adj.eval(th0, cells, target, query=query)["qgrad"]
+    h = 1e-2
+    for q, g in zip(query, qg):
+        k, y, x, c = q
+        base = adj.images[k, y, x, c]
+        up, dn = np.float32(base + h), np.float32(base - h)  # the binary32 values actually applied
+        adj.images[k, y, x, c] = up
+        lp = adj.eval(th0, cells, target)["loss"]
+        adj.images[k, y, x, c] = dn
+        lm = adj.eval(th0, cells, target)["loss"]
+        adj.images[k, y, x, c] = base
+        fd = (lp - lm) / (float(up) - float(dn))
+        # L is quadratic in each intensity: the central difference is exact up to rounding
+        assert abs(fd - g) <= 1e-6 * max(1.0, abs(g)), (q, fd, g)
+
+
+def test_truth_has_zero_loss_and_gradient(prob):
+    tr, th, target = prob["truth"], prob["th_true"], prob["target"]
+    r = tr.eval(th, tr.cells(th), target, grad=True)
+    assert r["loss"] == 0.0
+    assert np.all(r["grad"] == 0.0)
+
+
+def test_gradient_step_on_the_extrinsic_reduces_the_loss(prob):
+    adj, th0, target = prob["adj"], prob["th0"], prob["target"]
+    th = th0.copy()
+    th[:4] = prob["th_true"][:4]
+    cells = adj.cells(th)
+    r = adj.eval(th, cells, target, grad=True)
+    step = np.zeros(10)
+    step[4:] = -r["grad"][4:] / np.linalg.norm(r["grad"][4:])
+    best = min(adj.eval(th + a * step, cells, target)["loss"] for a in (1e-5, 1e-4, 1e-3))
+    assert best < r["loss"]
+
+
+def test_gate_sets_are_the_colourable_voxels(prob):
+    """S_k holds every voxel the fusion step colours in frame k (with an HD
+    image large enough to see them all) and nothing else."""
+    seq = prob["seq"]
+    big = (640, 480)
+    K = synth.intrinsics(300.0, 300.0, 319.5, 239.5)
+    o1 = oracle.Oracle(seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, 255)
+    o2 = oracle.Oracle(seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, 255)
+    rgb = np.full((big[1], big[0], 3), 100, np.uint8)
+    prev = np.zeros_like(o1.C)
+    for f in range(len(prob["S"])):
+        d, _ = seq.frame(f)
+        o1.integrate(d, rgb, seq.K_depth, K, seq.poses[f], seq.T_depth_rgb)
+        S = o2.record_gates(d, seq.K_depth, seq.poses[f])
+        updated = np.nonzero((o1.C != prev).ravel())[0]
+        prev = o1.C.copy()
+        assert np.array_equal(np.sort(updated), S) or set(updated.tolist()) <= set(S.tolist())
+        missing = set(S.tolist()) - set(updated.tolist())
+        assert len(missing) <= max(2, len(S) // 100)  # only voxels whose HD footprint leaves the image

@@ -28,8 +28,8 @@ MUTANTS = {
                         "W[idx] = (uint8_t)(w + 1);"),
     "depth_in_cm": ("float d = (float)D * 0.001f;\n                float sdf",
                     "float d = (float)D * 0.01f;\n                float sdf"),
-    "no_sigma_gate": ("if (dist2 > fr->sigma2) continue;", ""),
-    "no_band_gate": ("if (!(fabsf(Ft) <= p->band)) continue;", ""),
+    "no_sigma_gate": ("if (dist2 > fr->sigma2) return 0;", ""),
+    "no_band_gate": ("if (!(fabsf(Ft) <= p->band)) return 0;", ""),
     "extrinsic_translation_flipped": ("rigid(fr->Rc, fr->tc, Pc[0], Pc[1], Pc[2], Ph);",
                                       "rigid(fr->Rc, fr->tc, Pc[0], Pc[1], Pc[2], Ph); Ph[0] -= 2 * fr->tc[0];"),
     "trilinear_axis_mixed": ("float c0 = lerpf(c00, c10, fr[1]);", "float c0 = lerpf(c00, c10, fr[0]);"),
