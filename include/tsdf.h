@@ -218,6 +218,57 @@ typedef struct {
 tsdf_status tsdf_profile_enable(tsdf_volume* vol, int32_t enable);
 tsdf_status tsdf_profile_read(tsdf_volume* vol, tsdf_profile_report* out);
 
+/* ------------------------------------------------------------------------
+ * Photometric colour loss and its adjoint (calibration refinement of the HD
+ * camera).  Not in the paper, which takes the calibration of Section IV.A as
+ * given: this differentiates the fused colour volume with respect to the HD
+ * images, the HD intrinsics (Eq. 4) and the depth-to-HD extrinsic (Eq. 3).
+ *
+ * Over a recorded frame sequence, S_k is the set of colour voxels that pass
+ * the depth-side gates of frame k (Eq. 5, Eq. 6 frustum and D > 0, Eq. 7 and
+ * the trilinear band gate, against the geometry after frame k's update); it
+ * does not depend on the HD camera.  For each voxel v in the union of the S_k
+ * the forward pass gives the unrounded mean of its bilinear HD samples over
+ * the frames whose 2x2 sample footprint lies inside the image,
+ *   C_v = (1/n_v) sum_k bilinear(I_k, K_hd T P_vc)   (Eq. 9 with W = 1),
+ * and the backward pass maps dL/dC to dL/dI_k, dL/dK_hd = (fx, fy, cx, cy)
+ * and dL/dxi for a left perturbation T(xi) = exp(xi^) T of the extrinsic at
+ * the given T, xi = (rho, phi), translation first.
+ * ---------------------------------------------------------------------- */
+typedef struct tsdf_adjoint tsdf_adjoint;
+
+/* Buffers for up to max_frames (1..64) recorded frames and max_pairs
+ * (frame, voxel) pairs, drawn from vol's allocator; vol provides the geometry
+ * volume, its stream and scratch.  Errors: INVALID_ARG, OOM. */
+tsdf_status tsdf_adjoint_create(tsdf_volume* vol, int32_t max_frames, int64_t max_pairs, tsdf_adjoint** out);
+/* Fuse the geometry of one frame into vol (as tsdf_integrate does) and record
+ * S_k; arguments as in tsdf_integrate.  Frames are numbered 0.. in order. */
+tsdf_status tsdf_adjoint_record(tsdf_adjoint* adj, const uint16_t* depth_mm, tsdf_image_size dsz,
+                                const float K_depth[9], const float T_world_depth[16]);
+/* Close the recording: builds the voxel union (n_voxels slots).  Errors: OOM
+ * when a buffer overflowed during recording. */
+tsdf_status tsdf_adjoint_finalize(tsdf_adjoint* adj, int64_t* n_voxels);
+/* Linear colour index of each slot (n_voxels uint32, host or device). */
+tsdf_status tsdf_adjoint_voxels(tsdf_adjoint* adj, uint32_t* voxels);
+/* The recorded (voxel, frame) pairs in recording order within no fixed order
+ * per frame (uint32 linear colour index, uint8 frame; host or device; either
+ * may be NULL) and their count. */
+tsdf_status tsdf_adjoint_pairs(tsdf_adjoint* adj, uint32_t* voxels, uint8_t* frames, int64_t* n_pairs);
+/* Forward pass.  images: device float32 n_frames x csz.height x csz.width x 3
+ * HD intensities; K_rgb4 = (fx, fy, cx, cy); T_depth_rgb row-major 4x4 (host).
+ * colours: device float32 n_voxels x 3; counts: device int32 n_voxels (n_v).
+ * Asynchronous on vol's stream. */
+tsdf_status tsdf_adjoint_forward(tsdf_adjoint* adj, const float* images, tsdf_image_size csz, const float K_rgb4[4],
+                                 const float T_depth_rgb[16], float* colours, int32_t* counts);
+/* Backward pass at the camera of the preceding forward pass.  grad_colours:
+ * device float32 n_voxels x 3 (dL/dC); grad_images: device float32 like
+ * images, ACCUMULATED into; grad_theta: host double[10] = dL/d(fx, fy, cx, cy,
+ * rho, phi).  Synchronous (returns after grad_theta is written). */
+tsdf_status tsdf_adjoint_backward(tsdf_adjoint* adj, const float* images, tsdf_image_size csz, const float K_rgb4[4],
+                                  const float T_depth_rgb[16], const float* grad_colours, float* grad_images,
+                                  double grad_theta[10]);
+void tsdf_adjoint_destroy(tsdf_adjoint* adj);
+
 /* Allocation-free geometry fusion.  (The paper has no counterpart: this is an
  * interface for callers that cannot allocate device memory, for example code
  * running while another framework owns the device allocator, or a host with a

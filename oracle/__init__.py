@@ -93,6 +93,8 @@ def _load():
         lib.orc_adj_cells.restype = None
         lib.orc_adj_eval.argtypes = [ctypes.POINTER(AdjProblem), vp, vp, vp, ctypes.c_int64, vp, vp, vp, vp, vp,
                                      ctypes.c_int64, vp]
+        lib.orc_adj_cells32.argtypes = [ctypes.POINTER(AdjProblem), vp, vp, vp]
+        lib.orc_adj_cells32.restype = None
         lib.orc_adj_eval.restype = ctypes.c_double
         _lib = lib
     return _lib
@@ -228,6 +230,15 @@ class Adjoint:
         th = np.ascontiguousarray(theta, np.float64)
         cells = np.empty(2 * len(self.idx), np.int32)
         self.lib.orc_adj_cells(ctypes.byref(self.p), th.ctypes.data, cells.ctypes.data)
+        return cells
+
+    def cells32(self, K4, T):
+        """Cells chosen in binary32 with the kernels' operation order, for
+        the binary32 camera K4 = (fx, fy, cx, cy) and 4x4 T."""
+        k4 = np.ascontiguousarray(K4, np.float32)
+        t = np.ascontiguousarray(np.asarray(T, np.float32).reshape(16))
+        cells = np.empty(2 * len(self.idx), np.int32)
+        self.lib.orc_adj_cells32(ctypes.byref(self.p), k4.ctypes.data, t.ctypes.data, cells.ctypes.data)
         return cells
 
     def eval(self, theta, cells, target=None, grad=False, query=None):

@@ -33,7 +33,9 @@ EXPORTS = [
     "tsdf_params_default", "tsdf_create", "tsdf_create_ex", "tsdf_integrate", "tsdf_read", "tsdf_write",
     "tsdf_synchronize", "tsdf_save", "tsdf_load", "tsdf_destroy", "tsdf_set_stream", "tsdf_get_info",
     "tsdf_get_stats", "tsdf_status_string", "tsdf_last_error", "tsdf_profile_enable", "tsdf_profile_read",
-    "tsdf_integrate_geometry_static",
+    "tsdf_integrate_geometry_static", "tsdf_adjoint_create", "tsdf_adjoint_record", "tsdf_adjoint_finalize",
+    "tsdf_adjoint_voxels", "tsdf_adjoint_pairs", "tsdf_adjoint_forward", "tsdf_adjoint_backward",
+    "tsdf_adjoint_destroy",
 ]
 PHASES = ["upload", "depth_tiles", "bricks", "geometry", "colour_list", "colour_cells", "colour"]
 
@@ -139,6 +141,18 @@ def load():
     lib.tsdf_integrate_geometry_static.argtypes = [i32p, ctypes.c_float, ctypes.c_float, ctypes.c_int32, fp, vp, vp,
                                                    vp, tsdf_image_size, fp, fp, vp]
     lib.tsdf_integrate_geometry_static.restype = ctypes.c_int
+    lib.tsdf_adjoint_create.argtypes = [vp, ctypes.c_int32, ctypes.c_int64, H]
+    lib.tsdf_adjoint_record.argtypes = [vp, vp, tsdf_image_size, fp, fp]
+    lib.tsdf_adjoint_finalize.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    lib.tsdf_adjoint_voxels.argtypes = [vp, vp]
+    lib.tsdf_adjoint_pairs.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_int64)]
+    lib.tsdf_adjoint_forward.argtypes = [vp, vp, tsdf_image_size, fp, fp, vp, vp]
+    lib.tsdf_adjoint_backward.argtypes = [vp, vp, tsdf_image_size, fp, fp, vp, vp, ctypes.POINTER(ctypes.c_double)]
+    lib.tsdf_adjoint_destroy.argtypes = [vp]
+    lib.tsdf_adjoint_destroy.restype = None
+    for name in ("tsdf_adjoint_create", "tsdf_adjoint_record", "tsdf_adjoint_finalize", "tsdf_adjoint_voxels",
+                 "tsdf_adjoint_pairs", "tsdf_adjoint_forward", "tsdf_adjoint_backward"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.tsdf_profile_enable.argtypes = [vp, ctypes.c_int32]
     lib.tsdf_profile_read.argtypes = [vp, ctypes.POINTER(tsdf_profile_report)]
     for name in ("tsdf_create", "tsdf_create_ex", "tsdf_integrate", "tsdf_read", "tsdf_write", "tsdf_synchronize",
@@ -298,6 +312,60 @@ def tsdf_integrate_geometry_static(dims, voxel_size, mu, max_weight, origin, tsd
                                                  _ptr(tsdf, np.float32, keep), _ptr(w, np.uint8, keep),
                                                  _ptr(depth_mm, np.uint16, keep), tsdf_image_size(dw, dh), Kd[1],
                                                  Twd[1], ctypes.c_void_p(int(stream or 0))))
+
+
+def tsdf_adjoint_create(h, max_frames, max_pairs):
+    a = ctypes.c_void_p()
+    _check(load().tsdf_adjoint_create(h, int(max_frames), int(max_pairs), ctypes.byref(a)), h)
+    return a
+
+
+def tsdf_adjoint_record(a, h, depth_mm, K_depth, T_world_depth):
+    keep = []
+    dh, dw = _hw(depth_mm)
+    Kd, Twd = _mat(K_depth, 9), _mat(T_world_depth, 16)
+    _check(load().tsdf_adjoint_record(a, _ptr(depth_mm, np.uint16, keep), tsdf_image_size(dw, dh), Kd[1], Twd[1]), h)
+
+
+def tsdf_adjoint_finalize(a, h):
+    n = ctypes.c_int64()
+    _check(load().tsdf_adjoint_finalize(a, ctypes.byref(n)), h)
+    return int(n.value)
+
+
+def tsdf_adjoint_voxels(a, h, out):
+    keep = []
+    _check(load().tsdf_adjoint_voxels(a, _ptr(out, np.uint32, keep)), h)
+
+
+def tsdf_adjoint_pairs(a, h, voxels=None, frames=None):
+    keep = []
+    n = ctypes.c_int64()
+    _check(load().tsdf_adjoint_pairs(a, _ptr(voxels, np.uint32, keep), _ptr(frames, np.uint8, keep), ctypes.byref(n)), h)
+    return int(n.value)
+
+
+def tsdf_adjoint_forward(a, h, images, K4, T_depth_rgb, colours, counts):
+    keep = []
+    _, H, W, _ = tuple(images.shape)
+    k4, T = _mat(K4, 4), _mat(T_depth_rgb, 16)
+    _check(load().tsdf_adjoint_forward(a, _ptr(images, np.float32, keep), tsdf_image_size(W, H), k4[1], T[1],
+                                       _ptr(colours, np.float32, keep), _ptr(counts, np.int32, keep)), h)
+
+
+def tsdf_adjoint_backward(a, h, images, K4, T_depth_rgb, grad_colours, grad_images):
+    keep = []
+    _, H, W, _ = tuple(images.shape)
+    k4, T = _mat(K4, 4), _mat(T_depth_rgb, 16)
+    g = (ctypes.c_double * 10)()
+    _check(load().tsdf_adjoint_backward(a, _ptr(images, np.float32, keep), tsdf_image_size(W, H), k4[1], T[1],
+                                        _ptr(grad_colours, np.float32, keep), _ptr(grad_images, np.float32, keep), g), h)
+    return np.array(list(g), dtype=np.float64)
+
+
+def tsdf_adjoint_destroy(a):
+    if a:
+        load().tsdf_adjoint_destroy(a)
 
 
 def tsdf_profile_enable(h, enable=True):

@@ -1,0 +1,68 @@
+// Host-side internals shared by the C-ABI translation units: the handle
+// structure and the validation / allocation helpers of tsdf_api.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tsdf.h"
+#include "common.cuh"
+
+using tsdf::LaunchGrids;
+using tsdf::Scratch;
+using tsdf::Volumes;
+
+struct tsdf_volume {
+    int32_t ng[3], nc[3], nb[3], ncb[3];
+    float s_g, s_c, origin[3], mu, sigma, band;
+    int32_t max_weight, colour_mode, sample_mode, culling, free_space;
+    cudaStream_t stream;
+    tsdf_allocator alloc;
+    int device;
+    LaunchGrids grids;
+    Volumes vol;
+    Scratch scr;
+    uint32_t* depth_tiles;
+    size_t depth_tiles_cap;
+    uint16_t* d_depth;
+    size_t d_depth_cap;
+    uint8_t* d_rgb;
+    size_t d_rgb_cap;
+    int64_t frames;
+    int64_t device_bytes;
+    std::string last_error;
+    // phase timing (tsdf_profile_enable)
+    struct EventSet {
+        cudaEvent_t e[TSDF_PHASE_COUNT + 1];
+    };
+    bool profiling;
+    std::vector<EventSet> ev_pending, ev_pool;
+    double prof_ms[TSDF_PHASE_COUNT];
+    int64_t prof_frames;
+    struct Block {
+        void* p;
+        size_t bytes;
+    };
+    std::vector<Block> blocks;
+};
+
+
+namespace tsdf_host {
+tsdf_status fail(tsdf_volume* v, tsdf_status s, const std::string& msg);
+tsdf_status cuda_fail(tsdf_volume* v, cudaError_t e, const char* where);
+void* dev_alloc(tsdf_volume* v, size_t bytes);
+void dev_free(tsdf_volume* v, void* p);
+bool finite_all(const float* a, int n);
+bool is_device_ptr(const void* p);
+bool rigid_ok(const float T[16]);
+bool invert3(const float K[9], float out[9]);
+void frame_constants(const tsdf_volume* v, const float Kd[9], const float Kr[9], const float Twd[16],
+                     const float Tdr[16], int dw, int dh, int cw, int ch, tsdf::FrameConst& c);
+tsdf_status check_device_error(tsdf_volume* v);
+// Upload a frame's depth image (host or device) and size the depth-tile
+// buffer; sets *d_depth to the device copy.
+tsdf_status stage_depth(tsdf_volume* v, const uint16_t* depth_mm, tsdf_image_size dsz, int tiles,
+                        const uint16_t** d_depth);
+}  // namespace tsdf_host

@@ -39,6 +39,7 @@ struct FrameConst {
     int32_t tiles_x, tiles_y;
     int32_t kd_pinhole, kr_pinhole, kdi_pinhole;
     int32_t max_weight, free_space, sample_mode, colour_mode, culling;
+    int32_t record_mode;   // 1: the band kernel only records (adjoint gate recording); no colour update
 };
 
 // Min/max of F over observed voxels (w > 0) and min of w over the in-volume
@@ -88,7 +89,40 @@ struct Counters {
 
 // Device error word bits.
 enum : uint32_t {
-    ERR_TILE_RANGE = 1u,   // a colour voxel fell outside its brick's geometry tile
+    ERR_TILE_RANGE = 1u,       // a colour voxel fell outside its brick's geometry tile
+    ERR_RECORD_OVERFLOW = 2u,  // gate recording: band records exceeded their buffer
+    ERR_PAIR_OVERFLOW = 4u,    // gate recording: (frame, voxel) pairs exceeded their buffer
+    ERR_SLOT_OVERFLOW = 8u,    // adjoint: more distinct voxels or frames per voxel than reserved
+};
+
+// Adjoint (photometric loss) buffers.
+struct AdjFrame {  // world -> depth camera of one recorded frame (binary32 frame constants)
+    float R[9], t[3];
+};
+struct AdjBuffers {
+    uint32_t* pair_vox;     // linear colour index of each (frame, voxel) pair
+    uint8_t* pair_frame;    // its frame
+    uint32_t pair_cap;
+    int32_t* slot_of;       // dense colour-volume map: slot of a voxel, -1 none
+    uint32_t* V;            // voxel of each slot
+    uint32_t* slot_count;   // frames per slot
+    uint8_t* slot_frames;   // slot_cap x max_frames frame ids, ascending after finalize
+    int32_t* n_valid;       // samples inside the HD image per slot (forward)
+    uint32_t slot_cap;
+    int32_t max_frames;
+    AdjFrame* frames;
+    uint32_t* counters;     // [0] pairs, [1] slots
+    double* partials;       // per-block gradient partials (10 each)
+    double* grad;           // 10 reduced gradient entries
+};
+// Camera of the HD image for the adjoint: K (fx, fy, cx, cy) and the
+// depth-to-HD transform at the linearisation point.
+struct AdjCamera {
+    float fx, fy, cx, cy;
+    float R[9], t[3];
+    int32_t width, height, n_frames;
+    int32_t nc[3];
+    float s_c, origin[3];
 };
 
 // Device scratch for one frame.
@@ -155,6 +189,14 @@ struct VolumeDesc {
 };
 void geometry_frame_constants(const VolumeDesc& d, const float Kd[9], const float Twd[16], int dw, int dh,
                               FrameConst& c);
+
+cudaError_t launch_frame_record(const FrameConst& c, const Volumes& v, const Scratch& s, const uint16_t* depth,
+                                const LaunchGrids& g, const AdjBuffers& a, int frame, cudaStream_t stream);
+cudaError_t launch_adjoint_finalize(const AdjBuffers& a, uint32_t n_pairs_max, cudaStream_t stream);
+cudaError_t launch_adjoint_forward(const AdjCamera& cam, const AdjBuffers& a, uint32_t n_slots, const float* images,
+                                   float* C, int32_t* n_out, cudaStream_t stream);
+cudaError_t launch_adjoint_backward(const AdjCamera& cam, const AdjBuffers& a, uint32_t n_slots, const float* images,
+                                    const float* grad_C, float* grad_images, int blocks, cudaStream_t stream);
 
 // ------------------------------------------------------------ addressing --
 __host__ __device__ __forceinline__ int64_t brick_offset(int x, int y, int z, const int32_t nb[3]) {

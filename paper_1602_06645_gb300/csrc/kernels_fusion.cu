@@ -16,6 +16,7 @@
 #include <cstdint>
 
 #include "common.cuh"
+#include "device_math.cuh"
 
 namespace tsdf {
 namespace {
@@ -26,77 +27,6 @@ constexpr int TILE_G = BRICK + 2;          // geometry tile edge: brick + 1-voxe
 constexpr int TILE_G3 = TILE_G * TILE_G * TILE_G;
 constexpr int CELLS = BRICK + 1;           // trilinear cells whose corners lie in the tile
 constexpr int CELLS3 = CELLS * CELLS * CELLS;
-
-// ------------------------------------------------------------- helpers ---
-// Eq. 1 / 4 / 6: (xh, yh, zh) = K (X, Y, Z), u = xh * (1/zh), v = yh * (1/zh).
-// With a pinhole K (zero skew and bottom row (0, 0, 1)) the zero terms are
-// dropped; that changes at most the sign of a zero xh or yh, which rounds to
-// the same pixel.
-__device__ __forceinline__ bool project(const float* K, int pinhole, float X, float Y, float Z, float& u, float& v) {
-    float xh, yh, zh;
-    if (pinhole) {
-        xh = fmaf(K[0], X, K[2] * Z);
-        yh = fmaf(K[4], Y, K[5] * Z);
-        zh = Z;
-    } else {
-        xh = fmaf(K[0], X, fmaf(K[1], Y, K[2] * Z));
-        yh = fmaf(K[3], X, fmaf(K[4], Y, K[5] * Z));
-        zh = fmaf(K[6], X, fmaf(K[7], Y, K[8] * Z));
-    }
-    if (!(zh > 0.0f)) return false;
-    float rz = __frcp_rn(zh);
-    u = xh * rz;
-    v = yh * rz;
-    return true;
-}
-
-// Nearest pixel, half-up: floor(u + 1/2).  With t = u + 1/2, the bounds
-// 0 <= floor(t) <= W - 1 are tested in float as 0 <= t < W (NaN fails), and
-// only then is t converted with rounding toward minus infinity.
-__device__ __forceinline__ bool nearest_pixel(float u, float v, int W, int H, int& iu, int& iv) {
-    const float tu = u + 0.5f, tv = v + 0.5f;
-    if (!(tu >= 0.0f && tu < (float)W && tv >= 0.0f && tv < (float)H)) return false;
-    iu = __float2int_rd(tu);
-    iv = __float2int_rd(tv);
-    return true;
-}
-
-// y = R x + t, row by row as fmaf(R0, x, fmaf(R1, y, fmaf(R2, z, t))).
-__device__ __forceinline__ void rigid(const float* R, const float* t, float x, float y, float z, float& X,
-                                      float& Y, float& Z) {
-    X = fmaf(R[0], x, fmaf(R[1], y, fmaf(R[2], z, t[0])));
-    Y = fmaf(R[3], x, fmaf(R[4], y, fmaf(R[5], z, t[1])));
-    Z = fmaf(R[6], x, fmaf(R[7], y, fmaf(R[8], z, t[2])));
-}
-
-// Back-projection d * K_c^-1 (iu, iv, 1) of a depth pixel (Eq. 7).
-__device__ __forceinline__ void back_project(const FrameConst& c, int iu, int iv, float d, float& X, float& Y,
-                                             float& Z) {
-    float fu = (float)iu, fv = (float)iv;
-    if (c.kdi_pinhole) {
-        X = d * fmaf(c.Kdi[0], fu, c.Kdi[2]);
-        Y = d * fmaf(c.Kdi[4], fv, c.Kdi[5]);
-        Z = d;
-    } else {
-        X = d * fmaf(c.Kdi[0], fu, fmaf(c.Kdi[1], fv, c.Kdi[2]));
-        Y = d * fmaf(c.Kdi[3], fu, fmaf(c.Kdi[4], fv, c.Kdi[5]));
-        Z = d * fmaf(c.Kdi[6], fu, fmaf(c.Kdi[7], fv, c.Kdi[8]));
-    }
-}
-
-__device__ __forceinline__ float lerp(float a, float b, float t) { return fmaf(t, b - a, a); }
-
-// Warp-aggregated append of `pred` items to list[ctr++].
-__device__ __forceinline__ void append(bool pred, uint32_t value, uint32_t* ctr, uint32_t* list) {
-    unsigned mask = __ballot_sync(0xffffffffu, pred);
-    if (!mask) return;
-    int lane = threadIdx.x & 31;
-    int leader = __ffs(mask) - 1;
-    uint32_t base = 0;
-    if (lane == leader) base = atomicAdd(ctr, (uint32_t)__popc(mask));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (pred) list[base + __popc(mask & ((1u << lane) - 1u))] = value;
-}
 
 // ------------------------------------------------------- depth tiles ----
 __global__ void __launch_bounds__(256) k_depth_tiles(FrameConst c, const uint16_t* __restrict__ depth,
@@ -637,6 +567,8 @@ __device__ uint32_t flush_records(const FrameConst& c, Volumes& vol, const uint1
         const uint2 r = S.out[i];
         if ((uint64_t)base + i < scr.vox_cap)
             scr.vox[base + i] = r;
+        else if (c.record_mode)
+            atomicOr(scr.err, ERR_RECORD_OVERFLOW);  // recording has no fallback; the host reports it
         else if (colour_after_band(c, vol.C, depth, rgb, (int)(r.x & 0xFFFFu), (int)(r.x >> 16), (int)r.y))
             ++done;
     }
@@ -1034,6 +966,54 @@ __global__ void __launch_bounds__(GEO_THREADS, 7) k_geometry_linear(FrameConst c
     if (lane == 0 && count) atomicAdd(&ctr->geo_updated, (unsigned long long)count);
 }
 
+// ----------------------------------------------------- gate recording ----
+// Adjoint gate recording: the colour voxels recorded by the band kernel that
+// also pass Eq. 5, Eq. 6 (frustum, D > 0) and Eq. 7 in this frame are
+// appended to the (frame, voxel) pair list: the set S_k of the photometric
+// loss, which does not depend on the HD camera.
+__global__ void __launch_bounds__(256) k_colour_gates(FrameConst c, const uint16_t* __restrict__ depth, Scratch scr,
+                                                      AdjBuffers a, int frame) {
+    const uint32_t nv = min(scr.ctr->n_vox, scr.vox_cap);
+    for (uint32_t base = blockIdx.x * blockDim.x; base < nv; base += gridDim.x * blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        bool pass = false;
+        uint32_t lin = 0;
+        if (i < nv) {
+            const uint2 r = scr.vox[i];
+            const int kx = (int)(r.x & 0xFFFFu), ky = (int)(r.x >> 16), kz = (int)r.y;
+            const float pwx = fmaf((float)kx + 0.5f, c.s_c, c.origin[0]);
+            const float pwy = fmaf((float)ky + 0.5f, c.s_c, c.origin[1]);
+            const float pwz = fmaf((float)kz + 0.5f, c.s_c, c.origin[2]);
+            float X, Y, Z, u, v;
+            int iu, iv;
+            rigid(c.R, c.t, pwx, pwy, pwz, X, Y, Z);
+            if (project(c.Kd, c.kd_pinhole, X, Y, Z, u, v) && nearest_pixel(u, v, c.dw, c.dh, iu, iv)) {
+                const uint32_t D = __ldg(depth + (size_t)iv * c.dw + iu);
+                if (D != 0u) {
+                    float PdX, PdY, PdZ;
+                    back_project(c, iu, iv, (float)D * 0.001f, PdX, PdY, PdZ);
+                    const float ex = X - PdX, ey = Y - PdY, ez = Z - PdZ;
+                    pass = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) <= c.sigma2;
+                    lin = ((uint32_t)kz * (uint32_t)c.nc[1] + (uint32_t)ky) * (uint32_t)c.nc[0] + (uint32_t)kx;
+                }
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, pass);
+        uint32_t pos = 0;
+        const int lane = threadIdx.x & 31;
+        if (lane == 0 && m) pos = atomicAdd(&a.counters[0], (uint32_t)__popc(m));
+        pos = __shfl_sync(0xffffffffu, pos, 0) + __popc(m & ((1u << lane) - 1u));
+        if (pass) {
+            if (pos < a.pair_cap) {
+                a.pair_vox[pos] = lin;
+                a.pair_frame[pos] = (uint8_t)frame;
+            } else {
+                atomicOr(scr.err, ERR_PAIR_OVERFLOW);
+            }
+        }
+    }
+}
+
 __global__ void k_init_summaries(BrickSummary* summ, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
@@ -1121,6 +1101,28 @@ cudaError_t launch_geometry_static(const FrameConst& c, float* F, uint8_t* W, co
         k_geometry_linear<false, true><<<grid_geo, GEO_THREADS, 0, stream>>>(c, F, W, depth, ctr, geo_list);
     else
         k_geometry_linear<false, false><<<grid_geo, GEO_THREADS, 0, stream>>>(c, F, W, depth, ctr, geo_list);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_frame_record(const FrameConst& c, const Volumes& v, const Scratch& s, const uint16_t* depth,
+                                const LaunchGrids& g, const AdjBuffers& a, int frame, cudaStream_t stream) {
+    dim3 tg(c.tiles_x, c.tiles_y);
+    k_depth_tiles<<<tg, dim3(TILE_PX, TILE_PX), 0, stream>>>(c, depth, s.depth_tiles, s.ctr);
+    const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
+    k_bricks<<<(nbt + 255) / 256, 256, 0, stream>>>(c, v.summ, s.depth_tiles, s.ctr, s.geo_list, s.vis_list);
+    if (c.kd_pinhole && c.free_space)
+        k_geometry<true, true><<<g.geo, GEO_THREADS, 0, stream>>>(c, v, depth, s.ctr, s.geo_list);
+    else if (c.kd_pinhole)
+        k_geometry<true, false><<<g.geo, GEO_THREADS, 0, stream>>>(c, v, depth, s.ctr, s.geo_list);
+    else if (c.free_space)
+        k_geometry<false, true><<<g.geo, GEO_THREADS, 0, stream>>>(c, v, depth, s.ctr, s.geo_list);
+    else
+        k_geometry<false, false><<<g.geo, GEO_THREADS, 0, stream>>>(c, v, depth, s.ctr, s.geo_list);
+    unsigned gl = (nbt + 255) / 256;
+    if (gl > 1024u) gl = 1024u;
+    k_colour_list<<<gl, 256, 0, stream>>>(c, v.summ, s.ctr, s.vis_list, s.col_list);
+    k_colour_band<<<g.col, COL_THREADS, colour_smem_bytes(), stream>>>(c, v, depth, nullptr, s);
+    k_colour_gates<<<g.vox, 256, 0, stream>>>(c, depth, s, a, frame);
     return cudaGetLastError();
 }
 

@@ -16,45 +16,12 @@
 #include <vector>
 
 #include "../../include/tsdf.h"
+#include "api_internal.h"
 #include "common.cuh"
 
 using namespace tsdf;
 
-struct tsdf_volume {
-    int32_t ng[3], nc[3], nb[3], ncb[3];
-    float s_g, s_c, origin[3], mu, sigma, band;
-    int32_t max_weight, colour_mode, sample_mode, culling, free_space;
-    cudaStream_t stream;
-    tsdf_allocator alloc;
-    int device;
-    LaunchGrids grids;
-    Volumes vol;
-    Scratch scr;
-    uint32_t* depth_tiles;
-    size_t depth_tiles_cap;
-    uint16_t* d_depth;
-    size_t d_depth_cap;
-    uint8_t* d_rgb;
-    size_t d_rgb_cap;
-    int64_t frames;
-    int64_t device_bytes;
-    std::string last_error;
-    // phase timing (tsdf_profile_enable)
-    struct EventSet {
-        cudaEvent_t e[TSDF_PHASE_COUNT + 1];
-    };
-    bool profiling;
-    std::vector<EventSet> ev_pending, ev_pool;
-    double prof_ms[TSDF_PHASE_COUNT];
-    int64_t prof_frames;
-    struct Block {
-        void* p;
-        size_t bytes;
-    };
-    std::vector<Block> blocks;
-};
-
-namespace {
+namespace tsdf_host {
 
 constexpr int64_t MAX_DIM = 4096;
 constexpr int32_t MAX_IMAGE = 16384;
@@ -263,7 +230,35 @@ tsdf_status write_volume(tsdf_volume* v, T* brick, const T* src, const int32_t d
     return st;
 }
 
-}  // namespace
+tsdf_status stage_depth(tsdf_volume* v, const uint16_t* depth_mm, tsdf_image_size dsz, int tiles,
+                        const uint16_t** d_depth) {
+    const size_t dbytes = (size_t)dsz.width * dsz.height * sizeof(uint16_t);
+    *d_depth = depth_mm;
+    if (!is_device_ptr(depth_mm)) {
+        if (v->d_depth_cap < dbytes) {
+            dev_free(v, v->d_depth);
+            v->d_depth = (uint16_t*)dev_alloc(v, dbytes);
+            v->d_depth_cap = v->d_depth ? dbytes : 0;
+            if (!v->d_depth) return fail(v, TSDF_ERR_OOM, "depth staging buffer");
+        }
+        cudaError_t e = cudaMemcpyAsync(v->d_depth, depth_mm, dbytes, cudaMemcpyHostToDevice, v->stream);
+        if (e != cudaSuccess) return cuda_fail(v, e, "depth upload");
+        *d_depth = v->d_depth;
+    }
+    const size_t tbytes = (size_t)tiles * sizeof(uint32_t);
+    if (v->depth_tiles_cap < tbytes) {
+        dev_free(v, v->depth_tiles);
+        v->depth_tiles = (uint32_t*)dev_alloc(v, tbytes);
+        v->depth_tiles_cap = v->depth_tiles ? tbytes : 0;
+        if (!v->depth_tiles) return fail(v, TSDF_ERR_OOM, "depth tile buffer");
+    }
+    v->scr.depth_tiles = v->depth_tiles;
+    return TSDF_OK;
+}
+
+}  // namespace tsdf_host
+
+using namespace tsdf_host;
 
 
 namespace tsdf {
