@@ -77,13 +77,11 @@ __global__ void __launch_bounds__(256) k_depth_tiles(FrameConst c, const uint16_
 // (all F = 1, all w = max_weight), where (1 * w + 1) / (w + 1) = 1.  The
 // visible list (the colour candidates) also drops bricks lying in front of
 // the nearest depth by more than sigma + margin.
-__global__ void __launch_bounds__(256) k_bricks(FrameConst c, const BrickSummary* __restrict__ summ,
-                                                const uint32_t* __restrict__ tiles, Counters* __restrict__ ctr,
-                                                uint32_t* __restrict__ geo_list, uint32_t* __restrict__ vis_list) {
-    const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
-    uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
-    bool in = b < nbt;
-    bool vis = in, geo = in;
+__device__ __forceinline__ void brick_flags(const FrameConst& c, const BrickSummary* __restrict__ summ,
+                                            const uint32_t* __restrict__ tiles, uint32_t b, bool in, bool& geo,
+                                            bool& vis) {
+    vis = in;
+    geo = in;
     if (in && c.culling) {
         int bx = b % c.nb[0], by = (b / c.nb[0]) % c.nb[1], bz = b / (c.nb[0] * c.nb[1]);
         float lo[3], hi[3];
@@ -151,6 +149,15 @@ __global__ void __launch_bounds__(256) k_bricks(FrameConst c, const BrickSummary
             if (c.kdi_pinhole && zmax < (float)dmin * 0.001f - c.cull_behind) vis = false;
         }
     }
+}
+
+__global__ void __launch_bounds__(256) k_bricks(FrameConst c, const BrickSummary* __restrict__ summ,
+                                                const uint32_t* __restrict__ tiles, Counters* __restrict__ ctr,
+                                                uint32_t* __restrict__ geo_list, uint32_t* __restrict__ vis_list) {
+    const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
+    uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    bool geo, vis;
+    brick_flags(c, summ, tiles, b, b < nbt, geo, vis);
     append(geo, b, &ctr->n_geo, geo_list);
     append(vis, b, &ctr->n_vis, vis_list);
 }
@@ -167,6 +174,140 @@ __global__ void __launch_bounds__(256) k_bricks(FrameConst c, const BrickSummary
 // requested before the projections so their latency overlaps the arithmetic;
 // all 16 depth fetches of a lane are issued together.  The warp then writes
 // the brick summary (min/max F over observed voxels, min w).
+// TSDF update of geometry brick b by one warp (lane = lane index); adds the
+// number of updated voxels to count and 1 to changed if any voxel changed.
+template <bool PINHOLE, bool FREE_SPACE>
+__device__ __forceinline__ void geometry_brick(const FrameConst& c, const Volumes& vol,
+                                               const uint16_t* __restrict__ depth, uint32_t b, int lane,
+                                               uint32_t& count, uint32_t& changed) {
+    const int lx = (lane & 1) * 4, ly = (lane >> 1) & 7, lz = lane >> 4;
+    const int bx = b % c.nb[0], by = (b / c.nb[0]) % c.nb[1], bz = b / (c.nb[0] * c.nb[1]);
+    float* Fb = vol.F + (size_t)b * BRICK_VOX + lane * 4;
+    uint8_t* Wb = vol.W + (size_t)b * BRICK_VOX + lane * 4;
+    float4 f[4];
+    uint32_t wv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        f[j] = *reinterpret_cast<const float4*>(Fb + 128 * j);
+        wv[j] = *reinterpret_cast<const uint32_t*>(Wb + 128 * j);
+    }
+    const int gy = by * BRICK + ly;
+    const float py = fmaf((float)gy + 0.5f, c.s_g, c.origin[1]);
+    float px[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) px[i] = fmaf((float)(bx * BRICK + lx + i) + 0.5f, c.s_g, c.origin[0]);
+    float fmn = FLT_MAX, fmx = -FLT_MAX;
+    uint32_t wmn = 0xFFFFFFFFu, upd_all = 0, lom = 0, him = 0;
+    const float lo_thr = c.band + CELL_EPS, hi_thr = -c.band - CELL_EPS;
+    // two halves of 8 voxels (groups j = 2h, 2h + 1) keep the live set small
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        int pix[8];
+        float Zc[8];
+        uint32_t inb = 0;
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+            const int gz = bz * BRICK + lz + 2 * (2 * h + jj);
+            const float pz = fmaf((float)gz + 0.5f, c.s_g, c.origin[2]);
+            const float B0 = fmaf(c.R[1], py, fmaf(c.R[2], pz, c.t[0]));
+            const float B1 = fmaf(c.R[4], py, fmaf(c.R[5], pz, c.t[1]));
+            const float B2 = fmaf(c.R[7], py, fmaf(c.R[8], pz, c.t[2]));
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int k = 4 * jj + i;
+                pix[k] = -1;
+                Zc[k] = 0.0f;
+                if (!(gy < c.ng[1] && gz < c.ng[2] && bx * BRICK + lx + i < c.ng[0])) continue;
+                inb |= 1u << k;
+                const float X = fmaf(c.R[0], px[i], B0), Y = fmaf(c.R[3], px[i], B1), Z = fmaf(c.R[6], px[i], B2);
+                float u, v;
+                int iu, iv;
+                if (!project(c.Kd, PINHOLE, X, Y, Z, u, v)) continue;
+                if (!nearest_pixel(u, v, c.dw, c.dh, iu, iv)) continue;
+                pix[k] = iv * c.dw + iu;
+                Zc[k] = Z;
+            }
+        }
+        uint32_t D[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) D[k] = pix[k] >= 0 ? (uint32_t)__ldg(depth + pix[k]) : 0u;
+        uint32_t upd = 0;
+        float tv[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            tv[k] = 0.0f;
+            if (D[k] == 0u) continue;
+            const float d = (float)D[k] * 0.001f;
+            const float sdf = d - Zc[k];
+            if (sdf < -c.mu) continue;
+            if (!FREE_SPACE && sdf > c.mu) continue;
+            tv[k] = fminf(1.0f, sdf * c.inv_mu);
+            upd |= 1u << k;
+        }
+        upd_all |= upd << (8 * h);
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+            const int j = 2 * h + jj;
+            float fv[4] = {f[j].x, f[j].y, f[j].z, f[j].w};
+            uint32_t wn = wv[j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int k = 4 * jj + i;
+                uint32_t w = (wv[j] >> (8 * i)) & 0xFFu;
+                if (upd & (1u << k)) {
+                    const float wf = (float)w;
+                    fv[i] = __fdiv_rn(fmaf(fv[i], wf, tv[k]), wf + 1.0f);
+                    w = min(w + 1u, (uint32_t)c.max_weight);
+                    wn = (wn & ~(0xFFu << (8 * i))) | (w << (8 * i));
+                }
+                if (inb & (1u << k)) {
+                    wmn = min(wmn, w);
+                    if (w) {
+                        fmn = fminf(fmn, fv[i]);
+                        fmx = fmaxf(fmx, fv[i]);
+                    }
+                    lom |= (w != 0u && fv[i] <= lo_thr ? 1u : 0u) << (4 * j + i);
+                    him |= (w != 0u && fv[i] >= hi_thr ? 1u : 0u) << (4 * j + i);
+                }
+            }
+            if ((upd >> (4 * jj)) & 0xFu) {
+                *reinterpret_cast<float4*>(Fb + 128 * j) = make_float4(fv[0], fv[1], fv[2], fv[3]);
+                *reinterpret_cast<uint32_t*>(Wb + 128 * j) = wn;
+            }
+        }
+    }
+    count += __popc(upd_all);
+    // bricks where nothing changed keep their summary
+    if (!__any_sync(0xffffffffu, upd_all != 0u)) return;
+    ++changed;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        fmn = fminf(fmn, __shfl_xor_sync(0xffffffffu, fmn, o));
+        fmx = fmaxf(fmx, __shfl_xor_sync(0xffffffffu, fmx, o));
+    }
+    wmn = __reduce_min_sync(0xffffffffu, wmn);
+    // band flags (see BrickSummary): voxel 4 j + i of this lane sits at
+    // x = lx + i, y = ly, z = lz + 2 j
+    uint32_t bflags = 0;
+    {
+        const uint32_t fm[6] = {lx == 0 ? 0x1111u : 0u, lx == 4 ? 0x8888u : 0u, ly == 0 ? 0xFFFFu : 0u,
+                                ly == 7 ? 0xFFFFu : 0u, lz == 0 ? 0x000Fu : 0u, lz == 1 ? 0xF000u : 0u};
+        bflags = (lom ? 1u : 0u) | (him ? 2u : 0u);
+#pragma unroll
+        for (int f = 0; f < 6; ++f)
+            bflags |= ((lom & fm[f]) ? 1u : 0u) << (2 + 2 * f) | ((him & fm[f]) ? 1u : 0u) << (3 + 2 * f);
+    }
+    bflags = __reduce_or_sync(0xffffffffu, bflags);
+    if (lane == 0) {
+        BrickSummary sm;
+        sm.fmin = fmn == FLT_MAX ? __int_as_float(0x7f800000) : fmn;
+        sm.fmax = fmx == -FLT_MAX ? __int_as_float(0xff800000) : fmx;
+        sm.wmin = wmn == 0xFFFFFFFFu ? 0u : wmn;
+        sm.flags = bflags;
+        vol.summ[b] = sm;
+    }
+}
+
 template <bool PINHOLE, bool FREE_SPACE>
 __global__ void __launch_bounds__(GEO_THREADS, 7) k_geometry(FrameConst c, Volumes vol, const uint16_t* __restrict__ depth,
                                                           Counters* __restrict__ ctr,
@@ -175,136 +316,9 @@ __global__ void __launch_bounds__(GEO_THREADS, 7) k_geometry(FrameConst c, Volum
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t n = ctr->n_geo;
-    const int lx = (lane & 1) * 4, ly = (lane >> 1) & 7, lz = lane >> 4;
     uint32_t count = 0, changed = 0;
-    for (uint32_t item = warp; item < n; item += nwarps) {
-        const uint32_t b = list[item];
-        const int bx = b % c.nb[0], by = (b / c.nb[0]) % c.nb[1], bz = b / (c.nb[0] * c.nb[1]);
-        float* Fb = vol.F + (size_t)b * BRICK_VOX + lane * 4;
-        uint8_t* Wb = vol.W + (size_t)b * BRICK_VOX + lane * 4;
-        float4 f[4];
-        uint32_t wv[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            f[j] = *reinterpret_cast<const float4*>(Fb + 128 * j);
-            wv[j] = *reinterpret_cast<const uint32_t*>(Wb + 128 * j);
-        }
-        const int gy = by * BRICK + ly;
-        const float py = fmaf((float)gy + 0.5f, c.s_g, c.origin[1]);
-        float px[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) px[i] = fmaf((float)(bx * BRICK + lx + i) + 0.5f, c.s_g, c.origin[0]);
-        float fmn = FLT_MAX, fmx = -FLT_MAX;
-        uint32_t wmn = 0xFFFFFFFFu, upd_all = 0, lom = 0, him = 0;
-        const float lo_thr = c.band + CELL_EPS, hi_thr = -c.band - CELL_EPS;
-        // two halves of 8 voxels (groups j = 2h, 2h + 1) keep the live set small
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            int pix[8];
-            float Zc[8];
-            uint32_t inb = 0;
-#pragma unroll
-            for (int jj = 0; jj < 2; ++jj) {
-                const int gz = bz * BRICK + lz + 2 * (2 * h + jj);
-                const float pz = fmaf((float)gz + 0.5f, c.s_g, c.origin[2]);
-                const float B0 = fmaf(c.R[1], py, fmaf(c.R[2], pz, c.t[0]));
-                const float B1 = fmaf(c.R[4], py, fmaf(c.R[5], pz, c.t[1]));
-                const float B2 = fmaf(c.R[7], py, fmaf(c.R[8], pz, c.t[2]));
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int k = 4 * jj + i;
-                    pix[k] = -1;
-                    Zc[k] = 0.0f;
-                    if (!(gy < c.ng[1] && gz < c.ng[2] && bx * BRICK + lx + i < c.ng[0])) continue;
-                    inb |= 1u << k;
-                    const float X = fmaf(c.R[0], px[i], B0), Y = fmaf(c.R[3], px[i], B1), Z = fmaf(c.R[6], px[i], B2);
-                    float u, v;
-                    int iu, iv;
-                    if (!project(c.Kd, PINHOLE, X, Y, Z, u, v)) continue;
-                    if (!nearest_pixel(u, v, c.dw, c.dh, iu, iv)) continue;
-                    pix[k] = iv * c.dw + iu;
-                    Zc[k] = Z;
-                }
-            }
-            uint32_t D[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) D[k] = pix[k] >= 0 ? (uint32_t)__ldg(depth + pix[k]) : 0u;
-            uint32_t upd = 0;
-            float tv[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                tv[k] = 0.0f;
-                if (D[k] == 0u) continue;
-                const float d = (float)D[k] * 0.001f;
-                const float sdf = d - Zc[k];
-                if (sdf < -c.mu) continue;
-                if (!FREE_SPACE && sdf > c.mu) continue;
-                tv[k] = fminf(1.0f, sdf * c.inv_mu);
-                upd |= 1u << k;
-            }
-            upd_all |= upd << (8 * h);
-#pragma unroll
-            for (int jj = 0; jj < 2; ++jj) {
-                const int j = 2 * h + jj;
-                float fv[4] = {f[j].x, f[j].y, f[j].z, f[j].w};
-                uint32_t wn = wv[j];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int k = 4 * jj + i;
-                    uint32_t w = (wv[j] >> (8 * i)) & 0xFFu;
-                    if (upd & (1u << k)) {
-                        const float wf = (float)w;
-                        fv[i] = __fdiv_rn(fmaf(fv[i], wf, tv[k]), wf + 1.0f);
-                        w = min(w + 1u, (uint32_t)c.max_weight);
-                        wn = (wn & ~(0xFFu << (8 * i))) | (w << (8 * i));
-                    }
-                    if (inb & (1u << k)) {
-                        wmn = min(wmn, w);
-                        if (w) {
-                            fmn = fminf(fmn, fv[i]);
-                            fmx = fmaxf(fmx, fv[i]);
-                        }
-                        lom |= (w != 0u && fv[i] <= lo_thr ? 1u : 0u) << (4 * j + i);
-                        him |= (w != 0u && fv[i] >= hi_thr ? 1u : 0u) << (4 * j + i);
-                    }
-                }
-                if ((upd >> (4 * jj)) & 0xFu) {
-                    *reinterpret_cast<float4*>(Fb + 128 * j) = make_float4(fv[0], fv[1], fv[2], fv[3]);
-                    *reinterpret_cast<uint32_t*>(Wb + 128 * j) = wn;
-                }
-            }
-        }
-        count += __popc(upd_all);
-        // bricks where nothing changed keep their summary
-        if (!__any_sync(0xffffffffu, upd_all != 0u)) continue;
-        ++changed;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            fmn = fminf(fmn, __shfl_xor_sync(0xffffffffu, fmn, o));
-            fmx = fmaxf(fmx, __shfl_xor_sync(0xffffffffu, fmx, o));
-        }
-        wmn = __reduce_min_sync(0xffffffffu, wmn);
-        // band flags (see BrickSummary): voxel 4 j + i of this lane sits at
-        // x = lx + i, y = ly, z = lz + 2 j
-        uint32_t bflags = 0;
-        {
-            const uint32_t fm[6] = {lx == 0 ? 0x1111u : 0u, lx == 4 ? 0x8888u : 0u, ly == 0 ? 0xFFFFu : 0u,
-                                    ly == 7 ? 0xFFFFu : 0u, lz == 0 ? 0x000Fu : 0u, lz == 1 ? 0xF000u : 0u};
-            bflags = (lom ? 1u : 0u) | (him ? 2u : 0u);
-#pragma unroll
-            for (int f = 0; f < 6; ++f)
-                bflags |= ((lom & fm[f]) ? 1u : 0u) << (2 + 2 * f) | ((him & fm[f]) ? 1u : 0u) << (3 + 2 * f);
-        }
-        bflags = __reduce_or_sync(0xffffffffu, bflags);
-        if (lane == 0) {
-            BrickSummary sm;
-            sm.fmin = fmn == FLT_MAX ? __int_as_float(0x7f800000) : fmn;
-            sm.fmax = fmx == -FLT_MAX ? __int_as_float(0xff800000) : fmx;
-            sm.wmin = wmn == 0xFFFFFFFFu ? 0u : wmn;
-            sm.flags = bflags;
-            vol.summ[b] = sm;
-        }
-    }
+    for (uint32_t item = warp; item < n; item += nwarps)
+        geometry_brick<PINHOLE, FREE_SPACE>(c, vol, depth, list[item], lane, count, changed);
     count = __reduce_add_sync(0xffffffffu, count);
     if (lane == 0 && count) atomicAdd(&ctr->geo_updated, (unsigned long long)count);
     if (lane == 0 && changed) atomicAdd(&ctr->n_geo_changed, changed);
@@ -319,6 +333,34 @@ __global__ void __launch_bounds__(GEO_THREADS, 7) k_geometry(FrameConst c, Volum
 // those layers.  A face neighbour contributes its touching face layer; an
 // edge or corner neighbour contributes only voxels on all of its touching
 // faces, so the AND of those faces' flags is still a necessary condition.
+// Colour-candidate test of a visible geometry brick (see above).
+__device__ __forceinline__ bool colour_candidate(const FrameConst& c, const BrickSummary* __restrict__ summ,
+                                                 uint32_t b) {
+    if (!c.culling) return true;
+    const int bx = b % c.nb[0], by = (b / c.nb[0]) % c.nb[1], bz = b / (c.nb[0] * c.nb[1]);
+    uint32_t acc = summ[b].flags & 3u;
+    for (int dz = -1; dz <= 1 && acc != 3u; ++dz) {
+        const int z = bz + dz;
+        if (z < 0 || z >= c.nb[2]) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int y = by + dy;
+            if (y < 0 || y >= c.nb[1]) continue;
+            for (int dx = -1; dx <= 1; ++dx) {
+                const int x = bx + dx;
+                if (x < 0 || x >= c.nb[0] || (dx == 0 && dy == 0 && dz == 0)) continue;
+                const uint32_t f = summ[((size_t)z * c.nb[1] + y) * c.nb[0] + x].flags;
+                // the neighbour at -x touches with its +x face (bits 4-5), etc.
+                uint32_t m = 3u;
+                if (dx) m &= f >> (dx < 0 ? 4 : 2);
+                if (dy) m &= f >> (dy < 0 ? 8 : 6);
+                if (dz) m &= f >> (dz < 0 ? 12 : 10);
+                acc |= m & 3u;
+            }
+        }
+    }
+    return acc == 3u;
+}
+
 __global__ void __launch_bounds__(256) k_colour_list(FrameConst c, const BrickSummary* __restrict__ summ,
                                                      Counters* __restrict__ ctr, const uint32_t* __restrict__ vis_list,
                                                      uint32_t* __restrict__ col_list) {
@@ -330,30 +372,7 @@ __global__ void __launch_bounds__(256) k_colour_list(FrameConst c, const BrickSu
         if (i < n) {
             b = vis_list[i];
             act = true;
-            if (c.culling) {
-                const int bx = b % c.nb[0], by = (b / c.nb[0]) % c.nb[1], bz = b / (c.nb[0] * c.nb[1]);
-                uint32_t acc = summ[b].flags & 3u;
-                for (int dz = -1; dz <= 1 && acc != 3u; ++dz) {
-                    const int z = bz + dz;
-                    if (z < 0 || z >= c.nb[2]) continue;
-                    for (int dy = -1; dy <= 1; ++dy) {
-                        const int y = by + dy;
-                        if (y < 0 || y >= c.nb[1]) continue;
-                        for (int dx = -1; dx <= 1; ++dx) {
-                            const int x = bx + dx;
-                            if (x < 0 || x >= c.nb[0] || (dx == 0 && dy == 0 && dz == 0)) continue;
-                            const uint32_t f = summ[((size_t)z * c.nb[1] + y) * c.nb[0] + x].flags;
-                            // the neighbour at -x touches with its +x face (bits 4-5), etc.
-                            uint32_t m = 3u;
-                            if (dx) m &= f >> (dx < 0 ? 4 : 2);
-                            if (dy) m &= f >> (dy < 0 ? 8 : 6);
-                            if (dz) m &= f >> (dz < 0 ? 12 : 10);
-                            acc |= m & 3u;
-                        }
-                    }
-                }
-                act = acc == 3u;
-            }
+            act = colour_candidate(c, summ, b);
         }
         append(act, b, &ctr->n_col, col_list);
     }
@@ -576,6 +595,244 @@ __device__ uint32_t flush_records(const FrameConst& c, Volumes& vol, const uint1
     return done;
 }
 
+// Band gate of the colour voxels owned by geometry brick b, by one warp with
+// shared-memory slot S (steps 1-4 above).
+__device__ __forceinline__ void band_brick(const FrameConst& c, Volumes& vol, const uint16_t* __restrict__ depth,
+                                           const uint8_t* __restrict__ rgb, const Scratch& scr, ColourSlot& S,
+                                           uint32_t b, int lane, uint32_t& count, uint32_t& n_active,
+                                           uint32_t& n_cells) {
+    const unsigned full = 0xffffffffu;
+    const float lo_thr = c.band + CELL_EPS, hi_thr = -c.band - CELL_EPS;
+    const int bb[3] = {(int)(b % c.nb[0]), (int)((b / c.nb[0]) % c.nb[1]), (int)(b / (c.nb[0] * c.nb[1]))};
+    int k0[3], k1[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) owned_range(bb[a], c.ng[a], c.nc[a], k0[a], k1[a]);
+    if (lane < 27) {
+        const int x = bb[0] + lane % 3 - 1, y = bb[1] + (lane / 3) % 3 - 1, z = bb[2] + lane / 9 - 1;
+        S.nbr[lane] = (x >= 0 && y >= 0 && z >= 0 && x < c.nb[0] && y < c.nb[1] && z < c.nb[2])
+                          ? (int32_t)(((int64_t)z * c.nb[1] + y) * c.nb[0] + x)
+                          : -1;
+        S.start[lane / 9][lane % 9] = 0;
+        S.end[lane / 9][lane % 9] = 0;
+    }
+    __syncwarp();
+
+    // 1a. centre brick: four float4 of F and four words of w per lane
+    {
+        const float* Fb = vol.F + (size_t)b * BRICK_VOX + lane * 4;
+        const uint8_t* Wb = vol.W + (size_t)b * BRICK_VOX + lane * 4;
+        float4 f[4];
+        uint32_t wv[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            f[j] = *reinterpret_cast<const float4*>(Fb + 128 * j);
+            wv[j] = *reinterpret_cast<const uint32_t*>(Wb + 128 * j);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int q = lane + 32 * j;
+            const int x0 = (q & 1) * 4 + 1, y = ((q >> 1) & 7) + 1, z = (q >> 4) + 1;
+            stage(S, x0 + 0, y, z, f[j].x, wv[j] & 0xFFu, lo_thr, hi_thr);
+            stage(S, x0 + 1, y, z, f[j].y, (wv[j] >> 8) & 0xFFu, lo_thr, hi_thr);
+            stage(S, x0 + 2, y, z, f[j].z, (wv[j] >> 16) & 0xFFu, lo_thr, hi_thr);
+            stage(S, x0 + 3, y, z, f[j].w, wv[j] >> 24, lo_thr, hi_thr);
+        }
+    }
+    // 1b. halo: 6 faces x 64, 12 edges x 8, 8 corners = 488 voxels
+    {
+        int txs[16], tys[16], tzs[16];
+#pragma unroll
+        for (int i = 0; i < 12; ++i) {  // faces: i = 2 * face + half
+            const int face = i >> 1, q = lane + 32 * (i & 1);
+            const int axis = face >> 1, side = (face & 1) ? TILE_G - 1 : 0;
+            const int a = (q & 7) + 1, bq = (q >> 3) + 1;
+            txs[i] = axis == 0 ? side : a;
+            tys[i] = axis == 1 ? side : (axis == 0 ? a : bq);
+            tzs[i] = axis == 2 ? side : bq;
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {  // edges
+            const int q = lane + 32 * i, e = q >> 3, m = (q & 7) + 1;
+            const int axis = e >> 2, s1 = (e & 1) ? TILE_G - 1 : 0, s2 = (e & 2) ? TILE_G - 1 : 0;
+            txs[12 + i] = axis == 0 ? m : s1;
+            tys[12 + i] = axis == 1 ? m : (axis == 0 ? s1 : s2);
+            tzs[12 + i] = axis == 2 ? m : s2;
+        }
+        txs[15] = (lane & 1) ? TILE_G - 1 : 0;  // corners (lanes 0..7)
+        tys[15] = (lane & 2) ? TILE_G - 1 : 0;
+        tzs[15] = (lane & 4) ? TILE_G - 1 : 0;
+        float hf[16];
+        uint32_t hw[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int64_t off = (i < 15 || lane < 8) ? tile_offset(S, txs[i], tys[i], tzs[i]) : -1;
+            hf[i] = off >= 0 ? vol.F[off] : 0.0f;
+            hw[i] = off >= 0 ? (uint32_t)vol.W[off] : 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            if (i < 15 || lane < 8) stage(S, txs[i], tys[i], tzs[i], hf[i], hw[i], lo_thr, hi_thr);
+    }
+    // 1c. per-axis colour tables: trilinear cell and fraction of each owned index
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int ka = a == 0 ? k0[0] : (a == 1 ? k0[1] : k0[2]);
+        const int nk = (a == 0 ? k1[0] : (a == 1 ? k1[1] : k1[2])) - ka;
+        const int ta = (a == 0 ? bb[0] : (a == 1 ? bb[1] : bb[2])) * BRICK - 1;
+        const float oa = a == 0 ? c.origin[0] : (a == 1 ? c.origin[1] : c.origin[2]);
+        for (int j = lane; j < nk; j += 32) {
+            const float p = fmaf((float)(ka + j) + 0.5f, c.s_c, oa);
+            const float g = fmaf(p - oa, c.inv_sg, -0.5f);
+            const float i0 = floorf(g);
+            int cell = (int)i0 - ta;
+            if (cell < 0 || cell >= CELLS) {
+                atomicOr(scr.err, ERR_TILE_RANGE);
+                cell = -1;
+            }
+            S.frac[a][j] = g - i0;
+            S.cellof[a][j] = (int8_t)cell;
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int nk = a == 0 ? k1[0] - k0[0] : (a == 1 ? k1[1] - k0[1] : k1[2] - k0[2]);
+        for (int j = lane; j < nk; j += 32) {
+            const int cell = S.cellof[a][j];
+            if (cell < 0) continue;
+            if (j == 0 || S.cellof[a][j - 1] != cell) S.start[a][cell] = (uint8_t)j;
+            if (j == nk - 1 || S.cellof[a][j + 1] != cell) S.end[a][cell] = (uint8_t)(j + 1);
+        }
+    }
+    __syncwarp();
+
+    // 2. row masks (row = z * 10 + y, bit = x)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = lane + 32 * i;
+        if (r < TILE_G * TILE_G) {
+            uint32_t mo = 0, ml = 0, mh = 0;
+#pragma unroll
+            for (int x = 0; x < TILE_G; ++x) {
+                const uint32_t fl = S.flag[r * TILE_G + x];
+                mo |= (fl & 1u) << x;
+                ml |= ((fl >> 1) & 1u) << x;
+                mh |= ((fl >> 2) & 1u) << x;
+            }
+            S.row[0][r] = (uint16_t)mo;
+            S.row[1][r] = (uint16_t)ml;
+            S.row[2][r] = (uint16_t)mh;
+        }
+    }
+    __syncwarp();
+
+    // 3. active cells, compacted
+    uint32_t xmask = 0;
+    int shx, shy, shz;
+    {
+        int mx = 0, my = 0, mz = 0;
+#pragma unroll
+        for (int cell = 0; cell < CELLS; ++cell) {
+            const int nx = S.end[0][cell] - S.start[0][cell];
+            xmask |= (nx > 0 ? 1u : 0u) << cell;
+            mx = max(mx, nx);
+            my = max(my, S.end[1][cell] - S.start[1][cell]);
+            mz = max(mz, S.end[2][cell] - S.start[2][cell]);
+        }
+        shx = ceil_log2(mx);
+        shy = ceil_log2(my);
+        shz = ceil_log2(mz);
+    }
+    uint32_t act[3];
+    uint32_t total = 0;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const int yz = lane + 32 * r;
+        act[r] = 0;
+        if (yz < CELLS * CELLS) {
+            const int cy = yz % CELLS, cz = yz / CELLS;
+            if (S.end[1][cy] > S.start[1][cy] && S.end[2][cz] > S.start[2][cz]) {
+                const int r00 = cz * TILE_G + cy, r10 = r00 + 1, r01 = r00 + TILE_G, r11 = r01 + 1;
+                uint32_t o = S.row[0][r00] & S.row[0][r10] & S.row[0][r01] & S.row[0][r11];
+                o &= o >> 1;
+                uint32_t a = o & xmask;
+                if (c.culling) {
+                    uint32_t l = S.row[1][r00] | S.row[1][r10] | S.row[1][r01] | S.row[1][r11];
+                    uint32_t h = S.row[2][r00] | S.row[2][r10] | S.row[2][r01] | S.row[2][r11];
+                    a &= (l | (l >> 1)) & (h | (h >> 1));
+                }
+                act[r] = a & 0x1FFu;
+            }
+        }
+        total += __popc(act[r]);
+    }
+    uint32_t incl = total;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(full, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const uint32_t nact = __shfl_sync(full, incl, 31);
+    if (nact == 0) return;  // no colour voxel of this brick can pass the band gate
+    ++n_active;
+    n_cells += nact;
+    uint32_t pos = incl - total;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        uint32_t a = act[r];
+        const int yz = lane + 32 * r;
+        while (a) {
+            const int cx = __ffs(a) - 1;
+            a &= a - 1;
+            S.cells[pos++] = (uint16_t)(yz * CELLS + cx);
+        }
+    }
+    __syncwarp();
+
+    // 4. band gate of each colour voxel of the active cells; records
+    const uint32_t sh = shx + shy + shz;
+    const uint32_t units = nact << sh;
+    const uint32_t lanemask_lt = (1u << lane) - 1u;
+    uint32_t nstage = 0;
+    for (uint32_t ub = 0; ub < units; ub += 32) {
+        const uint32_t u = ub + lane;
+        bool pass = false;
+        uint2 rec = make_uint2(0u, 0u);
+        if (u < units) {
+            const uint32_t cellid = S.cells[u >> sh];
+            const uint32_t sub = u & ((1u << sh) - 1u);
+            const int cx = cellid % CELLS, cy = (cellid / CELLS) % CELLS, cz = cellid / (CELLS * CELLS);
+            const int jx = S.start[0][cx] + (int)(sub & ((1u << shx) - 1u));
+            const int jy = S.start[1][cy] + (int)((sub >> shx) & ((1u << shy) - 1u));
+            const int jz = S.start[2][cz] + (int)(sub >> (shx + shy));
+            if (jx < S.end[0][cx] && jy < S.end[1][cy] && jz < S.end[2][cz]) {
+                const int o = (cz * TILE_G + cy) * TILE_G + cx;
+                const float fx = S.frac[0][jx], fy = S.frac[1][jy], fz = S.frac[2][jz];
+                const float c00 = lerp(S.F[o], S.F[o + 1], fx);
+                const float c10 = lerp(S.F[o + TILE_G], S.F[o + TILE_G + 1], fx);
+                const float c01 = lerp(S.F[o + TILE_G * TILE_G], S.F[o + TILE_G * TILE_G + 1], fx);
+                const float c11 =
+                    lerp(S.F[o + TILE_G * TILE_G + TILE_G], S.F[o + TILE_G * TILE_G + TILE_G + 1], fx);
+                const float c0 = lerp(c00, c10, fy);
+                const float c1 = lerp(c01, c11, fy);
+                const float Ft = lerp(c0, c1, fz);
+                pass = fabsf(Ft) <= c.band;
+                rec = make_uint2((uint32_t)(k0[0] + jx) | ((uint32_t)(k0[1] + jy) << 16), (uint32_t)(k0[2] + jz));
+            }
+        }
+        const uint32_t m = __ballot_sync(full, pass);
+        if (pass) S.out[nstage + __popc(m & lanemask_lt)] = rec;
+        nstage += __popc(m);
+        if (nstage > STAGE - 32) {
+            __syncwarp();
+            count += flush_records(c, vol, depth, rgb, scr, S, nstage, lane);
+            nstage = 0;
+        }
+    }
+    __syncwarp();
+    if (nstage) count += flush_records(c, vol, depth, rgb, scr, S, nstage, lane);
+}
+
 __global__ void __launch_bounds__(COL_THREADS, 5) k_colour_band(FrameConst c, Volumes vol,
                                                                 const uint16_t* __restrict__ depth,
                                                                 const uint8_t* __restrict__ rgb, Scratch scr) {
@@ -585,242 +842,14 @@ __global__ void __launch_bounds__(COL_THREADS, 5) k_colour_band(FrameConst c, Vo
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
     const uint32_t n = ctr->n_col;
-    const float lo_thr = c.band + CELL_EPS, hi_thr = -c.band - CELL_EPS;
     uint32_t count = 0, n_active = 0, n_cells = 0;
     for (;;) {
         uint32_t item = 0;
         if (lane == 0) item = atomicAdd(&ctr->col_next, 1u);
         item = __shfl_sync(full, item, 0);
         if (item >= n) break;
-        const uint32_t b = scr.col_list[item];
-        const int bb[3] = {(int)(b % c.nb[0]), (int)((b / c.nb[0]) % c.nb[1]), (int)(b / (c.nb[0] * c.nb[1]))};
-        int k0[3], k1[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) owned_range(bb[a], c.ng[a], c.nc[a], k0[a], k1[a]);
-        if (lane < 27) {
-            const int x = bb[0] + lane % 3 - 1, y = bb[1] + (lane / 3) % 3 - 1, z = bb[2] + lane / 9 - 1;
-            S.nbr[lane] = (x >= 0 && y >= 0 && z >= 0 && x < c.nb[0] && y < c.nb[1] && z < c.nb[2])
-                              ? (int32_t)(((int64_t)z * c.nb[1] + y) * c.nb[0] + x)
-                              : -1;
-            S.start[lane / 9][lane % 9] = 0;
-            S.end[lane / 9][lane % 9] = 0;
-        }
+        band_brick(c, vol, depth, rgb, scr, S, scr.col_list[item], lane, count, n_active, n_cells);
         __syncwarp();
-
-        // 1a. centre brick: four float4 of F and four words of w per lane
-        {
-            const float* Fb = vol.F + (size_t)b * BRICK_VOX + lane * 4;
-            const uint8_t* Wb = vol.W + (size_t)b * BRICK_VOX + lane * 4;
-            float4 f[4];
-            uint32_t wv[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                f[j] = *reinterpret_cast<const float4*>(Fb + 128 * j);
-                wv[j] = *reinterpret_cast<const uint32_t*>(Wb + 128 * j);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int q = lane + 32 * j;
-                const int x0 = (q & 1) * 4 + 1, y = ((q >> 1) & 7) + 1, z = (q >> 4) + 1;
-                stage(S, x0 + 0, y, z, f[j].x, wv[j] & 0xFFu, lo_thr, hi_thr);
-                stage(S, x0 + 1, y, z, f[j].y, (wv[j] >> 8) & 0xFFu, lo_thr, hi_thr);
-                stage(S, x0 + 2, y, z, f[j].z, (wv[j] >> 16) & 0xFFu, lo_thr, hi_thr);
-                stage(S, x0 + 3, y, z, f[j].w, wv[j] >> 24, lo_thr, hi_thr);
-            }
-        }
-        // 1b. halo: 6 faces x 64, 12 edges x 8, 8 corners = 488 voxels
-        {
-            int txs[16], tys[16], tzs[16];
-#pragma unroll
-            for (int i = 0; i < 12; ++i) {  // faces: i = 2 * face + half
-                const int face = i >> 1, q = lane + 32 * (i & 1);
-                const int axis = face >> 1, side = (face & 1) ? TILE_G - 1 : 0;
-                const int a = (q & 7) + 1, bq = (q >> 3) + 1;
-                txs[i] = axis == 0 ? side : a;
-                tys[i] = axis == 1 ? side : (axis == 0 ? a : bq);
-                tzs[i] = axis == 2 ? side : bq;
-            }
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {  // edges
-                const int q = lane + 32 * i, e = q >> 3, m = (q & 7) + 1;
-                const int axis = e >> 2, s1 = (e & 1) ? TILE_G - 1 : 0, s2 = (e & 2) ? TILE_G - 1 : 0;
-                txs[12 + i] = axis == 0 ? m : s1;
-                tys[12 + i] = axis == 1 ? m : (axis == 0 ? s1 : s2);
-                tzs[12 + i] = axis == 2 ? m : s2;
-            }
-            txs[15] = (lane & 1) ? TILE_G - 1 : 0;  // corners (lanes 0..7)
-            tys[15] = (lane & 2) ? TILE_G - 1 : 0;
-            tzs[15] = (lane & 4) ? TILE_G - 1 : 0;
-            float hf[16];
-            uint32_t hw[16];
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int64_t off = (i < 15 || lane < 8) ? tile_offset(S, txs[i], tys[i], tzs[i]) : -1;
-                hf[i] = off >= 0 ? vol.F[off] : 0.0f;
-                hw[i] = off >= 0 ? (uint32_t)vol.W[off] : 0u;
-            }
-#pragma unroll
-            for (int i = 0; i < 16; ++i)
-                if (i < 15 || lane < 8) stage(S, txs[i], tys[i], tzs[i], hf[i], hw[i], lo_thr, hi_thr);
-        }
-        // 1c. per-axis colour tables: trilinear cell and fraction of each owned index
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const int ka = a == 0 ? k0[0] : (a == 1 ? k0[1] : k0[2]);
-            const int nk = (a == 0 ? k1[0] : (a == 1 ? k1[1] : k1[2])) - ka;
-            const int ta = (a == 0 ? bb[0] : (a == 1 ? bb[1] : bb[2])) * BRICK - 1;
-            const float oa = a == 0 ? c.origin[0] : (a == 1 ? c.origin[1] : c.origin[2]);
-            for (int j = lane; j < nk; j += 32) {
-                const float p = fmaf((float)(ka + j) + 0.5f, c.s_c, oa);
-                const float g = fmaf(p - oa, c.inv_sg, -0.5f);
-                const float i0 = floorf(g);
-                int cell = (int)i0 - ta;
-                if (cell < 0 || cell >= CELLS) {
-                    atomicOr(scr.err, ERR_TILE_RANGE);
-                    cell = -1;
-                }
-                S.frac[a][j] = g - i0;
-                S.cellof[a][j] = (int8_t)cell;
-            }
-        }
-        __syncwarp();
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const int nk = a == 0 ? k1[0] - k0[0] : (a == 1 ? k1[1] - k0[1] : k1[2] - k0[2]);
-            for (int j = lane; j < nk; j += 32) {
-                const int cell = S.cellof[a][j];
-                if (cell < 0) continue;
-                if (j == 0 || S.cellof[a][j - 1] != cell) S.start[a][cell] = (uint8_t)j;
-                if (j == nk - 1 || S.cellof[a][j + 1] != cell) S.end[a][cell] = (uint8_t)(j + 1);
-            }
-        }
-        __syncwarp();
-
-        // 2. row masks (row = z * 10 + y, bit = x)
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int r = lane + 32 * i;
-            if (r < TILE_G * TILE_G) {
-                uint32_t mo = 0, ml = 0, mh = 0;
-#pragma unroll
-                for (int x = 0; x < TILE_G; ++x) {
-                    const uint32_t fl = S.flag[r * TILE_G + x];
-                    mo |= (fl & 1u) << x;
-                    ml |= ((fl >> 1) & 1u) << x;
-                    mh |= ((fl >> 2) & 1u) << x;
-                }
-                S.row[0][r] = (uint16_t)mo;
-                S.row[1][r] = (uint16_t)ml;
-                S.row[2][r] = (uint16_t)mh;
-            }
-        }
-        __syncwarp();
-
-        // 3. active cells, compacted
-        uint32_t xmask = 0;
-        int shx, shy, shz;
-        {
-            int mx = 0, my = 0, mz = 0;
-#pragma unroll
-            for (int cell = 0; cell < CELLS; ++cell) {
-                const int nx = S.end[0][cell] - S.start[0][cell];
-                xmask |= (nx > 0 ? 1u : 0u) << cell;
-                mx = max(mx, nx);
-                my = max(my, S.end[1][cell] - S.start[1][cell]);
-                mz = max(mz, S.end[2][cell] - S.start[2][cell]);
-            }
-            shx = ceil_log2(mx);
-            shy = ceil_log2(my);
-            shz = ceil_log2(mz);
-        }
-        uint32_t act[3];
-        uint32_t total = 0;
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            const int yz = lane + 32 * r;
-            act[r] = 0;
-            if (yz < CELLS * CELLS) {
-                const int cy = yz % CELLS, cz = yz / CELLS;
-                if (S.end[1][cy] > S.start[1][cy] && S.end[2][cz] > S.start[2][cz]) {
-                    const int r00 = cz * TILE_G + cy, r10 = r00 + 1, r01 = r00 + TILE_G, r11 = r01 + 1;
-                    uint32_t o = S.row[0][r00] & S.row[0][r10] & S.row[0][r01] & S.row[0][r11];
-                    o &= o >> 1;
-                    uint32_t a = o & xmask;
-                    if (c.culling) {
-                        uint32_t l = S.row[1][r00] | S.row[1][r10] | S.row[1][r01] | S.row[1][r11];
-                        uint32_t h = S.row[2][r00] | S.row[2][r10] | S.row[2][r01] | S.row[2][r11];
-                        a &= (l | (l >> 1)) & (h | (h >> 1));
-                    }
-                    act[r] = a & 0x1FFu;
-                }
-            }
-            total += __popc(act[r]);
-        }
-        uint32_t incl = total;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t v = __shfl_up_sync(full, incl, o);
-            if (lane >= o) incl += v;
-        }
-        const uint32_t nact = __shfl_sync(full, incl, 31);
-        if (nact == 0) continue;  // no colour voxel of this brick can pass the band gate
-        ++n_active;
-        n_cells += nact;
-        uint32_t pos = incl - total;
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            uint32_t a = act[r];
-            const int yz = lane + 32 * r;
-            while (a) {
-                const int cx = __ffs(a) - 1;
-                a &= a - 1;
-                S.cells[pos++] = (uint16_t)(yz * CELLS + cx);
-            }
-        }
-        __syncwarp();
-
-        // 4. band gate of each colour voxel of the active cells; records
-        const uint32_t sh = shx + shy + shz;
-        const uint32_t units = nact << sh;
-        const uint32_t lanemask_lt = (1u << lane) - 1u;
-        uint32_t nstage = 0;
-        for (uint32_t ub = 0; ub < units; ub += 32) {
-            const uint32_t u = ub + lane;
-            bool pass = false;
-            uint2 rec = make_uint2(0u, 0u);
-            if (u < units) {
-                const uint32_t cellid = S.cells[u >> sh];
-                const uint32_t sub = u & ((1u << sh) - 1u);
-                const int cx = cellid % CELLS, cy = (cellid / CELLS) % CELLS, cz = cellid / (CELLS * CELLS);
-                const int jx = S.start[0][cx] + (int)(sub & ((1u << shx) - 1u));
-                const int jy = S.start[1][cy] + (int)((sub >> shx) & ((1u << shy) - 1u));
-                const int jz = S.start[2][cz] + (int)(sub >> (shx + shy));
-                if (jx < S.end[0][cx] && jy < S.end[1][cy] && jz < S.end[2][cz]) {
-                    const int o = (cz * TILE_G + cy) * TILE_G + cx;
-                    const float fx = S.frac[0][jx], fy = S.frac[1][jy], fz = S.frac[2][jz];
-                    const float c00 = lerp(S.F[o], S.F[o + 1], fx);
-                    const float c10 = lerp(S.F[o + TILE_G], S.F[o + TILE_G + 1], fx);
-                    const float c01 = lerp(S.F[o + TILE_G * TILE_G], S.F[o + TILE_G * TILE_G + 1], fx);
-                    const float c11 =
-                        lerp(S.F[o + TILE_G * TILE_G + TILE_G], S.F[o + TILE_G * TILE_G + TILE_G + 1], fx);
-                    const float c0 = lerp(c00, c10, fy);
-                    const float c1 = lerp(c01, c11, fy);
-                    const float Ft = lerp(c0, c1, fz);
-                    pass = fabsf(Ft) <= c.band;
-                    rec = make_uint2((uint32_t)(k0[0] + jx) | ((uint32_t)(k0[1] + jy) << 16), (uint32_t)(k0[2] + jz));
-                }
-            }
-            const uint32_t m = __ballot_sync(full, pass);
-            if (pass) S.out[nstage + __popc(m & lanemask_lt)] = rec;
-            nstage += __popc(m);
-            if (nstage > STAGE - 32) {
-                __syncwarp();
-                count += flush_records(c, vol, depth, rgb, scr, S, nstage, lane);
-                nstage = 0;
-            }
-        }
-        __syncwarp();
-        if (nstage) count += flush_records(c, vol, depth, rgb, scr, S, nstage, lane);
     }
     count = __reduce_add_sync(full, count);
     if (lane == 0) {  // n_active and n_cells are the same in every lane
