@@ -219,6 +219,57 @@ tsdf_status tsdf_profile_enable(tsdf_volume* vol, int32_t enable);
 tsdf_status tsdf_profile_read(tsdf_volume* vol, tsdf_profile_report* out);
 
 /* ------------------------------------------------------------------------
+ * Batched fusion: many independent scans (volumes of any sizes), one frame
+ * each per step, fused by one persistent cooperative kernel launch, captured
+ * in a CUDA graph, whose phases (depth tiles, bricks, geometry, colour
+ * candidates, band gate, colour voxels) each span all scans, separated by a
+ * grid barrier whose waits are bounded (1 s).  Results are identical to
+ * calling tsdf_integrate on each volume.
+ * ---------------------------------------------------------------------- */
+typedef struct tsdf_batch tsdf_batch;
+
+/* One scan's frame; fields as in tsdf_integrate.  Images must be device
+ * pointers, valid until the step has run. */
+typedef struct {
+    const uint16_t* depth_mm;
+    tsdf_image_size dsz;
+    const uint8_t* rgb_hwc;
+    tsdf_image_size csz;
+    const float* K_depth;       /* 9, host */
+    const float* K_rgb;         /* 9, host */
+    const float* T_world_depth; /* 16, host */
+    const float* T_depth_rgb;   /* 16, host */
+} tsdf_frame;
+
+/* A batch over n (1..256) distinct volumes sharing one device and stream
+ * (the batch keeps them in descending size order internally).  The volumes
+ * stay owned by the caller and must outlive the batch. */
+tsdf_status tsdf_batch_create(tsdf_volume* const* volumes, int32_t n, tsdf_batch** out);
+/* Fuse frames[i] into volume i (the caller's order) for every scan; queued
+ * on the volumes' stream. */
+tsdf_status tsdf_batch_integrate(tsdf_batch* batch, const tsdf_frame* frames);
+/* Wait for queued steps; TSDF_ERR_TIMEOUT if a grid-barrier wait gave up
+ * (the barrier state is then reset; that step's scans are left partially
+ * updated), or a volume's recorded device error. */
+tsdf_status tsdf_batch_synchronize(tsdf_batch* batch);
+/* Schedule: blocks per SM of the persistent launch (1..max, the occupancy
+ * limit) and whether steps replay a CUDA graph. */
+tsdf_status tsdf_batch_set_schedule(tsdf_batch* batch, int32_t blocks_per_sm, int32_t use_graph);
+tsdf_status tsdf_batch_get_schedule(const tsdf_batch* batch, int32_t* blocks_per_sm, int32_t* max_blocks_per_sm,
+                                    int32_t* use_graph);
+/* Autotuner: times each blocks-per-SM candidate (median over `rounds`
+ * interleaved rounds) on freshly created clones of the batch's volumes fed
+ * with `frames`, keeps the fastest in the batch's schedule and reports it;
+ * ms_per_candidate (nullable) receives max_blocks_per_sm median times.  The
+ * batch's own volumes are not touched. */
+tsdf_status tsdf_batch_autotune(tsdf_batch* batch, const tsdf_frame* frames, int32_t rounds,
+                                int32_t* best_blocks_per_sm, float* ms_per_candidate);
+/* Failure injection for tests: in the next step one block never arrives at
+ * the first grid barrier, so the other blocks' bounded waits run out. */
+tsdf_status tsdf_batch_inject_stall(tsdf_batch* batch);
+void tsdf_batch_destroy(tsdf_batch* batch);
+
+/* ------------------------------------------------------------------------
  * Photometric colour loss and its adjoint (calibration refinement of the HD
  * camera).  Not in the paper, which takes the calibration of Section IV.A as
  * given: this differentiates the fused colour volume with respect to the HD

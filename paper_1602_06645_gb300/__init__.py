@@ -35,7 +35,9 @@ EXPORTS = [
     "tsdf_get_stats", "tsdf_status_string", "tsdf_last_error", "tsdf_profile_enable", "tsdf_profile_read",
     "tsdf_integrate_geometry_static", "tsdf_adjoint_create", "tsdf_adjoint_record", "tsdf_adjoint_finalize",
     "tsdf_adjoint_voxels", "tsdf_adjoint_pairs", "tsdf_adjoint_forward", "tsdf_adjoint_backward",
-    "tsdf_adjoint_destroy",
+    "tsdf_adjoint_destroy", "tsdf_batch_create", "tsdf_batch_integrate", "tsdf_batch_synchronize",
+    "tsdf_batch_set_schedule", "tsdf_batch_get_schedule", "tsdf_batch_autotune", "tsdf_batch_inject_stall",
+    "tsdf_batch_destroy",
 ]
 PHASES = ["upload", "depth_tiles", "bricks", "geometry", "colour_list", "colour_cells", "colour"]
 
@@ -92,6 +94,15 @@ class tsdf_profile_report(ctypes.Structure):
     _fields_ = [("frames", ctypes.c_int64), ("ms", ctypes.c_double * 7)]
 
 
+class tsdf_frame(ctypes.Structure):
+    _fields_ = [
+        ("depth_mm", ctypes.c_void_p), ("dsz", tsdf_image_size), ("rgb_hwc", ctypes.c_void_p),
+        ("csz", tsdf_image_size), ("K_depth", ctypes.POINTER(ctypes.c_float)),
+        ("K_rgb", ctypes.POINTER(ctypes.c_float)), ("T_world_depth", ctypes.POINTER(ctypes.c_float)),
+        ("T_depth_rgb", ctypes.POINTER(ctypes.c_float)),
+    ]
+
+
 class TsdfError(RuntimeError):
     def __init__(self, status, msg=""):
         self.status = status
@@ -141,6 +152,20 @@ def load():
     lib.tsdf_integrate_geometry_static.argtypes = [i32p, ctypes.c_float, ctypes.c_float, ctypes.c_int32, fp, vp, vp,
                                                    vp, tsdf_image_size, fp, fp, vp]
     lib.tsdf_integrate_geometry_static.restype = ctypes.c_int
+    lib.tsdf_batch_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, H]
+    lib.tsdf_batch_integrate.argtypes = [vp, ctypes.POINTER(tsdf_frame)]
+    lib.tsdf_batch_synchronize.argtypes = [vp]
+    lib.tsdf_batch_set_schedule.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
+    i32o = ctypes.POINTER(ctypes.c_int32)
+    lib.tsdf_batch_get_schedule.argtypes = [vp, i32o, i32o, i32o]
+    lib.tsdf_batch_autotune.argtypes = [vp, ctypes.POINTER(tsdf_frame), ctypes.c_int32, i32o,
+                                        ctypes.POINTER(ctypes.c_float)]
+    lib.tsdf_batch_inject_stall.argtypes = [vp]
+    lib.tsdf_batch_destroy.argtypes = [vp]
+    lib.tsdf_batch_destroy.restype = None
+    for name in ("tsdf_batch_create", "tsdf_batch_integrate", "tsdf_batch_synchronize", "tsdf_batch_set_schedule",
+                 "tsdf_batch_get_schedule", "tsdf_batch_autotune", "tsdf_batch_inject_stall"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.tsdf_adjoint_create.argtypes = [vp, ctypes.c_int32, ctypes.c_int64, H]
     lib.tsdf_adjoint_record.argtypes = [vp, vp, tsdf_image_size, fp, fp]
     lib.tsdf_adjoint_finalize.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
@@ -314,6 +339,66 @@ def tsdf_integrate_geometry_static(dims, voxel_size, mu, max_weight, origin, tsd
                                                  Twd[1], ctypes.c_void_p(int(stream or 0))))
 
 
+def _frames(frames, keep):
+    """tsdf_frame array from (depth, rgb, K_depth, K_rgb, T_world_depth, T_depth_rgb) tuples of
+    CUDA tensors and host matrices."""
+    arr = (tsdf_frame * len(frames))()
+    for i, (d, c, Kd, Kr, Twd, Tdr) in enumerate(frames):
+        dh, dw = _hw(d)
+        ch, cw = _hw(c)
+        mats = [_mat(Kd, 9), _mat(Kr, 9), _mat(Twd, 16), _mat(Tdr, 16)]
+        keep.extend(mats)
+        arr[i] = tsdf_frame(_ptr(d, np.uint16, keep), tsdf_image_size(dw, dh), _ptr(c, np.uint8, keep),
+                            tsdf_image_size(cw, ch), *[m[1] for m in mats])
+    return arr
+
+
+def tsdf_batch_create(handles):
+    b = ctypes.c_void_p()
+    arr = (ctypes.c_void_p * len(handles))(*[h.value for h in handles])
+    _check(load().tsdf_batch_create(arr, len(handles), ctypes.byref(b)), handles[0])
+    return b
+
+
+def tsdf_batch_integrate(b, frames, err_handle=None):
+    keep = []
+    arr = _frames(frames, keep)
+    _check(load().tsdf_batch_integrate(b, arr), err_handle)
+
+
+def tsdf_batch_synchronize(b, err_handle=None):
+    _check(load().tsdf_batch_synchronize(b), err_handle)
+
+
+def tsdf_batch_set_schedule(b, blocks_per_sm, use_graph=True):
+    _check(load().tsdf_batch_set_schedule(b, int(blocks_per_sm), int(bool(use_graph))))
+
+
+def tsdf_batch_get_schedule(b):
+    x, m, g = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().tsdf_batch_get_schedule(b, ctypes.byref(x), ctypes.byref(m), ctypes.byref(g)))
+    return x.value, m.value, bool(g.value)
+
+
+def tsdf_batch_autotune(b, frames, rounds=3):
+    keep = []
+    arr = _frames(frames, keep)
+    _, mx, _ = tsdf_batch_get_schedule(b)
+    best = ctypes.c_int32()
+    ms = (ctypes.c_float * mx)()
+    _check(load().tsdf_batch_autotune(b, arr, int(rounds), ctypes.byref(best), ms))
+    return best.value, list(ms)
+
+
+def tsdf_batch_inject_stall(b):
+    _check(load().tsdf_batch_inject_stall(b))
+
+
+def tsdf_batch_destroy(b):
+    if b:
+        load().tsdf_batch_destroy(b)
+
+
 def tsdf_adjoint_create(h, max_frames, max_pairs):
     a = ctypes.c_void_p()
     _check(load().tsdf_adjoint_create(h, int(max_frames), int(max_pairs), ctypes.byref(a)), h)
@@ -480,3 +565,38 @@ class Volume:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Batch:
+    """Many volumes fused together: one persistent, graph-captured launch per step."""
+
+    def __init__(self, volumes):
+        self.volumes = list(volumes)
+        self.b = tsdf_batch_create([v.h for v in self.volumes])
+
+    def integrate(self, frames):
+        """frames[i] = (depth, rgb, K_depth, K_rgb, T_world_depth, T_depth_rgb) for volume i; images on the GPU."""
+        tsdf_batch_integrate(self.b, frames, self.volumes[0].h)
+
+    def synchronize(self):
+        tsdf_batch_synchronize(self.b, self.volumes[0].h)
+
+    def set_schedule(self, blocks_per_sm, use_graph=True):
+        tsdf_batch_set_schedule(self.b, blocks_per_sm, use_graph)
+
+    def schedule(self):
+        return tsdf_batch_get_schedule(self.b)
+
+    def autotune(self, frames, rounds=3):
+        return tsdf_batch_autotune(self.b, frames, rounds)
+
+    def close(self):
+        if getattr(self, "b", None):
+            tsdf_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

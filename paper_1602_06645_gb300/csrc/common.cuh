@@ -190,6 +190,33 @@ struct VolumeDesc {
 void geometry_frame_constants(const VolumeDesc& d, const float Kd[9], const float Twd[16], int dw, int dh,
                               FrameConst& c);
 
+// One scan of a batched frame step: its frame constants, volumes, scratch and
+// this step's device images.
+struct ScanDesc {
+    FrameConst c;
+    Volumes vol;
+    Scratch scr;
+    const uint16_t* depth;
+    const uint8_t* rgb;
+};
+// Grid barrier and work counters of the batched persistent kernel.
+struct BatchSync {
+    unsigned int count;      // blocks arrived at the current barrier
+    unsigned int gen;        // barrier generation
+    unsigned int err;        // 1: a barrier wait gave up (bounded wait)
+    unsigned int band_next;  // band-phase work counter
+    unsigned int stall;      // test injection: block 0 skips the first barrier of the next step
+    unsigned int pad[3];
+};
+constexpr int MAX_BATCH = 256;  // scans per batched launch
+// One frame step of n scans in a single cooperative launch: depth tiles,
+// bricks, geometry, colour candidates, band gate and colour voxels, with a
+// bounded grid barrier between phases.  Scans are processed in descriptor
+// order (put the largest first).
+cudaError_t launch_batch_step(const ScanDesc* descs, int n, BatchSync* sync, int grid, cudaStream_t stream);
+int batch_blocks_per_sm();
+size_t batch_smem_bytes();
+
 cudaError_t launch_frame_record(const FrameConst& c, const Volumes& v, const Scratch& s, const uint16_t* depth,
                                 const LaunchGrids& g, const AdjBuffers& a, int frame, cudaStream_t stream);
 cudaError_t launch_adjoint_finalize(const AdjBuffers& a, uint32_t n_pairs_max, cudaStream_t stream);

@@ -575,7 +575,7 @@ __device__ __forceinline__ int ceil_log2(int v) {
 
 // Move n staged records to the global list; those beyond its capacity are
 // finished here.  Returns the number of colour voxels updated here.
-__device__ uint32_t flush_records(const FrameConst& c, Volumes& vol, const uint16_t* __restrict__ depth,
+__device__ uint32_t flush_records(const FrameConst& c, const Volumes& vol, const uint16_t* __restrict__ depth,
                                   const uint8_t* __restrict__ rgb, const Scratch& scr, ColourSlot& S, uint32_t n,
                                   int lane) {
     uint32_t base = 0;
@@ -597,7 +597,7 @@ __device__ uint32_t flush_records(const FrameConst& c, Volumes& vol, const uint1
 
 // Band gate of the colour voxels owned by geometry brick b, by one warp with
 // shared-memory slot S (steps 1-4 above).
-__device__ __forceinline__ void band_brick(const FrameConst& c, Volumes& vol, const uint16_t* __restrict__ depth,
+__device__ __forceinline__ void band_brick(const FrameConst& c, const Volumes& vol, const uint16_t* __restrict__ depth,
                                            const uint8_t* __restrict__ rgb, const Scratch& scr, ColourSlot& S,
                                            uint32_t b, int lane, uint32_t& count, uint32_t& n_active,
                                            uint32_t& n_cells) {
@@ -1043,6 +1043,216 @@ __global__ void __launch_bounds__(256) k_colour_gates(FrameConst c, const uint16
     }
 }
 
+// ------------------------------------------------------ batched scans ----
+// Bounded grid barrier (all blocks co-resident: cooperative launch).  The
+// generation is read before arriving, the last block to arrive resets the
+// count and advances the generation; the others wait for the advance for at
+// most BARRIER_TIMEOUT_NS of wall time (%globaltimer) or BARRIER_SPINS polls,
+// after which the wait gives up, sets the error word and the kernel returns.
+constexpr unsigned long long BARRIER_TIMEOUT_NS = 1000000000ull;  // 1 s
+constexpr unsigned BARRIER_SPINS = 1u << 28;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ bool grid_barrier(BatchSync* s, unsigned nblocks) {
+    __syncthreads();
+    int ok = 1;
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = &s->gen;
+        const unsigned g = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&s->count, 1u);
+        if (arrived == nblocks - 1) {
+            s->count = 0;
+            __threadfence();
+            atomicAdd(&s->gen, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            unsigned spins = 0;
+            while (*vgen == g) {
+                ++spins;
+                if ((spins & 255u) == 0u &&
+                    (global_ns() - t0 > BARRIER_TIMEOUT_NS || spins > BARRIER_SPINS || *(volatile unsigned*)&s->err)) {
+                    atomicOr(&s->err, 1u);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+    }
+    return __syncthreads_and(ok) != 0;
+}
+
+// Per-block exclusive prefix over the scans of a per-scan count, each count
+// rounded up to a multiple of `pad`; pre[n] is the total.
+template <typename F>
+__device__ __forceinline__ void scan_prefix(uint32_t* pre, int n, uint32_t pad, F count) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int i = 0; i < n; ++i) {
+            pre[i] = acc;
+            acc += (count(i) + pad - 1) / pad * pad;
+        }
+        pre[n] = acc;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ int find_scan(const uint32_t* pre, int n, uint32_t item) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {  // last i with pre[i] <= item
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(COL_THREADS, 4) k_batch_step(const ScanDesc* __restrict__ descs, int n,
+                                                            BatchSync* sync) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ColourSlot& S = reinterpret_cast<ColourSlot*>(smem_raw)[threadIdx.x >> 5];
+    __shared__ uint32_t pre[MAX_BATCH + 1];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t nthreads = gridDim.x * blockDim.x;
+    const uint32_t warp = tid >> 5, nwarps = nthreads >> 5;
+
+    // P0: counters of every scan (fold the previous frame into the totals), depth tiles
+    if (tid < (uint32_t)n) {
+        Counters* ctr = descs[tid].scr.ctr;
+        ctr->tot_geo_updated += ctr->geo_updated;
+        ctr->tot_col_updated += ctr->col_updated;
+        ctr->tot_geo_bricks += ctr->n_geo;
+        ctr->tot_col_bricks += ctr->n_col;
+        ctr->tot_vis_bricks += ctr->n_vis;
+        ctr->tot_cells += ctr->n_cells;
+        ctr->tot_col_active += ctr->n_col_active;
+        ctr->tot_geo_changed += ctr->n_geo_changed;
+        ctr->frames += 1ull;
+        ctr->n_geo = ctr->n_vis = ctr->n_col = 0;
+        ctr->geo_next = ctr->col_next = 0;
+        ctr->n_cells = ctr->n_vox = 0;
+        ctr->n_col_active = ctr->n_geo_changed = 0;
+        ctr->geo_updated = ctr->col_updated = 0ull;
+    }
+    if (tid == 0) sync->band_next = 0;
+    if (blockIdx.x == 0 && *(volatile unsigned*)&sync->stall) return;  // test injection: never arrive
+    scan_prefix(pre, n, 1, [&](int i) { return (uint32_t)(descs[i].c.tiles_x * descs[i].c.tiles_y); });
+    for (uint32_t item = warp; item < pre[n]; item += nwarps) {  // one warp per 16x16 depth tile
+        const int s = find_scan(pre, n, item);
+        const FrameConst& c = descs[s].c;
+        const uint32_t t = item - pre[s];
+        const int tx = t % c.tiles_x, ty = t / c.tiles_x;
+        uint32_t mn = 0xFFFFu, mx = 0u;
+        for (int k = lane; k < TILE_PX * TILE_PX; k += 32) {
+            const int px = tx * TILE_PX + (k & (TILE_PX - 1)), py = ty * TILE_PX + k / TILE_PX;
+            const uint32_t D = (px < c.dw && py < c.dh) ? descs[s].depth[(size_t)py * c.dw + px] : 0u;
+            if (D) mn = min(mn, D);
+            mx = max(mx, D);
+        }
+        mn = __reduce_min_sync(full, mn);
+        mx = __reduce_max_sync(full, mx);
+        if (lane == 0) descs[s].scr.depth_tiles[t] = mn | (mx << 16);
+    }
+    if (!grid_barrier(sync, gridDim.x)) return;
+
+    // P1: bricks (each scan's range padded to whole warps, so a warp never mixes scans)
+    scan_prefix(pre, n, 32, [&](int i) { return (uint32_t)(descs[i].c.nb[0] * descs[i].c.nb[1] * descs[i].c.nb[2]); });
+    for (uint32_t base = warp * 32; base < pre[n]; base += nthreads) {
+        const uint32_t item = base + lane;
+        const int s = find_scan(pre, n, base);
+        const ScanDesc& d = descs[s];
+        const uint32_t b = item - pre[s];
+        const uint32_t nbt = (uint32_t)d.c.nb[0] * d.c.nb[1] * d.c.nb[2];
+        bool geo, vis;
+        brick_flags(d.c, d.vol.summ, d.scr.depth_tiles, b, b < nbt, geo, vis);
+        append(geo, b, &d.scr.ctr->n_geo, d.scr.geo_list);
+        append(vis, b, &d.scr.ctr->n_vis, d.scr.vis_list);
+    }
+    if (!grid_barrier(sync, gridDim.x)) return;
+
+    // P2: geometry, one warp per listed brick
+    scan_prefix(pre, n, 1, [&](int i) { return descs[i].scr.ctr->n_geo; });
+    for (uint32_t item = warp; item < pre[n]; item += nwarps) {
+        const int s = find_scan(pre, n, item);
+        const ScanDesc& d = descs[s];
+        const uint32_t b = d.scr.geo_list[item - pre[s]];
+        uint32_t count = 0, changed = 0;
+        if (d.c.kd_pinhole && d.c.free_space)
+            geometry_brick<true, true>(d.c, d.vol, d.depth, b, lane, count, changed);
+        else if (d.c.kd_pinhole)
+            geometry_brick<true, false>(d.c, d.vol, d.depth, b, lane, count, changed);
+        else if (d.c.free_space)
+            geometry_brick<false, true>(d.c, d.vol, d.depth, b, lane, count, changed);
+        else
+            geometry_brick<false, false>(d.c, d.vol, d.depth, b, lane, count, changed);
+        count = __reduce_add_sync(full, count);
+        if (lane == 0) {
+            if (count) atomicAdd(&d.scr.ctr->geo_updated, (unsigned long long)count);
+            if (changed) atomicAdd(&d.scr.ctr->n_geo_changed, changed);
+        }
+    }
+    if (!grid_barrier(sync, gridDim.x)) return;
+
+    // P3: colour candidates
+    scan_prefix(pre, n, 32, [&](int i) { return descs[i].scr.ctr->n_vis; });
+    for (uint32_t base = warp * 32; base < pre[n]; base += nthreads) {
+        const uint32_t item = base + lane;
+        const int s = find_scan(pre, n, base);
+        const ScanDesc& d = descs[s];
+        const uint32_t i = item - pre[s];
+        const bool in = i < d.scr.ctr->n_vis;
+        const uint32_t b = in ? d.scr.vis_list[i] : 0u;
+        append(in && colour_candidate(d.c, d.vol.summ, b), b, &d.scr.ctr->n_col, d.scr.col_list);
+    }
+    if (!grid_barrier(sync, gridDim.x)) return;
+
+    // P4: band gate, one warp per candidate, taken with an atomic counter
+    scan_prefix(pre, n, 1, [&](int i) { return descs[i].scr.ctr->n_col; });
+    for (;;) {
+        uint32_t item = 0;
+        if (lane == 0) item = atomicAdd(&sync->band_next, 1u);
+        item = __shfl_sync(full, item, 0);
+        if (item >= pre[n]) break;
+        const int s = find_scan(pre, n, item);
+        const ScanDesc& d = descs[s];
+        uint32_t count = 0, n_active = 0, n_cells = 0;
+        band_brick(d.c, d.vol, d.depth, d.rgb, d.scr, S, d.scr.col_list[item - pre[s]], lane, count, n_active, n_cells);
+        __syncwarp();
+        count = __reduce_add_sync(full, count);
+        if (lane == 0) {
+            if (count) atomicAdd(&d.scr.ctr->col_updated, (unsigned long long)count);
+            if (n_active) atomicAdd(&d.scr.ctr->n_col_active, n_active);
+            if (n_cells) atomicAdd(&d.scr.ctr->n_cells, n_cells);
+        }
+    }
+    if (!grid_barrier(sync, gridDim.x)) return;
+
+    // P5: colour voxels that passed the band gate
+    scan_prefix(pre, n, 32, [&](int i) { return min(descs[i].scr.ctr->n_vox, descs[i].scr.vox_cap); });
+    for (uint32_t base = warp * 32; base < pre[n]; base += nthreads) {
+        const uint32_t item = base + lane;
+        const int s = find_scan(pre, n, base);
+        const ScanDesc& d = descs[s];
+        const uint32_t i = item - pre[s];
+        bool upd = false;
+        if (i < min(d.scr.ctr->n_vox, d.scr.vox_cap)) {
+            const uint2 r = d.scr.vox[i];
+            upd = colour_after_band(d.c, d.vol.C, d.depth, d.rgb, (int)(r.x & 0xFFFFu), (int)(r.x >> 16), (int)r.y);
+        }
+        const uint32_t cnt = __popc(__ballot_sync(full, upd));
+        if (lane == 0 && cnt) atomicAdd(&d.scr.ctr->col_updated, (unsigned long long)cnt);
+    }
+}
+
 __global__ void k_init_summaries(BrickSummary* summ, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
@@ -1153,6 +1363,28 @@ cudaError_t launch_frame_record(const FrameConst& c, const Volumes& v, const Scr
     k_colour_band<<<g.col, COL_THREADS, colour_smem_bytes(), stream>>>(c, v, depth, nullptr, s);
     k_colour_gates<<<g.vox, 256, 0, stream>>>(c, depth, s, a, frame);
     return cudaGetLastError();
+}
+
+size_t batch_smem_bytes() { return colour_smem_bytes(); }
+
+int batch_blocks_per_sm() {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_step, COL_THREADS, batch_smem_bytes());
+    return n > 0 ? n : 1;
+}
+
+cudaError_t launch_batch_step(const ScanDesc* descs, int n, BatchSync* sync, int grid, cudaStream_t stream) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(COL_THREADS);
+    cfg.dynamicSmemBytes = batch_smem_bytes();
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;  // all blocks co-resident: the grid barrier can complete
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_batch_step, descs, n, sync);
 }
 
 }  // namespace tsdf
