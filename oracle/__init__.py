@@ -96,6 +96,10 @@ def _load():
         lib.orc_adj_cells32.argtypes = [ctypes.POINTER(AdjProblem), vp, vp, vp]
         lib.orc_adj_cells32.restype = None
         lib.orc_adj_eval.restype = ctypes.c_double
+        lib.orc_sparse_frame.argtypes = [ctypes.POINTER(Params), vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int,
+                                         ctypes.c_int, vp, vp, vp, vp, ctypes.c_int64, vp, vp, vp, ctypes.c_int64,
+                                         vp, vp, vp]
+        lib.orc_sparse_frame.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -118,28 +122,35 @@ def colour_voxel(dims_geo, dims_col, voxel_size):
     return float(np.float32(float(dims_geo[0]) * float(voxel_size) / float(dims_col[0])))
 
 
+def make_params(dims_geo, dims_col, voxel_size, mu, max_weight, sigma=0.020, band=None, colour_mode=0,
+                sample_mode=0, update_free_space=1, origin=None, n_threads=1):
+    """orc_params for the two volumes (Section IV.B)."""
+    p = Params()
+    p.ng[:] = [int(v) for v in dims_geo]
+    p.nc[:] = [int(v) for v in dims_col]
+    p.s_g = float(voxel_size)
+    p.s_c = colour_voxel(dims_geo, dims_col, voxel_size)
+    o = volume_geometry(dims_geo, voxel_size) if origin is None else origin
+    p.origin[:] = [float(v) for v in o]
+    p.mu = float(mu)
+    p.max_weight = int(max_weight)
+    p.sigma = float(sigma)
+    # default band: one colour voxel either side of the zero crossing, in
+    # normalised TSDF units (binary32 quotient)
+    p.band = float(np.float32(p.s_c) / np.float32(p.mu)) if band is None else float(band)
+    p.colour_mode, p.sample_mode = int(colour_mode), int(sample_mode)
+    p.update_free_space, p.n_threads = int(update_free_space), int(n_threads)
+    return p
+
+
 class Oracle:
     """Holds the two volumes (linear, x fastest) and integrates frames on the CPU."""
 
     def __init__(self, dims_geo, dims_col, voxel_size, mu, max_weight, sigma=0.020, band=None,
                  colour_mode=0, sample_mode=0, update_free_space=1, origin=None, n_threads=1):
         self.lib = _load()
-        p = Params()
-        p.ng[:] = [int(v) for v in dims_geo]
-        p.nc[:] = [int(v) for v in dims_col]
-        p.s_g = float(voxel_size)
-        p.s_c = colour_voxel(dims_geo, dims_col, voxel_size)
-        o = volume_geometry(dims_geo, voxel_size) if origin is None else origin
-        p.origin[:] = [float(v) for v in o]
-        p.mu = float(mu)
-        p.max_weight = int(max_weight)
-        p.sigma = float(sigma)
-        # default band: one colour voxel either side of the zero crossing, in
-        # normalised TSDF units (binary32 quotient)
-        p.band = float(np.float32(p.s_c) / np.float32(p.mu)) if band is None else float(band)
-        p.colour_mode, p.sample_mode = int(colour_mode), int(sample_mode)
-        p.update_free_space, p.n_threads = int(update_free_space), int(n_threads)
-        self.p = p
+        self.p = make_params(dims_geo, dims_col, voxel_size, mu, max_weight, sigma, band, colour_mode, sample_mode,
+                             update_free_space, origin, n_threads)
         gx, gy, gz = dims_geo
         cx, cy, cz = dims_col
         self.F = np.zeros((gz, gy, gx), dtype=np.float32)
@@ -197,6 +208,38 @@ class Oracle:
     @property
     def colour_weight(self):
         return (self.C >> 24).astype(np.uint8)
+
+
+class SparseOracle:
+    """The same frame updates as Oracle, applied only to sampled voxels: a set
+    of geometry voxels and a set of colour voxels, each given by linear
+    indices (x fastest).  The colour band gate reads its trilinear corners from
+    the geometry samples, so the geometry set must hold every corner of every
+    colour sample; corners it lacks are counted in `missing`."""
+
+    def __init__(self, geo_index, col_index, dims_geo, dims_col, voxel_size, mu, max_weight, **kw):
+        self.lib = _load()
+        self.p = make_params(dims_geo, dims_col, voxel_size, mu, max_weight, **kw)
+        self.geo_index = np.unique(np.asarray(geo_index, dtype=np.uint64))
+        self.col_index = np.unique(np.asarray(col_index, dtype=np.uint64))
+        self.F = np.zeros(len(self.geo_index), np.float32)
+        self.W = np.zeros(len(self.geo_index), np.uint8)
+        self.C = np.zeros(len(self.col_index), np.uint32)
+        self.missing = np.zeros(1, np.int64)
+
+    def integrate(self, depth, rgb, K_depth, K_rgb, T_world_depth, T_depth_rgb):
+        depth = np.ascontiguousarray(depth, dtype=np.uint16)
+        rgb = np.ascontiguousarray(rgb, dtype=np.uint8)
+        dh, dw = depth.shape
+        ch, cw, _ = rgb.shape
+        Kd, Kr = _f32(K_depth, (3, 3)), _f32(K_rgb, (3, 3))
+        Twd, Tdr = _f32(T_world_depth, (4, 4)), _f32(T_depth_rgb, (4, 4))
+        self.lib.orc_sparse_frame(ctypes.byref(self.p), depth.ctypes.data, dw, dh, rgb.ctypes.data, cw, ch,
+                                  Kd.ctypes.data, Kr.ctypes.data, Twd.ctypes.data, Tdr.ctypes.data,
+                                  len(self.geo_index), self.geo_index.ctypes.data, self.F.ctypes.data,
+                                  self.W.ctypes.data, len(self.col_index), self.col_index.ctypes.data,
+                                  self.C.ctypes.data, self.missing.ctypes.data)
+        return int(self.missing[0])
 
 
 class Adjoint:

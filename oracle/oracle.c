@@ -134,6 +134,31 @@ static float lerpf(float a, float b, float t) { return fmaf(t, b - a, a); }
  *   t = min(1, sdf / mu),
  *   F <- (F w + t) / (w + 1),  w <- min(w + 1, max_weight).
  * Averaging continues with w = max_weight once the cap is reached. */
+/* One geometry voxel (x, y, z) whose F and w are at *Fv, *Wv; returns 1 if
+ * it was updated. */
+static int geo_voxel(const orc_params* p, const orc_frame* fr, float* Fv, uint8_t* Wv, const uint16_t* depth, int x,
+                     int y, int z) {
+    float P[3];
+    rigid(fr->R, fr->t, centre(p->origin[0], x, p->s_g), centre(p->origin[1], y, p->s_g),
+          centre(p->origin[2], z, p->s_g), P);
+    float u, v;
+    int iu, iv;
+    if (!project(fr->Kd, P[0], P[1], P[2], &u, &v)) return 0;
+    if (!nearest_pixel(u, v, fr->dw, fr->dh, &iu, &iv)) return 0;
+    uint16_t D = depth[(size_t)iv * fr->dw + iu];
+    if (D == 0) return 0;
+    float d = (float)D * 0.001f;
+    float sdf = d - P[2];
+    if (sdf < -p->mu) return 0;
+    if (!p->update_free_space && sdf > p->mu) return 0;
+    float t = fminf(1.0f, sdf * fr->inv_mu);
+    int w = *Wv;
+    float wf = (float)w;
+    *Fv = fmaf(*Fv, wf, t) / (wf + 1.0f);
+    *Wv = (uint8_t)(w + 1 < p->max_weight ? w + 1 : p->max_weight);
+    return 1;
+}
+
 static long long orc_geometry(const orc_params* p, const orc_frame* fr, float* F, uint8_t* W,
                               const uint16_t* depth) {
     const int nx = p->ng[0], ny = p->ng[1], nz = p->ng[2];
@@ -142,26 +167,8 @@ static long long orc_geometry(const orc_params* p, const orc_frame* fr, float* F
     for (int z = 0; z < nz; ++z) {
         for (int y = 0; y < ny; ++y) {
             for (int x = 0; x < nx; ++x) {
-                float P[3];
-                rigid(fr->R, fr->t, centre(p->origin[0], x, p->s_g), centre(p->origin[1], y, p->s_g),
-                      centre(p->origin[2], z, p->s_g), P);
-                float u, v;
-                int iu, iv;
-                if (!project(fr->Kd, P[0], P[1], P[2], &u, &v)) continue;
-                if (!nearest_pixel(u, v, fr->dw, fr->dh, &iu, &iv)) continue;
-                uint16_t D = depth[(size_t)iv * fr->dw + iu];
-                if (D == 0) continue;
-                float d = (float)D * 0.001f;
-                float sdf = d - P[2];
-                if (sdf < -p->mu) continue;
-                if (!p->update_free_space && sdf > p->mu) continue;
-                float t = fminf(1.0f, sdf * fr->inv_mu);
                 size_t idx = ((size_t)z * ny + y) * nx + x;
-                int w = W[idx];
-                float wf = (float)w;
-                F[idx] = fmaf(F[idx], wf, t) / (wf + 1.0f);
-                W[idx] = (uint8_t)(w + 1 < p->max_weight ? w + 1 : p->max_weight);
-                ++updated;
+                updated += geo_voxel(p, fr, &F[idx], &W[idx], depth, x, y, z);
             }
         }
     }
@@ -172,8 +179,24 @@ static long long orc_geometry(const orc_params* p, const orc_frame* fr, float* F
 /* Trilinear TSDF at grid coordinate g (geometry voxel units, centres at
  * integers).  Returns 0 when any of the 8 corners is outside the volume or
  * has weight 0 (never observed). */
-static int trilinear(const orc_params* p, const float* F, const uint8_t* W, const float g[3], float* out) {
-    const int nx = p->ng[0], ny = p->ng[1], nz = p->ng[2];
+/* Geometry voxel (x, y, z) as seen by the band gate: returns its weight
+ * (0 = never observed) and its TSDF in *f. */
+typedef int (*corner_fn)(const void* ctx, int x, int y, int z, float* f);
+
+typedef struct {
+    const orc_params* p;
+    const float* F;
+    const uint8_t* W;
+} dense_geo;
+
+static int dense_corner(const void* ctx, int x, int y, int z, float* f) {
+    const dense_geo* d = (const dense_geo*)ctx;
+    size_t idx = ((size_t)z * d->p->ng[1] + y) * d->p->ng[0] + x;
+    *f = d->F[idx];
+    return d->W[idx];
+}
+
+static int trilinear(const orc_params* p, corner_fn corner, const void* ctx, const float g[3], float* out) {
     float i0f[3], fr[3];
     int i0[3];
     for (int a = 0; a < 3; ++a) {
@@ -186,11 +209,10 @@ static int trilinear(const orc_params* p, const float* F, const uint8_t* W, cons
     for (int dz = 0; dz < 2; ++dz)
         for (int dy = 0; dy < 2; ++dy)
             for (int dx = 0; dx < 2; ++dx) {
-                size_t idx = ((size_t)(i0[2] + dz) * ny + (i0[1] + dy)) * nx + (i0[0] + dx);
-                if (W[idx] == 0) return 0;
-                c[dz][dy][dx] = F[idx];
+                float f;
+                if (corner(ctx, i0[0] + dx, i0[1] + dy, i0[2] + dz, &f) == 0) return 0;
+                c[dz][dy][dx] = f;
             }
-    (void)nz;
     /* lerp along x, then y, then z */
     float c00 = lerpf(c[0][0][0], c[0][0][1], fr[0]);
     float c10 = lerpf(c[0][1][0], c[0][1][1], fr[0]);
@@ -260,7 +282,7 @@ static int orc_paper_normal_update(const orc_params* p, const orc_frame* fr, con
  * D > 0), Eq. 7 (sigma) and the trilinear band gate.  On success returns 1
  * with the voxel in the current depth camera (Pc), its depth pixel and the
  * back-projected depth point (Pd). */
-static int colour_depth_gates(const orc_params* p, const orc_frame* fr, const float* F, const uint8_t* W,
+static int colour_depth_gates(const orc_params* p, const orc_frame* fr, corner_fn corner, const void* ctx,
                               const uint16_t* depth, int x, int y, int z, float Pc[3], int* iu, int* iv,
                               float Pd[3]) {
     float pw[3] = {centre(p->origin[0], x, p->s_c), centre(p->origin[1], y, p->s_c), centre(p->origin[2], z, p->s_c)};
@@ -277,44 +299,49 @@ static int colour_depth_gates(const orc_params* p, const orc_frame* fr, const fl
     if (dist2 > fr->sigma2) return 0;
     float g[3], Ft;
     for (int a = 0; a < 3; ++a) g[a] = fmaf(pw[a] - p->origin[a], fr->inv_sg, -0.5f);
-    if (!trilinear(p, F, W, g, &Ft)) return 0;
+    if (!trilinear(p, corner, ctx, g, &Ft)) return 0;
     if (!(fabsf(Ft) <= p->band)) return 0;
+    return 1;
+}
+
+/* One colour voxel (x, y, z) whose packed colour is at *Cv; the band gate
+ * reads the geometry through `corner`.  Returns 1 if it was updated. */
+static int colour_voxel(const orc_params* p, const orc_frame* fr, corner_fn corner, const void* ctx, uint32_t* Cv,
+                        const uint16_t* depth, const uint8_t* rgb, int x, int y, int z) {
+    float Pc[3], Pd[3];
+    int iu, iv;
+    if (!colour_depth_gates(p, fr, corner, ctx, depth, x, y, z, Pc, &iu, &iv, Pd)) return 0;
+    float Ph[3];
+    rigid(fr->Rc, fr->tc, Pc[0], Pc[1], Pc[2], Ph);
+    float uh, vh;
+    if (!project(fr->Kr, Ph[0], Ph[1], Ph[2], &uh, &vh)) return 0;
+    uint32_t s[3];
+    if (!sample_rgb(p, fr, rgb, uh, vh, s)) return 0;
+    if (p->colour_mode == 1) return orc_paper_normal_update(p, fr, depth, iu, iv, Pd, Pc, Cv, s);
+    uint32_t cv = *Cv;
+    uint32_t w = cv >> 24;
+    uint32_t out = 0;
+    for (int c = 0; c < 3; ++c) {
+        uint32_t cc = (cv >> (8 * c)) & 0xFFu;
+        uint32_t nc = (cc * w + s[c] + ((w + 1u) >> 1)) / (w + 1u);
+        out |= nc << (8 * c);
+    }
+    uint32_t wn = w + 1u < (uint32_t)p->max_weight ? w + 1u : (uint32_t)p->max_weight;
+    *Cv = out | (wn << 24);
     return 1;
 }
 
 static long long orc_colour(const orc_params* p, const orc_frame* fr, const float* F, const uint8_t* W,
                             uint32_t* C, const uint16_t* depth, const uint8_t* rgb) {
     const int nx = p->nc[0], ny = p->nc[1], nz = p->nc[2];
+    const dense_geo geo = {p, F, W};
     long long updated = 0;
 #pragma omp parallel for reduction(+ : updated) num_threads(p->n_threads > 0 ? p->n_threads : 1) schedule(dynamic, 1)
     for (int z = 0; z < nz; ++z) {
         for (int y = 0; y < ny; ++y) {
             for (int x = 0; x < nx; ++x) {
-                float Pc[3], Pd[3];
-                int iu, iv;
-                if (!colour_depth_gates(p, fr, F, W, depth, x, y, z, Pc, &iu, &iv, Pd)) continue;
-                float Ph[3];
-                rigid(fr->Rc, fr->tc, Pc[0], Pc[1], Pc[2], Ph);
-                float uh, vh;
-                if (!project(fr->Kr, Ph[0], Ph[1], Ph[2], &uh, &vh)) continue;
-                uint32_t s[3];
-                if (!sample_rgb(p, fr, rgb, uh, vh, s)) continue;
                 size_t idx = ((size_t)z * ny + y) * nx + x;
-                if (p->colour_mode == 1) {
-                    updated += orc_paper_normal_update(p, fr, depth, iu, iv, Pd, Pc, &C[idx], s);
-                    continue;
-                }
-                uint32_t cv = C[idx];
-                uint32_t w = cv >> 24;
-                uint32_t out = 0;
-                for (int c = 0; c < 3; ++c) {
-                    uint32_t cc = (cv >> (8 * c)) & 0xFFu;
-                    uint32_t nc = (cc * w + s[c] + ((w + 1u) >> 1)) / (w + 1u);
-                    out |= nc << (8 * c);
-                }
-                uint32_t wn = w + 1u < (uint32_t)p->max_weight ? w + 1u : (uint32_t)p->max_weight;
-                C[idx] = out | (wn << 24);
-                ++updated;
+                updated += colour_voxel(p, fr, dense_corner, &geo, &C[idx], depth, rgb, x, y, z);
             }
         }
     }
@@ -422,15 +449,74 @@ long long orc_record_gates(const orc_params* p, float* F, uint8_t* W, const uint
     orc_frame_setup(&fr, p, Kd, Kd, Twd, I, dw, dh, dw, dh);
     orc_geometry(p, &fr, F, W, depth);
     const int nx = p->nc[0], ny = p->nc[1], nz = p->nc[2];
+    const dense_geo geo = {p, F, W};
     long long n = 0;
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
                 float Pc[3], Pd[3];
                 int iu, iv;
-                if (!colour_depth_gates(p, &fr, F, W, depth, x, y, z, Pc, &iu, &iv, Pd)) continue;
+                if (!colour_depth_gates(p, &fr, dense_corner, &geo, depth, x, y, z, Pc, &iu, &iv, Pd)) continue;
                 if (n < cap) out[n] = (uint32_t)(((size_t)z * ny + y) * nx + x);
                 ++n;
             }
     return n;
+}
+
+/* ---------------------------------------------------------- sampled ---- */
+/* Sampled replay of one frame, for parity checks at sizes where the whole
+ * volumes are too large for the oracle: the same per-voxel updates as
+ * orc_integrate, applied to a list of geometry voxels (linear indices,
+ * ascending, with their F and w) and then to a list of colour voxels (with
+ * their packed colours).  The band gate of a colour voxel reads its trilinear
+ * corners from the geometry list; a corner missing from the list is counted
+ * in *missing and read as unobserved.  Returns 0. */
+typedef struct {
+    const orc_params* p;
+    const uint64_t* lin;
+    const float* F;
+    const uint8_t* W;
+    int64_t n;
+    long long* missing;
+} sparse_geo;
+
+static int sparse_corner(const void* ctx, int x, int y, int z, float* f) {
+    const sparse_geo* s = (const sparse_geo*)ctx;
+    uint64_t key = ((uint64_t)z * (uint64_t)s->p->ng[1] + (uint64_t)y) * (uint64_t)s->p->ng[0] + (uint64_t)x;
+    int64_t lo = 0, hi = s->n - 1;
+    while (lo <= hi) {
+        int64_t mid = (lo + hi) / 2;
+        if (s->lin[mid] == key) {
+            *f = s->F[mid];
+            return s->W[mid];
+        }
+        if (s->lin[mid] < key) lo = mid + 1; else hi = mid - 1;
+    }
+    #pragma omp atomic
+    (*s->missing)++;
+    *f = 0.0f;
+    return 0;
+}
+
+int orc_sparse_frame(const orc_params* p, const uint16_t* depth, int dw, int dh, const uint8_t* rgb, int cw, int ch,
+                     const float Kd[9], const float Kr[9], const float Twd[16], const float Tdr[16], int64_t ng,
+                     const uint64_t* g_lin, float* gF, uint8_t* gW, int64_t nc, const uint64_t* c_lin, uint32_t* cC,
+                     long long* missing) {
+    orc_frame fr;
+    orc_frame_setup(&fr, p, Kd, Kr, Twd, Tdr, dw, dh, cw, ch);
+    const uint64_t gx = (uint64_t)p->ng[0], gy = (uint64_t)p->ng[1];
+    const uint64_t cx = (uint64_t)p->nc[0], cy = (uint64_t)p->nc[1];
+#pragma omp parallel for num_threads(p->n_threads > 0 ? p->n_threads : 1) schedule(dynamic, 256)
+    for (int64_t i = 0; i < ng; ++i) {
+        uint64_t l = g_lin[i];
+        geo_voxel(p, &fr, &gF[i], &gW[i], depth, (int)(l % gx), (int)((l / gx) % gy), (int)(l / (gx * gy)));
+    }
+    sparse_geo geo = {p, g_lin, gF, gW, ng, missing};
+#pragma omp parallel for num_threads(p->n_threads > 0 ? p->n_threads : 1) schedule(dynamic, 256)
+    for (int64_t i = 0; i < nc; ++i) {
+        uint64_t l = c_lin[i];
+        colour_voxel(p, &fr, sparse_corner, &geo, &cC[i], depth, rgb, (int)(l % cx), (int)((l / cx) % cy),
+                     (int)(l / (cx * cy)));
+    }
+    return 0;
 }

@@ -21,13 +21,13 @@ MUTANTS = {
     "pixel_floor_not_round": ("float fu = floorf(u + 0.5f), fv = floorf(v + 0.5f);",
                               "float fu = floorf(u), fv = floorf(v);"),
     "sdf_sign": ("float sdf = d - P[2];", "float sdf = P[2] - d;"),
-    "hidden_not_skipped": ("if (sdf < -p->mu) continue;", ""),
+    "hidden_not_skipped": ("if (sdf < -p->mu) return 0;", ""),
     "no_truncation": ("float t = fminf(1.0f, sdf * fr->inv_mu);", "float t = sdf * fr->inv_mu;"),
-    "plain_mean": ("F[idx] = fmaf(F[idx], wf, t) / (wf + 1.0f);", "F[idx] = (F[idx] + t) * 0.5f;"),
-    "weight_uncapped": ("W[idx] = (uint8_t)(w + 1 < p->max_weight ? w + 1 : p->max_weight);",
-                        "W[idx] = (uint8_t)(w + 1);"),
-    "depth_in_cm": ("float d = (float)D * 0.001f;\n                float sdf",
-                    "float d = (float)D * 0.01f;\n                float sdf"),
+    "plain_mean": ("*Fv = fmaf(*Fv, wf, t) / (wf + 1.0f);", "*Fv = (*Fv + t) * 0.5f;"),
+    "weight_uncapped": ("*Wv = (uint8_t)(w + 1 < p->max_weight ? w + 1 : p->max_weight);",
+                        "*Wv = (uint8_t)(w + 1);"),
+    "depth_in_cm": ("float d = (float)D * 0.001f;\n    float sdf",
+                    "float d = (float)D * 0.01f;\n    float sdf"),
     "no_sigma_gate": ("if (dist2 > fr->sigma2) return 0;", ""),
     "no_band_gate": ("if (!(fabsf(Ft) <= p->band)) return 0;", ""),
     "extrinsic_translation_flipped": ("rigid(fr->Rc, fr->tc, Pc[0], Pc[1], Pc[2], Ph);",
@@ -44,7 +44,8 @@ MUTANTS = {
     "eq10_additive": ("uint32_t wn = wp + (wq * (255u - wp) + 127u) / 255u;",
                       "uint32_t wn = wp + wq > 255u ? 255u : wp + wq;"),
     "no_08_gate": ("if (!(5u * wq > 4u * wp)) return 0;", ""),
-    "unobserved_corner_used": ("if (W[idx] == 0) return 0;", ""),
+    "unobserved_corner_used": ("if (corner(ctx, i0[0] + dx, i0[1] + dy, i0[2] + dz, &f) == 0) return 0;",
+                               "corner(ctx, i0[0] + dx, i0[1] + dy, i0[2] + dz, &f);"),
 }
 
 

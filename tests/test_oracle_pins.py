@@ -486,3 +486,29 @@ def test_brute_force_tiny_volumes_match_binary64(oracle_lib, seed, sample_mode):
     np.testing.assert_array_equal(o.colour_rgb[okc], m.C[okc])
     assert (o.W > 0).sum() > 50
     assert (o.colour_weight > 0).sum() > 20
+
+
+@pytest.mark.parametrize("colour_mode", [0, 1])
+def test_sampled_replay_equals_the_dense_oracle(oracle_lib, colour_mode):
+    """The sampled replay used for full-size parity applies the same per-voxel
+    updates as the dense oracle: on samples chosen from the inputs (tests/
+    samples.py) it gives the dense oracle's values exactly, and the geometry
+    sample holds every corner the colour band gate reads."""
+    from paper_1602_06645_gb300 import synth
+    from samples import scan_samples
+    seq = synth.sequence_small(n_frames=4, dims_geo=48, ratio=2)
+    geo, col = scan_samples(seq, range(4), n_col=3000, n_geo=4000, seed=5)
+    kw = dict(colour_mode=colour_mode)
+    o = oracle.Oracle(seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, seq.max_weight, **kw)
+    s = oracle.SparseOracle(geo, col, seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, seq.max_weight, **kw)
+    for f in range(4):
+        d, c = seq.frame(f)
+        o.integrate(d, c, seq.K_depth, seq.K_rgb, seq.poses[f], seq.T_depth_rgb)
+        assert s.integrate(d, c, seq.K_depth, seq.K_rgb, seq.poses[f], seq.T_depth_rgb) == 0
+    gi, ci = s.geo_index.astype(np.int64), s.col_index.astype(np.int64)
+    np.testing.assert_array_equal(o.F.reshape(-1)[gi].view(np.uint32), s.F.view(np.uint32))
+    np.testing.assert_array_equal(o.W.reshape(-1)[gi], s.W)
+    np.testing.assert_array_equal(o.C.reshape(-1)[ci], s.C)
+    # the samples exercise the gates: most colour samples were coloured, some were not
+    w = s.C >> 24
+    assert 0.15 < (w > 0).mean() < 0.99 and (s.W > 0).mean() > 0.2 and (s.W == 0).any()
