@@ -1,0 +1,84 @@
+"""Parity at full size: the 512^3 geometry / 1024^3 colour scan, run exactly
+as the benchmark runs it (frames resident on the device, culling on, the
+caller's stream), compared with the oracle on sampled voxels.
+
+The oracle replays the same frames on a sample of voxels chosen from the
+inputs (tests/samples.py): weights and colours must match bit for bit, the
+TSDF within 1e-5.  Properties that hold for every voxel are checked over the
+whole volumes on the device.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from samples import scan_samples
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1602_06645_gb300 as T  # noqa: E402
+from paper_1602_06645_gb300 import synth  # noqa: E402
+
+NT = os.cpu_count() or 1
+F_TOL = 1e-5
+N_FRAMES, STRIDE = 30, 10
+
+
+@pytest.fixture(scope="module", params=["plain", "paper_normal"])
+def fullsize(request):
+    kw = {"plain": {}, "paper_normal": dict(colour_mode=1)}[request.param]
+    seq = synth.sequence_scan(n_frames=N_FRAMES, frame_stride=STRIDE)
+    geo, col = scan_samples(seq, range(0, N_FRAMES, 3), n_col=24000, n_geo=40000, seed=11)
+    s = oracle.SparseOracle(geo, col, seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, seq.max_weight,
+                            n_threads=NT, **kw)
+    stream = torch.cuda.current_stream()
+    vol = T.Volume(seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, seq.max_weight, stream=stream.cuda_stream,
+                   **kw)
+    missing = 0
+    for f in range(N_FRAMES):
+        d, c = seq.frame(f)
+        missing += s.integrate(d, c, seq.K_depth, seq.K_rgb, seq.poses[f], seq.T_depth_rgb)
+        dd, cd = torch.from_numpy(d.view(np.int16)).cuda(), torch.from_numpy(c).cuda()
+        vol.integrate(dd, cd, seq.K_depth, seq.K_rgb, seq.poses[f], seq.T_depth_rgb)
+    F, W, C = vol.read_torch()
+    gi = torch.from_numpy(s.geo_index.astype(np.int64)).cuda()
+    ci = torch.from_numpy(s.col_index.astype(np.int64)).cuda()
+    out = dict(seq=seq, s=s, missing=missing, F=F.reshape(-1)[gi].cpu().numpy(), W=W.reshape(-1)[gi].cpu().numpy(),
+               C=C.reshape(-1)[ci].cpu().numpy().view(np.uint32), Fd=F, Wd=W, Cd=C, info=vol.info())
+    yield out
+    vol.close()
+
+
+def test_sampled_geometry_matches_the_oracle(fullsize):
+    s = fullsize["s"]
+    assert fullsize["missing"] == 0
+    np.testing.assert_array_equal(fullsize["W"], s.W)
+    dF = np.abs(fullsize["F"] - s.F)
+    assert dF.max() <= F_TOL, dF.max()
+    assert (s.W > 0).sum() > 10000 and (s.W == 0).sum() > 1000
+
+
+def test_sampled_colours_match_the_oracle(fullsize):
+    s = fullsize["s"]
+    bad = np.nonzero(fullsize["C"] != s.C)[0]
+    assert bad.size == 0, "%d of %d colour samples differ, first at linear %d: gpu %08x oracle %08x" % (
+        bad.size, s.C.size, int(s.col_index[bad[0]]), int(fullsize["C"][bad[0]]), int(s.C[bad[0]]))
+    w = s.C >> 24
+    assert (w > 0).sum() > 4000 and (w > 1).sum() > 1000
+
+
+def test_whole_volume_invariants(fullsize):
+    """For every voxel: weights within the cap, the TSDF in [-1, 1], and a
+    voxel never observed keeps TSDF 0 and colour 0."""
+    seq, F, W, C = fullsize["seq"], fullsize["Fd"], fullsize["Wd"], fullsize["Cd"]
+    assert int(W.max()) <= seq.max_weight
+    assert bool(torch.isfinite(F).all()) and float(F.abs().max()) <= 1.0
+    assert not bool(F[W == 0].any())
+    wc = (C >> 24) & 0xFF
+    assert int(wc.max()) <= seq.max_weight
+    assert not bool((C[wc == 0] != 0).any())
+    assert fullsize["info"].frames == N_FRAMES
