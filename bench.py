@@ -43,7 +43,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="scan",
-                    help="scan (512^3/1024^3) | small (128^3/256^3) | sweep256 | sweep512 | sweep768 | sweep1024")
+                    help="scan (512^3/1024^3) | small (128^3/256^3) | sweep256 | sweep512 | sweep768 | sweep1024 | "
+                         "scan_r1 | batched (64 scans) | adjoint (256^3/512^3, 20 frames)")
     ap.add_argument("--dense", action="store_true", help="culling off (dense sweep of every brick)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -361,10 +362,214 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------ batched -----
+def autotune_cache_path():
+    base = os.environ.get("TSDF_AUTOTUNE_CACHE")
+    if base:
+        return base
+    root = os.environ.get("XDG_CACHE_HOME", os.path.join(os.path.expanduser("~"), ".cache"))
+    return os.path.join(root, "paper_1602_06645_gb300", "autotune.json")
+
+
+def tuned_schedule(batch, frames, key):
+    """Blocks per SM for this batch: from the cache when the device and the
+    batch's shape were tuned before, else from the native autotuner."""
+    path = autotune_cache_path()
+    try:
+        with open(path) as f:
+            cache = json.load(f)
+    except Exception:
+        cache = {}
+    if key in cache:
+        batch.set_schedule(int(cache[key]["blocks_per_sm"]), True)
+        return cache[key], True
+    best, ms = batch.autotune(frames, rounds=3)
+    cache[key] = {"blocks_per_sm": best, "ms_per_candidate": ms}
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        with open(path, "w") as f:
+            json.dump(cache, f, indent=1)
+    except Exception:
+        pass
+    return cache[key], False
+
+
+def run_batched(args):
+    """64 independent scans (geometry edges log-uniform in 64..384, colour 2x,
+    720p RGB): one persistent graph-captured launch per step against 64
+    sequential tsdf_integrate calls, on the same frames."""
+    import hashlib
+
+    import torch
+    import paper_1602_06645_gb300 as T
+    from paper_1602_06645_gb300 import synth
+
+    torch.cuda.set_device(0)
+    T.load()
+    n_scans = int(os.environ.get("BATCH_SCANS", "64"))
+    nf = args.warmup + args.steps
+    edges = synth.batched_edges(n_scans)
+    t0 = time.perf_counter()
+    data = []
+    for i, e in enumerate(edges):
+        seq = synth.sequence_batched_scan(i, n_frames=nf, edge=e)
+        frames = []
+        for f in range(nf):
+            d, c = seq.frame(f)
+            frames.append((torch.from_numpy(d.view(np.int16)).cuda(), torch.from_numpy(c).cuda(), seq.K_depth,
+                           seq.K_rgb, seq.poses[f], seq.T_depth_rgb))
+        data.append((seq, frames))
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    nominal = sum(int(np.prod(s.dims_geo)) + int(np.prod(s.dims_col)) for s, _ in data)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def timed(step_fn):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for f in range(args.warmup):
+            step_fn(f)
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step_fn(args.warmup + i)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        return float(sum(a.elapsed_time(b) for a, b in ev))
+
+    # batched
+    vols = [T.Volume(s.dims_geo, s.dims_col, s.voxel_size, s.mu, s.max_weight, stream=stream.cuda_stream)
+            for s, _ in data]
+    batch = T.Batch(vols)
+    key = "%s|%s" % (torch.cuda.get_device_name(0), hashlib.sha1(json.dumps(edges).encode()).hexdigest()[:12])
+    sched, cached = tuned_schedule(batch, [fr[0] for _, fr in data], key)
+    ms_batched = timed(lambda f: batch.integrate([fr[f] for _, fr in data]))
+    batch.synchronize()
+    stats_b = [v.stats() for v in vols]
+    batch.close()
+    for v in vols:
+        v.close()
+    # sequential per-scan launches on fresh volumes, same frames
+    vols = [T.Volume(s.dims_geo, s.dims_col, s.voxel_size, s.mu, s.max_weight, stream=stream.cuda_stream)
+            for s, _ in data]
+
+    def seq_step(f):
+        for v, (_, fr) in zip(vols, data):
+            v.integrate(*fr[f])
+
+    ms_seq = timed(seq_step)
+    for v in vols:
+        v.close()
+    K = max(args.steps, 1)
+    line = {
+        "metric": "voxel-updates/s (nominal, geo+colour), batched scans", "value": nominal * K / (ms_batched / 1e3),
+        "unit": "voxel-updates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_batched / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+u8", "data": "synthetic",
+        "config": {"workload": "batched_%d_scans" % n_scans, "edges": edges, "rgb": "1280x720", "depth": "640x480",
+                   "l2": "flushed between steps (256 MiB write)", "schedule_blocks_per_sm": sched["blocks_per_sm"],
+                   "schedule_from_cache": cached, "cuda_graph": True},
+        "sequential": {"value": nominal * K / (ms_seq / 1e3), "ms_per_step": ms_seq / K,
+                       "launches_per_step": 6 * n_scans},
+        "speedup_vs_sequential": ms_seq / ms_batched,
+        "scan_frames_per_s": n_scans * K / (ms_batched / 1e3),
+        "gpu_launches": K,
+        "autotune_ms_per_candidate": sched.get("ms_per_candidate"),
+        "updated_per_step": {"geo": sum(s.total_geo_updated for s in stats_b) / K,
+                             "col": sum(s.total_col_updated for s in stats_b) / K},
+        "frame_generation_s": gen_s,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ adjoint -----
+def run_adjoint(args):
+    """Photometric adjoint at 256^3 / 512^3 with 20 frames of 1920x1080: gate
+    recording, then forward + backward per step, against the plain fusion of
+    the same 20 frames."""
+    import torch
+    import paper_1602_06645_gb300 as T
+    from paper_1602_06645_gb300 import synth
+    from paper_1602_06645_gb300.adjoint import Adjoint
+
+    torch.cuda.set_device(0)
+    T.load()
+    n_frames = 20
+    seq = synth.sequence_adjoint(n_frames=n_frames)
+    frames = [seq.frame(f) for f in range(n_frames)]
+    stream = torch.cuda.current_stream()
+    depth = [torch.from_numpy(d.view(np.int16)).cuda() for d, _ in frames]
+    rgb8 = [torch.from_numpy(c).cuda() for _, c in frames]
+    images = torch.stack([c.float() for c in rgb8]).contiguous()
+
+    def ev_time(fn, reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    # plain fusion of the 20 frames (fresh volume each repetition)
+    def plain():
+        v = T.Volume(seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, seq.max_weight, stream=stream.cuda_stream)
+        for f in range(n_frames):
+            v.integrate(depth[f], rgb8[f], seq.K_depth, seq.K_rgb, seq.poses[f], seq.T_depth_rgb)
+        v.synchronize()
+        v.close()
+
+    plain()
+    ms_plain = ev_time(plain, 3)
+    vol = T.Volume(seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, seq.max_weight, stream=stream.cuda_stream)
+    adj = Adjoint(vol, n_frames, max_pairs=1 << 26)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for f in range(n_frames):
+        adj.record(depth[f], seq.K_depth, seq.poses[f])
+    nv = adj.finalize()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms_record = t0.elapsed_time(t1)
+    K4 = np.array([seq.K_rgb[0, 0], seq.K_rgb[1, 1], seq.K_rgb[0, 2], seq.K_rgb[1, 2]], np.float32)
+    Tm = np.asarray(seq.T_depth_rgb, np.float32)
+    gI = torch.zeros_like(images)
+    C, n = adj.forward(images, K4, Tm)
+    target = C.detach() + 1.0
+
+    def fwd_bwd():
+        C, n = adj.forward(images, K4, Tm)
+        adj.backward(images, K4, Tm, (2.0 * (C - target)).contiguous(), gI)
+
+    for _ in range(args.warmup):
+        fwd_bwd()
+    ms_fb = ev_time(fwd_bwd, max(args.steps, 1))
+    ms_f = ev_time(lambda: adj.forward(images, K4, Tm), max(args.steps, 1))
+    vox, fr = adj.pairs()
+    line = {
+        "metric": "adjoint forward+backward time (20 frames, 256^3/512^3)", "value": ms_fb, "unit": "ms",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_fb, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": seq.name, "frames": n_frames, "rgb": "%dx%d" % seq.rgb_size,
+                   "voxels": nv, "pairs": int(len(vox))},
+        "forward_ms": ms_f, "record_ms": ms_record, "plain_fusion_20_frames_ms": ms_plain,
+        "pairs_per_s_fwd_bwd": len(vox) / (ms_fb / 1e3),
+    }
+    adj.close()
+    vol.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
+    elif args.workload == "adjoint":
+        run_adjoint(args)
     else:
         run_ours(args)
 
