@@ -47,7 +47,8 @@ def fullsize(request):
     F, W, C = vol.read_torch()
     gi = torch.from_numpy(s.geo_index.astype(np.int64)).cuda()
     ci = torch.from_numpy(s.col_index.astype(np.int64)).cuda()
-    out = dict(mode=request.param, seq=seq, s=s, missing=missing, F=F.reshape(-1)[gi].cpu().numpy(), W=W.reshape(-1)[gi].cpu().numpy(),
+    out = dict(mode=request.param, seq=seq, s=s, missing=missing, F=F.reshape(-1)[gi].cpu().numpy(),
+               W=W.reshape(-1)[gi].cpu().numpy(),
                C=C.reshape(-1)[ci].cpu().numpy().view(np.uint32), Fd=F, Wd=W, Cd=C, info=vol.info())
     yield out
     vol.close()
