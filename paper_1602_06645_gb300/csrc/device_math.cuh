@@ -40,6 +40,28 @@ __device__ __forceinline__ bool nearest_pixel(float u, float v, int W, int H, in
     return true;
 }
 
+// project() then nearest_pixel() without branches: true with the pixel's
+// linear index when the point is in front of the camera and its nearest pixel
+// is inside the image (same operations, same rounding); else false, pix = 0.
+__device__ __forceinline__ bool project_pixel(const float* K, int pinhole, float X, float Y, float Z, int W, int H,
+                                              int& pix) {
+    float xh, yh, zh;
+    if (pinhole) {
+        xh = fmaf(K[0], X, K[2] * Z);
+        yh = fmaf(K[4], Y, K[5] * Z);
+        zh = Z;
+    } else {
+        xh = fmaf(K[0], X, fmaf(K[1], Y, K[2] * Z));
+        yh = fmaf(K[3], X, fmaf(K[4], Y, K[5] * Z));
+        zh = fmaf(K[6], X, fmaf(K[7], Y, K[8] * Z));
+    }
+    const float rz = __frcp_rn(zh);
+    const float tu = xh * rz + 0.5f, tv = yh * rz + 0.5f;
+    const bool ok = zh > 0.0f && tu >= 0.0f && tu < (float)W && tv >= 0.0f && tv < (float)H;
+    pix = ok ? __float2int_rd(tv) * W + __float2int_rd(tu) : 0;
+    return ok;
+}
+
 // y = R x + t, row by row as fmaf(R0, x, fmaf(R1, y, fmaf(R2, z, t))).
 __device__ __forceinline__ void rigid(const float* R, const float* t, float x, float y, float z, float& X,
                                       float& Y, float& Z) {

@@ -171,9 +171,9 @@ __global__ void __launch_bounds__(256) k_bricks(FrameConst c, const BrickSummary
 // float4 groups q = l + 32 j (j = 0..3) of the brick: voxels 4q..4q+3, i.e.
 // x in {0..3} or {4..7}, y = (l >> 1) & 7, z = (l >> 4) + 2 j.  Each group of
 // the warp is 512 contiguous bytes of F and 128 of w.  The brick's F and w are
-// requested before the projections so their latency overlaps the arithmetic;
-// all 16 depth fetches of a lane are issued together.  The warp then writes
-// the brick summary (min/max F over observed voxels, min w).
+// requested before the projections so their latency overlaps the arithmetic.
+// The warp then writes the brick summary (min/max F over observed voxels,
+// min w, band flags).
 // TSDF update of geometry brick b by one warp (lane = lane index); adds the
 // number of updated voxels to count and 1 to changed if any voxel changed.
 template <bool PINHOLE, bool FREE_SPACE>
@@ -191,112 +191,89 @@ __device__ __forceinline__ void geometry_brick(const FrameConst& c, const Volume
         f[j] = *reinterpret_cast<const float4*>(Fb + 128 * j);
         wv[j] = *reinterpret_cast<const uint32_t*>(Wb + 128 * j);
     }
-    const int gy = by * BRICK + ly;
+    const int gx0 = bx * BRICK + lx, gy = by * BRICK + ly;
+    const bool yin = gy < c.ng[1];
     const float py = fmaf((float)gy + 0.5f, c.s_g, c.origin[1]);
     float px[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) px[i] = fmaf((float)(bx * BRICK + lx + i) + 0.5f, c.s_g, c.origin[0]);
+    for (int i = 0; i < 4; ++i) px[i] = fmaf((float)(gx0 + i) + 0.5f, c.s_g, c.origin[0]);
+    // min / max of F over this lane's observed voxels: all of them, and those
+    // on the brick faces x = lx + {0, 3} and z = lz + {0, 6} (band flags)
     float fmn = FLT_MAX, fmx = -FLT_MAX;
-    uint32_t wmn = 0xFFFFFFFFu, upd_all = 0, lom = 0, him = 0;
-    const float lo_thr = c.band + CELL_EPS, hi_thr = -c.band - CELL_EPS;
-    // two halves of 8 voxels (groups j = 2h, 2h + 1) keep the live set small
+    float mn_x0 = FLT_MAX, mx_x0 = -FLT_MAX, mn_x3 = FLT_MAX, mx_x3 = -FLT_MAX;
+    float mn_z0 = FLT_MAX, mx_z0 = -FLT_MAX, mn_z3 = FLT_MAX, mx_z3 = -FLT_MAX;
+    uint32_t wmn = 0xFFFFFFFFu, nupd = 0;
+    // Straight-line code per voxel: a voxel outside the volume or the image
+    // reads depth pixel 0 and is masked, so every depth fetch is unconditional
+    // and the compiler can issue them together.
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        int pix[8];
-        float Zc[8];
-        uint32_t inb = 0;
+    for (int j = 0; j < 4; ++j) {
+        const int gz = bz * BRICK + lz + 2 * j;
+        const bool zin = yin && gz < c.ng[2];
+        const float pz = fmaf((float)gz + 0.5f, c.s_g, c.origin[2]);
+        const float B0 = fmaf(c.R[1], py, fmaf(c.R[2], pz, c.t[0]));
+        const float B1 = fmaf(c.R[4], py, fmaf(c.R[5], pz, c.t[1]));
+        const float B2 = fmaf(c.R[7], py, fmaf(c.R[8], pz, c.t[2]));
+        float fv[4] = {f[j].x, f[j].y, f[j].z, f[j].w};
+        uint32_t wn = wv[j];
+        bool gupd = false;
 #pragma unroll
-        for (int jj = 0; jj < 2; ++jj) {
-            const int gz = bz * BRICK + lz + 2 * (2 * h + jj);
-            const float pz = fmaf((float)gz + 0.5f, c.s_g, c.origin[2]);
-            const float B0 = fmaf(c.R[1], py, fmaf(c.R[2], pz, c.t[0]));
-            const float B1 = fmaf(c.R[4], py, fmaf(c.R[5], pz, c.t[1]));
-            const float B2 = fmaf(c.R[7], py, fmaf(c.R[8], pz, c.t[2]));
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int k = 4 * jj + i;
-                pix[k] = -1;
-                Zc[k] = 0.0f;
-                if (!(gy < c.ng[1] && gz < c.ng[2] && bx * BRICK + lx + i < c.ng[0])) continue;
-                inb |= 1u << k;
-                const float X = fmaf(c.R[0], px[i], B0), Y = fmaf(c.R[3], px[i], B1), Z = fmaf(c.R[6], px[i], B2);
-                float u, v;
-                int iu, iv;
-                if (!project(c.Kd, PINHOLE, X, Y, Z, u, v)) continue;
-                if (!nearest_pixel(u, v, c.dw, c.dh, iu, iv)) continue;
-                pix[k] = iv * c.dw + iu;
-                Zc[k] = Z;
+        for (int i = 0; i < 4; ++i) {
+            const bool valid = zin && gx0 + i < c.ng[0];
+            const float X = fmaf(c.R[0], px[i], B0), Y = fmaf(c.R[3], px[i], B1), Z = fmaf(c.R[6], px[i], B2);
+            int pix;
+            const bool seen = project_pixel(c.Kd, PINHOLE, X, Y, Z, c.dw, c.dh, pix) && valid;
+            uint32_t D = __ldg(depth + (seen ? pix : 0));
+            D = seen ? D : 0u;
+            const float d = (float)D * 0.001f;
+            const float sdf = d - Z;
+            const bool up = D != 0u && !(sdf < -c.mu) && (FREE_SPACE || !(sdf > c.mu));
+            uint32_t w = (wn >> (8 * i)) & 0xFFu;
+            if (up) {
+                const float t = fminf(1.0f, sdf * c.inv_mu);
+                const float wf = (float)w;
+                fv[i] = __fdiv_rn(fmaf(fv[i], wf, t), wf + 1.0f);
+                w = min(w + 1u, (uint32_t)c.max_weight);
+                wn = (wn & ~(0xFFu << (8 * i))) | (w << (8 * i));
             }
+            gupd |= up;
+            nupd += up ? 1u : 0u;
+            wmn = min(wmn, valid ? w : 0xFFFFFFFFu);
+            const bool obs = valid && w != 0u;
+            const float fl = obs ? fv[i] : FLT_MAX, fh = obs ? fv[i] : -FLT_MAX;
+            fmn = fminf(fmn, fl);
+            fmx = fmaxf(fmx, fh);
+            if (i == 0) { mn_x0 = fminf(mn_x0, fl); mx_x0 = fmaxf(mx_x0, fh); }
+            if (i == 3) { mn_x3 = fminf(mn_x3, fl); mx_x3 = fmaxf(mx_x3, fh); }
+            if (j == 0) { mn_z0 = fminf(mn_z0, fl); mx_z0 = fmaxf(mx_z0, fh); }
+            if (j == 3) { mn_z3 = fminf(mn_z3, fl); mx_z3 = fmaxf(mx_z3, fh); }
         }
-        uint32_t D[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) D[k] = pix[k] >= 0 ? (uint32_t)__ldg(depth + pix[k]) : 0u;
-        uint32_t upd = 0;
-        float tv[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            tv[k] = 0.0f;
-            if (D[k] == 0u) continue;
-            const float d = (float)D[k] * 0.001f;
-            const float sdf = d - Zc[k];
-            if (sdf < -c.mu) continue;
-            if (!FREE_SPACE && sdf > c.mu) continue;
-            tv[k] = fminf(1.0f, sdf * c.inv_mu);
-            upd |= 1u << k;
-        }
-        upd_all |= upd << (8 * h);
-#pragma unroll
-        for (int jj = 0; jj < 2; ++jj) {
-            const int j = 2 * h + jj;
-            float fv[4] = {f[j].x, f[j].y, f[j].z, f[j].w};
-            uint32_t wn = wv[j];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int k = 4 * jj + i;
-                uint32_t w = (wv[j] >> (8 * i)) & 0xFFu;
-                if (upd & (1u << k)) {
-                    const float wf = (float)w;
-                    fv[i] = __fdiv_rn(fmaf(fv[i], wf, tv[k]), wf + 1.0f);
-                    w = min(w + 1u, (uint32_t)c.max_weight);
-                    wn = (wn & ~(0xFFu << (8 * i))) | (w << (8 * i));
-                }
-                if (inb & (1u << k)) {
-                    wmn = min(wmn, w);
-                    if (w) {
-                        fmn = fminf(fmn, fv[i]);
-                        fmx = fmaxf(fmx, fv[i]);
-                    }
-                    lom |= (w != 0u && fv[i] <= lo_thr ? 1u : 0u) << (4 * j + i);
-                    him |= (w != 0u && fv[i] >= hi_thr ? 1u : 0u) << (4 * j + i);
-                }
-            }
-            if ((upd >> (4 * jj)) & 0xFu) {
-                *reinterpret_cast<float4*>(Fb + 128 * j) = make_float4(fv[0], fv[1], fv[2], fv[3]);
-                *reinterpret_cast<uint32_t*>(Wb + 128 * j) = wn;
-            }
+        if (gupd) {
+            *reinterpret_cast<float4*>(Fb + 128 * j) = make_float4(fv[0], fv[1], fv[2], fv[3]);
+            *reinterpret_cast<uint32_t*>(Wb + 128 * j) = wn;
         }
     }
-    count += __popc(upd_all);
+    count += nupd;
     // bricks where nothing changed keep their summary
-    if (!__any_sync(0xffffffffu, upd_all != 0u)) return;
+    if (!__any_sync(0xffffffffu, nupd != 0u)) return;
     ++changed;
+    // band flags (see BrickSummary): this lane's voxels sit at x = lx + i,
+    // y = ly, z = lz + 2 j, so it holds the -x face when lx = 0 (i = 0), +x
+    // when lx = 4 (i = 3), -y / +y when ly = 0 / 7, -z when lz = 0 (j = 0)
+    // and +z when lz = 1 (j = 3)
+    const float lo_thr = c.band + CELL_EPS, hi_thr = -c.band - CELL_EPS;
+    auto lohi = [&](bool on, float mn, float mx) -> uint32_t {
+        return on ? (mn <= lo_thr ? 1u : 0u) | (mx >= hi_thr ? 2u : 0u) : 0u;
+    };
+    uint32_t bflags = lohi(true, fmn, fmx) | lohi(lx == 0, mn_x0, mx_x0) << 2 | lohi(lx == 4, mn_x3, mx_x3) << 4 |
+                      lohi(ly == 0, fmn, fmx) << 6 | lohi(ly == 7, fmn, fmx) << 8 |
+                      lohi(lz == 0, mn_z0, mx_z0) << 10 | lohi(lz == 1, mn_z3, mx_z3) << 12;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         fmn = fminf(fmn, __shfl_xor_sync(0xffffffffu, fmn, o));
         fmx = fmaxf(fmx, __shfl_xor_sync(0xffffffffu, fmx, o));
     }
     wmn = __reduce_min_sync(0xffffffffu, wmn);
-    // band flags (see BrickSummary): voxel 4 j + i of this lane sits at
-    // x = lx + i, y = ly, z = lz + 2 j
-    uint32_t bflags = 0;
-    {
-        const uint32_t fm[6] = {lx == 0 ? 0x1111u : 0u, lx == 4 ? 0x8888u : 0u, ly == 0 ? 0xFFFFu : 0u,
-                                ly == 7 ? 0xFFFFu : 0u, lz == 0 ? 0x000Fu : 0u, lz == 1 ? 0xF000u : 0u};
-        bflags = (lom ? 1u : 0u) | (him ? 2u : 0u);
-#pragma unroll
-        for (int f = 0; f < 6; ++f)
-            bflags |= ((lom & fm[f]) ? 1u : 0u) << (2 + 2 * f) | ((him & fm[f]) ? 1u : 0u) << (3 + 2 * f);
-    }
     bflags = __reduce_or_sync(0xffffffffu, bflags);
     if (lane == 0) {
         BrickSummary sm;
