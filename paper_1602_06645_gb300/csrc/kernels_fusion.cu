@@ -360,14 +360,15 @@ __global__ void __launch_bounds__(256) k_colour_list(FrameConst c, const BrickSu
 // axis: 16 bb Nc <= (2k + 1) Ng < 16 (bb + 1) Nc (exact integer arithmetic, so
 // every colour voxel belongs to exactly one geometry brick).
 __device__ __forceinline__ void owned_range(int bb, int ng, int nc, int& k0, int& k1) {
-    auto lo = [&](long long B) -> long long {  // smallest k with (2k+1) ng >= 16 B nc
-        long long num = 16ll * B * nc - ng;  // 2k ng >= num
+    auto lo = [&](int B) -> int {  // smallest k with (2k+1) ng >= 16 B nc
+        const long long num = 16ll * B * nc - ng;  // 2k ng >= num
         if (num <= 0) return 0;
-        long long den = 2ll * ng;
-        return (num + den - 1) / den;
+        const unsigned den = 2u * (unsigned)ng;
+        if (num < (1ll << 31)) return (int)(((unsigned)num + den - 1u) / den);  // 32-bit division when it fits
+        return (int)((num + den - 1) / (long long)den);
     };
-    k0 = (int)min((long long)nc, lo(bb));
-    k1 = (int)min((long long)nc, lo(bb + 1));  // exclusive
+    k0 = min(nc, lo(bb));
+    k1 = min(nc, lo(bb + 1));  // exclusive
 }
 
 // HD sample (Eq. 9): nearest pixel, or bilinear over the 2x2 neighbourhood
@@ -544,20 +545,20 @@ __device__ __forceinline__ int64_t tile_offset(const ColourSlot& S, int tx, int 
     return (int64_t)nb * BRICK_VOX + (lz * BRICK + ly) * BRICK + lx;
 }
 
-__device__ __forceinline__ int ceil_log2(int v) {
-    int s = 0;
-    while ((1 << s) < v) ++s;
-    return s;
+// The band kernel's overflow path, kept out of line: inlined, its registers
+// and code weigh on the whole band kernel although it almost never runs.
+__device__ __noinline__ bool colour_after_band_outlined(const FrameConst& c, uint32_t* __restrict__ C,
+                                                        const uint16_t* __restrict__ depth,
+                                                        const uint8_t* __restrict__ rgb, int kx, int ky, int kz) {
+    return colour_after_band(c, C, depth, rgb, kx, ky, kz);
 }
 
-// Move n staged records to the global list; those beyond its capacity are
-// finished here.  Returns the number of colour voxels updated here.
-__device__ uint32_t flush_records(const FrameConst& c, const Volumes& vol, const uint16_t* __restrict__ depth,
-                                  const uint8_t* __restrict__ rgb, const Scratch& scr, ColourSlot& S, uint32_t n,
-                                  int lane) {
-    uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(&scr.ctr->n_vox, n);
-    base = __shfl_sync(0xffffffffu, base, 0);
+// Write n staged records to the global list from slot `base` on (warp-
+// uniform); those beyond its capacity are finished here.  Returns the number
+// of colour voxels updated here.
+__device__ uint32_t write_records(const FrameConst& c, const Volumes& vol, const uint16_t* __restrict__ depth,
+                                  const uint8_t* __restrict__ rgb, const Scratch& scr, const ColourSlot& S,
+                                  uint32_t n, uint32_t base, int lane) {
     uint32_t done = 0;
     for (uint32_t i = lane; i < n; i += 32) {
         const uint2 r = S.out[i];
@@ -565,11 +566,21 @@ __device__ uint32_t flush_records(const FrameConst& c, const Volumes& vol, const
             scr.vox[base + i] = r;
         else if (c.record_mode)
             atomicOr(scr.err, ERR_RECORD_OVERFLOW);  // recording has no fallback; the host reports it
-        else if (colour_after_band(c, vol.C, depth, rgb, (int)(r.x & 0xFFFFu), (int)(r.x >> 16), (int)r.y))
+        else if (colour_after_band_outlined(c, vol.C, depth, rgb, (int)(r.x & 0xFFFFu), (int)(r.x >> 16), (int)r.y))
             ++done;
     }
     __syncwarp();
     return done;
+}
+
+// Claim slots for n staged records and write them.
+__device__ uint32_t flush_records(const FrameConst& c, const Volumes& vol, const uint16_t* __restrict__ depth,
+                                  const uint8_t* __restrict__ rgb, const Scratch& scr, const ColourSlot& S,
+                                  uint32_t n, int lane) {
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&scr.ctr->n_vox, n);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    return write_records(c, vol, depth, rgb, scr, S, n, base, lane);
 }
 
 // Band gate of the colour voxels owned by geometry brick b, by one warp with
@@ -705,20 +716,14 @@ __device__ __forceinline__ void band_brick(const FrameConst& c, const Volumes& v
 
     // 3. active cells, compacted
     uint32_t xmask = 0;
-    int shx, shy, shz;
-    {
-        int mx = 0, my = 0, mz = 0;
+    int mx = 0, my = 0, mz = 0;  // most colour indices of one cell, per axis
 #pragma unroll
-        for (int cell = 0; cell < CELLS; ++cell) {
-            const int nx = S.end[0][cell] - S.start[0][cell];
-            xmask |= (nx > 0 ? 1u : 0u) << cell;
-            mx = max(mx, nx);
-            my = max(my, S.end[1][cell] - S.start[1][cell]);
-            mz = max(mz, S.end[2][cell] - S.start[2][cell]);
-        }
-        shx = ceil_log2(mx);
-        shy = ceil_log2(my);
-        shz = ceil_log2(mz);
+    for (int cell = 0; cell < CELLS; ++cell) {
+        const int nx = S.end[0][cell] - S.start[0][cell];
+        xmask |= (nx > 0 ? 1u : 0u) << cell;
+        mx = max(mx, nx);
+        my = max(my, S.end[1][cell] - S.start[1][cell]);
+        mz = max(mz, S.end[2][cell] - S.start[2][cell]);
     }
     uint32_t act[3];
     uint32_t total = 0;
@@ -766,44 +771,65 @@ __device__ __forceinline__ void band_brick(const FrameConst& c, const Volumes& v
     }
     __syncwarp();
 
-    // 4. band gate of each colour voxel of the active cells; records
-    const uint32_t sh = shx + shy + shz;
-    const uint32_t units = nact << sh;
+    // 4. band gate of the colour voxels of the active cells, one lane per
+    // cell: the x-lerps of an index jx serve every (jy, jz) of the cell and
+    // the y-lerps of (jx, jy) every jz (the same operations as one lerp chain
+    // per voxel).  Loops run to the warp-wide most indices per axis so the
+    // record ballots stay uniform.
     const uint32_t lanemask_lt = (1u << lane) - 1u;
     uint32_t nstage = 0;
-    for (uint32_t ub = 0; ub < units; ub += 32) {
-        const uint32_t u = ub + lane;
-        bool pass = false;
-        uint2 rec = make_uint2(0u, 0u);
-        if (u < units) {
-            const uint32_t cellid = S.cells[u >> sh];
-            const uint32_t sub = u & ((1u << sh) - 1u);
+    for (uint32_t cb = 0; cb < nact; cb += 32) {
+        const bool live = cb + lane < nact;
+        int sx = 0, ex = 0, sy = 0, ey = 0, sz = 0, ez = 0;
+        float q000 = 0.0f, q100 = 0.0f, q010 = 0.0f, q110 = 0.0f, q001 = 0.0f, q101 = 0.0f, q011 = 0.0f,
+              q111 = 0.0f;
+        if (live) {
+            const uint32_t cellid = S.cells[cb + lane];
             const int cx = cellid % CELLS, cy = (cellid / CELLS) % CELLS, cz = cellid / (CELLS * CELLS);
-            const int jx = S.start[0][cx] + (int)(sub & ((1u << shx) - 1u));
-            const int jy = S.start[1][cy] + (int)((sub >> shx) & ((1u << shy) - 1u));
-            const int jz = S.start[2][cz] + (int)(sub >> (shx + shy));
-            if (jx < S.end[0][cx] && jy < S.end[1][cy] && jz < S.end[2][cz]) {
-                const int o = (cz * TILE_G + cy) * TILE_G + cx;
-                const float fx = S.frac[0][jx], fy = S.frac[1][jy], fz = S.frac[2][jz];
-                const float c00 = lerp(S.F[o], S.F[o + 1], fx);
-                const float c10 = lerp(S.F[o + TILE_G], S.F[o + TILE_G + 1], fx);
-                const float c01 = lerp(S.F[o + TILE_G * TILE_G], S.F[o + TILE_G * TILE_G + 1], fx);
-                const float c11 =
-                    lerp(S.F[o + TILE_G * TILE_G + TILE_G], S.F[o + TILE_G * TILE_G + TILE_G + 1], fx);
-                const float c0 = lerp(c00, c10, fy);
-                const float c1 = lerp(c01, c11, fy);
-                const float Ft = lerp(c0, c1, fz);
-                pass = fabsf(Ft) <= c.band;
-                rec = make_uint2((uint32_t)(k0[0] + jx) | ((uint32_t)(k0[1] + jy) << 16), (uint32_t)(k0[2] + jz));
-            }
+            sx = S.start[0][cx];
+            ex = S.end[0][cx];
+            sy = S.start[1][cy];
+            ey = S.end[1][cy];
+            sz = S.start[2][cz];
+            ez = S.end[2][cz];
+            const int o = (cz * TILE_G + cy) * TILE_G + cx;
+            q000 = S.F[o];
+            q100 = S.F[o + 1];
+            q010 = S.F[o + TILE_G];
+            q110 = S.F[o + TILE_G + 1];
+            q001 = S.F[o + TILE_G * TILE_G];
+            q101 = S.F[o + TILE_G * TILE_G + 1];
+            q011 = S.F[o + TILE_G * TILE_G + TILE_G];
+            q111 = S.F[o + TILE_G * TILE_G + TILE_G + 1];
         }
-        const uint32_t m = __ballot_sync(full, pass);
-        if (pass) S.out[nstage + __popc(m & lanemask_lt)] = rec;
-        nstage += __popc(m);
-        if (nstage > STAGE - 32) {
-            __syncwarp();
-            count += flush_records(c, vol, depth, rgb, scr, S, nstage, lane);
-            nstage = 0;
+        for (int ix = 0; ix < mx; ++ix) {
+            const int jx = sx + ix;
+            const bool vx = live && jx < ex;
+            const float fx = S.frac[0][vx ? jx : 0];
+            const float c00 = lerp(q000, q100, fx), c10 = lerp(q010, q110, fx);
+            const float c01 = lerp(q001, q101, fx), c11 = lerp(q011, q111, fx);
+            for (int iy = 0; iy < my; ++iy) {
+                const int jy = sy + iy;
+                const bool vy = vx && jy < ey;
+                const float fy = S.frac[1][vy ? jy : 0];
+                const float c0 = lerp(c00, c10, fy), c1 = lerp(c01, c11, fy);
+                for (int iz = 0; iz < mz; ++iz) {
+                    const int jz = sz + iz;
+                    const bool vz = vy && jz < ez;
+                    const float fz = S.frac[2][vz ? jz : 0];
+                    const bool pass = vz && fabsf(lerp(c0, c1, fz)) <= c.band;
+                    const uint32_t m = __ballot_sync(full, pass);
+                    if (pass)
+                        S.out[nstage + __popc(m & lanemask_lt)] =
+                            make_uint2((uint32_t)(k0[0] + jx) | ((uint32_t)(k0[1] + jy) << 16), (uint32_t)(k0[2] + jz));
+                    nstage += __popc(m);
+                    if (nstage > STAGE - 32) {
+                        __syncwarp();
+                        count += flush_records(c, vol, depth, rgb, scr, S, nstage, lane);
+                        nstage = 0;
+                    }
+                }
+            }
         }
     }
     __syncwarp();
@@ -820,11 +846,13 @@ __global__ void __launch_bounds__(COL_THREADS, 5) k_colour_band(FrameConst c, Vo
     const unsigned full = 0xffffffffu;
     const uint32_t n = ctr->n_col;
     uint32_t count = 0, n_active = 0, n_cells = 0;
+    // the next item's index is claimed while the current one is processed
+    uint32_t next = 0;
+    if (lane == 0) next = atomicAdd(&ctr->col_next, 1u);
     for (;;) {
-        uint32_t item = 0;
-        if (lane == 0) item = atomicAdd(&ctr->col_next, 1u);
-        item = __shfl_sync(full, item, 0);
+        const uint32_t item = __shfl_sync(full, next, 0);
         if (item >= n) break;
+        if (lane == 0) next = atomicAdd(&ctr->col_next, 1u);
         band_brick(c, vol, depth, rgb, scr, S, scr.col_list[item], lane, count, n_active, n_cells);
         __syncwarp();
     }
