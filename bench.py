@@ -277,20 +277,27 @@ def run_ours(args):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     K = max(args.steps, 1)
     geo_bytes = 10.0 * st.total_geo_updated / K            # F (4 B) + w (1 B), read and written
-    col_bytes = (8.0 * st.total_col_updated                 # packed RGBW, read and written
-                 + 5.0 * 1000 * st.total_col_bricks) / K    # geometry tile (10^3 F + w) per colour brick
+    band_bytes = 5.0 * 1000 * st.total_col_bricks / K       # geometry tile (10^3 F + w) per candidate brick
+    vox_bytes = 8.0 * st.total_col_updated / K              # packed RGBW, read and written
     kern = {"geometry": (phases["geometry"] / K, geo_bytes),
-            "colour": ((phases["colour_cells"] + phases["colour"]) / K, col_bytes)}
+            "colour_band": (phases["colour_cells"] / K, band_bytes),
+            "colour_voxels": (phases["colour"] / K, vox_bytes)}
     dom = max(kern, key=lambda k: kern[k][0])
     ms_launch, bytes_launch = kern[dom]
     achieved = bytes_launch / (ms_launch / 1e3) / 1e9 if ms_launch > 0 else 0.0
-    traffic = None
+    # DRAM traffic from the committed ncu capture, scaled to this launch by the
+    # updated voxels; null when the kernel source changed since the capture
+    traffic, traffic_note = None, None
     try:
+        import hashlib
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             tr = json.load(f)
-        if tr.get("workload") == seq.name and tr.get("kernel") == dom and not args.dense:
-            traffic = tr.get("bytes_per_launch")
-    except Exception:
+        with open(os.path.join(ROOT, "paper_1602_06645_gb300", "csrc", "kernels_fusion.cu"), "rb") as f:
+            same_src = hashlib.sha256(f.read()).hexdigest() == tr.get("kernels_fusion_sha256")
+        if tr.get("workload") == seq.name and tr.get("kernel") == dom == "geometry" and same_src and not args.dense:
+            traffic = tr["bytes_per_unit"] * st.total_geo_updated / K
+            traffic_note = "ncu dram bytes per updated voxel (%s) x updated voxels per launch" % tr["source"]
+    except (OSError, ValueError, KeyError):
         pass
 
     result = {
@@ -310,7 +317,8 @@ def run_ours(args):
                       "geo_changed_bricks": st.total_geo_changed_bricks / K},
         "phase_ms_per_frame": {k: v / max(pframes, 1) for k, v in phases.items()},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": traffic, "bytes_per_launch": bytes_launch,
+                     "frac": achieved / hbm, "traffic": traffic, "traffic_source": traffic_note,
+                     "bytes_per_launch": bytes_launch,
                      "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                      else "fallback 6.8 TB/s"},
         "gpu_launches": 6 * args.steps,  # depth tiles, bricks, geometry, colour list, colour cells, colour voxels

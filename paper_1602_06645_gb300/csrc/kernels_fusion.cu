@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(256) k_bricks(FrameConst c, const BrickSummary
 // min w, band flags).
 // TSDF update of geometry brick b by one warp (lane = lane index); adds the
 // number of updated voxels to count and 1 to changed if any voxel changed.
-template <bool PINHOLE, bool FREE_SPACE>
+template <bool PINHOLE, bool FREE_SPACE, bool ALIGNED = false>
 __device__ __forceinline__ void geometry_brick(const FrameConst& c, const Volumes& vol,
                                                const uint16_t* __restrict__ depth, uint32_t b, int lane,
                                                uint32_t& count, uint32_t& changed) {
@@ -219,7 +219,7 @@ __device__ __forceinline__ void geometry_brick(const FrameConst& c, const Volume
         bool gupd = false;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const bool valid = zin && gx0 + i < c.ng[0];
+            const bool valid = ALIGNED || (zin && gx0 + i < c.ng[0]);  // ALIGNED: dims are multiples of 8
             const float X = fmaf(c.R[0], px[i], B0), Y = fmaf(c.R[3], px[i], B1), Z = fmaf(c.R[6], px[i], B2);
             int pix;
             const bool seen = project_pixel(c.Kd, PINHOLE, X, Y, Z, c.dw, c.dh, pix) && valid;
@@ -285,7 +285,7 @@ __device__ __forceinline__ void geometry_brick(const FrameConst& c, const Volume
     }
 }
 
-template <bool PINHOLE, bool FREE_SPACE>
+template <bool PINHOLE, bool FREE_SPACE, bool ALIGNED>
 __global__ void __launch_bounds__(GEO_THREADS, 7) k_geometry(FrameConst c, Volumes vol, const uint16_t* __restrict__ depth,
                                                           Counters* __restrict__ ctr,
                                                           const uint32_t* __restrict__ list) {
@@ -295,10 +295,32 @@ __global__ void __launch_bounds__(GEO_THREADS, 7) k_geometry(FrameConst c, Volum
     const uint32_t n = ctr->n_geo;
     uint32_t count = 0, changed = 0;
     for (uint32_t item = warp; item < n; item += nwarps)
-        geometry_brick<PINHOLE, FREE_SPACE>(c, vol, depth, list[item], lane, count, changed);
+        geometry_brick<PINHOLE, FREE_SPACE, ALIGNED>(c, vol, depth, list[item], lane, count, changed);
     count = __reduce_add_sync(0xffffffffu, count);
     if (lane == 0 && count) atomicAdd(&ctr->geo_updated, (unsigned long long)count);
     if (lane == 0 && changed) atomicAdd(&ctr->n_geo_changed, changed);
+}
+
+// Launch the k_geometry instance for this frame's camera model, free-space
+// mode and volume shape (every dimension a multiple of 8: no bounds tests).
+cudaError_t launch_k_geometry(const FrameConst& c, const Volumes& v, const Scratch& s, const uint16_t* depth,
+                              int grid, cudaStream_t stream) {
+    const bool aligned = c.ng[0] % BRICK == 0 && c.ng[1] % BRICK == 0 && c.ng[2] % BRICK == 0;
+    const int key = (c.kd_pinhole ? 4 : 0) | (c.free_space ? 2 : 0) | (aligned ? 1 : 0);
+    switch (key) {
+#define TSDF_GEO_CASE(k, P, F, A) \
+    case k: k_geometry<P, F, A><<<grid, GEO_THREADS, 0, stream>>>(c, v, depth, s.ctr, s.geo_list); break;
+        TSDF_GEO_CASE(0, false, false, false)
+        TSDF_GEO_CASE(1, false, false, true)
+        TSDF_GEO_CASE(2, false, true, false)
+        TSDF_GEO_CASE(3, false, true, true)
+        TSDF_GEO_CASE(4, true, false, false)
+        TSDF_GEO_CASE(5, true, false, true)
+        TSDF_GEO_CASE(6, true, true, false)
+        TSDF_GEO_CASE(7, true, true, true)
+#undef TSDF_GEO_CASE
+    }
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------- colour list ----
@@ -1280,7 +1302,7 @@ cudaError_t launch_init_summaries(BrickSummary* summ, int64_t n, cudaStream_t st
 
 int geometry_blocks_per_sm() {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_geometry<true, true>, GEO_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_geometry<true, true, true>, GEO_THREADS, 0);
     return n > 0 ? n : 1;
 }
 
@@ -1311,14 +1333,7 @@ cudaError_t launch_frame(const FrameConst& c, const Volumes& v, const Scratch& s
     const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
     k_bricks<<<(nbt + 255) / 256, 256, 0, stream>>>(c, v.summ, s.depth_tiles, s.ctr, s.geo_list, s.vis_list);
     mark(2);
-    if (c.kd_pinhole && c.free_space)
-        k_geometry<true, true><<<grid_geo, GEO_THREADS, 0, stream>>>(c, v, depth, s.ctr, s.geo_list);
-    else if (c.kd_pinhole)
-        k_geometry<true, false><<<grid_geo, GEO_THREADS, 0, stream>>>(c, v, depth, s.ctr, s.geo_list);
-    else if (c.free_space)
-        k_geometry<false, true><<<grid_geo, GEO_THREADS, 0, stream>>>(c, v, depth, s.ctr, s.geo_list);
-    else
-        k_geometry<false, false><<<grid_geo, GEO_THREADS, 0, stream>>>(c, v, depth, s.ctr, s.geo_list);
+    launch_k_geometry(c, v, s, depth, grid_geo, stream);
     mark(3);
     unsigned gl = (nbt + 255) / 256;
     if (gl > 1024u) gl = 1024u;
@@ -1354,14 +1369,7 @@ cudaError_t launch_frame_record(const FrameConst& c, const Volumes& v, const Scr
     k_depth_tiles<<<tg, dim3(TILE_PX, TILE_PX), 0, stream>>>(c, depth, s.depth_tiles, s.ctr);
     const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
     k_bricks<<<(nbt + 255) / 256, 256, 0, stream>>>(c, v.summ, s.depth_tiles, s.ctr, s.geo_list, s.vis_list);
-    if (c.kd_pinhole && c.free_space)
-        k_geometry<true, true><<<g.geo, GEO_THREADS, 0, stream>>>(c, v, depth, s.ctr, s.geo_list);
-    else if (c.kd_pinhole)
-        k_geometry<true, false><<<g.geo, GEO_THREADS, 0, stream>>>(c, v, depth, s.ctr, s.geo_list);
-    else if (c.free_space)
-        k_geometry<false, true><<<g.geo, GEO_THREADS, 0, stream>>>(c, v, depth, s.ctr, s.geo_list);
-    else
-        k_geometry<false, false><<<g.geo, GEO_THREADS, 0, stream>>>(c, v, depth, s.ctr, s.geo_list);
+    launch_k_geometry(c, v, s, depth, g.geo, stream);
     unsigned gl = (nbt + 255) / 256;
     if (gl > 1024u) gl = 1024u;
     k_colour_list<<<gl, 256, 0, stream>>>(c, v.summ, s.ctr, s.vis_list, s.col_list);
