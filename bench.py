@@ -150,6 +150,20 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
+# ------------------------------------------------------- multi-rank ----
+def reduce_over_ranks(dist, device, max_values=(), sum_values=()):
+    """(max over ranks of each of max_values, sum over ranks of each of
+    sum_values); the identity when dist is None (one rank)."""
+    if dist is None:
+        return [float(v) for v in max_values], [float(v) for v in sum_values]
+    import torch
+    mx = torch.tensor([float(v) for v in max_values] or [0.0], dtype=torch.float64, device=device)
+    sm = torch.tensor([float(v) for v in sum_values] or [0.0], dtype=torch.float64, device=device)
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return mx.tolist()[:len(max_values)], sm.tolist()[:len(sum_values)]
+
+
 # ------------------------------------------------------- CPU oracle -----
 def oracle_sample(seq, frames, n_threads):
     """Time the oracle on the central 1/8 of both volumes (half of each edge)
@@ -264,12 +278,7 @@ def run_ours(args):
 
     nominal = nominal_voxels(seq)
     units = nominal * args.steps
-    if dist:
-        t = torch.tensor([total_ms, float(units)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        total_ms, units = float(tmax[0]), float(t[1])
+    (total_ms,), (units,) = reduce_over_ranks(dist, "cuda", [total_ms], [units])
     value = units / (total_ms / 1e3)
 
     # ---- roofline of the dominant kernel (algorithmic bytes / event time)
@@ -344,10 +353,7 @@ def run_ours(args):
             vol2.stats()  # device -> host read of the frame's counters (synchronising)
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t[0])
+        (e2e_s,), _ = reduce_over_ranks(dist, "cuda", [e2e_s])
         vol2.close()
         h2d = frames[0][0].nbytes + frames[0][1].nbytes
         result["e2e"] = {"value": units / e2e_s, "unit": "voxel-updates/s", "h2d_bytes_per_step": int(h2d),
