@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="scan",
                     help="scan (512^3/1024^3) | small (128^3/256^3) | sweep256 | sweep512 | sweep768 | sweep1024 | "
-                         "scan_r1 | batched (64 scans) | adjoint (256^3/512^3, 20 frames)")
+                         "scan_r1 | batched (64 scans) | adjoint (256^3/512^3, 20 frames) | <any of the first>_fused "
+                         "(one persistent launch per frame)")
     ap.add_argument("--dense", action="store_true", help="culling off (dense sweep of every brick)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -496,6 +497,73 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_fused(args):
+    """One scan through the single-launch form: a batch of one volume (all
+    phases of a frame in one persistent graph-captured launch), against the
+    six-kernel path on the same frames and a check that both give the same
+    volumes."""
+    import torch
+    import paper_1602_06645_gb300 as T
+
+    torch.cuda.set_device(0)
+    T.load()
+    base = args.workload[:-len("_fused")]
+    n = args.warmup + args.steps
+    seq = make_sequence(base, n, 0)
+    t0 = time.perf_counter()
+    frames = [(torch.from_numpy(d.view(np.int16)).cuda(), torch.from_numpy(c).cuda(), seq.K_depth, seq.K_rgb,
+               seq.poses[f], seq.T_depth_rgb) for f, (d, c) in enumerate(render_frames(seq, n))]
+    gen_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def timed(step_fn):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for f in range(args.warmup):
+            step_fn(f)
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step_fn(args.warmup + i)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        return float(sum(a.elapsed_time(b) for a, b in ev))
+
+    def volume():
+        return T.Volume(seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, seq.max_weight,
+                        stream=stream.cuda_stream)
+
+    vf = volume()
+    batch = T.Batch([vf])
+    key = "%s|fused|%s" % (torch.cuda.get_device_name(0), seq.name)
+    sched, cached = tuned_schedule(batch, [frames[0]], key)
+    ms_fused = timed(lambda f: batch.integrate([frames[f]]))
+    batch.synchronize()
+    vp = volume()
+    ms_plain = timed(lambda f: vp.integrate(*frames[f]))
+    vp.synchronize()
+    same = all(bool(torch.equal(a, b)) for a, b in zip(vf.read_torch(), vp.read_torch()))
+    batch.close()
+    vf.close()
+    vp.close()
+    K = max(args.steps, 1)
+    nominal = nominal_voxels(seq)
+    line = {
+        "metric": "voxel-updates/s (nominal, geo+colour), single-launch form", "value": nominal * K / (ms_fused / 1e3),
+        "unit": "voxel-updates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_fused / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+u8", "data": "synthetic",
+        "config": {"workload": seq.name + "_one_launch", "l2": "flushed between steps (256 MiB write)",
+                   "schedule_blocks_per_sm": sched["blocks_per_sm"], "schedule_from_cache": cached,
+                   "cuda_graph": True},
+        "plain": {"value": nominal * K / (ms_plain / 1e3), "ms_per_step": ms_plain / K, "launches_per_step": 6},
+        "fused_over_plain_time": ms_fused / ms_plain, "volumes_identical": same,
+        "gpu_launches": K, "frame_generation_s": gen_s,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------ adjoint -----
 def run_adjoint(args):
     """Photometric adjoint at 256^3 / 512^3 with 20 frames of 1920x1080: gate
@@ -584,6 +652,8 @@ def main():
         run_batched(args)
     elif args.workload == "adjoint":
         run_adjoint(args)
+    elif args.workload.endswith("_fused"):
+        run_fused(args)
     else:
         run_ours(args)
 

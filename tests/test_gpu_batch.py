@@ -116,3 +116,20 @@ def test_stalled_barrier_times_out_and_the_batch_recovers(data, reference):
     for (a, r) in zip(out, reference):
         for x, y in zip(a, r):
             np.testing.assert_array_equal(x, y)
+
+
+@pytest.mark.parametrize("edge", [48, 44])
+def test_one_scan_in_one_launch_equals_plain(edge):
+    """A batch of one volume is the single-launch fused form of the frame
+    (geometry, band gate and colour in one persistent launch with grid
+    barriers): same volumes as the six-kernel path."""
+    one = scans(n_frames=4, edges=[edge])
+    vol = make_volumes(one)[0]
+    for fr in one[0][1]:
+        vol.integrate(*fr)
+    ref = vol.read()
+    vol.close()
+    out, stats = run_batch(one)
+    for a, b in zip(ref, out[0]):
+        np.testing.assert_array_equal(a, b)
+    assert stats[0].total_col_updated > 100
