@@ -301,9 +301,9 @@ tsdf_status tsdf_adjoint_record(tsdf_adjoint* adj, const uint16_t* depth_mm, tsd
 tsdf_status tsdf_adjoint_finalize(tsdf_adjoint* adj, int64_t* n_voxels);
 /* Linear colour index of each slot (n_voxels uint32, host or device). */
 tsdf_status tsdf_adjoint_voxels(tsdf_adjoint* adj, uint32_t* voxels);
-/* The recorded (voxel, frame) pairs in recording order within no fixed order
- * per frame (uint32 linear colour index, uint8 frame; host or device; either
- * may be NULL) and their count. */
+/* The recorded (voxel, frame) pairs, grouped by frame in recording order and
+ * in no fixed order within a frame (uint32 linear colour index, uint8 frame;
+ * host or device; either may be NULL), and their count. */
 tsdf_status tsdf_adjoint_pairs(tsdf_adjoint* adj, uint32_t* voxels, uint8_t* frames, int64_t* n_pairs);
 /* Forward pass.  images: device float32 n_frames x csz.height x csz.width x 3
  * HD intensities; K_rgb4 = (fx, fy, cx, cy); T_depth_rgb row-major 4x4 (host).
