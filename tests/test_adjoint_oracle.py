@@ -145,3 +145,46 @@ def test_gate_sets_are_the_colourable_voxels(prob):
         assert np.array_equal(np.sort(updated), S) or set(updated.tolist()) <= set(S.tolist())
         missing = set(S.tolist()) - set(updated.tolist())
         assert len(missing) <= max(2, len(S) // 100)  # only voxels whose HD footprint leaves the image
+
+
+def test_forward_of_linear_images_is_the_mean_projected_pixel(prob):
+    """Bilinear interpolation reproduces a linear image exactly, so with HD
+    images I_k(x, y) = a_k x + b_k y + c_k the fused colour of a voxel is the
+    mean over its in-image frames of a_k u_k + b_k v_k + c_k, where (u_k, v_k)
+    is the voxel centre moved by (R_n, t_n) (Eq. 5), by the extrinsic T0
+    (Eq. 3) and projected with K_hd (Eq. 4) — computed here in numpy."""
+    seq, o, S, adj = prob["seq"], prob["o"], prob["S"], prob["adj"]
+    n, H, W, _ = adj.images.shape
+    ab = np.array([[0.5, 0.25, 3.0], [-0.125, 0.75, 90.0], [0.3125, -0.0625, 40.0]])  # per channel
+    xs, ys = np.meshgrid(np.arange(W, dtype=np.float64), np.arange(H, dtype=np.float64))
+    imgs = np.stack([np.stack([ab[c, 0] * xs + ab[c, 1] * ys + ab[c, 2] + 7.0 * k for c in range(3)], -1)
+                     for k in range(n)]).astype(np.float32)
+    lin = oracle.Adjoint(imgs, adj.Rn, adj.tn, S, seq.dims_col, o.p.s_c, list(o.p.origin),
+                         np.asarray(perturbed(seq.T_depth_rgb)))
+    th = prob["th0"]
+    r = lin.eval(th, lin.cells(th))
+    # numpy: voxel centres -> depth camera -> HD camera -> pixel
+    nc = seq.dims_col
+    V = lin.V.astype(np.int64)
+    ijk = np.stack([V % nc[0], (V // nc[0]) % nc[1], V // (nc[0] * nc[1])], 1).astype(np.float64)
+    pw = np.asarray(o.p.origin, np.float64) + (ijk + 0.5) * np.float64(o.p.s_c)
+    T0 = np.asarray(perturbed(seq.T_depth_rgb), np.float64)
+    fx, fy, cx, cy = th[:4]
+    acc = np.zeros((len(V), 3))
+    cnt = np.zeros(len(V), np.int64)
+    for k in range(n):
+        members = np.isin(lin.V, S[k])
+        Pc = pw @ adj.Rn[k].reshape(3, 3).astype(np.float64).T + adj.tn[k].astype(np.float64)
+        Ph = Pc @ T0[:3, :3].T + T0[:3, 3]
+        u, v = fx * Ph[:, 0] / Ph[:, 2] + cx, fy * Ph[:, 1] / Ph[:, 2] + cy
+        inside = members & (np.floor(u) >= 0) & (np.floor(u) + 1 <= W - 1) & (np.floor(v) >= 0) & \
+            (np.floor(v) + 1 <= H - 1)
+        val = ab[:, 0][None, :] * u[:, None] + ab[:, 1][None, :] * v[:, None] + ab[:, 2][None, :] + 7.0 * k
+        acc[inside] += val[inside]
+        cnt += inside
+    ok = cnt > 0
+    assert ok.sum() > 1000
+    # the count of in-image frames may differ only for samples within rounding of the image border
+    assert (r["n"][ok] == cnt[ok]).mean() > 0.999
+    same = ok & (r["n"] == cnt)
+    np.testing.assert_allclose(r["C"][same], acc[same] / cnt[same, None], rtol=0, atol=1e-4)
