@@ -7,7 +7,8 @@ baseline leg of ``bench.py`` are the only callers.  The CUDA path in
 ``oracle.c`` is the plain per-voxel definition (Section IV.B, Eq. 5-7, 9 and
 the inherited KinectFusion TSDF update; Eq. 8-10 as colour mode 1) in binary32
 with a fixed operation order; ``adjoint.c`` is the binary64 photometric loss
-and its analytic gradient (the calibration-refinement extension).
+and its analytic gradient (the calibration-refinement extension);
+``raycast.c`` ray-casts the volumes (range, vertex, normal and colour maps).
 """
 from __future__ import annotations
 
@@ -18,7 +19,7 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, "oracle.c"), os.path.join(_HERE, "adjoint.c")]
+_SRCS = [os.path.join(_HERE, "oracle.c"), os.path.join(_HERE, "adjoint.c"), os.path.join(_HERE, "raycast.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 # -ffp-contract=off: no implicit fused multiply-adds; the operation order in the
@@ -64,6 +65,19 @@ class AdjProblem(ctypes.Structure):
     ]
 
 
+class RcVolume(ctypes.Structure):
+    _fields_ = [("ng", ctypes.c_int32 * 3), ("nc", ctypes.c_int32 * 3), ("s_g", ctypes.c_float),
+                ("s_c", ctypes.c_float), ("origin", ctypes.c_float * 3), ("F", ctypes.c_void_p),
+                ("W", ctypes.c_void_p), ("C", ctypes.c_void_p)]
+
+
+class RcCamera(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("Kinv", ctypes.c_float * 9),
+                ("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3), ("near_", ctypes.c_float),
+                ("far_", ctypes.c_float), ("step_far", ctypes.c_float), ("step_near", ctypes.c_float),
+                ("inv_sg", ctypes.c_float), ("inv_sc", ctypes.c_float)]
+
+
 _lib = None
 
 
@@ -100,6 +114,9 @@ def _load():
                                          ctypes.c_int, vp, vp, vp, vp, ctypes.c_int64, vp, vp, vp, ctypes.c_int64,
                                          vp, vp, vp]
         lib.orc_sparse_frame.restype = ctypes.c_int
+        lib.orc_raycast.argtypes = [ctypes.POINTER(RcVolume), ctypes.POINTER(RcCamera), vp, vp, vp, vp]
+        lib.orc_raycast.restype = ctypes.c_longlong
+        assert lib.orc_rc_sizes(0) == ctypes.sizeof(RcVolume) and lib.orc_rc_sizes(1) == ctypes.sizeof(RcCamera)
         _lib = lib
     return _lib
 
@@ -299,3 +316,42 @@ class Adjoint:
                                      None if q is None else q.ctypes.data, 0 if q is None else len(q),
                                      None if qg is None else qg.ctypes.data)
         return dict(loss=loss, C=C, n=n, grad=g, qgrad=qg)
+
+
+def raycast(F, W, C, s_g, s_c, origin, K, T_world_camera, size, near, far, step_far=None, step_near=None,
+            mu=None):
+    """Ray-cast linear volumes F, W (Nz, Ny, Nx) and packed colours C (or
+    None) from a pinhole camera (raycast.c).  Steps default to half the
+    truncation distance mu in truncated free space and half a geometry voxel
+    elsewhere.  Returns dict(range (H, W), vertex (H, W, 3), normal (H, W, 3),
+    rgbw (H, W), hits)."""
+    lib = _load()
+    F = np.ascontiguousarray(F, np.float32)
+    W = np.ascontiguousarray(W, np.uint8)
+    v = RcVolume()
+    v.ng[:] = [F.shape[2], F.shape[1], F.shape[0]]
+    v.s_g, v.s_c = float(s_g), float(s_c)
+    v.origin[:] = [float(o) for o in origin]
+    v.F, v.W = F.ctypes.data, W.ctypes.data
+    if C is not None:
+        C = np.ascontiguousarray(C, np.uint32)
+        v.nc[:] = [C.shape[2], C.shape[1], C.shape[0]]
+        v.C = C.ctypes.data
+    c = RcCamera()
+    c.width, c.height = int(size[0]), int(size[1])
+    c.Kinv[:] = [float(x) for x in np.linalg.inv(np.asarray(K, np.float64)).astype(np.float32).reshape(9)]
+    T = np.asarray(T_world_camera, np.float32)
+    c.R[:] = [float(x) for x in T[:3, :3].reshape(9)]
+    c.t[:] = [float(x) for x in T[:3, 3]]
+    mu = 3.0 * s_g if mu is None else mu
+    c.near_, c.far_ = float(near), float(far)
+    c.step_far = float(np.float32(0.5 * mu)) if step_far is None else float(step_far)
+    c.step_near = float(np.float32(0.5 * s_g)) if step_near is None else float(step_near)
+    c.inv_sg = float(np.float32(1.0 / np.float64(np.float32(s_g))))
+    c.inv_sc = float(np.float32(1.0 / np.float64(np.float32(s_c))))
+    H, Wd = c.height, c.width
+    out = dict(range=np.zeros((H, Wd), np.float32), vertex=np.zeros((H, Wd, 3), np.float32),
+               normal=np.zeros((H, Wd, 3), np.float32), rgbw=np.zeros((H, Wd), np.uint32))
+    out["hits"] = int(lib.orc_raycast(ctypes.byref(v), ctypes.byref(c), out["range"].ctypes.data,
+                                      out["vertex"].ctypes.data, out["normal"].ctypes.data, out["rgbw"].ctypes.data))
+    return out

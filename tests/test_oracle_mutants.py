@@ -48,20 +48,35 @@ MUTANTS = {
                                "corner(ctx, i0[0] + dx, i0[1] + dy, i0[2] + dz, &f);"),
 }
 
+# Slips in the ray caster (oracle/raycast.c), caught by tests/test_raycast_oracle.py.
+RAYCAST_MUTANTS = {
+    "rc_refine_wrong_end": ("float ts = fmaf(t - tp, Fp / (Fp - F), tp);", "float ts = fmaf(t - tp, F / (Fp - F), tp);"),
+    "rc_normal_sign": ("if (good) n[a] = fp - fm;", "if (good) n[a] = fm - fp;"),
+    "rc_back_faces": ("if (ok && has_prev && Fp > 0.0f && F <= 0.0f) {", "if (ok && has_prev && Fp * F <= 0.0f) {"),
+    "rc_direction_not_normalised": ("c->R[3 * a + 2] * dc[2])) * nd;", "c->R[3 * a + 2] * dc[2]));"),
+    "rc_colour_index_geometry_voxel": ("float q = floorf((vert[a] - v->origin[a]) * c->inv_sc);",
+                                       "float q = floorf((vert[a] - v->origin[a]) * c->inv_sg);"),
+    "rc_unobserved_used": ("if (v->W[idx] == 0) return 0;", ""),
+    "rc_pose_transposed": ("d[a] = fmaf(c->R[3 * a], dc[0], fmaf(c->R[3 * a + 1], dc[1], c->R[3 * a + 2] * dc[2])) * nd;",
+                           "d[a] = fmaf(c->R[a], dc[0], fmaf(c->R[a + 3], dc[1], c->R[a + 6] * dc[2])) * nd;"),
+}
+ALL = {**{k: ("oracle.c", "tests/test_oracle_pins.py") + v for k, v in MUTANTS.items()},
+       **{k: ("raycast.c", "tests/test_raycast_oracle.py") + v for k, v in RAYCAST_MUTANTS.items()}}
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
+
+@pytest.mark.parametrize("name", sorted(ALL))
 def test_pins_catch_mutant(tmp_path, name):
-    before, after = MUTANTS[name]
-    src = open(os.path.join(ROOT, "oracle", "oracle.c")).read()
+    fname, pins, before, after = ALL[name]
+    src = open(os.path.join(ROOT, "oracle", fname)).read()
     assert src.count(before) == 1, "mutation site not found: " + name
     d = tmp_path / "repo"
     shutil.copytree(os.path.join(ROOT, "oracle"), d / "oracle",
                     ignore=shutil.ignore_patterns("*.so", "*.tmp*", "__pycache__"))
-    (d / "oracle" / "oracle.c").write_text(src.replace(before, after))
+    (d / "oracle" / fname).write_text(src.replace(before, after))
     shutil.copytree(os.path.join(ROOT, "tests"), d / "tests", ignore=shutil.ignore_patterns("__pycache__"))
     os.symlink(os.path.join(ROOT, "paper_1602_06645_gb300"), d / "paper_1602_06645_gb300")
     shutil.copy(os.path.join(ROOT, "pytest.ini"), d / "pytest.ini")
-    r = subprocess.run([sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-q", "-x",
+    r = subprocess.run([sys.executable, "-m", "pytest", pins, "-q", "-x",
                         "-p", "no:cacheprovider", "-m", "not gpu"],
                        cwd=d, capture_output=True, text=True, timeout=600)
     assert r.returncode == 1, "pins did not catch mutant %s:\n%s" % (name, r.stdout[-2000:])
