@@ -356,6 +356,45 @@ tsdf_status tsdf_integrate_geometry_static(const int32_t dims[3], float voxel_si
                                            const uint16_t* depth_dev, tsdf_image_size dsz, const float K_depth[9],
                                            const float T_world_depth[16], void* stream);
 
+/* ------------------------------------------------------------------------
+ * Ray casting of the fused volumes.  The paper shows the scan to the user by
+ * ray casting the geometry and colour volumes (abstract) and tracks the camera
+ * against a surface vertex map predicted by ray tracing the geometry volume
+ * (Section III).  Output goes to plain buffers (no graphics API).
+ *
+ * Per pixel (x, y) of a camera with intrinsics K and pose T_world_camera
+ * (camera -> world, x right, y down, z forward), all binary32:
+ *   dc = K^-1 (x, y, 1) (K^-1 in binary64 rounded once), d = R dc / |dc|,
+ *   p(t) = o + t d per axis as fmaf(t, d, o), t the distance from the camera
+ *   centre o.  The TSDF at p is the trilinear interpolation used by the colour
+ *   band gate (it exists only when its 8 corners are inside the volume and
+ *   observed).  From t = near, samples step by step_far where the TSDF exists
+ *   and is >= 1 (truncated free space) and by step_near elsewhere; the first
+ *   sample with TSDF <= 0 whose previous sample had TSDF > 0 is a hit, refined
+ *   by linear interpolation of the zero crossing; the march ends without a hit
+ *   once t > far.  At the hit vertex v: the normal is the normalised central
+ *   difference of the TSDF over +-1 geometry voxel along each axis (pointing to
+ *   free space; (0, 0, 0) when a difference sample does not exist) and the
+ *   colour is the packed RGBW of the colour voxel holding v (0 outside).
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    float near_m, far_m;    /* march range along each ray, metres: 0 <= near < far <= 1000 */
+    float step_far;         /* step in truncated free space, metres; 0 = mu / 2 */
+    float step_near;        /* step elsewhere, metres; 0 = geometry voxel / 2; needs far / step_near <= 2^22 */
+} tsdf_raycast_params;
+
+/* Ray-cast width x height pixels.  Outputs (any may be NULL; host or device
+ * pointers, row-major, pixel (x, y) at y * width + x): range (float, the hit's
+ * t, 0 for a miss), vertex and normal (3 floats per pixel, world frame, zero
+ * for a miss), rgbw (packed colour, 0 for a miss or outside the colour
+ * volume).  Ordered on the volume's stream; returns after host outputs are
+ * written, device outputs are ready when the stream reaches that point.
+ * Errors: INVALID_ARG (NULL vol or K/T, size outside 1..16384, non-finite or
+ * singular K, T not a rigid motion, bad range or steps), OOM. */
+tsdf_status tsdf_raycast(tsdf_volume* vol, const float K[9], const float T_world_camera[16], tsdf_image_size size,
+                         const tsdf_raycast_params* params, float* range, float* vertex, float* normal,
+                         uint32_t* rgbw);
+
 /* Human-readable text of a status, and the last error message of a handle
  * (empty if none).  The strings are owned by the library. */
 const char* tsdf_status_string(tsdf_status s);

@@ -37,7 +37,7 @@ EXPORTS = [
     "tsdf_adjoint_voxels", "tsdf_adjoint_pairs", "tsdf_adjoint_forward", "tsdf_adjoint_backward",
     "tsdf_adjoint_destroy", "tsdf_batch_create", "tsdf_batch_integrate", "tsdf_batch_synchronize",
     "tsdf_batch_set_schedule", "tsdf_batch_get_schedule", "tsdf_batch_autotune", "tsdf_batch_inject_stall",
-    "tsdf_batch_destroy",
+    "tsdf_batch_destroy", "tsdf_raycast",
 ]
 PHASES = ["upload", "depth_tiles", "bricks", "geometry", "colour_list", "colour_cells", "colour"]
 
@@ -178,6 +178,8 @@ def load():
     for name in ("tsdf_adjoint_create", "tsdf_adjoint_record", "tsdf_adjoint_finalize", "tsdf_adjoint_voxels",
                  "tsdf_adjoint_pairs", "tsdf_adjoint_forward", "tsdf_adjoint_backward"):
         getattr(lib, name).restype = ctypes.c_int
+    lib.tsdf_raycast.argtypes = [vp, fp, fp, tsdf_image_size, ctypes.POINTER(tsdf_raycast_params), vp, vp, vp, vp]
+    lib.tsdf_raycast.restype = ctypes.c_int
     lib.tsdf_profile_enable.argtypes = [vp, ctypes.c_int32]
     lib.tsdf_profile_read.argtypes = [vp, ctypes.POINTER(tsdf_profile_report)]
     for name in ("tsdf_create", "tsdf_create_ex", "tsdf_integrate", "tsdf_read", "tsdf_write", "tsdf_synchronize",
@@ -186,6 +188,11 @@ def load():
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
+
+
+class tsdf_raycast_params(ctypes.Structure):
+    _fields_ = [("near_m", ctypes.c_float), ("far_m", ctypes.c_float), ("step_far", ctypes.c_float),
+                ("step_near", ctypes.c_float)]
 
 
 # ------------------------------------------------------------ marshalling --
@@ -288,6 +295,15 @@ def tsdf_write(h, tsdf=None, w_geo=None, rgbw=None):
     keep = []
     _check(load().tsdf_write(h, _ptr(tsdf, np.float32, keep), _ptr(w_geo, np.uint8, keep),
                              _ptr(rgbw, np.uint32, keep)), h)
+
+
+def tsdf_raycast(h, K, T_world_camera, size, params=None, range_=None, vertex=None, normal=None, rgbw=None):
+    keep = []
+    mats = [_mat(K, 9), _mat(T_world_camera, 16)]
+    _check(load().tsdf_raycast(h, mats[0][1], mats[1][1], tsdf_image_size(int(size[0]), int(size[1])),
+                               ctypes.byref(params) if params is not None else None,
+                               _ptr(range_, np.float32, keep), _ptr(vertex, np.float32, keep),
+                               _ptr(normal, np.float32, keep), _ptr(rgbw, np.uint32, keep)), h)
 
 
 def tsdf_synchronize(h):
@@ -524,6 +540,24 @@ class Volume:
         C = torch.empty((cz, cy, cx), dtype=torch.int32, device=device)
         tsdf_read(self.h, F, W, C)
         return F, W, C
+
+    def raycast(self, K, T_world_camera, size, near=0.1, far=4.0, step_far=0.0, step_near=0.0, device=None):
+        """Ray-cast the volumes from a camera (tsdf_raycast): dict of range
+        (H, W), vertex and normal (H, W, 3) and rgbw (H, W, packed), as numpy
+        arrays, or as device tensors when device is given."""
+        w, h = int(size[0]), int(size[1])
+        p = tsdf_raycast_params(float(near), float(far), float(step_far), float(step_near))
+        if device is None:
+            out = dict(range=np.empty((h, w), np.float32), vertex=np.empty((h, w, 3), np.float32),
+                       normal=np.empty((h, w, 3), np.float32), rgbw=np.empty((h, w), np.uint32))
+        else:
+            import torch
+            out = dict(range=torch.empty((h, w), dtype=torch.float32, device=device),
+                       vertex=torch.empty((h, w, 3), dtype=torch.float32, device=device),
+                       normal=torch.empty((h, w, 3), dtype=torch.float32, device=device),
+                       rgbw=torch.empty((h, w), dtype=torch.int32, device=device))
+        tsdf_raycast(self.h, K, T_world_camera, (w, h), p, out["range"], out["vertex"], out["normal"], out["rgbw"])
+        return out
 
     def write(self, F=None, W=None, C=None):
         tsdf_write(self.h, F, W, C)

@@ -225,6 +225,22 @@ cudaError_t launch_adjoint_forward(const AdjCamera& cam, const AdjBuffers& a, ui
 cudaError_t launch_adjoint_backward(const AdjCamera& cam, const AdjBuffers& a, uint32_t n_slots, const float* images,
                                     const float* grad_C, float* grad_images, int blocks, cudaStream_t stream);
 
+// ------------------------------------------------------------ ray casting --
+// Constants of one ray-casting call (see tsdf_raycast in tsdf.h): K^-1 and the
+// camera pose (camera -> world), volume geometry, march range and steps.
+struct RayConst {
+    float Kinv[9], R[9], t[3];
+    float origin[3];
+    float s_g, inv_sg, inv_sc;
+    float near_, far_, step_far, step_near;
+    int32_t ng[3], nb[3], nc[3], ncb[3];
+    int32_t width, height;
+    uint32_t max_iter;  // bound on samples per ray (never reached for valid parameters)
+};
+cudaError_t launch_raycast(const RayConst& c, const float* F, const uint8_t* W, const uint32_t* C,
+                           const BrickSummary* summ, float* range, float* vertex, float* normal, uint32_t* rgbw,
+                           cudaStream_t stream);
+
 // ------------------------------------------------------------ addressing --
 __host__ __device__ __forceinline__ int64_t brick_offset(int x, int y, int z, const int32_t nb[3]) {
     int64_t b = ((int64_t)(z >> 3) * nb[1] + (y >> 3)) * nb[0] + (x >> 3);
