@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--workload", default="scan",
                     help="scan (512^3/1024^3) | small (128^3/256^3) | sweep256 | sweep512 | sweep768 | sweep1024 | "
                          "scan_r1 | batched (64 scans) | adjoint (256^3/512^3, 20 frames) | <any of the first>_fused "
-                         "(one persistent launch per frame)")
+                         "(one persistent launch per frame) | raycast (640x480 casts of the scan volumes)")
     ap.add_argument("--dense", action="store_true", help="culling off (dense sweep of every brick)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -564,6 +564,51 @@ def run_fused(args):
     print(json.dumps(line), flush=True)
 
 
+def run_raycast(args):
+    """Ray casting (tsdf_raycast) of the scan volumes after 60 fused frames:
+    640x480 range/vertex/normal/colour maps from the next cameras of the
+    orbit, device outputs, L2 flushed between casts."""
+    import torch
+    import paper_1602_06645_gb300 as T
+
+    torch.cuda.set_device(0)
+    T.load()
+    n_fuse = 60
+    seq = make_sequence("scan", n_fuse + args.warmup + args.steps, 0)
+    stream = torch.cuda.current_stream()
+    vol = T.Volume(seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, seq.max_weight, stream=stream.cuda_stream)
+    for f in range(n_fuse):
+        d, c = seq.frame(f)
+        vol.integrate(d, c, seq.K_depth, seq.K_rgb, seq.poses[f], seq.T_depth_rgb)
+    size = (640, 480)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    hits = []
+    for i in range(args.warmup):
+        vol.raycast(seq.K_depth, seq.poses[n_fuse + i], size, 0.1, 4.0, device="cuda")
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        out = vol.raycast(seq.K_depth, seq.poses[n_fuse + args.warmup + i], size, 0.1, 4.0, device="cuda")
+        ev[i][1].record(stream)
+        hits.append(out["range"] > 0)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    K = max(args.steps, 1)
+    rays = size[0] * size[1]
+    line = {
+        "metric": "rays/s (640x480 ray casts of the fused scan volumes)", "value": rays * K / (sum(ms) / 1e3),
+        "unit": "rays/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": sum(ms) / K,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": seq.name + "_raycast_640x480", "fused_frames": n_fuse, "near_far_m": [0.1, 4.0],
+                   "l2": "flushed between steps (256 MiB write)"},
+        "hit_fraction": float(torch.stack(hits).float().mean()), "gpu_launches": K,
+    }
+    vol.close()
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------ adjoint -----
 def run_adjoint(args):
     """Photometric adjoint at 256^3 / 512^3 with 20 frames of 1920x1080: gate
@@ -654,6 +699,8 @@ def main():
         run_adjoint(args)
     elif args.workload.endswith("_fused"):
         run_fused(args)
+    elif args.workload == "raycast":
+        run_raycast(args)
     else:
         run_ours(args)
 

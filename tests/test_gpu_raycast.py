@@ -80,8 +80,9 @@ def test_oracle_fused_sequence_from_a_view():
     K = synth.intrinsics(262.5, 262.5, 159.5, 119.5)
     for f in (0, 2):
         g = vol.raycast(K, seq.poses[f], size, 0.1, 3.0)
-        r = oracle.raycast(o.F, o.W, o.C, seq.voxel_size, vol.info().voxel_col, vol.info().origin, K, seq.poses[f],
-                           size, 0.1, 3.0, step_far=float(np.float32(0.5 * np.float64(np.float32(seq.mu)))),
+        info = vol.info()
+        r = oracle.raycast(o.F, o.W, o.C, seq.voxel_size, info.voxel_col, info.origin, K, seq.poses[f], size, 0.1,
+                           3.0, step_far=float(np.float32(0.5 * np.float64(np.float32(seq.mu)))),
                            step_near=float(np.float32(0.5 * np.float64(np.float32(seq.voxel_size)))))
         assert_same(g, r, "frame %d" % f)
         assert r["hits"] > 0.3 * size[0] * size[1]
