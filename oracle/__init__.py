@@ -8,7 +8,9 @@ baseline leg of ``bench.py`` are the only callers.  The CUDA path in
 the inherited KinectFusion TSDF update; Eq. 8-10 as colour mode 1) in binary32
 with a fixed operation order; ``adjoint.c`` is the binary64 photometric loss
 and its analytic gradient (the calibration-refinement extension);
-``raycast.c`` ray-casts the volumes (range, vertex, normal and colour maps).
+``raycast.c`` ray-casts the volumes (range, vertex, normal and colour maps);
+``mesh.c`` extracts the zero level set as triangles and fills per-polygon
+texture maps from the colour volume (Eq. 11-14).
 """
 from __future__ import annotations
 
@@ -19,7 +21,7 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, "oracle.c"), os.path.join(_HERE, "adjoint.c"), os.path.join(_HERE, "raycast.c")]
+_SRCS = [os.path.join(_HERE, f) for f in ("oracle.c", "adjoint.c", "raycast.c", "mesh.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 # -ffp-contract=off: no implicit fused multiply-adds; the operation order in the
@@ -78,6 +80,16 @@ class RcCamera(ctypes.Structure):
                 ("inv_sg", ctypes.c_float), ("inv_sc", ctypes.c_float)]
 
 
+class MeshVolume(ctypes.Structure):
+    _fields_ = [("ng", ctypes.c_int32 * 3), ("s_g", ctypes.c_float), ("origin", ctypes.c_float * 3),
+                ("F", ctypes.c_void_p), ("W", ctypes.c_void_p)]
+
+
+class ColourVolume(ctypes.Structure):
+    _fields_ = [("nc", ctypes.c_int32 * 3), ("s_c", ctypes.c_float), ("origin", ctypes.c_float * 3),
+                ("C", ctypes.c_void_p)]
+
+
 _lib = None
 
 
@@ -117,6 +129,13 @@ def _load():
         lib.orc_raycast.argtypes = [ctypes.POINTER(RcVolume), ctypes.POINTER(RcCamera), vp, vp, vp, vp]
         lib.orc_raycast.restype = ctypes.c_longlong
         assert lib.orc_rc_sizes(0) == ctypes.sizeof(RcVolume) and lib.orc_rc_sizes(1) == ctypes.sizeof(RcCamera)
+        lib.orc_mesh.argtypes = [ctypes.POINTER(MeshVolume), vp, ctypes.c_longlong]
+        lib.orc_mesh.restype = ctypes.c_longlong
+        lib.orc_texture_sizes.argtypes = [vp, ctypes.c_longlong, ctypes.c_float, ctypes.c_int, vp]
+        lib.orc_texture_sizes.restype = ctypes.c_longlong
+        lib.orc_texture_fill.argtypes = [ctypes.POINTER(ColourVolume), vp, ctypes.c_longlong, vp, vp, vp]
+        lib.orc_texture_fill.restype = None
+        assert lib.orc_mesh_sizes(0) == ctypes.sizeof(MeshVolume) and lib.orc_mesh_sizes(1) == ctypes.sizeof(ColourVolume)
         _lib = lib
     return _lib
 
@@ -355,3 +374,42 @@ def raycast(F, W, C, s_g, s_c, origin, K, T_world_camera, size, near, far, step_
     out["hits"] = int(lib.orc_raycast(ctypes.byref(v), ctypes.byref(c), out["range"].ctypes.data,
                                       out["vertex"].ctypes.data, out["normal"].ctypes.data, out["rgbw"].ctypes.data))
     return out
+
+
+def mesh(F, W, s_g, origin):
+    """Triangles (n, 3, 3) of the zero level set of linear volumes F, W
+    (Nz, Ny, Nx) by marching tetrahedra (mesh.c), in cell order."""
+    lib = _load()
+    F = np.ascontiguousarray(F, np.float32)
+    W = np.ascontiguousarray(W, np.uint8)
+    v = MeshVolume()
+    v.ng[:] = [F.shape[2], F.shape[1], F.shape[0]]
+    v.s_g = float(s_g)
+    v.origin[:] = [float(o) for o in origin]
+    v.F, v.W = F.ctypes.data, W.ctypes.data
+    n = int(lib.orc_mesh(ctypes.byref(v), None, 0))
+    out = np.zeros((n, 3, 3), np.float32)
+    lib.orc_mesh(ctypes.byref(v), out.ctypes.data, n)
+    return out
+
+
+def texture_maps(tris, C, s_c, origin, size_pixel, max_side=1024):
+    """Per-triangle texture maps (Eq. 11-14, mesh.c): (wh (n, 2) int32,
+    offsets (n + 1) int64, texels uint32 packed RGBA)."""
+    lib = _load()
+    tris = np.ascontiguousarray(tris, np.float32).reshape(-1, 9)
+    n = len(tris)
+    wh = np.zeros((n, 2), np.int32)
+    total = int(lib.orc_texture_sizes(tris.ctypes.data, n, float(size_pixel), int(max_side), wh.ctypes.data))
+    off = np.zeros(n + 1, np.int64)
+    off[1:] = np.cumsum(wh[:, 0].astype(np.int64) * wh[:, 1])
+    assert off[-1] == total
+    C = np.ascontiguousarray(C, np.uint32)
+    cv = ColourVolume()
+    cv.nc[:] = [C.shape[2], C.shape[1], C.shape[0]]
+    cv.s_c = float(s_c)
+    cv.origin[:] = [float(o) for o in origin]
+    cv.C = C.ctypes.data
+    texels = np.zeros(total, np.uint32)
+    lib.orc_texture_fill(ctypes.byref(cv), tris.ctypes.data, n, wh.ctypes.data, off.ctypes.data, texels.ctypes.data)
+    return wh, off, texels

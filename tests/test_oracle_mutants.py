@@ -60,8 +60,23 @@ RAYCAST_MUTANTS = {
     "rc_pose_transposed": ("d[a] = fmaf(c->R[3 * a], dc[0], fmaf(c->R[3 * a + 1], dc[1], c->R[3 * a + 2] * dc[2])) * nd;",
                            "d[a] = fmaf(c->R[a], dc[0], fmaf(c->R[a + 3], dc[1], c->R[a + 6] * dc[2])) * nd;"),
 }
+# Slips in mesh extraction and texture maps (oracle/mesh.c), caught by tests/test_mesh_oracle.py.
+MESH_MUTANTS = {
+    "mt_orientation_flipped": ("    if (dot < 0.0f) {\n        memcpy(out + 3", "    if (dot > 0.0f) {\n        memcpy(out + 3"),
+    "mt_edge_from_wrong_end": ("out[ax] = fmaf(t, Pq - Pp, Pp);", "out[ax] = fmaf(t, Pp - Pq, Pq);"),
+    "mt_inconsistent_split": ("static const int TET_AXES[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};",
+                              "static const int TET_AXES[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 0, 1}};"),
+    "mt_quad_wrong_diagonal": ("memcpy(tri, q[0], 12); memcpy(tri + 3, q[2], 12); memcpy(tri + 6, q[3], 12);",
+                               "memcpy(tri, q[1], 12); memcpy(tri + 3, q[2], 12); memcpy(tri + 6, q[3], 12);"),
+    "tx_green_blue_swapped": ("p[a] = fmaf((float)j, blue[a], fmaf((float)i, green[a], T[a]));",
+                              "p[a] = fmaf((float)i, blue[a], fmaf((float)j, green[a], T[a]));"),
+    "tx_divide_by_w": ("green[a] = (T[3 + a] - T[a]) / (float)(w - 1);", "green[a] = (T[3 + a] - T[a]) / (float)w;"),
+    "tx_unobserved_colour_used": ("if ((c >> 24) == 0u) continue;", ""),
+    "tx_size_truncated": ("float q = floorf(dist / size_pixel + 0.5f);", "float q = floorf(dist / size_pixel);"),
+}
 ALL = {**{k: ("oracle.c", "tests/test_oracle_pins.py") + v for k, v in MUTANTS.items()},
-       **{k: ("raycast.c", "tests/test_raycast_oracle.py") + v for k, v in RAYCAST_MUTANTS.items()}}
+       **{k: ("raycast.c", "tests/test_raycast_oracle.py") + v for k, v in RAYCAST_MUTANTS.items()},
+       **{k: ("mesh.c", "tests/test_mesh_oracle.py") + v for k, v in MESH_MUTANTS.items()}}
 
 
 @pytest.mark.parametrize("name", sorted(ALL))
