@@ -395,6 +395,52 @@ tsdf_status tsdf_raycast(tsdf_volume* vol, const float K[9], const float T_world
                          const tsdf_raycast_params* params, float* range, float* vertex, float* normal,
                          uint32_t* rgbw);
 
+/* ------------------------------------------------------------------------
+ * Mesh extraction and per-polygon texture maps.  The paper extracts a polygon
+ * mesh from the TSDF volume (Section IV.C) and textures each polygon with its
+ * own 2D map sampled from the colour volume (Section IV.D, Eq. 11-14).
+ *
+ * Mesh: the zero level set of the TSDF by marching tetrahedra.  A cell is the
+ * cube of eight neighbouring geometry voxels (corner k = (k & 1, (k >> 1) & 1,
+ * k >> 2)) and is meshed only when all eight are observed.  It is split into
+ * six tetrahedra along the diagonal from corner 0 to corner 7 (for each axis
+ * order (x,y,z), (x,z,y), (y,x,z), (y,z,x), (z,x,y), (z,y,x): corners 0, 0 + a0,
+ * 0 + a0 + a1, 7), the same split on both sides of a shared face, so the
+ * surface has no cracks.  A corner is inside when F < 0.  A tetrahedron with a
+ * lone corner gives the triangle on its three edges; one with two inside
+ * corners i1, i2 and outside corners o1, o2 (tetrahedron order) gives the quad
+ * on edges (i1,o1), (i1,o2), (i2,o2), (i2,o1) as triangles ((i1,o1), (i1,o2),
+ * (i2,o2)) and ((i1,o1), (i2,o2), (i2,o1)).  The vertex on edge (p, q), p the
+ * lower voxel index: t = F_p / (F_p - F_q), v = fmaf(t, P_q - P_p, P_p), P the
+ * voxel centre.  Triangles are wound so that their normal points to free
+ * space (F > 0).  Binary32, operation order as in the reference definition.
+ * ---------------------------------------------------------------------- */
+/* Write up to capacity triangles (9 floats each: v0, v1, v2; host or device
+ * pointer, may be NULL with capacity 0) in no fixed order and set
+ * *n_triangles to the number the volume has (more than capacity means the
+ * output was cut short: call again with more room).  Errors: INVALID_ARG,
+ * OOM. */
+tsdf_status tsdf_mesh(tsdf_volume* vol, float* triangles, int64_t capacity, int64_t* n_triangles);
+
+/* Texture map layout (Eq. 11-12): for n triangles (V_a, V_b, V_c as 9 floats
+ * each) and the size of a texel on the model, w = max(2, round(|V_a V_b| /
+ * size_pixel)) and h = max(2, round(|V_a V_c| / size_pixel)) (round half up,
+ * at most max_side), written to wh (2n int32: w, h), and the texel offsets of
+ * the maps laid one after another (offsets: n + 1 int64, offsets[n] = total).
+ * Pointers host or device.  Errors: INVALID_ARG, OOM. */
+tsdf_status tsdf_texture_layout(tsdf_volume* vol, const float* triangles, int64_t n, float size_pixel,
+                                int32_t max_side, int32_t* wh, int64_t* offsets);
+/* Texture maps (Eq. 13-14): texel (i, j) of triangle t, i the column along
+ * V_aV_green = V_aV_b / (w - 1) and j the row along V_aV_blue = V_aV_c / (h - 1),
+ * lies at V_a + i V_aV_green + j V_aV_blue and takes the trilinear
+ * interpolation of the colour volume there over observed colour voxels only
+ * (each channel rounded half up; alpha 255; 0 when no corner is observed).
+ * Maps are row-major (h rows of w texels) at texels + offsets[t], packed
+ * R | G << 8 | B << 16 | A << 24.  wh and offsets as tsdf_texture_layout gave
+ * them; pointers host or device.  Errors: INVALID_ARG, OOM. */
+tsdf_status tsdf_texture_fill(tsdf_volume* vol, const float* triangles, int64_t n, const int32_t* wh,
+                              const int64_t* offsets, uint32_t* texels);
+
 /* Human-readable text of a status, and the last error message of a handle
  * (empty if none).  The strings are owned by the library. */
 const char* tsdf_status_string(tsdf_status s);

@@ -37,7 +37,7 @@ EXPORTS = [
     "tsdf_adjoint_voxels", "tsdf_adjoint_pairs", "tsdf_adjoint_forward", "tsdf_adjoint_backward",
     "tsdf_adjoint_destroy", "tsdf_batch_create", "tsdf_batch_integrate", "tsdf_batch_synchronize",
     "tsdf_batch_set_schedule", "tsdf_batch_get_schedule", "tsdf_batch_autotune", "tsdf_batch_inject_stall",
-    "tsdf_batch_destroy", "tsdf_raycast",
+    "tsdf_batch_destroy", "tsdf_raycast", "tsdf_mesh", "tsdf_texture_layout", "tsdf_texture_fill",
 ]
 PHASES = ["upload", "depth_tiles", "bricks", "geometry", "colour_list", "colour_cells", "colour"]
 
@@ -180,6 +180,11 @@ def load():
         getattr(lib, name).restype = ctypes.c_int
     lib.tsdf_raycast.argtypes = [vp, fp, fp, tsdf_image_size, ctypes.POINTER(tsdf_raycast_params), vp, vp, vp, vp]
     lib.tsdf_raycast.restype = ctypes.c_int
+    lib.tsdf_mesh.argtypes = [vp, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
+    lib.tsdf_texture_layout.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_float, ctypes.c_int32, vp, vp]
+    lib.tsdf_texture_fill.argtypes = [vp, vp, ctypes.c_int64, vp, vp, vp]
+    for name in ("tsdf_mesh", "tsdf_texture_layout", "tsdf_texture_fill"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.tsdf_profile_enable.argtypes = [vp, ctypes.c_int32]
     lib.tsdf_profile_read.argtypes = [vp, ctypes.POINTER(tsdf_profile_report)]
     for name in ("tsdf_create", "tsdf_create_ex", "tsdf_integrate", "tsdf_read", "tsdf_write", "tsdf_synchronize",
@@ -304,6 +309,25 @@ def tsdf_raycast(h, K, T_world_camera, size, params=None, range_=None, vertex=No
                                ctypes.byref(params) if params is not None else None,
                                _ptr(range_, np.float32, keep), _ptr(vertex, np.float32, keep),
                                _ptr(normal, np.float32, keep), _ptr(rgbw, np.uint32, keep)), h)
+
+
+def tsdf_mesh(h, triangles=None, capacity=0):
+    keep = []
+    n = ctypes.c_int64()
+    _check(load().tsdf_mesh(h, _ptr(triangles, np.float32, keep), int(capacity), ctypes.byref(n)), h)
+    return n.value
+
+
+def tsdf_texture_layout(h, triangles, n, size_pixel, max_side, wh, offsets):
+    keep = []
+    _check(load().tsdf_texture_layout(h, _ptr(triangles, np.float32, keep), int(n), float(size_pixel),
+                                      int(max_side), _ptr(wh, np.int32, keep), _ptr(offsets, np.int64, keep)), h)
+
+
+def tsdf_texture_fill(h, triangles, n, wh, offsets, texels):
+    keep = []
+    _check(load().tsdf_texture_fill(h, _ptr(triangles, np.float32, keep), int(n), _ptr(wh, np.int32, keep),
+                                    _ptr(offsets, np.int64, keep), _ptr(texels, np.uint32, keep)), h)
 
 
 def tsdf_synchronize(h):
@@ -558,6 +582,41 @@ class Volume:
                        rgbw=torch.empty((h, w), dtype=torch.int32, device=device))
         tsdf_raycast(self.h, K, T_world_camera, (w, h), p, out["range"], out["vertex"], out["normal"], out["rgbw"])
         return out
+
+    def mesh(self, capacity=None, device=None):
+        """Triangles (n, 3, 3) of the TSDF zero level set (tsdf_mesh), in no
+        fixed order; numpy, or a device tensor when device is given."""
+        if capacity is None:
+            capacity = tsdf_mesh(self.h, None, 0)
+        if device is None:
+            out = np.empty((int(capacity), 3, 3), np.float32)
+        else:
+            import torch
+            out = torch.empty((int(capacity), 3, 3), dtype=torch.float32, device=device)
+        n = tsdf_mesh(self.h, out if capacity else None, capacity)
+        return out[:min(n, int(capacity))]
+
+    def texture_maps(self, triangles, size_pixel, max_side=1024):
+        """Per-triangle texture maps (tsdf_texture_layout + tsdf_texture_fill):
+        (wh (n, 2), offsets (n + 1), texels) as numpy arrays, or as device
+        tensors when triangles is a device tensor."""
+        n = len(triangles)
+        if hasattr(triangles, "is_cuda") and triangles.is_cuda:
+            import torch
+            dev = triangles.device
+            tri = triangles.reshape(n, 9).contiguous()
+            wh = torch.empty((n, 2), dtype=torch.int32, device=dev)
+            off = torch.empty(n + 1, dtype=torch.int64, device=dev)
+            tsdf_texture_layout(self.h, tri, n, size_pixel, max_side, wh, off)
+            tex = torch.empty(int(off[n].item()), dtype=torch.int32, device=dev)
+        else:
+            tri = np.ascontiguousarray(triangles, np.float32).reshape(n, 9)
+            wh = np.empty((n, 2), np.int32)
+            off = np.empty(n + 1, np.int64)
+            tsdf_texture_layout(self.h, tri, n, size_pixel, max_side, wh, off)
+            tex = np.empty(int(off[n]), np.uint32)
+        tsdf_texture_fill(self.h, tri, n, wh, off, tex)
+        return wh, off, tex
 
     def write(self, F=None, W=None, C=None):
         tsdf_write(self.h, F, W, C)

@@ -241,6 +241,33 @@ cudaError_t launch_raycast(const RayConst& c, const float* F, const uint8_t* W, 
                            const BrickSummary* summ, float* range, float* vertex, float* normal, uint32_t* rgbw,
                            cudaStream_t stream);
 
+// ------------------------------------------------- mesh and texture maps --
+// Geometry of the volume for mesh extraction (see tsdf_mesh in tsdf.h).
+struct MeshConst {
+    int32_t ng[3], nb[3];
+    float s_g;
+    float origin[3];
+};
+// Candidate bricks (cells whose corners can have both signs), then one warp per
+// candidate; triangles are appended at *count (slots beyond cap are counted,
+// not written).
+cudaError_t launch_mesh(const MeshConst& c, const float* F, const uint8_t* W, const BrickSummary* summ,
+                        uint32_t* list, uint32_t* n_list, float* out, uint64_t cap, unsigned long long* count,
+                        cudaStream_t stream);
+// Colour volume for texture maps (see tsdf_texture_fill in tsdf.h).
+struct ColourConst {
+    int32_t nc[3], ncb[3];
+    float s_c, inv_sc;
+    float origin[3];
+};
+// Eq. 11-12 sizes of n triangles into wh and their exclusive texel offsets
+// into off[0..n] (block sums in `scratch`, (n + 1023) / 1024 + 1 entries).
+cudaError_t launch_texture_layout(const float* tris, int64_t n, float size_pixel, int32_t max_side, int32_t* wh,
+                                  int64_t* off, int64_t* scratch, cudaStream_t stream);
+cudaError_t launch_texture_fill(const ColourConst& c, const uint32_t* C, const float* tris, int64_t n,
+                                const int32_t* wh, const int64_t* off, int64_t total, uint32_t* texels,
+                                cudaStream_t stream);
+
 // ------------------------------------------------------------ addressing --
 __host__ __device__ __forceinline__ int64_t brick_offset(int x, int y, int z, const int32_t nb[3]) {
     int64_t b = ((int64_t)(z >> 3) * nb[1] + (y >> 3)) * nb[0] + (x >> 3);
