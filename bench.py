@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--workload", default="scan",
                     help="scan (512^3/1024^3) | small (128^3/256^3) | sweep256 | sweep512 | sweep768 | sweep1024 | "
                          "scan_r1 | batched (64 scans) | adjoint (256^3/512^3, 20 frames) | <any of the first>_fused "
-                         "(one persistent launch per frame) | raycast (640x480 casts of the scan volumes)")
+                         "(one persistent launch per frame) | raycast (640x480 casts of the scan volumes) | "
+                         "mesh (mesh + texture maps of the scan volumes)")
     ap.add_argument("--dense", action="store_true", help="culling off (dense sweep of every brick)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -609,6 +610,63 @@ def run_raycast(args):
     print(json.dumps(line), flush=True)
 
 
+def run_mesh(args):
+    """Mesh extraction and texture maps of the scan volumes after 60 fused
+    frames: tsdf_mesh into a device buffer, then the texture layout and fill
+    of every triangle at one colour voxel per texel, L2 flushed between steps."""
+    import torch
+    import paper_1602_06645_gb300 as T
+
+    torch.cuda.set_device(0)
+    T.load()
+    n_fuse = 60
+    seq = make_sequence("scan", n_fuse, 0)
+    stream = torch.cuda.current_stream()
+    vol = T.Volume(seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, seq.max_weight, stream=stream.cuda_stream)
+    for f in range(n_fuse):
+        d, c = seq.frame(f)
+        vol.integrate(d, c, seq.K_depth, seq.K_rgb, seq.poses[f], seq.T_depth_rgb)
+    n_tri = T.tsdf_mesh(vol.h, None, 0)
+    tris = torch.empty((n_tri, 3, 3), dtype=torch.float32, device="cuda")
+    size = float(vol.info().voxel_col)
+    wh = torch.empty((n_tri, 2), dtype=torch.int32, device="cuda")
+    off = torch.empty(n_tri + 1, dtype=torch.int64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    texels = None
+    ev = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        T.tsdf_mesh(vol.h, tris, n_tri)
+        e[1].record(stream)
+        T.tsdf_texture_layout(vol.h, tris, n_tri, size, 1024, wh, off)
+        if texels is None:
+            texels = torch.empty(int(off[n_tri].item()), dtype=torch.int32, device="cuda")
+        T.tsdf_texture_fill(vol.h, tris, n_tri, wh, off, texels)
+        e[2].record(stream)
+        if i >= args.warmup:
+            ev.append(e)
+    torch.cuda.synchronize()
+    mesh_ms = [a.elapsed_time(b) for a, b, _ in ev]
+    tex_ms = [b.elapsed_time(c) for _, b, c in ev]
+    K = max(args.steps, 1)
+    total_ms = sum(mesh_ms) + sum(tex_ms)
+    n_tex = texels.numel()
+    line = {
+        "metric": "triangles/s (mesh extraction + texture maps of the fused scan)",
+        "value": n_tri * K / (total_ms / 1e3), "unit": "triangles/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+u8", "data": "synthetic",
+        "config": {"workload": seq.name + "_mesh_texture", "fused_frames": n_fuse, "size_pixel_m": size,
+                   "l2": "flushed between steps (256 MiB write)"},
+        "triangles": n_tri, "texels": n_tex, "mesh_ms": sum(mesh_ms) / K, "texture_ms": sum(tex_ms) / K,
+        "texels_per_s": n_tex * K / (sum(tex_ms) / 1e3), "gpu_launches": 7 * K,
+    }
+    vol.close()
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------ adjoint -----
 def run_adjoint(args):
     """Photometric adjoint at 256^3 / 512^3 with 20 frames of 1920x1080: gate
@@ -701,6 +759,8 @@ def main():
         run_fused(args)
     elif args.workload == "raycast":
         run_raycast(args)
+    elif args.workload == "mesh":
+        run_mesh(args)
     else:
         run_ours(args)
 
