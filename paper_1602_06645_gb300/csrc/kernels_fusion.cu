@@ -77,6 +77,45 @@ __global__ void __launch_bounds__(256) k_depth_tiles(FrameConst c, const uint16_
 // (all F = 1, all w = max_weight), where (1 * w + 1) / (w + 1) = 1.  The
 // visible list (the colour candidates) also drops bricks lying in front of
 // the nearest depth by more than sigma + margin.
+// Image-plane footprint of the axis-aligned box [lo, hi] (world): the bounds
+// of its 8 projected corners, its camera-z range, whether some corner is (near)
+// behind the camera (straddle: the footprint is then the whole image) and
+// whether every corner is behind it (behind: no point of the box projects).
+struct Footprint {
+    float umin, umax, vmin, vmax, zmin, zmax;
+    bool straddle, behind;
+};
+
+__device__ __forceinline__ Footprint box_footprint(const FrameConst& c, const float lo[3], const float hi[3]) {
+    Footprint f{FLT_MAX, -FLT_MAX, FLT_MAX, -FLT_MAX, FLT_MAX, -FLT_MAX, false, true};
+    for (int k = 0; k < 8; ++k) {
+        float x = (k & 1) ? hi[0] : lo[0], y = (k & 2) ? hi[1] : lo[1], z = (k & 4) ? hi[2] : lo[2];
+        float X = c.R[0] * x + c.R[1] * y + c.R[2] * z + c.t[0];
+        float Y = c.R[3] * x + c.R[4] * y + c.R[5] * z + c.t[1];
+        float Z = c.R[6] * x + c.R[7] * y + c.R[8] * z + c.t[2];
+        float xh = c.Kd[0] * X + c.Kd[1] * Y + c.Kd[2] * Z;
+        float yh = c.Kd[3] * X + c.Kd[4] * Y + c.Kd[5] * Z;
+        float zh = c.Kd[6] * X + c.Kd[7] * Y + c.Kd[8] * Z;
+        f.zmin = fminf(f.zmin, Z);
+        f.zmax = fmaxf(f.zmax, Z);
+        f.behind = f.behind && zh <= 0.0f;
+        if (zh <= 1e-4f) { f.straddle = true; continue; }
+        float u = __fdividef(xh, zh), v = __fdividef(yh, zh);
+        f.umin = fminf(f.umin, u); f.umax = fmaxf(f.umax, u);
+        f.vmin = fminf(f.vmin, v); f.vmax = fmaxf(f.vmax, v);
+    }
+    return f;
+}
+
+// The footprint lies beyond the image by more than the padding (2 pixels,
+// far above the error of the approximate quotients), or the box is wholly
+// behind the camera: no voxel in it projects into the image.
+__device__ __forceinline__ bool outside_image(const FrameConst& c, const Footprint& f) {
+    if (f.behind) return true;
+    return !f.straddle && (f.umax < -2.0f || f.vmax < -2.0f || f.umin > (float)c.dw + 1.0f ||
+                           f.vmin > (float)c.dh + 1.0f);
+}
+
 __device__ __forceinline__ void brick_flags(const FrameConst& c, const BrickSummary* __restrict__ summ,
                                             const uint32_t* __restrict__ tiles, uint32_t b, bool in, bool& geo,
                                             bool& vis) {
@@ -90,36 +129,19 @@ __device__ __forceinline__ void brick_flags(const FrameConst& c, const BrickSumm
             lo[a] = c.origin[a] + ((float)(bc[a] * BRICK) - 0.5f) * c.s_g;
             hi[a] = c.origin[a] + ((float)(bc[a] * BRICK + BRICK) + 0.5f) * c.s_g;
         }
-        float umin = FLT_MAX, umax = -FLT_MAX, vmin = FLT_MAX, vmax = -FLT_MAX;
-        float zmin = FLT_MAX, zmax = -FLT_MAX;
-        bool straddle = false;
-        for (int k = 0; k < 8; ++k) {
-            float x = (k & 1) ? hi[0] : lo[0], y = (k & 2) ? hi[1] : lo[1], z = (k & 4) ? hi[2] : lo[2];
-            float X = c.R[0] * x + c.R[1] * y + c.R[2] * z + c.t[0];
-            float Y = c.R[3] * x + c.R[4] * y + c.R[5] * z + c.t[1];
-            float Z = c.R[6] * x + c.R[7] * y + c.R[8] * z + c.t[2];
-            float xh = c.Kd[0] * X + c.Kd[1] * Y + c.Kd[2] * Z;
-            float yh = c.Kd[3] * X + c.Kd[4] * Y + c.Kd[5] * Z;
-            float zh = c.Kd[6] * X + c.Kd[7] * Y + c.Kd[8] * Z;
-            zmin = fminf(zmin, Z);
-            zmax = fmaxf(zmax, Z);
-            if (zh <= 1e-4f) { straddle = true; continue; }
-            float u = xh / zh, v = yh / zh;
-            umin = fminf(umin, u); umax = fmaxf(umax, u);
-            vmin = fminf(vmin, v); vmax = fmaxf(vmax, v);
-        }
+        const Footprint fp = box_footprint(c, lo, hi);
+        float umin = fp.umin, umax = fp.umax, vmin = fp.vmin, vmax = fp.vmax;
+        const float zmin = fp.zmin, zmax = fp.zmax;
+        const bool straddle = fp.straddle;
         int px0 = 0, px1 = c.dw - 1, py0 = 0, py1 = c.dh - 1;
-        if (!straddle) {
-            // beyond the image by more than the padding: invisible
-            if (umax < -2.0f || vmax < -2.0f || umin > (float)c.dw + 1.0f || vmin > (float)c.dh + 1.0f) {
-                vis = false;
-            } else {
-                // clamp before converting so the integer bounds cannot overflow
-                umin = fmaxf(umin, -4.0f); umax = fminf(umax, (float)c.dw + 4.0f);
-                vmin = fmaxf(vmin, -4.0f); vmax = fminf(vmax, (float)c.dh + 4.0f);
-                px0 = max(0, (int)floorf(umin) - 2); px1 = min(c.dw - 1, (int)ceilf(umax) + 2);
-                py0 = max(0, (int)floorf(vmin) - 2); py1 = min(c.dh - 1, (int)ceilf(vmax) + 2);
-            }
+        if (outside_image(c, fp)) {
+            vis = false;
+        } else if (!straddle) {
+            // clamp before converting so the integer bounds cannot overflow
+            umin = fmaxf(umin, -4.0f); umax = fminf(umax, (float)c.dw + 4.0f);
+            vmin = fmaxf(vmin, -4.0f); vmax = fminf(vmax, (float)c.dh + 4.0f);
+            px0 = max(0, (int)floorf(umin) - 2); px1 = min(c.dw - 1, (int)ceilf(umax) + 2);
+            py0 = max(0, (int)floorf(vmin) - 2); py1 = min(c.dh - 1, (int)ceilf(vmax) + 2);
         }
         uint32_t dmin = 0xFFFFu, dmax = 0u;
         if (vis) {
