@@ -217,6 +217,12 @@ typedef struct {
 } tsdf_profile_report;
 tsdf_status tsdf_profile_enable(tsdf_volume* vol, int32_t enable);
 tsdf_status tsdf_profile_read(tsdf_volume* vol, tsdf_profile_report* out);
+/* Restrict timing to the phases in mask (bit k = phase k; default all):
+ * events are recorded only at the boundaries of those phases, so a single
+ * timed kernel costs two event records per frame instead of eight.  Phases
+ * outside the mask report 0 ms.  Errors: INVALID_ARG (mask outside
+ * 1 .. 2^TSDF_PHASE_COUNT - 1). */
+tsdf_status tsdf_profile_phases(tsdf_volume* vol, uint32_t mask);
 
 /* ------------------------------------------------------------------------
  * Batched fusion: many independent scans (volumes of any sizes), one frame

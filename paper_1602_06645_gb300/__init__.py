@@ -38,6 +38,7 @@ EXPORTS = [
     "tsdf_adjoint_destroy", "tsdf_batch_create", "tsdf_batch_integrate", "tsdf_batch_synchronize",
     "tsdf_batch_set_schedule", "tsdf_batch_get_schedule", "tsdf_batch_autotune", "tsdf_batch_inject_stall",
     "tsdf_batch_destroy", "tsdf_raycast", "tsdf_mesh", "tsdf_texture_layout", "tsdf_texture_fill",
+    "tsdf_profile_phases",
 ]
 PHASES = ["upload", "depth_tiles", "bricks", "geometry", "colour_list", "colour_cells", "colour"]
 
@@ -186,6 +187,8 @@ def load():
     for name in ("tsdf_mesh", "tsdf_texture_layout", "tsdf_texture_fill"):
         getattr(lib, name).restype = ctypes.c_int
     lib.tsdf_profile_enable.argtypes = [vp, ctypes.c_int32]
+    lib.tsdf_profile_phases.argtypes = [vp, ctypes.c_uint32]
+    lib.tsdf_profile_phases.restype = ctypes.c_int
     lib.tsdf_profile_read.argtypes = [vp, ctypes.POINTER(tsdf_profile_report)]
     for name in ("tsdf_create", "tsdf_create_ex", "tsdf_integrate", "tsdf_read", "tsdf_write", "tsdf_synchronize",
                  "tsdf_save", "tsdf_load", "tsdf_set_stream", "tsdf_get_info", "tsdf_get_stats",
@@ -328,6 +331,10 @@ def tsdf_texture_fill(h, triangles, n, wh, offsets, texels):
     keep = []
     _check(load().tsdf_texture_fill(h, _ptr(triangles, np.float32, keep), int(n), _ptr(wh, np.int32, keep),
                                     _ptr(offsets, np.int64, keep), _ptr(texels, np.uint32, keep)), h)
+
+
+def tsdf_profile_phases(h, mask):
+    _check(load().tsdf_profile_phases(h, int(mask)), h)
 
 
 def tsdf_synchronize(h):
@@ -629,6 +636,13 @@ class Volume:
 
     def info(self):
         return tsdf_get_info(self.h)
+
+    def profile_phases(self, phases):
+        """Time only the named phases (see PHASES) from now on."""
+        mask = 0
+        for name in phases:
+            mask |= 1 << PHASES.index(name)
+        tsdf_profile_phases(self.h, mask)
 
     def profile(self, enable=True):
         tsdf_profile_enable(self.h, enable)

@@ -38,6 +38,7 @@ struct tsdf_volume {
         cudaEvent_t e[TSDF_PHASE_COUNT + 1];
     };
     bool profiling;
+    uint32_t prof_mask;  // phases timed (bit k = phase k)
     std::vector<EventSet> ev_pending, ev_pool;
     double prof_ms[TSDF_PHASE_COUNT];
     int64_t prof_frames;

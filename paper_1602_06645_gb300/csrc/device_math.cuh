@@ -87,6 +87,17 @@ __device__ __forceinline__ void back_project(const FrameConst& c, int iu, int iv
 
 __device__ __forceinline__ float lerp(float a, float b, float t) { return fmaf(t, b - a, a); }
 
+// Entry of a kernel of the per-frame chain.  Launched with programmatic
+// stream serialization, a kernel may start while its predecessor drains:
+// griddepcontrol.wait holds it until the predecessor grid has completed and
+// its writes are visible (a no-op after a normal launch), and
+// griddepcontrol.launch_dependents lets the next kernel of the chain be
+// scheduled as soon as this one's blocks retire.
+__device__ __forceinline__ void chain_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Warp-aggregated append of `pred` items to list[ctr++].
 __device__ __forceinline__ void append(bool pred, uint32_t value, uint32_t* ctr, uint32_t* list) {
     unsigned mask = __ballot_sync(0xffffffffu, pred);

@@ -31,6 +31,7 @@ constexpr int CELLS3 = CELLS * CELLS * CELLS;
 // ------------------------------------------------------- depth tiles ----
 __global__ void __launch_bounds__(256) k_depth_tiles(FrameConst c, const uint16_t* __restrict__ depth,
                                                      uint32_t* __restrict__ tiles, Counters* __restrict__ ctr) {
+    chain_enter();
     __shared__ uint32_t s_min[8], s_max[8];
     int px = blockIdx.x * TILE_PX + threadIdx.x;
     int py = blockIdx.y * TILE_PX + threadIdx.y;
@@ -176,6 +177,7 @@ __device__ __forceinline__ void brick_flags(const FrameConst& c, const BrickSumm
 __global__ void __launch_bounds__(256) k_bricks(FrameConst c, const BrickSummary* __restrict__ summ,
                                                 const uint32_t* __restrict__ tiles, Counters* __restrict__ ctr,
                                                 uint32_t* __restrict__ geo_list, uint32_t* __restrict__ vis_list) {
+    chain_enter();
     const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
     uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
     bool geo, vis;
@@ -311,6 +313,7 @@ template <bool PINHOLE, bool FREE_SPACE, bool ALIGNED>
 __global__ void __launch_bounds__(GEO_THREADS, 7) k_geometry(FrameConst c, Volumes vol, const uint16_t* __restrict__ depth,
                                                           Counters* __restrict__ ctr,
                                                           const uint32_t* __restrict__ list) {
+    chain_enter();
     const int lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -323,6 +326,24 @@ __global__ void __launch_bounds__(GEO_THREADS, 7) k_geometry(FrameConst c, Volum
     if (lane == 0 && changed) atomicAdd(&ctr->n_geo_changed, changed);
 }
 
+// Launch with programmatic stream serialization (the kernel begins with
+// chain_enter()), so its launch overlaps the drain of the kernel before it.
+template <typename... Params, typename... Args>
+cudaError_t launch_chained(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                           Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Params>(args)...);
+}
+
 // Launch the k_geometry instance for this frame's camera model, free-space
 // mode and volume shape (every dimension a multiple of 8: no bounds tests).
 cudaError_t launch_k_geometry(const FrameConst& c, const Volumes& v, const Scratch& s, const uint16_t* depth,
@@ -331,7 +352,8 @@ cudaError_t launch_k_geometry(const FrameConst& c, const Volumes& v, const Scrat
     const int key = (c.kd_pinhole ? 4 : 0) | (c.free_space ? 2 : 0) | (aligned ? 1 : 0);
     switch (key) {
 #define TSDF_GEO_CASE(k, P, F, A) \
-    case k: k_geometry<P, F, A><<<grid, GEO_THREADS, 0, stream>>>(c, v, depth, s.ctr, s.geo_list); break;
+    case k: return launch_chained(k_geometry<P, F, A>, dim3(grid), dim3(GEO_THREADS), 0, stream, c, v, depth, \
+                                  s.ctr, s.geo_list);
         TSDF_GEO_CASE(0, false, false, false)
         TSDF_GEO_CASE(1, false, false, true)
         TSDF_GEO_CASE(2, false, true, false)
@@ -385,6 +407,7 @@ __device__ __forceinline__ bool colour_candidate(const FrameConst& c, const Bric
 __global__ void __launch_bounds__(256) k_colour_list(FrameConst c, const BrickSummary* __restrict__ summ,
                                                      Counters* __restrict__ ctr, const uint32_t* __restrict__ vis_list,
                                                      uint32_t* __restrict__ col_list) {
+    chain_enter();
     const uint32_t n = ctr->n_vis;
     for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
         const uint32_t i = base + threadIdx.x;
@@ -883,6 +906,7 @@ __device__ __forceinline__ void band_brick(const FrameConst& c, const Volumes& v
 __global__ void __launch_bounds__(COL_THREADS, 5) k_colour_band(FrameConst c, Volumes vol,
                                                                 const uint16_t* __restrict__ depth,
                                                                 const uint8_t* __restrict__ rgb, Scratch scr) {
+    chain_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ColourSlot& S = reinterpret_cast<ColourSlot*>(smem_raw)[threadIdx.x >> 5];
     Counters* __restrict__ ctr = scr.ctr;
@@ -913,6 +937,7 @@ __global__ void __launch_bounds__(COL_THREADS, 5) k_colour_band(FrameConst c, Vo
 // bricks.
 __global__ void __launch_bounds__(256) k_colour_voxels(FrameConst c, Volumes vol, const uint16_t* __restrict__ depth,
                                                        const uint8_t* __restrict__ rgb, Scratch scr) {
+    chain_enter();
     Counters* __restrict__ ctr = scr.ctr;
     const uint32_t nv = min(ctr->n_vox, scr.vox_cap);
     uint32_t count = 0;
@@ -1346,26 +1371,33 @@ cudaError_t launch_frame(const FrameConst& c, const Volumes& v, const Scratch& s
                          const uint8_t* rgb, const LaunchGrids& g, cudaStream_t stream, cudaEvent_t* ev) {
     const int grid_geo = g.geo, grid_col = g.col;
     auto mark = [&](int i) {
-        if (ev) cudaEventRecord(ev[i], stream);
+        if (ev && ev[i]) cudaEventRecord(ev[i], stream);
     };
     mark(0);
     dim3 tg(c.tiles_x, c.tiles_y);
-    k_depth_tiles<<<tg, dim3(TILE_PX, TILE_PX), 0, stream>>>(c, depth, s.depth_tiles, s.ctr);
+    cudaError_t e = launch_chained(k_depth_tiles, tg, dim3(TILE_PX, TILE_PX), 0, stream, c, depth, s.depth_tiles,
+                                   s.ctr);
     mark(1);
     const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
-    k_bricks<<<(nbt + 255) / 256, 256, 0, stream>>>(c, v.summ, s.depth_tiles, s.ctr, s.geo_list, s.vis_list);
+    if (e == cudaSuccess)
+        e = launch_chained(k_bricks, dim3((nbt + 255) / 256), dim3(256), 0, stream, c, v.summ, s.depth_tiles, s.ctr,
+                           s.geo_list, s.vis_list);
     mark(2);
-    launch_k_geometry(c, v, s, depth, grid_geo, stream);
+    if (e == cudaSuccess) e = launch_k_geometry(c, v, s, depth, grid_geo, stream);
     mark(3);
     unsigned gl = (nbt + 255) / 256;
     if (gl > 1024u) gl = 1024u;
-    k_colour_list<<<gl, 256, 0, stream>>>(c, v.summ, s.ctr, s.vis_list, s.col_list);
+    if (e == cudaSuccess)
+        e = launch_chained(k_colour_list, dim3(gl), dim3(256), 0, stream, c, v.summ, s.ctr, s.vis_list, s.col_list);
     mark(4);
-    k_colour_band<<<grid_col, COL_THREADS, colour_smem_bytes(), stream>>>(c, v, depth, rgb, s);
+    if (e == cudaSuccess)
+        e = launch_chained(k_colour_band, dim3(grid_col), dim3(COL_THREADS), colour_smem_bytes(), stream, c, v,
+                           depth, rgb, s);
     mark(5);
-    k_colour_voxels<<<g.vox, 256, 0, stream>>>(c, v, depth, rgb, s);
+    if (e == cudaSuccess)
+        e = launch_chained(k_colour_voxels, dim3(g.vox), dim3(256), 0, stream, c, v, depth, rgb, s);
     mark(6);
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_geometry_static(const FrameConst& c, float* F, uint8_t* W, const uint16_t* depth, Counters* ctr,

@@ -341,6 +341,7 @@ tsdf_status tsdf_create_ex(const int32_t dims_geo[3], const int32_t dims_col[3],
     if (!(p.sigma > 0.0f) || !std::isfinite(p.sigma)) return TSDF_ERR_INVALID_ARG;
     if (p.colour_mode < 0 || p.colour_mode > 1 || p.sample_mode < 0 || p.sample_mode > 1) return TSDF_ERR_INVALID_ARG;
     tsdf_volume* v = new (std::nothrow) tsdf_volume();
+    if (v) v->prof_mask = (1u << TSDF_PHASE_COUNT) - 1u;
     if (!v) return TSDF_ERR_OOM;
     v->stream = (cudaStream_t)p.stream;
     v->alloc = p.allocator;
@@ -490,7 +491,7 @@ tsdf_status tsdf_integrate(tsdf_volume* v, const uint16_t* depth_mm, tsdf_image_
         v->ev_pending.push_back(v->ev_pool.back());
         v->ev_pool.pop_back();
         evs = &v->ev_pending.back();
-        cudaEventRecord(evs->e[0], v->stream);
+        if (v->prof_mask & 1u) cudaEventRecord(evs->e[0], v->stream);
     }
     if (!is_device_ptr(depth_mm)) {
         if (v->d_depth_cap < dbytes) {
@@ -522,7 +523,11 @@ tsdf_status tsdf_integrate(tsdf_volume* v, const uint16_t* depth_mm, tsdf_image_
         if (!v->depth_tiles) return fail(v, TSDF_ERR_OOM, "depth tile buffer");
     }
     v->scr.depth_tiles = v->depth_tiles;
-    e = launch_frame(c, v->vol, v->scr, d_depth, d_rgb, v->grids, v->stream, evs ? evs->e + 1 : nullptr);
+    // boundary k + 1 (after phase k, before phase k + 1) is recorded when either side is timed
+    cudaEvent_t marks[TSDF_PHASE_COUNT];
+    for (int k = 0; k < TSDF_PHASE_COUNT; ++k)
+        marks[k] = (evs && (v->prof_mask & (3u << k))) ? evs->e[k + 1] : nullptr;
+    e = launch_frame(c, v->vol, v->scr, d_depth, d_rgb, v->grids, v->stream, evs ? marks : nullptr);
     if (e != cudaSuccess) return cuda_fail(v, e, "integrate launch");
     ++v->frames;
     return TSDF_OK;
@@ -606,7 +611,8 @@ static tsdf_status drain_profile(tsdf_volume* v) {
     for (auto& es : v->ev_pending) {
         for (int k = 0; k < TSDF_PHASE_COUNT; ++k) {
             float ms = 0.0f;
-            if (cudaEventElapsedTime(&ms, es.e[k], es.e[k + 1]) == cudaSuccess) v->prof_ms[k] += ms;
+            if ((v->prof_mask >> k) & 1u)
+                if (cudaEventElapsedTime(&ms, es.e[k], es.e[k + 1]) == cudaSuccess) v->prof_ms[k] += ms;
         }
         ++v->prof_frames;
         v->ev_pool.push_back(es);
@@ -625,6 +631,18 @@ tsdf_status tsdf_profile_enable(tsdf_volume* v, int32_t enable) {
     v->prof_frames = 0;
     cudaError_t e = cudaMemsetAsync(v->scr.ctr, 0, sizeof(Counters), v->stream);
     return e == cudaSuccess ? TSDF_OK : cuda_fail(v, e, "counter reset");
+}
+
+tsdf_status tsdf_profile_phases(tsdf_volume* v, uint32_t mask) {
+    if (!v) return TSDF_ERR_INVALID_ARG;
+    if (mask == 0u || mask >= (1u << TSDF_PHASE_COUNT))
+        return fail(v, TSDF_ERR_INVALID_ARG, "profile: phase mask outside 1 .. 2^7 - 1");
+    tsdf_status s = drain_profile(v);
+    if (s != TSDF_OK) return s;
+    v->prof_mask = mask;
+    for (double& x : v->prof_ms) x = 0.0;
+    v->prof_frames = 0;
+    return TSDF_OK;
 }
 
 tsdf_status tsdf_profile_read(tsdf_volume* v, tsdf_profile_report* out) {

@@ -240,3 +240,28 @@ def test_invalid_frame_arguments_are_rejected():
             v.integrate(*args)
         assert e.value.status == T.TSDF_ERR_INVALID_ARG
     v.close()
+
+
+def test_phase_profile_and_phase_mask():
+    """Phase timing sees every phase of a frame; with a mask only the chosen
+    phase is timed, and the volumes do not depend on either."""
+    seq = synth.sequence_small(n_frames=3, dims_geo=48, seed=9)
+    vols = [T.Volume(seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, seq.max_weight) for _ in range(2)]
+    vols[0].profile(True)
+    vols[1].profile(True)
+    vols[1].profile_phases(["geometry"])
+    for f in range(3):
+        d, c = seq.frame(f)
+        for v in vols:
+            v.integrate(d, c, seq.K_depth, seq.K_rgb, seq.poses[f], seq.T_depth_rgb)
+    full, n_full = vols[0].profile_read()
+    one, n_one = vols[1].profile_read()
+    assert n_full == n_one == 3
+    assert all(full[k] > 0 for k in T.PHASES)
+    assert one["geometry"] > 0 and all(one[k] == 0 for k in T.PHASES if k != "geometry")
+    for a, b in zip(vols[0].read(), vols[1].read()):
+        np.testing.assert_array_equal(a, b)
+    with pytest.raises(T.TsdfError):
+        T.tsdf_profile_phases(vols[0].h, 0)
+    for v in vols:
+        v.close()
