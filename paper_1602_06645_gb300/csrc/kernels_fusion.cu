@@ -89,19 +89,39 @@ struct Footprint {
 
 __device__ __forceinline__ Footprint box_footprint(const FrameConst& c, const float lo[3], const float hi[3]) {
     Footprint f{FLT_MAX, -FLT_MAX, FLT_MAX, -FLT_MAX, FLT_MAX, -FLT_MAX, false, true};
+    // camera and homogeneous image coordinates are affine in the corner, so
+    // the corners are the lo corner plus sums of three edge vectors
+    float X0[3], dX[3][3], h0[3], dh[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        X0[r] = c.R[3 * r] * lo[0] + c.R[3 * r + 1] * lo[1] + c.R[3 * r + 2] * lo[2] + c.t[r];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) dX[r][a] = c.R[3 * r + a] * (hi[a] - lo[a]);
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        h0[r] = c.Kd[3 * r] * X0[0] + c.Kd[3 * r + 1] * X0[1] + c.Kd[3 * r + 2] * X0[2];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            dh[r][a] = c.Kd[3 * r] * dX[0][a] + c.Kd[3 * r + 1] * dX[1][a] + c.Kd[3 * r + 2] * dX[2][a];
+    }
+#pragma unroll
     for (int k = 0; k < 8; ++k) {
-        float x = (k & 1) ? hi[0] : lo[0], y = (k & 2) ? hi[1] : lo[1], z = (k & 4) ? hi[2] : lo[2];
-        float X = c.R[0] * x + c.R[1] * y + c.R[2] * z + c.t[0];
-        float Y = c.R[3] * x + c.R[4] * y + c.R[5] * z + c.t[1];
-        float Z = c.R[6] * x + c.R[7] * y + c.R[8] * z + c.t[2];
-        float xh = c.Kd[0] * X + c.Kd[1] * Y + c.Kd[2] * Z;
-        float yh = c.Kd[3] * X + c.Kd[4] * Y + c.Kd[5] * Z;
-        float zh = c.Kd[6] * X + c.Kd[7] * Y + c.Kd[8] * Z;
+        float Z = X0[2], xh = h0[0], yh = h0[1], zh = h0[2];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            if ((k >> a) & 1) {
+                Z += dX[2][a];
+                xh += dh[0][a];
+                yh += dh[1][a];
+                zh += dh[2][a];
+            }
         f.zmin = fminf(f.zmin, Z);
         f.zmax = fmaxf(f.zmax, Z);
-        f.behind = f.behind && zh <= 0.0f;
+        f.behind = f.behind && zh < -1e-5f;  // margin over the rounding of the corner sums
         if (zh <= 1e-4f) { f.straddle = true; continue; }
-        float u = __fdividef(xh, zh), v = __fdividef(yh, zh);
+        const float rz = __frcp_rn(zh);
+        const float u = xh * rz, v = yh * rz;
         f.umin = fminf(f.umin, u); f.umax = fmaxf(f.umax, u);
         f.vmin = fminf(f.vmin, v); f.vmax = fmaxf(f.vmax, v);
     }
@@ -117,6 +137,27 @@ __device__ __forceinline__ bool outside_image(const FrameConst& c, const Footpri
                            f.vmin > (float)c.dh + 1.0f);
 }
 
+// Quick conservative test for a pinhole depth camera: the ball around the
+// padded brick (centre p, radius r) lies wholly behind the camera, or wholly
+// in front and beyond the image: then no voxel of the brick projects into
+// the image.  Over the ball X' is within X +- r, Y' within Y +- r and Z' within
+// Z +- r > 0, so u = fx X' / Z' + cx is bounded by its values at those ends.
+__device__ __forceinline__ bool ball_outside_image(const FrameConst& c, const float p[3], float r) {
+    const float X = c.R[0] * p[0] + c.R[1] * p[1] + c.R[2] * p[2] + c.t[0];
+    const float Y = c.R[3] * p[0] + c.R[4] * p[1] + c.R[5] * p[2] + c.t[1];
+    const float Z = c.R[6] * p[0] + c.R[7] * p[1] + c.R[8] * p[2] + c.t[2];
+    if (Z + r < 0.0f) return true;
+    if (!(Z - r > 1e-3f)) return false;  // may straddle the camera plane: decide with the box
+    const float i0 = __frcp_rn(Z - r), i1 = __frcp_rn(Z + r);
+    const float xa = X - r, xb = X + r, ya = Y - r, yb = Y + r;
+    const float u0 = c.Kd[0] * xa * i0, u1 = c.Kd[0] * xa * i1, u2 = c.Kd[0] * xb * i0, u3 = c.Kd[0] * xb * i1;
+    const float v0 = c.Kd[4] * ya * i0, v1 = c.Kd[4] * ya * i1, v2 = c.Kd[4] * yb * i0, v3 = c.Kd[4] * yb * i1;
+    const float umin = fminf(fminf(u0, u1), fminf(u2, u3)) + c.Kd[2], umax = fmaxf(fmaxf(u0, u1), fmaxf(u2, u3)) + c.Kd[2];
+    const float vmin = fminf(fminf(v0, v1), fminf(v2, v3)) + c.Kd[5], vmax = fmaxf(fmaxf(v0, v1), fmaxf(v2, v3)) + c.Kd[5];
+    // one pixel more than the box test's padding covers the rounding here
+    return umax < -3.0f || vmax < -3.0f || umin > (float)c.dw + 2.0f || vmin > (float)c.dh + 2.0f;
+}
+
 __device__ __forceinline__ void brick_flags(const FrameConst& c, const BrickSummary* __restrict__ summ,
                                             const uint32_t* __restrict__ tiles, uint32_t b, bool in, bool& geo,
                                             bool& vis) {
@@ -124,6 +165,17 @@ __device__ __forceinline__ void brick_flags(const FrameConst& c, const BrickSumm
     geo = in;
     if (in && c.culling) {
         int bx = b % c.nb[0], by = (b / c.nb[0]) % c.nb[1], bz = b / (c.nb[0] * c.nb[1]);
+        if (c.kd_pinhole) {
+            const float p[3] = {c.origin[0] + (float)(bx * BRICK + BRICK / 2) * c.s_g,
+                                c.origin[1] + (float)(by * BRICK + BRICK / 2) * c.s_g,
+                                c.origin[2] + (float)(bz * BRICK + BRICK / 2) * c.s_g};
+            // half-diagonal of the padded brick (4.5 voxels per axis) with 0.1 % and 10 um to spare
+            const float r = fmaf(7.8e-3f, c.s_g, 1e-5f) + 4.5f * 1.7320508f * c.s_g;
+            if (ball_outside_image(c, p, r)) {
+                vis = geo = false;
+                return;
+            }
+        }
         float lo[3], hi[3];
         int bc[3] = {bx, by, bz};
         for (int a = 0; a < 3; ++a) {
