@@ -176,6 +176,7 @@ __device__ __forceinline__ void brick_flags(const FrameConst& c, const BrickSumm
                 return;
             }
         }
+        const BrickSummary s = summ[b];  // read early: its latency overlaps the footprint and tile reads
         float lo[3], hi[3];
         int bc[3] = {bx, by, bz};
         for (int a = 0; a < 3; ++a) {
@@ -199,13 +200,19 @@ __device__ __forceinline__ void brick_flags(const FrameConst& c, const BrickSumm
         uint32_t dmin = 0xFFFFu, dmax = 0u;
         if (vis) {
             int tx0 = px0 / TILE_PX, tx1 = px1 / TILE_PX, ty0 = py0 / TILE_PX, ty1 = py1 / TILE_PX;
-            if ((tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= 64) {
-                for (int ty = ty0; ty <= ty1; ++ty)
-                    for (int tx = tx0; tx <= tx1; ++tx) {
-                        uint32_t tv = tiles[ty * c.tiles_x + tx];
-                        dmin = min(dmin, tv & 0xFFFFu);
-                        dmax = max(dmax, tv >> 16);
+            if ((tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= 64 && tx1 - tx0 < 8) {
+                // the reads of a tile row are independent: issue them together
+                for (int ty = ty0; ty <= ty1; ++ty) {
+                    const uint32_t* row = tiles + ty * c.tiles_x + tx0;
+                    uint32_t tv[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) tv[i] = tx0 + i <= tx1 ? __ldg(row + i) : 0xFFFFu;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        dmin = min(dmin, tv[i] & 0xFFFFu);
+                        dmax = max(dmax, tv[i] >> 16);
                     }
+                }
             } else {
                 dmin = 1u;
                 dmax = 0xFFFFu;
@@ -215,7 +222,6 @@ __device__ __forceinline__ void brick_flags(const FrameConst& c, const BrickSumm
         }
         geo = vis;
         if (vis) {
-            const BrickSummary s = summ[b];
             bool sat = c.free_space == 0 || (s.fmin == 1.0f && s.wmin == (uint32_t)c.max_weight);
             if (sat && zmax < (float)dmin * 0.001f - c.mu - 2e-3f) geo = false;
             // colour: Eq. 7 needs |Z - d| <= sigma (pinhole K_c: the back-projected
@@ -226,6 +232,37 @@ __device__ __forceinline__ void brick_flags(const FrameConst& c, const BrickSumm
     }
 }
 
+// Append the flagged values of a whole block to two lists with one atomic per
+// list per block (all threads of the block call it): thousands of warps
+// finishing together would otherwise queue on the two counters.
+template <int NT>
+__device__ __forceinline__ void block_append2(bool p0, bool p1, uint32_t value, uint32_t* ctr0, uint32_t* list0,
+                                              uint32_t* ctr1, uint32_t* list1) {
+    constexpr int NW = NT / 32;
+    __shared__ uint32_t off[2][NW + 1];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned m0 = __ballot_sync(0xffffffffu, p0), m1 = __ballot_sync(0xffffffffu, p1);
+    if (lane == 0) {
+        off[0][wid] = __popc(m0);
+        off[1][wid] = __popc(m1);
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        uint32_t tot = 0;
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t n = off[threadIdx.x][w];
+            off[threadIdx.x][w] = tot;
+            tot += n;
+        }
+        off[threadIdx.x][NW] = tot ? atomicAdd(threadIdx.x ? ctr1 : ctr0, tot) : 0u;
+    }
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    if (p0) list0[off[0][NW] + off[0][wid] + __popc(m0 & lt)] = value;
+    if (p1) list1[off[1][NW] + off[1][wid] + __popc(m1 & lt)] = value;
+    __syncthreads();  // off is reused by the block's next call
+}
+
 __global__ void __launch_bounds__(256) k_bricks(FrameConst c, const BrickSummary* __restrict__ summ,
                                                 const uint32_t* __restrict__ tiles, Counters* __restrict__ ctr,
                                                 uint32_t* __restrict__ geo_list, uint32_t* __restrict__ vis_list) {
@@ -234,8 +271,7 @@ __global__ void __launch_bounds__(256) k_bricks(FrameConst c, const BrickSummary
     uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
     bool geo, vis;
     brick_flags(c, summ, tiles, b, b < nbt, geo, vis);
-    append(geo, b, &ctr->n_geo, geo_list);
-    append(vis, b, &ctr->n_vis, vis_list);
+    block_append2<256>(geo, vis, b, &ctr->n_geo, geo_list, &ctr->n_vis, vis_list);
 }
 
 // ---------------------------------------------------------- geometry ----
@@ -434,7 +470,8 @@ __device__ __forceinline__ bool colour_candidate(const FrameConst& c, const Bric
     if (!c.culling) return true;
     const int bx = b % c.nb[0], by = (b / c.nb[0]) % c.nb[1], bz = b / (c.nb[0] * c.nb[1]);
     uint32_t acc = summ[b].flags & 3u;
-    for (int dz = -1; dz <= 1 && acc != 3u; ++dz) {
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz) {  // no early exit: the 27 reads are independent
         const int z = bz + dz;
         if (z < 0 || z >= c.nb[2]) continue;
         for (int dy = -1; dy <= 1; ++dy) {
@@ -456,7 +493,9 @@ __device__ __forceinline__ bool colour_candidate(const FrameConst& c, const Bric
     return acc == 3u;
 }
 
-__global__ void __launch_bounds__(256) k_colour_list(FrameConst c, const BrickSummary* __restrict__ summ,
+constexpr int LIST_THREADS = 256;
+
+__global__ void __launch_bounds__(LIST_THREADS) k_colour_list(FrameConst c, const BrickSummary* __restrict__ summ,
                                                      Counters* __restrict__ ctr, const uint32_t* __restrict__ vis_list,
                                                      uint32_t* __restrict__ col_list) {
     chain_enter();
@@ -470,7 +509,7 @@ __global__ void __launch_bounds__(256) k_colour_list(FrameConst c, const BrickSu
             act = true;
             act = colour_candidate(c, summ, b);
         }
-        append(act, b, &ctr->n_col, col_list);
+        block_append2<LIST_THREADS>(act, false, b, &ctr->n_col, col_list, nullptr, nullptr);
     }
 }
 
@@ -1437,10 +1476,11 @@ cudaError_t launch_frame(const FrameConst& c, const Volumes& v, const Scratch& s
     mark(2);
     if (e == cudaSuccess) e = launch_k_geometry(c, v, s, depth, grid_geo, stream);
     mark(3);
-    unsigned gl = (nbt + 255) / 256;
+    unsigned gl = (nbt + LIST_THREADS - 1) / LIST_THREADS;
     if (gl > 1024u) gl = 1024u;
     if (e == cudaSuccess)
-        e = launch_chained(k_colour_list, dim3(gl), dim3(256), 0, stream, c, v.summ, s.ctr, s.vis_list, s.col_list);
+        e = launch_chained(k_colour_list, dim3(gl), dim3(LIST_THREADS), 0, stream, c, v.summ, s.ctr, s.vis_list,
+                           s.col_list);
     mark(4);
     if (e == cudaSuccess)
         e = launch_chained(k_colour_band, dim3(grid_col), dim3(COL_THREADS), colour_smem_bytes(), stream, c, v,
@@ -1476,9 +1516,9 @@ cudaError_t launch_frame_record(const FrameConst& c, const Volumes& v, const Scr
     const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
     k_bricks<<<(nbt + 255) / 256, 256, 0, stream>>>(c, v.summ, s.depth_tiles, s.ctr, s.geo_list, s.vis_list);
     launch_k_geometry(c, v, s, depth, g.geo, stream);
-    unsigned gl = (nbt + 255) / 256;
+    unsigned gl = (nbt + LIST_THREADS - 1) / LIST_THREADS;
     if (gl > 1024u) gl = 1024u;
-    k_colour_list<<<gl, 256, 0, stream>>>(c, v.summ, s.ctr, s.vis_list, s.col_list);
+    k_colour_list<<<gl, LIST_THREADS, 0, stream>>>(c, v.summ, s.ctr, s.vis_list, s.col_list);
     k_colour_band<<<g.col, COL_THREADS, colour_smem_bytes(), stream>>>(c, v, depth, nullptr, s);
     k_colour_gates<<<g.vox, 256, 0, stream>>>(c, depth, s, a, frame);
     return cudaGetLastError();
