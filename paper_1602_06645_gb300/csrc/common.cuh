@@ -137,11 +137,26 @@ struct Scratch {
     uint32_t vox_cap;
 };
 
+// Per-axis tables of the colour grid, built once on the host with the band
+// kernel's binary32 operations: for colour index k on axis a, the trilinear
+// fraction of its centre (frac) and its geometry cell relative to the owning
+// brick's 10-voxel tile (cell, 0..8); for brick coordinate bb, the first owned
+// colour index (k0[bb], owned range k0[bb] .. k0[bb + 1] - 1) and, per tile
+// cell, the owned indices that fall in it (span[bb * 9 + cell] = first | end << 8,
+// relative to k0[bb]).
+struct AxisTables {
+    const float* frac[3];
+    const int8_t* cell[3];
+    const int32_t* k0[3];
+    const uint16_t* span[3];
+};
+
 struct Volumes {
     float* F;
     uint8_t* W;
     uint32_t* C;
     BrickSummary* summ;
+    AxisTables tab;
 };
 
 // ------------------------------------------------------------- launchers --

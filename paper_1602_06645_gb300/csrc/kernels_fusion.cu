@@ -514,21 +514,6 @@ __global__ void __launch_bounds__(LIST_THREADS) k_colour_list(FrameConst c, cons
 }
 
 // ------------------------------------------------------------ colour ----
-// Range of colour indices whose centres lie in geometry brick bb along one
-// axis: 16 bb Nc <= (2k + 1) Ng < 16 (bb + 1) Nc (exact integer arithmetic, so
-// every colour voxel belongs to exactly one geometry brick).
-__device__ __forceinline__ void owned_range(int bb, int ng, int nc, int& k0, int& k1) {
-    auto lo = [&](int B) -> int {  // smallest k with (2k+1) ng >= 16 B nc
-        const long long num = 16ll * B * nc - ng;  // 2k ng >= num
-        if (num <= 0) return 0;
-        const unsigned den = 2u * (unsigned)ng;
-        if (num < (1ll << 31)) return (int)(((unsigned)num + den - 1u) / den);  // 32-bit division when it fits
-        return (int)((num + den - 1) / (long long)den);
-    };
-    k0 = min(nc, lo(bb));
-    k1 = min(nc, lo(bb + 1));  // exclusive
-}
-
 // HD sample (Eq. 9): nearest pixel, or bilinear over the 2x2 neighbourhood
 // (inside the image), rounded half-up.
 __device__ __forceinline__ bool sample_rgb(const FrameConst& c, const uint8_t* __restrict__ rgb, float u, float v,
@@ -676,7 +661,6 @@ struct ColourSlot {  // one warp's shared-memory working set (~11 KB)
     uint16_t row[3][TILE_G * TILE_G];
     uint16_t cells[CELLS3];
     float frac[3][MAXK];
-    int8_t cellof[3][MAXK];
     uint8_t start[3][CELLS], end[3][CELLS];
     int32_t nbr[27];  // neighbour brick indices, -1 outside the volume
     uint2 out[STAGE];
@@ -750,16 +734,21 @@ __device__ __forceinline__ void band_brick(const FrameConst& c, const Volumes& v
     const unsigned full = 0xffffffffu;
     const float lo_thr = c.band + CELL_EPS, hi_thr = -c.band - CELL_EPS;
     const int bb[3] = {(int)(b % c.nb[0]), (int)((b / c.nb[0]) % c.nb[1]), (int)(b / (c.nb[0] * c.nb[1]))};
-    int k0[3], k1[3];
+    // owned colour ranges and per-cell spans from the per-axis tables
+    int k0[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) owned_range(bb[a], c.ng[a], c.nc[a], k0[a], k1[a]);
+    for (int a = 0; a < 3; ++a) k0[a] = __ldg(vol.tab.k0[a] + bb[a]);
     if (lane < 27) {
         const int x = bb[0] + lane % 3 - 1, y = bb[1] + (lane / 3) % 3 - 1, z = bb[2] + lane / 9 - 1;
         S.nbr[lane] = (x >= 0 && y >= 0 && z >= 0 && x < c.nb[0] && y < c.nb[1] && z < c.nb[2])
                           ? (int32_t)(((int64_t)z * c.nb[1] + y) * c.nb[0] + x)
                           : -1;
-        S.start[lane / 9][lane % 9] = 0;
-        S.end[lane / 9][lane % 9] = 0;
+        const int a = lane / 9, cell = lane % 9;
+        const int ba = a == 0 ? bb[0] : (a == 1 ? bb[1] : bb[2]);  // no dynamic indexing of bb
+        const uint16_t* span = a == 0 ? vol.tab.span[0] : (a == 1 ? vol.tab.span[1] : vol.tab.span[2]);
+        const uint16_t sp = __ldg(span + ba * CELLS + cell);
+        S.start[a][cell] = (uint8_t)(sp & 0xFFu);
+        S.end[a][cell] = (uint8_t)(sp >> 8);
     }
     __syncwarp();
 
@@ -819,36 +808,11 @@ __device__ __forceinline__ void band_brick(const FrameConst& c, const Volumes& v
         for (int i = 0; i < 16; ++i)
             if (i < 15 || lane < 8) stage(S, txs[i], tys[i], tzs[i], hf[i], hw[i], lo_thr, hi_thr);
     }
-    // 1c. per-axis colour tables: trilinear cell and fraction of each owned index
+    // 1c. trilinear fraction of each owned colour index, from the per-axis tables
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const int ka = a == 0 ? k0[0] : (a == 1 ? k0[1] : k0[2]);
-        const int nk = (a == 0 ? k1[0] : (a == 1 ? k1[1] : k1[2])) - ka;
-        const int ta = (a == 0 ? bb[0] : (a == 1 ? bb[1] : bb[2])) * BRICK - 1;
-        const float oa = a == 0 ? c.origin[0] : (a == 1 ? c.origin[1] : c.origin[2]);
-        for (int j = lane; j < nk; j += 32) {
-            const float p = fmaf((float)(ka + j) + 0.5f, c.s_c, oa);
-            const float g = fmaf(p - oa, c.inv_sg, -0.5f);
-            const float i0 = floorf(g);
-            int cell = (int)i0 - ta;
-            if (cell < 0 || cell >= CELLS) {
-                atomicOr(scr.err, ERR_TILE_RANGE);
-                cell = -1;
-            }
-            S.frac[a][j] = g - i0;
-            S.cellof[a][j] = (int8_t)cell;
-        }
-    }
-    __syncwarp();
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const int nk = a == 0 ? k1[0] - k0[0] : (a == 1 ? k1[1] - k0[1] : k1[2] - k0[2]);
-        for (int j = lane; j < nk; j += 32) {
-            const int cell = S.cellof[a][j];
-            if (cell < 0) continue;
-            if (j == 0 || S.cellof[a][j - 1] != cell) S.start[a][cell] = (uint8_t)j;
-            if (j == nk - 1 || S.cellof[a][j + 1] != cell) S.end[a][cell] = (uint8_t)(j + 1);
-        }
+        const int nk = __ldg(vol.tab.k0[a] + bb[a] + 1) - k0[a];
+        for (int j = lane; j < nk; j += 32) S.frac[a][j] = __ldg(vol.tab.frac[a] + k0[a] + j);
     }
     __syncwarp();
 

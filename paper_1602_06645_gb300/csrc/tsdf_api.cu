@@ -322,6 +322,58 @@ const char* tsdf_status_string(tsdf_status s) {
 
 const char* tsdf_last_error(const tsdf_volume* v) { return v ? v->last_error.c_str() : ""; }
 
+// Per-axis colour tables (see AxisTables): the trilinear cell and fraction of
+// each colour index, computed with the same binary32 operations as the band
+// kernel (centre p = fmaf(k + 1/2, s_c, origin), g = fmaf(p - origin, 1/s_g,
+// -1/2), i0 = floor(g), fraction g - i0), the owned index range of each brick
+// coordinate (16 bb Nc <= (2k + 1) Ng < 16 (bb + 1) Nc) and the per-cell spans.
+static tsdf_status build_axis_tables(tsdf_volume* v) {
+    const float inv_sg = 1.0f / v->s_g;
+    for (int a = 0; a < 3; ++a) {
+        const int nc = v->nc[a], ng = v->ng[a], nb = v->nb[a];
+        std::vector<float> frac(nc);
+        std::vector<int8_t> cell(nc);
+        std::vector<int32_t> k0(nb + 1);
+        std::vector<uint16_t> span((size_t)nb * 9, 0);
+        for (int bb = 0; bb <= nb; ++bb) {
+            const long long num = 16ll * bb * nc - ng;  // smallest k with (2k + 1) ng >= 16 bb nc
+            const long long k = num <= 0 ? 0 : (num + 2ll * ng - 1) / (2ll * ng);
+            k0[bb] = (int32_t)std::min<long long>(nc, k);
+        }
+        for (int bb = 0; bb < nb; ++bb) {
+            const int ta = bb * BRICK - 1;
+            for (int k = k0[bb]; k < k0[bb + 1]; ++k) {
+                const float p = std::fmaf((float)k + 0.5f, v->s_c, v->origin[a]);
+                const float g = std::fmaf(p - v->origin[a], inv_sg, -0.5f);
+                const float i0 = std::floor(g);
+                const int rel = (int)i0 - ta;
+                if (rel < 0 || rel > BRICK) return fail(v, TSDF_ERR_INVALID_ARG, "colour grid does not fit the bricks");
+                frac[k] = g - i0;
+                cell[k] = (int8_t)rel;
+                const int j = k - k0[bb];
+                uint16_t& sp = span[(size_t)bb * 9 + rel];
+                if ((sp >> 8) == 0) sp = (uint16_t)(j | ((j + 1) << 8));
+                else sp = (uint16_t)((sp & 0xFFu) | ((j + 1) << 8));
+            }
+        }
+        float* d_frac = (float*)dev_alloc(v, nc * sizeof(float));
+        int8_t* d_cell = (int8_t*)dev_alloc(v, nc);
+        int32_t* d_k0 = (int32_t*)dev_alloc(v, (nb + 1) * sizeof(int32_t));
+        uint16_t* d_span = (uint16_t*)dev_alloc(v, (size_t)nb * 9 * sizeof(uint16_t));
+        if (!d_frac || !d_cell || !d_k0 || !d_span) return fail(v, TSDF_ERR_OOM, "colour axis tables");
+        cudaError_t e = cudaMemcpy(d_frac, frac.data(), nc * sizeof(float), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d_cell, cell.data(), nc, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d_k0, k0.data(), (nb + 1) * sizeof(int32_t), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d_span, span.data(), (size_t)nb * 9 * sizeof(uint16_t), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(v, e, "colour axis tables");
+        v->vol.tab.frac[a] = d_frac;
+        v->vol.tab.cell[a] = d_cell;
+        v->vol.tab.k0[a] = d_k0;
+        v->vol.tab.span[a] = d_span;
+    }
+    return TSDF_OK;
+}
+
 tsdf_status tsdf_create_ex(const int32_t dims_geo[3], const int32_t dims_col[3], float voxel_size, float mu,
                            int32_t max_weight, const tsdf_params* params, tsdf_volume** out) {
     if (!out || !dims_geo || !dims_col) return TSDF_ERR_INVALID_ARG;
@@ -419,6 +471,13 @@ tsdf_status tsdf_create_ex(const int32_t dims_geo[3], const int32_t dims_col[3],
         !v->scr.col_list || !v->scr.err || !v->scr.vox) {
         tsdf_destroy(v);
         return TSDF_ERR_OOM;
+    }
+    {
+        const tsdf_status ts = build_axis_tables(v);
+        if (ts != TSDF_OK) {
+            tsdf_destroy(v);
+            return ts;
+        }
     }
     e = cudaMemsetAsync(v->vol.F, 0, (size_t)nbt * BRICK_VOX * sizeof(float), v->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->vol.W, 0, (size_t)nbt * BRICK_VOX, v->stream);
