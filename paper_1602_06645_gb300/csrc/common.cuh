@@ -143,12 +143,14 @@ struct Scratch {
 // brick's 10-voxel tile (cell, 0..8); for brick coordinate bb, the first owned
 // colour index (k0[bb], owned range k0[bb] .. k0[bb + 1] - 1) and, per tile
 // cell, the owned indices that fall in it (span[bb * 9 + cell] = first | end << 8,
-// relative to k0[bb]).
+// relative to k0[bb]); info[bb] = mask of the tile cells that own indices
+// (9 bits) | most indices of one cell << 9.
 struct AxisTables {
     const float* frac[3];
     const int8_t* cell[3];
     const int32_t* k0[3];
     const uint16_t* span[3];
+    const uint16_t* info[3];
 };
 
 struct Volumes {

@@ -655,10 +655,11 @@ __device__ __forceinline__ bool colour_after_band(const FrameConst& c, uint32_t*
 constexpr int MAXK = 66;    // owned colour indices per axis (colour/geometry ratio <= 8)
 constexpr int STAGE = 256;  // per-warp record staging entries
 
-struct ColourSlot {  // one warp's shared-memory working set (~11 KB)
+struct ColourSlot {  // one warp's shared-memory working set (~9 KB)
     float F[TILE_G3];
-    uint8_t flag[TILE_G3];
-    uint16_t row[3][TILE_G * TILE_G];
+    // per tile row (z * 10 + y): bit x = observed, bit 10 + x = F <= band + eps,
+    // bit 20 + x = F >= -band - eps
+    uint32_t row[TILE_G * TILE_G];
     uint16_t cells[CELLS3];
     float frac[3][MAXK];
     uint8_t start[3][CELLS], end[3][CELLS];
@@ -667,11 +668,18 @@ struct ColourSlot {  // one warp's shared-memory working set (~11 KB)
 };
 
 // Store one staged geometry voxel with its flags.
+// Row-mask bits of one voxel (see ColourSlot::row), at x = 0.
+__device__ __forceinline__ uint32_t voxel_bits(float f, uint32_t w, float lo_thr, float hi_thr) {
+    return (w != 0u ? 1u : 0u) | (f <= lo_thr ? 1u << 10 : 0u) | (f >= hi_thr ? 1u << 20 : 0u);
+}
+
+// Store one staged geometry voxel and its row-mask bits.
 __device__ __forceinline__ void stage(ColourSlot& S, int tx, int ty, int tz, float f, uint32_t w, float lo_thr,
                                       float hi_thr) {
-    const int i = (tz * TILE_G + ty) * TILE_G + tx;
-    S.F[i] = f;
-    S.flag[i] = (uint8_t)((w != 0u ? 1u : 0u) | (f <= lo_thr ? 2u : 0u) | (f >= hi_thr ? 4u : 0u));
+    const int r = tz * TILE_G + ty;
+    S.F[r * TILE_G + tx] = f;
+    const uint32_t bits = voxel_bits(f, w, lo_thr, hi_thr) << tx;
+    if (bits) atomicOr(&S.row[r], bits);
 }
 
 // Offset of tile voxel (tx, ty, tz) in the brick-major volume, or -1.  Tile
@@ -750,6 +758,7 @@ __device__ __forceinline__ void band_brick(const FrameConst& c, const Volumes& v
         S.start[a][cell] = (uint8_t)(sp & 0xFFu);
         S.end[a][cell] = (uint8_t)(sp >> 8);
     }
+    for (int r = lane; r < TILE_G * TILE_G; r += 32) S.row[r] = 0u;
     __syncwarp();
 
     // 1a. centre brick: four float4 of F and four words of w per lane
@@ -767,10 +776,17 @@ __device__ __forceinline__ void band_brick(const FrameConst& c, const Volumes& v
         for (int j = 0; j < 4; ++j) {
             const int q = lane + 32 * j;
             const int x0 = (q & 1) * 4 + 1, y = ((q >> 1) & 7) + 1, z = (q >> 4) + 1;
-            stage(S, x0 + 0, y, z, f[j].x, wv[j] & 0xFFu, lo_thr, hi_thr);
-            stage(S, x0 + 1, y, z, f[j].y, (wv[j] >> 8) & 0xFFu, lo_thr, hi_thr);
-            stage(S, x0 + 2, y, z, f[j].z, (wv[j] >> 16) & 0xFFu, lo_thr, hi_thr);
-            stage(S, x0 + 3, y, z, f[j].w, wv[j] >> 24, lo_thr, hi_thr);
+            const int r = z * TILE_G + y, i = r * TILE_G + x0;
+            S.F[i] = f[j].x;
+            S.F[i + 1] = f[j].y;
+            S.F[i + 2] = f[j].z;
+            S.F[i + 3] = f[j].w;
+            const uint32_t bits = (voxel_bits(f[j].x, wv[j] & 0xFFu, lo_thr, hi_thr) |
+                                   voxel_bits(f[j].y, (wv[j] >> 8) & 0xFFu, lo_thr, hi_thr) << 1 |
+                                   voxel_bits(f[j].z, (wv[j] >> 16) & 0xFFu, lo_thr, hi_thr) << 2 |
+                                   voxel_bits(f[j].w, wv[j] >> 24, lo_thr, hi_thr) << 3)
+                                  << x0;
+            if (bits) atomicOr(&S.row[r], bits);
         }
     }
     // 1b. halo: 6 faces x 64, 12 edges x 8, 8 corners = 488 voxels
@@ -816,37 +832,12 @@ __device__ __forceinline__ void band_brick(const FrameConst& c, const Volumes& v
     }
     __syncwarp();
 
-    // 2. row masks (row = z * 10 + y, bit = x)
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int r = lane + 32 * i;
-        if (r < TILE_G * TILE_G) {
-            uint32_t mo = 0, ml = 0, mh = 0;
-#pragma unroll
-            for (int x = 0; x < TILE_G; ++x) {
-                const uint32_t fl = S.flag[r * TILE_G + x];
-                mo |= (fl & 1u) << x;
-                ml |= ((fl >> 1) & 1u) << x;
-                mh |= ((fl >> 2) & 1u) << x;
-            }
-            S.row[0][r] = (uint16_t)mo;
-            S.row[1][r] = (uint16_t)ml;
-            S.row[2][r] = (uint16_t)mh;
-        }
-    }
-    __syncwarp();
-
     // 3. active cells, compacted
-    uint32_t xmask = 0;
-    int mx = 0, my = 0, mz = 0;  // most colour indices of one cell, per axis
-#pragma unroll
-    for (int cell = 0; cell < CELLS; ++cell) {
-        const int nx = S.end[0][cell] - S.start[0][cell];
-        xmask |= (nx > 0 ? 1u : 0u) << cell;
-        mx = max(mx, nx);
-        my = max(my, S.end[1][cell] - S.start[1][cell]);
-        mz = max(mz, S.end[2][cell] - S.start[2][cell]);
-    }
+    // cells along x that own colour indices, and the most indices of one cell per axis
+    const uint32_t xinfo = __ldg(vol.tab.info[0] + bb[0]);
+    const uint32_t xmask = xinfo & 0x1FFu;
+    const int mx = (int)(xinfo >> 9), my = (int)(__ldg(vol.tab.info[1] + bb[1]) >> 9),
+              mz = (int)(__ldg(vol.tab.info[2] + bb[2]) >> 9);
     uint32_t act[3];
     uint32_t total = 0;
 #pragma unroll
@@ -856,13 +847,15 @@ __device__ __forceinline__ void band_brick(const FrameConst& c, const Volumes& v
         if (yz < CELLS * CELLS) {
             const int cy = yz % CELLS, cz = yz / CELLS;
             if (S.end[1][cy] > S.start[1][cy] && S.end[2][cz] > S.start[2][cz]) {
-                const int r00 = cz * TILE_G + cy, r10 = r00 + 1, r01 = r00 + TILE_G, r11 = r01 + 1;
-                uint32_t o = S.row[0][r00] & S.row[0][r10] & S.row[0][r01] & S.row[0][r11];
+                const int r00 = cz * TILE_G + cy;
+                const uint32_t w00 = S.row[r00], w10 = S.row[r00 + 1], w01 = S.row[r00 + TILE_G],
+                               w11 = S.row[r00 + TILE_G + 1];
+                uint32_t o = w00 & w10 & w01 & w11 & 0x3FFu;
                 o &= o >> 1;
                 uint32_t a = o & xmask;
                 if (c.culling) {
-                    uint32_t l = S.row[1][r00] | S.row[1][r10] | S.row[1][r01] | S.row[1][r11];
-                    uint32_t h = S.row[2][r00] | S.row[2][r10] | S.row[2][r01] | S.row[2][r11];
+                    const uint32_t any = w00 | w10 | w01 | w11;
+                    const uint32_t l = (any >> 10) & 0x3FFu, h = (any >> 20) & 0x3FFu;
                     a &= (l | (l >> 1)) & (h | (h >> 1));
                 }
                 act[r] = a & 0x1FFu;

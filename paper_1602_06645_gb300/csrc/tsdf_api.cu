@@ -356,20 +356,34 @@ static tsdf_status build_axis_tables(tsdf_volume* v) {
                 else sp = (uint16_t)((sp & 0xFFu) | ((j + 1) << 8));
             }
         }
+        std::vector<uint16_t> info(nb, 0);
+        for (int bb = 0; bb < nb; ++bb) {
+            uint32_t mask = 0, most = 0;
+            for (int cl = 0; cl < 9; ++cl) {
+                const uint16_t sp = span[(size_t)bb * 9 + cl];
+                const uint32_t n = (sp >> 8) - (sp & 0xFFu);
+                if (sp >> 8) mask |= 1u << cl;
+                most = std::max(most, (sp >> 8) ? n : 0u);
+            }
+            info[bb] = (uint16_t)(mask | (most << 9));
+        }
+        uint16_t* d_info = (uint16_t*)dev_alloc(v, nb * sizeof(uint16_t));
         float* d_frac = (float*)dev_alloc(v, nc * sizeof(float));
         int8_t* d_cell = (int8_t*)dev_alloc(v, nc);
         int32_t* d_k0 = (int32_t*)dev_alloc(v, (nb + 1) * sizeof(int32_t));
         uint16_t* d_span = (uint16_t*)dev_alloc(v, (size_t)nb * 9 * sizeof(uint16_t));
-        if (!d_frac || !d_cell || !d_k0 || !d_span) return fail(v, TSDF_ERR_OOM, "colour axis tables");
+        if (!d_frac || !d_cell || !d_k0 || !d_span || !d_info) return fail(v, TSDF_ERR_OOM, "colour axis tables");
         cudaError_t e = cudaMemcpy(d_frac, frac.data(), nc * sizeof(float), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(d_cell, cell.data(), nc, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(d_k0, k0.data(), (nb + 1) * sizeof(int32_t), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(d_span, span.data(), (size_t)nb * 9 * sizeof(uint16_t), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d_info, info.data(), nb * sizeof(uint16_t), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_fail(v, e, "colour axis tables");
         v->vol.tab.frac[a] = d_frac;
         v->vol.tab.cell[a] = d_cell;
         v->vol.tab.k0[a] = d_k0;
         v->vol.tab.span[a] = d_span;
+        v->vol.tab.info[a] = d_info;
     }
     return TSDF_OK;
 }
