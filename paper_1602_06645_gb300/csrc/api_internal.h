@@ -28,6 +28,20 @@ struct tsdf_volume {
     size_t depth_tiles_cap;
     uint16_t* d_depth;
     size_t d_depth_cap;
+    // Frame pipelining: the depth tiles and brick culling of frame k + 1 run on
+    // `side` while frame k's colour kernels finish on `stream`.  list_done is
+    // recorded on `stream` after frame k's colour list; bricks_done on `side`
+    // after frame k + 1's culling.  chain_ok: the last call that touched the
+    // volume on `stream` was a pipelined tsdf_integrate (else `side` waits for
+    // all of `stream` first).  Host depth frames alternate between two
+    // staging buffers.
+    cudaStream_t side;
+    cudaEvent_t list_done, bricks_done, main_tail;
+    bool chain_ok;
+    uint16_t* d_depth2;
+    size_t d_depth2_cap;
+    uint8_t* d_rgb2;
+    size_t d_rgb2_cap;
     uint8_t* d_rgb;
     size_t d_rgb_cap;
     int64_t frames;

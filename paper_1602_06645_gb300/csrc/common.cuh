@@ -170,6 +170,15 @@ cudaError_t launch_init_summaries(BrickSummary* summ, int64_t n, cudaStream_t st
 struct LaunchGrids {
     int geo, col, vox;  // persistent grid sizes (blocks) of the geometry and two colour kernels
 };
+// The same frame in two parts: depth tiles and brick culling (which read only
+// the depth image, the brick summaries and the tile buffer) and the rest
+// from the geometry update on.  `list_done` (nullable) is recorded after the
+// colour list, the last reader of the brick lists and tiles of this frame.
+cudaError_t launch_frame_pre(const FrameConst& c, const Volumes& v, const Scratch& s, const uint16_t* depth,
+                             cudaStream_t stream, cudaEvent_t* ev);
+cudaError_t launch_frame_post(const FrameConst& c, const Volumes& v, const Scratch& s, const uint16_t* depth,
+                              const uint8_t* rgb, const LaunchGrids& g, cudaStream_t stream, cudaEvent_t* ev,
+                              cudaEvent_t list_done);
 cudaError_t launch_frame(const FrameConst& c, const Volumes& v, const Scratch& s, const uint16_t* depth,
                          const uint8_t* rgb, const LaunchGrids& g, cudaStream_t stream, cudaEvent_t* ev = nullptr);
 int geometry_blocks_per_sm();

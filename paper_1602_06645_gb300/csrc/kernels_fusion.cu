@@ -46,21 +46,18 @@ __global__ void __launch_bounds__(256) k_depth_tiles(FrameConst c, const uint16_
         for (int i = 1; i < 8; ++i) { mn = min(mn, s_min[i]); mx = max(mx, s_max[i]); }
         tiles[blockIdx.y * c.tiles_x + blockIdx.x] = mn | (mx << 16);
         if (blockIdx.x == 0 && blockIdx.y == 0) {
-            // fold the previous frame's counters into the running totals
+            // fold the previous frame's geometry-side counters into the running
+            // totals (the colour side is folded by the geometry kernel, so this
+            // kernel may run while the previous frame's colour work finishes)
             ctr->tot_geo_updated += ctr->geo_updated;
-            ctr->tot_col_updated += ctr->col_updated;
             ctr->tot_geo_bricks += ctr->n_geo;
-            ctr->tot_col_bricks += ctr->n_col;
             ctr->tot_vis_bricks += ctr->n_vis;
-            ctr->tot_cells += ctr->n_cells;
-            ctr->tot_col_active += ctr->n_col_active;
             ctr->tot_geo_changed += ctr->n_geo_changed;
-            ctr->n_col_active = ctr->n_geo_changed = 0;
+            ctr->n_geo_changed = 0;
             ctr->frames += 1ull;
-            ctr->n_geo = ctr->n_vis = ctr->n_col = 0;
-            ctr->geo_next = ctr->col_next = 0;
-            ctr->n_cells = ctr->n_vox = 0;
-            ctr->geo_updated = ctr->col_updated = 0ull;
+            ctr->n_geo = ctr->n_vis = 0;
+            ctr->geo_next = 0;
+            ctr->geo_updated = 0ull;
         }
     }
 }
@@ -402,6 +399,16 @@ __global__ void __launch_bounds__(GEO_THREADS, 7) k_geometry(FrameConst c, Volum
                                                           Counters* __restrict__ ctr,
                                                           const uint32_t* __restrict__ list) {
     chain_enter();
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // fold the previous frame's colour-side counters into the running totals
+        ctr->tot_col_updated += ctr->col_updated;
+        ctr->tot_col_bricks += ctr->n_col;
+        ctr->tot_cells += ctr->n_cells;
+        ctr->tot_col_active += ctr->n_col_active;
+        ctr->n_col = ctr->col_next = 0;
+        ctr->n_cells = ctr->n_vox = ctr->n_col_active = 0;
+        ctr->col_updated = 0ull;
+    }
     const int lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -1415,9 +1422,8 @@ int voxel_blocks_per_sm() {
     return n > 0 ? n : 1;
 }
 
-cudaError_t launch_frame(const FrameConst& c, const Volumes& v, const Scratch& s, const uint16_t* depth,
-                         const uint8_t* rgb, const LaunchGrids& g, cudaStream_t stream, cudaEvent_t* ev) {
-    const int grid_geo = g.geo, grid_col = g.col;
+cudaError_t launch_frame_pre(const FrameConst& c, const Volumes& v, const Scratch& s, const uint16_t* depth,
+                             cudaStream_t stream, cudaEvent_t* ev) {
     auto mark = [&](int i) {
         if (ev && ev[i]) cudaEventRecord(ev[i], stream);
     };
@@ -1431,22 +1437,40 @@ cudaError_t launch_frame(const FrameConst& c, const Volumes& v, const Scratch& s
         e = launch_chained(k_bricks, dim3((nbt + 255) / 256), dim3(256), 0, stream, c, v.summ, s.depth_tiles, s.ctr,
                            s.geo_list, s.vis_list);
     mark(2);
-    if (e == cudaSuccess) e = launch_k_geometry(c, v, s, depth, grid_geo, stream);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_frame_post(const FrameConst& c, const Volumes& v, const Scratch& s, const uint16_t* depth,
+                              const uint8_t* rgb, const LaunchGrids& g, cudaStream_t stream, cudaEvent_t* ev,
+                              cudaEvent_t list_done) {
+    auto mark = [&](int i) {
+        if (ev && ev[i]) cudaEventRecord(ev[i], stream);
+    };
+    const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
+    cudaError_t e = launch_k_geometry(c, v, s, depth, g.geo, stream);
     mark(3);
     unsigned gl = (nbt + LIST_THREADS - 1) / LIST_THREADS;
     if (gl > 1024u) gl = 1024u;
     if (e == cudaSuccess)
         e = launch_chained(k_colour_list, dim3(gl), dim3(LIST_THREADS), 0, stream, c, v.summ, s.ctr, s.vis_list,
                            s.col_list);
+    if (list_done) cudaEventRecord(list_done, stream);
     mark(4);
     if (e == cudaSuccess)
-        e = launch_chained(k_colour_band, dim3(grid_col), dim3(COL_THREADS), colour_smem_bytes(), stream, c, v,
-                           depth, rgb, s);
+        e = launch_chained(k_colour_band, dim3(g.col), dim3(COL_THREADS), colour_smem_bytes(), stream, c, v, depth,
+                           rgb, s);
     mark(5);
     if (e == cudaSuccess)
         e = launch_chained(k_colour_voxels, dim3(g.vox), dim3(256), 0, stream, c, v, depth, rgb, s);
     mark(6);
     return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_frame(const FrameConst& c, const Volumes& v, const Scratch& s, const uint16_t* depth,
+                         const uint8_t* rgb, const LaunchGrids& g, cudaStream_t stream, cudaEvent_t* ev) {
+    cudaError_t e = launch_frame_pre(c, v, s, depth, stream, ev);
+    if (e == cudaSuccess) e = launch_frame_post(c, v, s, depth, rgb, g, stream, ev, nullptr);
+    return e;
 }
 
 cudaError_t launch_geometry_static(const FrameConst& c, float* F, uint8_t* W, const uint16_t* depth, Counters* ctr,

@@ -232,6 +232,7 @@ tsdf_status write_volume(tsdf_volume* v, T* brick, const T* src, const int32_t d
 
 tsdf_status stage_depth(tsdf_volume* v, const uint16_t* depth_mm, tsdf_image_size dsz, int tiles,
                         const uint16_t** d_depth) {
+    v->chain_ok = false;  // the caller runs a frame outside the integrate pipeline
     const size_t dbytes = (size_t)dsz.width * dsz.height * sizeof(uint16_t);
     *d_depth = depth_mm;
     if (!is_device_ptr(depth_mm)) {
@@ -450,6 +451,14 @@ tsdf_status tsdf_create_ex(const int32_t dims_geo[3], const int32_t dims_col[3],
         delete v;
         return TSDF_ERR_CUDA;
     }
+    if (cudaStreamCreateWithFlags(&v->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&v->list_done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&v->bricks_done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&v->main_tail, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        tsdf_destroy(v);
+        return TSDF_ERR_CUDA;
+    }
     v->grids.geo = sms * geometry_blocks_per_sm();
     v->grids.col = sms * colour_blocks_per_sm();
     v->grids.vox = sms * voxel_blocks_per_sm();
@@ -515,6 +524,12 @@ tsdf_status tsdf_create(const int32_t dims_geo[3], const int32_t dims_col[3], fl
 void tsdf_destroy(tsdf_volume* v) {
     if (!v) return;
     cudaStreamSynchronize(v->stream);
+    if (v->side) {
+        cudaStreamSynchronize(v->side);
+        cudaStreamDestroy(v->side);
+    }
+    for (cudaEvent_t x : {v->list_done, v->bricks_done, v->main_tail})
+        if (x) cudaEventDestroy(x);
     for (auto* list : {&v->ev_pending, &v->ev_pool})
         for (auto& es : *list)
             for (auto& x : es.e) cudaEventDestroy(x);
@@ -527,6 +542,7 @@ tsdf_status tsdf_set_stream(tsdf_volume* v, void* stream) {
     if (!v) return TSDF_ERR_INVALID_ARG;
     cudaStreamSynchronize(v->stream);
     v->stream = (cudaStream_t)stream;
+    v->chain_ok = false;
     return TSDF_OK;
 }
 
@@ -566,27 +582,50 @@ tsdf_status tsdf_integrate(tsdf_volume* v, const uint16_t* depth_mm, tsdf_image_
         evs = &v->ev_pending.back();
         if (v->prof_mask & 1u) cudaEventRecord(evs->e[0], v->stream);
     }
-    if (!is_device_ptr(depth_mm)) {
-        if (v->d_depth_cap < dbytes) {
-            dev_free(v, v->d_depth);
-            v->d_depth = (uint16_t*)dev_alloc(v, dbytes);
-            v->d_depth_cap = v->d_depth ? dbytes : 0;
-            if (!v->d_depth) return fail(v, TSDF_ERR_OOM, "depth staging buffer");
+    // Frame pipelining (see tsdf_volume::side): depth upload, depth tiles and
+    // brick culling go to the side stream, which waits only for the previous
+    // frame's colour list; the geometry update waits for them.  Timing of the
+    // first three phases needs them in stream order, so it turns this off.
+    const bool pipe = !(v->profiling && (v->prof_mask & 0x7u));
+    cudaStream_t pre = pipe ? v->side : v->stream;
+    if (pipe) {
+        if (v->chain_ok) {
+            e = cudaStreamWaitEvent(v->side, v->list_done, 0);
+        } else {
+            e = cudaEventRecord(v->main_tail, v->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(v->side, v->main_tail, 0);
         }
-        e = cudaMemcpyAsync(v->d_depth, depth_mm, dbytes, cudaMemcpyHostToDevice, v->stream);
-        if (e != cudaSuccess) return cuda_fail(v, e, "depth upload");
-        d_depth = v->d_depth;
+        if (e != cudaSuccess) return cuda_fail(v, e, "frame pipeline");
     }
-    if (!is_device_ptr(rgb_hwc)) {
-        if (v->d_rgb_cap < cbytes) {
-            dev_free(v, v->d_rgb);
-            v->d_rgb = (uint8_t*)dev_alloc(v, cbytes);
-            v->d_rgb_cap = v->d_rgb ? cbytes : 0;
-            if (!v->d_rgb) return fail(v, TSDF_ERR_OOM, "RGB staging buffer");
+    if (!is_device_ptr(depth_mm)) {
+        // host frames alternate between two staging buffers, since the colour
+        // kernels of the previous frame may still read the other one
+        const bool second = pipe && (v->frames & 1);
+        uint16_t*& buf = second ? v->d_depth2 : v->d_depth;
+        size_t& cap = second ? v->d_depth2_cap : v->d_depth_cap;
+        if (cap < dbytes) {
+            dev_free(v, buf);
+            buf = (uint16_t*)dev_alloc(v, dbytes);
+            cap = buf ? dbytes : 0;
+            if (!buf) return fail(v, TSDF_ERR_OOM, "depth staging buffer");
         }
-        e = cudaMemcpyAsync(v->d_rgb, rgb_hwc, cbytes, cudaMemcpyHostToDevice, v->stream);
+        e = cudaMemcpyAsync(buf, depth_mm, dbytes, cudaMemcpyHostToDevice, pre);
+        if (e != cudaSuccess) return cuda_fail(v, e, "depth upload");
+        d_depth = buf;
+    }
+    if (!is_device_ptr(rgb_hwc)) {  // likewise for the RGB frame
+        const bool second = pipe && (v->frames & 1);
+        uint8_t*& buf = second ? v->d_rgb2 : v->d_rgb;
+        size_t& cap = second ? v->d_rgb2_cap : v->d_rgb_cap;
+        if (cap < cbytes) {
+            dev_free(v, buf);
+            buf = (uint8_t*)dev_alloc(v, cbytes);
+            cap = buf ? cbytes : 0;
+            if (!buf) return fail(v, TSDF_ERR_OOM, "RGB staging buffer");
+        }
+        e = cudaMemcpyAsync(buf, rgb_hwc, cbytes, cudaMemcpyHostToDevice, pre);
         if (e != cudaSuccess) return cuda_fail(v, e, "RGB upload");
-        d_rgb = v->d_rgb;
+        d_rgb = buf;
     }
     const size_t tiles = (size_t)c.tiles_x * c.tiles_y * sizeof(uint32_t);
     if (v->depth_tiles_cap < tiles) {
@@ -600,8 +639,18 @@ tsdf_status tsdf_integrate(tsdf_volume* v, const uint16_t* depth_mm, tsdf_image_
     cudaEvent_t marks[TSDF_PHASE_COUNT];
     for (int k = 0; k < TSDF_PHASE_COUNT; ++k)
         marks[k] = (evs && (v->prof_mask & (3u << k))) ? evs->e[k + 1] : nullptr;
-    e = launch_frame(c, v->vol, v->scr, d_depth, d_rgb, v->grids, v->stream, evs ? marks : nullptr);
+    e = launch_frame_pre(c, v->vol, v->scr, d_depth, pre, evs && !pipe ? marks : nullptr);
     if (e != cudaSuccess) return cuda_fail(v, e, "integrate launch");
+    if (pipe) {
+        e = cudaEventRecord(v->bricks_done, v->side);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(v->stream, v->bricks_done, 0);
+        if (e != cudaSuccess) return cuda_fail(v, e, "frame pipeline");
+        if (marks[2]) cudaEventRecord(marks[2], v->stream);  // the geometry update starts here
+    }
+    e = launch_frame_post(c, v->vol, v->scr, d_depth, d_rgb, v->grids, v->stream, evs ? marks : nullptr,
+                          pipe ? v->list_done : nullptr);
+    if (e != cudaSuccess) return cuda_fail(v, e, "integrate launch");
+    v->chain_ok = pipe;
     ++v->frames;
     return TSDF_OK;
 }
@@ -622,6 +671,7 @@ tsdf_status tsdf_read(tsdf_volume* v, float* tsdf, uint8_t* w_geo, uint32_t* rgb
 
 tsdf_status tsdf_write(tsdf_volume* v, const float* tsdf, const uint8_t* w_geo, const uint32_t* rgbw) {
     if (!v) return TSDF_ERR_INVALID_ARG;
+    v->chain_ok = false;
     tsdf_status s = write_volume<float>(v, v->vol.F, tsdf, v->ng, launch_from_linear_f32);
     if (s == TSDF_OK) s = write_volume<uint8_t>(v, v->vol.W, w_geo, v->ng, launch_from_linear_u8);
     if (s == TSDF_OK) s = write_volume<uint32_t>(v, v->vol.C, rgbw, v->nc, launch_from_linear_u32);
@@ -697,6 +747,7 @@ static tsdf_status drain_profile(tsdf_volume* v) {
 
 tsdf_status tsdf_profile_enable(tsdf_volume* v, int32_t enable) {
     if (!v) return TSDF_ERR_INVALID_ARG;
+    v->chain_ok = false;
     tsdf_status s = drain_profile(v);
     if (s != TSDF_OK) return s;
     v->profiling = enable != 0;
@@ -708,6 +759,7 @@ tsdf_status tsdf_profile_enable(tsdf_volume* v, int32_t enable) {
 
 tsdf_status tsdf_profile_phases(tsdf_volume* v, uint32_t mask) {
     if (!v) return TSDF_ERR_INVALID_ARG;
+    v->chain_ok = false;
     if (mask == 0u || mask >= (1u << TSDF_PHASE_COUNT))
         return fail(v, TSDF_ERR_INVALID_ARG, "profile: phase mask outside 1 .. 2^7 - 1");
     tsdf_status s = drain_profile(v);
@@ -776,6 +828,7 @@ tsdf_status tsdf_save(tsdf_volume* v, const char* path) {
 
 tsdf_status tsdf_load(tsdf_volume* v, const char* path) {
     if (!v || !path) return TSDF_ERR_INVALID_ARG;
+    v->chain_ok = false;
     FILE* f = std::fopen(path, "rb");
     if (!f) return fail(v, TSDF_ERR_IO, std::string("cannot open ") + path);
     FileHeader h;
