@@ -374,8 +374,8 @@ tsdf_status tsdf_integrate_geometry_static(const int32_t dims[3], float voxel_si
  *   p(t) = o + t d per axis as fmaf(t, d, o), t the distance from the camera
  *   centre o.  The TSDF at p is the trilinear interpolation used by the colour
  *   band gate (it exists only when its 8 corners are inside the volume and
- *   observed).  From t = near, samples step by step_far where the TSDF exists
- *   and is >= 1 (truncated free space) and by step_near elsewhere; the first
+ *   observed).  From t = near, samples step by step_near where the TSDF exists
+ *   and is < 1 (inside the truncation band) and by step_far elsewhere; the first
  *   sample with TSDF <= 0 whose previous sample had TSDF > 0 is a hit, refined
  *   by linear interpolation of the zero crossing; the march ends without a hit
  *   once t > far.  At the hit vertex v: the normal is the normalised central
@@ -385,8 +385,8 @@ tsdf_status tsdf_integrate_geometry_static(const int32_t dims[3], float voxel_si
  * ---------------------------------------------------------------------- */
 typedef struct {
     float near_m, far_m;    /* march range along each ray, metres: 0 <= near < far <= 1000 */
-    float step_far;         /* step in truncated free space, metres; 0 = mu / 2 */
-    float step_near;        /* step elsewhere, metres; 0 = geometry voxel / 2; needs far / step_near <= 2^22 */
+    float step_far;         /* step outside the truncation band, metres; 0 = mu / 2 */
+    float step_near;        /* step inside it, metres; 0 = geometry voxel / 2; needs far / step_near <= 2^22 */
 } tsdf_raycast_params;
 
 /* Ray-cast width x height pixels.  Outputs (any may be NULL; host or device

@@ -21,8 +21,9 @@
  *     the volume and are observed (w > 0).
  *   march: t = near; at each sample the TSDF F(t) is taken; the first sample
  *     with F <= 0 whose predecessor (the sample just before) had F > 0 ends
- *     the march with a hit; the next t is t + (F exists and F >= 1 ? step_far
- *     : step_near); the march stops without a hit once t > far.
+ *     the march with a hit; the next t is t + (F exists and F < 1 ? step_near
+ *     : step_far), the fine step only inside the truncation band; the march
+ *     stops without a hit once t > far.
  *   hit: t* = fmaf(t - t_prev, F_prev / (F_prev - F), t_prev) (linear
  *     interpolation of the zero crossing), vertex v = p(t*).
  *   normal: n_a = F(v + s_g e_a) - F(v - s_g e_a) (central differences of the
@@ -142,7 +143,7 @@ static int rc_pixel(const orc_rc_volume* v, const orc_rc_camera* c, int x, int y
         }
         has_prev = ok;
         if (ok) { Fp = F; tp = t; }
-        t = t + ((ok && F >= 1.0f) ? c->step_far : c->step_near);
+        t = t + ((ok && F < 1.0f) ? c->step_near : c->step_far);
     }
     return 0;
 }

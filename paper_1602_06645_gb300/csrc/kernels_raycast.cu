@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(RC_BX * RC_BY) k_raycast(RayConst c, const flo
             Fp = Fs;
             tp = t;
         }
-        t = t + ((ok && Fs >= 1.0f) ? c.step_far : c.step_near);
+        t = t + ((ok && Fs < 1.0f) ? c.step_near : c.step_far);
     }
     const size_t i = (size_t)y * c.width + x;
     if (range) range[i] = out_t;
