@@ -345,7 +345,7 @@ void tsdf_adjoint_destroy(tsdf_adjoint* adj);
  *                   linear x-fastest, read and updated in place (start from
  *                   zeros for an empty volume)
  *   depth_dev       device uint16 millimetre depth image of dsz, at most
- *                   TSDF_STATIC_MAX_DEPTH_TILES tiles of 16x16 pixels
+ *                   TSDF_STATIC_MAX_DEPTH_TILES tiles of 8x8 pixels
  *   K_depth, T_world_depth  host pointers, as in tsdf_integrate
  *   stream          cudaStream_t the kernels are queued on (NULL = legacy default)
  * Sizes beyond the maxima, NULL pointers and invalid K / T are rejected with
@@ -356,7 +356,7 @@ void tsdf_adjoint_destroy(tsdf_adjoint* adj);
  * start at zero): calls whose work overlaps on the GPU race, so queue them on
  * one stream or wait between them.  Asynchronous with respect to the host. */
 #define TSDF_STATIC_MAX_BRICKS (1 << 20)     /* e.g. 512^3 voxels use 262,144 bricks */
-#define TSDF_STATIC_MAX_DEPTH_TILES 65536    /* e.g. 4096 x 4096 pixels use 65,536 tiles */
+#define TSDF_STATIC_MAX_DEPTH_TILES 262144   /* e.g. 4096 x 4096 pixels use 262,144 tiles */
 tsdf_status tsdf_integrate_geometry_static(const int32_t dims[3], float voxel_size, float mu, int32_t max_weight,
                                            const float origin[3], float* tsdf_dev, uint8_t* w_dev,
                                            const uint16_t* depth_dev, tsdf_image_size dsz, const float K_depth[9],

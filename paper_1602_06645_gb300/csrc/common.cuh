@@ -18,7 +18,8 @@ namespace tsdf {
 // brick of F is 2 KB, of w 512 B, of colour 2 KB: whole DRAM sectors.
 constexpr int BRICK = 8;
 constexpr int BRICK_VOX = BRICK * BRICK * BRICK;
-constexpr int TILE_PX = 16;  // depth-culling tiles are 16x16 pixels
+constexpr int TILE_PX = 8;         // depth-culling tiles are 8x8 pixels
+constexpr int TILE_BLOCK_PX = 16;  // k_depth_tiles: one 16x16-pixel block makes 2x2 tiles
 
 // Per-frame constants, passed by value as a kernel parameter.
 struct FrameConst {
@@ -131,7 +132,7 @@ struct Scratch {
     uint32_t* geo_list;
     uint32_t* vis_list;
     uint32_t* col_list;
-    uint32_t* depth_tiles;  // per 16x16 tile: min valid depth | max valid depth << 16
+    uint32_t* depth_tiles;  // per 8x8 tile: min valid depth | max valid depth << 16
     uint32_t* err;
     uint2* vox;           // colour voxels that passed the band gate this frame: x | y << 16, z
     uint32_t vox_cap;

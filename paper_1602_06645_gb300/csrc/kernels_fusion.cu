@@ -2,7 +2,7 @@
 // update, colour work list and colour update (Section IV.B).
 //
 // Order per frame on one stream:
-//   k_depth_tiles   min / max valid depth of each 16x16 depth tile; zeroes counters
+//   k_depth_tiles   min / max valid depth of each 8x8 depth tile; zeroes counters
 //   k_bricks        conservative per-brick visibility -> geometry and visible lists
 //   k_geometry      persistent: TSDF update of each listed brick, brick summaries
 //   k_colour_list   visible bricks whose 3x3x3 neighbourhood can hold |F| <= band
@@ -32,19 +32,37 @@ constexpr int CELLS3 = CELLS * CELLS * CELLS;
 __global__ void __launch_bounds__(256) k_depth_tiles(FrameConst c, const uint16_t* __restrict__ depth,
                                                      uint32_t* __restrict__ tiles, Counters* __restrict__ ctr) {
     chain_enter();
-    __shared__ uint32_t s_min[8], s_max[8];
-    int px = blockIdx.x * TILE_PX + threadIdx.x;
-    int py = blockIdx.y * TILE_PX + threadIdx.y;
-    uint32_t D = (px < c.dw && py < c.dh) ? depth[(size_t)py * c.dw + px] : 0u;
+    static_assert(TILE_BLOCK_PX == 2 * TILE_PX && TILE_PX == 8, "the lane layout below assumes 8x8 tiles");
+    // a 16x16-pixel block; warp w holds pixel rows 2w and 2w + 1, lane bit 3
+    // selects the left or right 8-pixel half: tile (hx, hy) of the block is
+    // half hx of warps 4 hy .. 4 hy + 3
+    __shared__ uint32_t s_min[8][2], s_max[8][2];
+    const int px = blockIdx.x * TILE_BLOCK_PX + threadIdx.x, py = blockIdx.y * TILE_BLOCK_PX + threadIdx.y;
+    const uint32_t D = (px < c.dw && py < c.dh) ? depth[(size_t)py * c.dw + px] : 0u;
     uint32_t mn = D ? D : 0xFFFFu, mx = D;
-    mn = __reduce_min_sync(0xffffffffu, mn);
-    mx = __reduce_max_sync(0xffffffffu, mx);
-    int tid = threadIdx.y * TILE_PX + threadIdx.x;
-    if ((tid & 31) == 0) { s_min[tid >> 5] = mn; s_max[tid >> 5] = mx; }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        if (o == 8) continue;  // keep the two halves apart
+        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    const int tid = threadIdx.y * TILE_BLOCK_PX + threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if ((lane & 23) == 0) {  // lanes 0 and 8
+        s_min[w][lane >> 3] = mn;
+        s_max[w][lane >> 3] = mx;
+    }
     __syncthreads();
+    if (tid < 4) {
+        const int hx = tid & 1, hy = tid >> 1;
+        uint32_t a = 0xFFFFu, b = 0u;
+        for (int k = 0; k < 4; ++k) {
+            a = min(a, s_min[4 * hy + k][hx]);
+            b = max(b, s_max[4 * hy + k][hx]);
+        }
+        const int tx = blockIdx.x * 2 + hx, ty = blockIdx.y * 2 + hy;
+        if (tx < c.tiles_x && ty < c.tiles_y) tiles[ty * c.tiles_x + tx] = a | (b << 16);
+    }
     if (tid == 0) {
-        for (int i = 1; i < 8; ++i) { mn = min(mn, s_min[i]); mx = max(mx, s_max[i]); }
-        tiles[blockIdx.y * c.tiles_x + blockIdx.x] = mn | (mx << 16);
         if (blockIdx.x == 0 && blockIdx.y == 0) {
             // fold the previous frame's geometry-side counters into the running
             // totals (the colour side is folded by the geometry kernel, so this
@@ -197,19 +215,21 @@ __device__ __forceinline__ void brick_flags(const FrameConst& c, const BrickSumm
         uint32_t dmin = 0xFFFFu, dmax = 0u;
         if (vis) {
             int tx0 = px0 / TILE_PX, tx1 = px1 / TILE_PX, ty0 = py0 / TILE_PX, ty1 = py1 / TILE_PX;
-            if ((tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= 64 && tx1 - tx0 < 8) {
-                // the reads of a tile row are independent: issue them together
-                for (int ty = ty0; ty <= ty1; ++ty) {
-                    const uint32_t* row = tiles + ty * c.tiles_x + tx0;
-                    uint32_t tv[8];
+            if ((tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= 256 && tx1 - tx0 < 16) {
+                // the reads of a tile row are independent: issue them together,
+                // eight at a time
+                for (int ty = ty0; ty <= ty1; ++ty)
+                    for (int x0 = tx0; x0 <= tx1; x0 += 8) {
+                        const uint32_t* row = tiles + ty * c.tiles_x + x0;
+                        uint32_t tv[8];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) tv[i] = tx0 + i <= tx1 ? __ldg(row + i) : 0xFFFFu;
+                        for (int i = 0; i < 8; ++i) tv[i] = x0 + i <= tx1 ? __ldg(row + i) : 0xFFFFu;
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        dmin = min(dmin, tv[i] & 0xFFFFu);
-                        dmax = max(dmax, tv[i] >> 16);
+                        for (int i = 0; i < 8; ++i) {
+                            dmin = min(dmin, tv[i] & 0xFFFFu);
+                            dmax = max(dmax, tv[i] >> 16);
+                        }
                     }
-                }
             } else {
                 dmin = 1u;
                 dmax = 0xFFFFu;
@@ -217,7 +237,8 @@ __device__ __forceinline__ void brick_flags(const FrameConst& c, const BrickSumm
             if (dmax == 0u) vis = false;                                   // no measurement under it
             else if (zmin > (float)dmax * 0.001f + c.cull_behind) vis = false;  // hidden behind every surface
         }
-        geo = vis;
+        // the geometry update skips sdf < -mu, so mu (not max(mu, sigma)) bounds it
+        geo = vis && !(zmin > (float)dmax * 0.001f + c.mu + 2e-3f);
         if (vis) {
             bool sat = c.free_space == 0 || (s.fmin == 1.0f && s.wmin == (uint32_t)c.max_weight);
             if (sat && zmax < (float)dmin * 0.001f - c.mu - 2e-3f) geo = false;
@@ -1052,7 +1073,7 @@ __global__ void __launch_bounds__(256) k_bricks_static(FrameConst c, const uint3
         if (vis) {
             uint32_t dmax = 0u;
             int tx0 = px0 / TILE_PX, tx1 = px1 / TILE_PX, ty0 = py0 / TILE_PX, ty1 = py1 / TILE_PX;
-            if ((tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= 64) {
+            if ((tx1 - tx0 + 1) * (ty1 - ty0 + 1) <= 256) {
                 for (int ty = ty0; ty <= ty1; ++ty)
                     for (int tx = tx0; tx <= tx1; ++tx) dmax = max(dmax, tiles[ty * c.tiles_x + tx] >> 16);
             } else {
@@ -1275,7 +1296,7 @@ __global__ void __launch_bounds__(COL_THREADS, 4) k_batch_step(const ScanDesc* _
     if (tid == 0) sync->band_next = 0;
     if (blockIdx.x == 0 && *(volatile unsigned*)&sync->stall) return;  // test injection: never arrive
     scan_prefix(pre, n, 1, [&](int i) { return (uint32_t)(descs[i].c.tiles_x * descs[i].c.tiles_y); });
-    for (uint32_t item = warp; item < pre[n]; item += nwarps) {  // one warp per 16x16 depth tile
+    for (uint32_t item = warp; item < pre[n]; item += nwarps) {  // one warp per depth tile
         const int s = find_scan(pre, n, item);
         const FrameConst& c = descs[s].c;
         const uint32_t t = item - pre[s];
@@ -1428,8 +1449,8 @@ cudaError_t launch_frame_pre(const FrameConst& c, const Volumes& v, const Scratc
         if (ev && ev[i]) cudaEventRecord(ev[i], stream);
     };
     mark(0);
-    dim3 tg(c.tiles_x, c.tiles_y);
-    cudaError_t e = launch_chained(k_depth_tiles, tg, dim3(TILE_PX, TILE_PX), 0, stream, c, depth, s.depth_tiles,
+    const dim3 tg((c.tiles_x + 1) / 2, (c.tiles_y + 1) / 2);
+    cudaError_t e = launch_chained(k_depth_tiles, tg, dim3(TILE_BLOCK_PX, TILE_BLOCK_PX), 0, stream, c, depth, s.depth_tiles,
                                    s.ctr);
     mark(1);
     const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
@@ -1475,8 +1496,8 @@ cudaError_t launch_frame(const FrameConst& c, const Volumes& v, const Scratch& s
 
 cudaError_t launch_geometry_static(const FrameConst& c, float* F, uint8_t* W, const uint16_t* depth, Counters* ctr,
                                    uint32_t* tiles, uint32_t* geo_list, int grid_geo, cudaStream_t stream) {
-    dim3 tg(c.tiles_x, c.tiles_y);
-    k_depth_tiles<<<tg, dim3(TILE_PX, TILE_PX), 0, stream>>>(c, depth, tiles, ctr);
+    const dim3 tg((c.tiles_x + 1) / 2, (c.tiles_y + 1) / 2);
+    k_depth_tiles<<<tg, dim3(TILE_BLOCK_PX, TILE_BLOCK_PX), 0, stream>>>(c, depth, tiles, ctr);
     const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
     k_bricks_static<<<(nbt + 255) / 256, 256, 0, stream>>>(c, tiles, ctr, geo_list);
     if (c.kd_pinhole && c.free_space)
@@ -1492,8 +1513,8 @@ cudaError_t launch_geometry_static(const FrameConst& c, float* F, uint8_t* W, co
 
 cudaError_t launch_frame_record(const FrameConst& c, const Volumes& v, const Scratch& s, const uint16_t* depth,
                                 const LaunchGrids& g, const AdjBuffers& a, int frame, cudaStream_t stream) {
-    dim3 tg(c.tiles_x, c.tiles_y);
-    k_depth_tiles<<<tg, dim3(TILE_PX, TILE_PX), 0, stream>>>(c, depth, s.depth_tiles, s.ctr);
+    const dim3 tg((c.tiles_x + 1) / 2, (c.tiles_y + 1) / 2);
+    k_depth_tiles<<<tg, dim3(TILE_BLOCK_PX, TILE_BLOCK_PX), 0, stream>>>(c, depth, s.depth_tiles, s.ctr);
     const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
     k_bricks<<<(nbt + 255) / 256, 256, 0, stream>>>(c, v.summ, s.depth_tiles, s.ctr, s.geo_list, s.vis_list);
     launch_k_geometry(c, v, s, depth, g.geo, stream);

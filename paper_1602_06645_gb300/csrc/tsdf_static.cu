@@ -20,7 +20,7 @@ using namespace tsdf;
 namespace {
 
 constexpr int64_t STATIC_MAX_BRICKS = TSDF_STATIC_MAX_BRICKS;   // 8^3 geometry bricks
-constexpr int64_t STATIC_MAX_TILES = TSDF_STATIC_MAX_DEPTH_TILES;  // 16x16 depth tiles
+constexpr int64_t STATIC_MAX_TILES = TSDF_STATIC_MAX_DEPTH_TILES;  // 8x8 depth tiles
 constexpr size_t COUNTERS_BYTES = 256;
 constexpr size_t TILES_BYTES = (size_t)STATIC_MAX_TILES * sizeof(uint32_t);
 constexpr size_t LIST_BYTES = (size_t)STATIC_MAX_BRICKS * sizeof(uint32_t);
