@@ -127,12 +127,15 @@ tsdf_status tsdf_create_ex(const int32_t dims_geo[3], const int32_t dims_col[3],
  *   depth_mm  dsz.height x dsz.width uint16, host or device pointer
  *   rgb_hwc   csz.height x csz.width x 3 uint8, host or device pointer
  *   K_depth, K_rgb, T_world_depth, T_depth_rgb: host pointers, read before return
- * Host images are copied with cudaMemcpyAsync on the handle's stream:
- * pageable memory is consumed before the call returns, page-locked memory when
- * the stream reaches the copy.  Device images are read in place by kernels
- * queued on the stream.  In both asynchronous cases the caller must not
- * overwrite the buffer until the stream has passed that point.  The call is
- * asynchronous with respect to the host.
+ * Host images are copied with cudaMemcpyAsync on the volume's internal
+ * second stream (which runs the frame's depth tiles and brick culling beside
+ * the previous frame's colour kernels, and which the handle's stream waits
+ * for before the frame's geometry update): pageable memory is consumed before
+ * the call returns, page-locked memory by the time the handle's stream
+ * reaches the frame's geometry update.  Device images are read in place by
+ * kernels queued on the streams.  In both asynchronous cases the caller must
+ * not overwrite the buffer until the handle's stream has passed the frame's
+ * last kernel.  The call is asynchronous with respect to the host.
  * Errors: INVALID_ARG (NULL pointers, sizes outside 1..16384, non-finite or
  * singular K, non-finite or non-rigid T with |R^T R - I| > 1e-4), OOM, CUDA. */
 tsdf_status tsdf_integrate(tsdf_volume* vol, const uint16_t* depth_mm, tsdf_image_size dsz, const uint8_t* rgb_hwc,
@@ -195,6 +198,21 @@ typedef struct {
     int64_t total_col_active_bricks, total_cells, total_geo_changed_bricks;
 } tsdf_stats;
 tsdf_status tsdf_get_stats(tsdf_volume* vol, tsdf_stats* out);
+
+/* Asynchronous form of tsdf_get_stats, for a caller that queues frame k + 1
+ * before it reads frame k's counters.  tsdf_stats_request queues, on the
+ * volume's stream after the work queued so far, a copy of the counters
+ * (TSDF_STATS_COPY_BYTES bytes, device to page-locked host memory owned by
+ * the volume) into slot 0 or 1, and returns without waiting.
+ * tsdf_stats_collect waits for the last copy into that slot and fills *out
+ * as tsdf_get_stats would have at the time of the request (a slot never
+ * requested reads as all zeros).  The next tsdf_integrate orders its depth
+ * tiles after a pending copy, so the copy sees the requested frame's
+ * counters complete; its uploads do not wait.  Slots other than 0 and 1 and
+ * NULL pointers are rejected with TSDF_ERR_INVALID_ARG. */
+#define TSDF_STATS_COPY_BYTES 128
+tsdf_status tsdf_stats_request(tsdf_volume* vol, int32_t slot);
+tsdf_status tsdf_stats_collect(tsdf_volume* vol, int32_t slot, tsdf_stats* out);
 
 /* Phase timing.  While enabled, tsdf_integrate records CUDA events on the
  * handle's stream around each phase of a frame; tsdf_profile_read waits for

@@ -32,7 +32,7 @@ TSDF_SAMPLE_NEAREST, TSDF_SAMPLE_BILINEAR = 0, 1
 EXPORTS = [
     "tsdf_params_default", "tsdf_create", "tsdf_create_ex", "tsdf_integrate", "tsdf_read", "tsdf_write",
     "tsdf_synchronize", "tsdf_save", "tsdf_load", "tsdf_destroy", "tsdf_set_stream", "tsdf_get_info",
-    "tsdf_get_stats", "tsdf_status_string", "tsdf_last_error", "tsdf_profile_enable", "tsdf_profile_read",
+    "tsdf_get_stats", "tsdf_stats_request", "tsdf_stats_collect", "tsdf_status_string", "tsdf_last_error", "tsdf_profile_enable", "tsdf_profile_read",
     "tsdf_integrate_geometry_static", "tsdf_adjoint_create", "tsdf_adjoint_record", "tsdf_adjoint_finalize",
     "tsdf_adjoint_voxels", "tsdf_adjoint_pairs", "tsdf_adjoint_forward", "tsdf_adjoint_backward",
     "tsdf_adjoint_destroy", "tsdf_batch_create", "tsdf_batch_integrate", "tsdf_batch_synchronize",
@@ -146,6 +146,8 @@ def load():
     lib.tsdf_set_stream.argtypes = [vp, vp]
     lib.tsdf_get_info.argtypes = [vp, ctypes.POINTER(tsdf_info)]
     lib.tsdf_get_stats.argtypes = [vp, ctypes.POINTER(tsdf_stats)]
+    lib.tsdf_stats_request.argtypes = [vp, ctypes.c_int32]
+    lib.tsdf_stats_collect.argtypes = [vp, ctypes.c_int32, ctypes.POINTER(tsdf_stats)]
     lib.tsdf_status_string.argtypes = [ctypes.c_int]
     lib.tsdf_status_string.restype = ctypes.c_char_p
     lib.tsdf_last_error.argtypes = [vp]
@@ -192,7 +194,7 @@ def load():
     lib.tsdf_profile_read.argtypes = [vp, ctypes.POINTER(tsdf_profile_report)]
     for name in ("tsdf_create", "tsdf_create_ex", "tsdf_integrate", "tsdf_read", "tsdf_write", "tsdf_synchronize",
                  "tsdf_save", "tsdf_load", "tsdf_set_stream", "tsdf_get_info", "tsdf_get_stats",
-                 "tsdf_profile_enable", "tsdf_profile_read"):
+                 "tsdf_stats_request", "tsdf_stats_collect", "tsdf_profile_enable", "tsdf_profile_read"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -367,6 +369,19 @@ def tsdf_get_info(h):
 def tsdf_get_stats(h):
     o = tsdf_stats()
     _check(load().tsdf_get_stats(h, ctypes.byref(o)), h)
+    return o
+
+
+STATS_COPY_BYTES = 128  # TSDF_STATS_COPY_BYTES: bytes one counter read copies to the host
+
+
+def tsdf_stats_request(h, slot):
+    _check(load().tsdf_stats_request(h, int(slot)), h)
+
+
+def tsdf_stats_collect(h, slot):
+    o = tsdf_stats()
+    _check(load().tsdf_stats_collect(h, int(slot), ctypes.byref(o)), h)
     return o
 
 
@@ -633,6 +648,14 @@ class Volume:
 
     def stats(self):
         return tsdf_get_stats(self.h)
+
+    def stats_request(self, slot):
+        """Queue a copy of the counters into slot 0 or 1 without waiting."""
+        tsdf_stats_request(self.h, slot)
+
+    def stats_collect(self, slot):
+        """Wait for slot's last copy and return it as stats() would have."""
+        return tsdf_stats_collect(self.h, slot)
 
     def info(self):
         return tsdf_get_info(self.h)

@@ -38,6 +38,14 @@ struct tsdf_volume {
     cudaStream_t side;
     cudaEvent_t list_done, bricks_done, main_tail;
     bool chain_ok;
+    // Asynchronous counter reads (tsdf_stats_request / tsdf_stats_collect):
+    // two page-locked copies of the counters and their completion events.  A
+    // request since the last frame makes the next frame's depth tiles wait for
+    // its copy (they reset the geometry-side counters).
+    tsdf::Counters* stats_host;
+    cudaEvent_t stats_ev[2];
+    cudaEvent_t stats_last;
+    bool stats_pending;
     uint16_t* d_depth2;
     size_t d_depth2_cap;
     uint8_t* d_rgb2;

@@ -454,11 +454,15 @@ tsdf_status tsdf_create_ex(const int32_t dims_geo[3], const int32_t dims_col[3],
     if (cudaStreamCreateWithFlags(&v->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&v->list_done, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&v->bricks_done, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&v->main_tail, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&v->main_tail, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&v->stats_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&v->stats_ev[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaMallocHost((void**)&v->stats_host, 2 * sizeof(Counters)) != cudaSuccess) {
         cudaGetLastError();
         tsdf_destroy(v);
         return TSDF_ERR_CUDA;
     }
+    std::memset(v->stats_host, 0, 2 * sizeof(Counters));
     v->grids.geo = sms * geometry_blocks_per_sm();
     v->grids.col = sms * colour_blocks_per_sm();
     v->grids.vox = sms * voxel_blocks_per_sm();
@@ -528,8 +532,9 @@ void tsdf_destroy(tsdf_volume* v) {
         cudaStreamSynchronize(v->side);
         cudaStreamDestroy(v->side);
     }
-    for (cudaEvent_t x : {v->list_done, v->bricks_done, v->main_tail})
+    for (cudaEvent_t x : {v->list_done, v->bricks_done, v->main_tail, v->stats_ev[0], v->stats_ev[1]})
         if (x) cudaEventDestroy(x);
+    if (v->stats_host) cudaFreeHost(v->stats_host);
     for (auto* list : {&v->ev_pending, &v->ev_pool})
         for (auto& es : *list)
             for (auto& x : es.e) cudaEventDestroy(x);
@@ -627,6 +632,14 @@ tsdf_status tsdf_integrate(tsdf_volume* v, const uint16_t* depth_mm, tsdf_image_
         if (e != cudaSuccess) return cuda_fail(v, e, "RGB upload");
         d_rgb = buf;
     }
+    if (pipe && v->stats_pending) {
+        // a counter read queued since the last frame must finish before the
+        // depth tiles reset the geometry-side counters (the uploads above
+        // need not wait for it)
+        e = cudaStreamWaitEvent(v->side, v->stats_last, 0);
+        if (e != cudaSuccess) return cuda_fail(v, e, "frame pipeline");
+    }
+    v->stats_pending = false;
     const size_t tiles = (size_t)c.tiles_x * c.tiles_y * sizeof(uint32_t);
     if (v->depth_tiles_cap < tiles) {
         dev_free(v, v->depth_tiles);
@@ -704,12 +717,9 @@ tsdf_status tsdf_get_info(const tsdf_volume* v, tsdf_info* o) {
     return TSDF_OK;
 }
 
-tsdf_status tsdf_get_stats(tsdf_volume* v, tsdf_stats* o) {
-    if (!v || !o) return TSDF_ERR_INVALID_ARG;
-    Counters h;
-    cudaError_t e = cudaMemcpyAsync(&h, v->scr.ctr, sizeof h, cudaMemcpyDeviceToHost, v->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(v->stream);
-    if (e != cudaSuccess) return cuda_fail(v, e, "stats read");
+static_assert(sizeof(Counters) == TSDF_STATS_COPY_BYTES, "the header states the size of one counter read");
+
+static void fill_stats(const tsdf_volume* v, const Counters& h, tsdf_stats* o) {
     o->geo_updated = (int64_t)h.geo_updated;
     o->col_updated = (int64_t)h.col_updated;
     o->geo_bricks = h.n_geo;
@@ -725,6 +735,36 @@ tsdf_status tsdf_get_stats(tsdf_volume* v, tsdf_stats* o) {
     o->total_col_active_bricks = (int64_t)(h.tot_col_active + h.n_col_active);
     o->total_cells = (int64_t)(h.tot_cells + h.n_cells);
     o->total_geo_changed_bricks = (int64_t)(h.tot_geo_changed + h.n_geo_changed);
+}
+
+tsdf_status tsdf_get_stats(tsdf_volume* v, tsdf_stats* o) {
+    if (!v || !o) return TSDF_ERR_INVALID_ARG;
+    Counters h;
+    cudaError_t e = cudaMemcpyAsync(&h, v->scr.ctr, sizeof h, cudaMemcpyDeviceToHost, v->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(v->stream);
+    if (e != cudaSuccess) return cuda_fail(v, e, "stats read");
+    fill_stats(v, h, o);
+    return TSDF_OK;
+}
+
+tsdf_status tsdf_stats_request(tsdf_volume* v, int32_t slot) {
+    if (!v) return TSDF_ERR_INVALID_ARG;
+    if (slot != 0 && slot != 1) return fail(v, TSDF_ERR_INVALID_ARG, "stats slot must be 0 or 1");
+    cudaError_t e = cudaMemcpyAsync(&v->stats_host[slot], v->scr.ctr, sizeof(Counters), cudaMemcpyDeviceToHost,
+                                    v->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(v->stats_ev[slot], v->stream);
+    if (e != cudaSuccess) return cuda_fail(v, e, "stats request");
+    v->stats_last = v->stats_ev[slot];
+    v->stats_pending = true;
+    return TSDF_OK;
+}
+
+tsdf_status tsdf_stats_collect(tsdf_volume* v, int32_t slot, tsdf_stats* o) {
+    if (!v || !o) return TSDF_ERR_INVALID_ARG;
+    if (slot != 0 && slot != 1) return fail(v, TSDF_ERR_INVALID_ARG, "stats slot must be 0 or 1");
+    const cudaError_t e = cudaEventSynchronize(v->stats_ev[slot]);
+    if (e != cudaSuccess) return cuda_fail(v, e, "stats collect");
+    fill_stats(v, v->stats_host[slot], o);
     return TSDF_OK;
 }
 

@@ -95,4 +95,12 @@ def test_null_handle_calls_are_rejected(T):
     assert lib.tsdf_read(None, None, None, None) == T.TSDF_ERR_INVALID_ARG
     assert lib.tsdf_save(None, b"x") == T.TSDF_ERR_INVALID_ARG
     assert lib.tsdf_get_info(None, None) == T.TSDF_ERR_INVALID_ARG
+    assert lib.tsdf_stats_request(None, 0) == T.TSDF_ERR_INVALID_ARG
+    assert lib.tsdf_stats_collect(None, 0, None) == T.TSDF_ERR_INVALID_ARG
     lib.tsdf_destroy(None)  # ignored
+
+
+def test_stats_copy_size_matches_the_header(T):
+    text = open(os.path.join(ROOT, "include", "tsdf.h")).read()
+    m = re.search(r"#define TSDF_STATS_COPY_BYTES (\d+)", text)
+    assert m and int(m.group(1)) == T.STATS_COPY_BYTES

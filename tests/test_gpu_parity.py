@@ -265,3 +265,50 @@ def test_phase_profile_and_phase_mask():
         T.tsdf_profile_phases(vols[0].h, 0)
     for v in vols:
         v.close()
+
+
+STAT_FIELDS = [f for f, _ in T.tsdf_stats._fields_]
+
+
+@pytest.mark.parametrize("device_inputs", [False, True])
+def test_async_stats_equal_synchronous_reads(device_inputs):
+    """Counters read with tsdf_stats_request / tsdf_stats_collect while the
+    next frame is already queued equal those of a synchronous read after each
+    frame, field by field (the next frame's depth tiles reset the
+    geometry-side counters, so they must wait for a pending copy)."""
+    seq = synth.sequence_small(n_frames=12)
+    frames = []
+    for f in range(12):
+        d, c = seq.frame(f)
+        if device_inputs:
+            d, c = torch.from_numpy(d.view(np.int16).copy()).cuda(), torch.from_numpy(c).cuda()
+        frames.append((d, c))
+    args = lambda f: (*frames[f], seq.K_depth, seq.K_rgb, seq.poses[f], seq.T_depth_rgb)
+    a = T.Volume(seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, seq.max_weight)
+    sync = []
+    for f in range(12):
+        a.integrate(*args(f))
+        sync.append(a.stats())
+    b = T.Volume(seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, seq.max_weight)
+    assert all(getattr(b.stats_collect(1), k) == 0 for k in STAT_FIELDS if k != "total_bricks")  # never requested
+    got = []
+    for f in range(12):
+        b.integrate(*args(f))
+        b.stats_request(f & 1)
+        if f:
+            got.append(b.stats_collect((f - 1) & 1))
+    got.append(b.stats_collect(11 & 1))
+    for f, (x, y) in enumerate(zip(sync, got)):
+        for k in STAT_FIELDS:
+            assert getattr(x, k) == getattr(y, k), (f, k, getattr(x, k), getattr(y, k))
+    assert sync[-1].frames_counted == 12 and sync[-1].geo_updated > 0
+    for bad in (-1, 2):
+        with pytest.raises(T.TsdfError):
+            b.stats_request(bad)
+        with pytest.raises(T.TsdfError):
+            b.stats_collect(bad)
+    Fa, Wa, Ca = a.read()
+    Fb, Wb, Cb = b.read()
+    a.close()
+    b.close()
+    assert np.array_equal(Fa, Fb) and np.array_equal(Wa, Wb) and np.array_equal(Ca, Cb)
