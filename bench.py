@@ -387,7 +387,7 @@ def run_ours(args):
         h2d = frames[0][0].nbytes + frames[0][1].nbytes
         assert last.frames_counted == args.warmup + args.steps
         result["e2e"] = {"value": units / e2e_s, "unit": "voxel-updates/s", "h2d_bytes_per_step": int(h2d),
-                         "d2h_bytes_per_step": T.STATS_COPY_BYTES, "frames_per_s": args.steps * world / e2e_s}
+                         "d2h_bytes_per_step": 2 * T.STATS_COPY_BYTES, "frames_per_s": args.steps * world / e2e_s}
 
     # ---- CPU baseline: the oracle on the host cores, bounded sample
     if world == 1 and rank == 0 and not args.no_cpu_baseline:

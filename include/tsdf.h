@@ -200,16 +200,19 @@ typedef struct {
 tsdf_status tsdf_get_stats(tsdf_volume* vol, tsdf_stats* out);
 
 /* Asynchronous form of tsdf_get_stats, for a caller that queues frame k + 1
- * before it reads frame k's counters.  tsdf_stats_request queues, on the
- * volume's stream after the work queued so far, a copy of the counters
- * (TSDF_STATS_COPY_BYTES bytes, device to page-locked host memory owned by
- * the volume) into slot 0 or 1, and returns without waiting.
- * tsdf_stats_collect waits for the last copy into that slot and fills *out
- * as tsdf_get_stats would have at the time of the request (a slot never
- * requested reads as all zeros).  The next tsdf_integrate orders its depth
- * tiles after a pending copy, so the copy sees the requested frame's
- * counters complete; its uploads do not wait.  Slots other than 0 and 1 and
- * NULL pointers are rejected with TSDF_ERR_INVALID_ARG. */
+ * before it reads frame k's counters.  tsdf_stats_request queues, after the
+ * work queued so far, a copy of the counters (TSDF_STATS_COPY_BYTES bytes,
+ * device to page-locked host memory owned by the volume) into slot 0 or 1,
+ * and returns without waiting.  After a frame integrated with its depth tiles
+ * and culling on the volume's second stream it queues two such copies: one on
+ * the second stream once the frame's colour list is done (for the counters
+ * the next frame's depth tiles reset, which it precedes) and one on the
+ * volume's stream (for the rest); after any other frame one copy on the
+ * volume's stream, which the next frame's depth tiles then wait for.
+ * tsdf_stats_collect waits for that slot's last request and fills *out as
+ * tsdf_get_stats would have at the time of the request (a slot never
+ * requested reads as zeros).  Slots other than 0 and 1 and NULL pointers are
+ * rejected with TSDF_ERR_INVALID_ARG. */
 #define TSDF_STATS_COPY_BYTES 128
 tsdf_status tsdf_stats_request(tsdf_volume* vol, int32_t slot);
 tsdf_status tsdf_stats_collect(tsdf_volume* vol, int32_t slot, tsdf_stats* out);

@@ -39,11 +39,17 @@ struct tsdf_volume {
     cudaEvent_t list_done, bricks_done, main_tail;
     bool chain_ok;
     // Asynchronous counter reads (tsdf_stats_request / tsdf_stats_collect):
-    // two page-locked copies of the counters and their completion events.  A
-    // request since the last frame makes the next frame's depth tiles wait for
-    // its copy (they reset the geometry-side counters).
+    // per slot, page-locked copies of the counters taken on `stream` (entry
+    // 2 slot) and, after a pipelined frame, on `side` (entry 2 slot + 1) with
+    // their completion events.  The next frame's depth tiles, queued on `side`
+    // behind the side copy, reset the geometry-side counters, so a split read
+    // takes those from the side copy (made once the frame's colour list is
+    // done) and the colour-side ones from the stream copy.  After a frame that
+    // was not pipelined the read is one stream copy, and the next frame's depth
+    // tiles wait for it (stats_pending).
     tsdf::Counters* stats_host;
-    cudaEvent_t stats_ev[2];
+    cudaEvent_t stats_ev[2], stats_ev_side[2];
+    bool stats_split[2];
     cudaEvent_t stats_last;
     bool stats_pending;
     uint16_t* d_depth2;

@@ -457,12 +457,14 @@ tsdf_status tsdf_create_ex(const int32_t dims_geo[3], const int32_t dims_col[3],
         cudaEventCreateWithFlags(&v->main_tail, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&v->stats_ev[0], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&v->stats_ev[1], cudaEventDisableTiming) != cudaSuccess ||
-        cudaMallocHost((void**)&v->stats_host, 2 * sizeof(Counters)) != cudaSuccess) {
+        cudaEventCreateWithFlags(&v->stats_ev_side[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&v->stats_ev_side[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaMallocHost((void**)&v->stats_host, 4 * sizeof(Counters)) != cudaSuccess) {
         cudaGetLastError();
         tsdf_destroy(v);
         return TSDF_ERR_CUDA;
     }
-    std::memset(v->stats_host, 0, 2 * sizeof(Counters));
+    std::memset(v->stats_host, 0, 4 * sizeof(Counters));
     v->grids.geo = sms * geometry_blocks_per_sm();
     v->grids.col = sms * colour_blocks_per_sm();
     v->grids.vox = sms * voxel_blocks_per_sm();
@@ -532,7 +534,8 @@ void tsdf_destroy(tsdf_volume* v) {
         cudaStreamSynchronize(v->side);
         cudaStreamDestroy(v->side);
     }
-    for (cudaEvent_t x : {v->list_done, v->bricks_done, v->main_tail, v->stats_ev[0], v->stats_ev[1]})
+    for (cudaEvent_t x : {v->list_done, v->bricks_done, v->main_tail, v->stats_ev[0], v->stats_ev[1],
+                          v->stats_ev_side[0], v->stats_ev_side[1]})
         if (x) cudaEventDestroy(x);
     if (v->stats_host) cudaFreeHost(v->stats_host);
     for (auto* list : {&v->ev_pending, &v->ev_pool})
@@ -750,21 +753,50 @@ tsdf_status tsdf_get_stats(tsdf_volume* v, tsdf_stats* o) {
 tsdf_status tsdf_stats_request(tsdf_volume* v, int32_t slot) {
     if (!v) return TSDF_ERR_INVALID_ARG;
     if (slot != 0 && slot != 1) return fail(v, TSDF_ERR_INVALID_ARG, "stats slot must be 0 or 1");
-    cudaError_t e = cudaMemcpyAsync(&v->stats_host[slot], v->scr.ctr, sizeof(Counters), cudaMemcpyDeviceToHost,
-                                    v->stream);
+    Counters* h = v->stats_host + 2 * slot;
+    cudaError_t e = cudaSuccess;
+    // after a pipelined frame, the geometry-side counters are copied on the
+    // side stream once the frame's colour list is done, ahead of the next
+    // frame's depth tiles (see tsdf_volume::stats_host)
+    const bool split = v->chain_ok;
+    if (split) {
+        e = cudaStreamWaitEvent(v->side, v->list_done, 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h + 1, v->scr.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, v->side);
+        if (e == cudaSuccess) e = cudaEventRecord(v->stats_ev_side[slot], v->side);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, v->scr.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, v->stream);
     if (e == cudaSuccess) e = cudaEventRecord(v->stats_ev[slot], v->stream);
     if (e != cudaSuccess) return cuda_fail(v, e, "stats request");
-    v->stats_last = v->stats_ev[slot];
-    v->stats_pending = true;
+    v->stats_split[slot] = split;
+    if (!split) {
+        v->stats_last = v->stats_ev[slot];
+        v->stats_pending = true;
+    }
     return TSDF_OK;
 }
 
 tsdf_status tsdf_stats_collect(tsdf_volume* v, int32_t slot, tsdf_stats* o) {
     if (!v || !o) return TSDF_ERR_INVALID_ARG;
     if (slot != 0 && slot != 1) return fail(v, TSDF_ERR_INVALID_ARG, "stats slot must be 0 or 1");
-    const cudaError_t e = cudaEventSynchronize(v->stats_ev[slot]);
+    cudaError_t e = cudaEventSynchronize(v->stats_ev[slot]);
+    if (e == cudaSuccess && v->stats_split[slot]) e = cudaEventSynchronize(v->stats_ev_side[slot]);
     if (e != cudaSuccess) return cuda_fail(v, e, "stats collect");
-    fill_stats(v, v->stats_host[slot], o);
+    Counters h = v->stats_host[2 * slot];
+    if (v->stats_split[slot]) {  // the geometry-side counters (those k_depth_tiles folds and resets)
+        const Counters& g = v->stats_host[2 * slot + 1];
+        h.n_geo = g.n_geo;
+        h.n_vis = g.n_vis;
+        h.geo_next = g.geo_next;
+        h.n_geo_changed = g.n_geo_changed;
+        h.geo_updated = g.geo_updated;
+        h.frames = g.frames;
+        h.tot_geo_updated = g.tot_geo_updated;
+        h.tot_geo_bricks = g.tot_geo_bricks;
+        h.tot_vis_bricks = g.tot_vis_bricks;
+        h.tot_geo_changed = g.tot_geo_changed;
+    }
+    fill_stats(v, h, o);
     return TSDF_OK;
 }
 

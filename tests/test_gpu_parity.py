@@ -270,12 +270,14 @@ def test_phase_profile_and_phase_mask():
 STAT_FIELDS = [f for f, _ in T.tsdf_stats._fields_]
 
 
-@pytest.mark.parametrize("device_inputs", [False, True])
-def test_async_stats_equal_synchronous_reads(device_inputs):
+@pytest.mark.parametrize("device_inputs,profiled", [(False, False), (True, False), (False, True)])
+def test_async_stats_equal_synchronous_reads(device_inputs, profiled):
     """Counters read with tsdf_stats_request / tsdf_stats_collect while the
     next frame is already queued equal those of a synchronous read after each
-    frame, field by field (the next frame's depth tiles reset the
-    geometry-side counters, so they must wait for a pending copy)."""
+    frame, field by field.  The next frame's depth tiles reset the
+    geometry-side counters: after a pipelined frame those are read from a
+    copy queued ahead of them, and with the first phases timed (no
+    pipelining) the depth tiles wait for the single copy."""
     seq = synth.sequence_small(n_frames=12)
     frames = []
     for f in range(12):
@@ -290,6 +292,8 @@ def test_async_stats_equal_synchronous_reads(device_inputs):
         a.integrate(*args(f))
         sync.append(a.stats())
     b = T.Volume(seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, seq.max_weight)
+    if profiled:
+        b.profile(True)
     assert all(getattr(b.stats_collect(1), k) == 0 for k in STAT_FIELDS if k != "total_bricks")  # never requested
     got = []
     for f in range(12):
