@@ -8,6 +8,7 @@ to this file.
 from __future__ import annotations
 
 import concurrent.futures
+import fcntl
 import os
 import subprocess
 import sys
@@ -42,17 +43,26 @@ def _compile(src, extra):
     newest = max([os.path.getmtime(src)] + [os.path.getmtime(d) for d in _deps()])
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest and not extra:
         return obj
-    cmd = ["nvcc", *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
+    tmp = obj + ".tmp%d" % os.getpid()
+    cmd = ["nvcc", *NVCC_FLAGS, *extra, "-c", src, "-o", tmp]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, " ".join(cmd), r.stderr))
     if r.stderr.strip():
         sys.stderr.write(r.stderr)
+    os.replace(tmp, obj)
     return obj
 
 
 def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     os.makedirs(BUILD_DIR, exist_ok=True)
+    # one build at a time (parallel test workers may all ask for one)
+    with open(os.path.join(BUILD_DIR, ".lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        return _build(force, verbose_ptxas)
+
+
+def _build(force: bool, verbose_ptxas: bool) -> str:
     srcs = sources()
     extra = ["-Xptxas", "-v"] if verbose_ptxas else []
     if force:

@@ -526,17 +526,20 @@ constexpr int LIST_THREADS = 256;
 __global__ void __launch_bounds__(LIST_THREADS) k_colour_list(FrameConst c, const BrickSummary* __restrict__ summ,
                                                      Counters* __restrict__ ctr, const uint32_t* __restrict__ vis_list,
                                                      uint32_t* __restrict__ col_list) {
-    chain_enter();
+    // The visible list and its length come from the brick culling, which had
+    // finished before the geometry kernel this one follows could start, so
+    // they are read before waiting for the geometry kernel (the summaries it
+    // writes are read after).
     const uint32_t n = ctr->n_vis;
+    const uint32_t i0 = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t b_next = i0 < n ? vis_list[i0] : 0u;
+    chain_enter();
     for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
         const uint32_t i = base + threadIdx.x;
-        bool act = false;
-        uint32_t b = 0;
-        if (i < n) {
-            b = vis_list[i];
-            act = true;
-            act = colour_candidate(c, summ, b);
-        }
+        const uint32_t b = b_next;
+        const uint32_t in = i + gridDim.x * blockDim.x;
+        b_next = in < n ? vis_list[in] : 0u;
+        const bool act = i < n && colour_candidate(c, summ, b);
         block_append2<LIST_THREADS>(act, false, b, &ctr->n_col, col_list, nullptr, nullptr);
     }
 }
