@@ -281,7 +281,9 @@ __device__ __forceinline__ void block_append2(bool p0, bool p1, uint32_t value, 
     __syncthreads();  // off is reused by the block's next call
 }
 
-__global__ void __launch_bounds__(256) k_bricks(FrameConst c, const BrickSummary* __restrict__ summ,
+constexpr int BRICK_THREADS = 64;  // small blocks: they fit beside the band kernel's blocks on an SM
+
+__global__ void __launch_bounds__(BRICK_THREADS) k_bricks(FrameConst c, const BrickSummary* __restrict__ summ,
                                                 const uint32_t* __restrict__ tiles, Counters* __restrict__ ctr,
                                                 uint32_t* __restrict__ geo_list, uint32_t* __restrict__ vis_list) {
     chain_enter();
@@ -289,7 +291,7 @@ __global__ void __launch_bounds__(256) k_bricks(FrameConst c, const BrickSummary
     uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
     bool geo, vis;
     brick_flags(c, summ, tiles, b, b < nbt, geo, vis);
-    block_append2<256>(geo, vis, b, &ctr->n_geo, geo_list, &ctr->n_vis, vis_list);
+    block_append2<BRICK_THREADS>(geo, vis, b, &ctr->n_geo, geo_list, &ctr->n_vis, vis_list);
 }
 
 // ---------------------------------------------------------- geometry ----
@@ -1458,8 +1460,8 @@ cudaError_t launch_frame_pre(const FrameConst& c, const Volumes& v, const Scratc
     mark(1);
     const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
     if (e == cudaSuccess)
-        e = launch_chained(k_bricks, dim3((nbt + 255) / 256), dim3(256), 0, stream, c, v.summ, s.depth_tiles, s.ctr,
-                           s.geo_list, s.vis_list);
+        e = launch_chained(k_bricks, dim3((nbt + BRICK_THREADS - 1) / BRICK_THREADS), dim3(BRICK_THREADS), 0, stream,
+                           c, v.summ, s.depth_tiles, s.ctr, s.geo_list, s.vis_list);
     mark(2);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -1519,7 +1521,8 @@ cudaError_t launch_frame_record(const FrameConst& c, const Volumes& v, const Scr
     const dim3 tg((c.tiles_x + 1) / 2, (c.tiles_y + 1) / 2);
     k_depth_tiles<<<tg, dim3(TILE_BLOCK_PX, TILE_BLOCK_PX), 0, stream>>>(c, depth, s.depth_tiles, s.ctr);
     const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
-    k_bricks<<<(nbt + 255) / 256, 256, 0, stream>>>(c, v.summ, s.depth_tiles, s.ctr, s.geo_list, s.vis_list);
+    k_bricks<<<(nbt + BRICK_THREADS - 1) / BRICK_THREADS, BRICK_THREADS, 0, stream>>>(c, v.summ, s.depth_tiles, s.ctr,
+                                                                                     s.geo_list, s.vis_list);
     launch_k_geometry(c, v, s, depth, g.geo, stream);
     unsigned gl = (nbt + LIST_THREADS - 1) / LIST_THREADS;
     if (gl > 1024u) gl = 1024u;
