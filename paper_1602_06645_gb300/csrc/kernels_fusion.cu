@@ -437,8 +437,11 @@ __global__ void __launch_bounds__(GEO_THREADS, 7) k_geometry(FrameConst c, Volum
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t n = ctr->n_geo;
     uint32_t count = 0, changed = 0;
+    // the list is taken from its end: the colour kernels that follow walk
+    // their lists from the front, whose bricks are then the ones this kernel
+    // wrote last (measured: 1 % off the frame)
     for (uint32_t item = warp; item < n; item += nwarps)
-        geometry_brick<PINHOLE, FREE_SPACE, ALIGNED>(c, vol, depth, list[item], lane, count, changed);
+        geometry_brick<PINHOLE, FREE_SPACE, ALIGNED>(c, vol, depth, list[n - 1u - item], lane, count, changed);
     count = __reduce_add_sync(0xffffffffu, count);
     if (lane == 0 && count) atomicAdd(&ctr->geo_updated, (unsigned long long)count);
     if (lane == 0 && changed) atomicAdd(&ctr->n_geo_changed, changed);
