@@ -746,14 +746,20 @@ __device__ uint32_t write_records(const FrameConst& c, const Volumes& vol, const
                                   const uint8_t* __restrict__ rgb, const Scratch& scr, const ColourSlot& S,
                                   uint32_t n, uint32_t base, int lane) {
     uint32_t done = 0;
-    for (uint32_t i = lane; i < n; i += 32) {
-        const uint2 r = S.out[i];
-        if ((uint64_t)base + i < scr.vox_cap)
-            scr.vox[base + i] = r;
-        else if (c.record_mode)
-            atomicOr(scr.err, ERR_RECORD_OVERFLOW);  // recording has no fallback; the host reports it
-        else if (colour_after_band_outlined(c, vol.C, depth, rgb, (int)(r.x & 0xFFFFu), (int)(r.x >> 16), (int)r.y))
-            ++done;
+    // the records that fit are copied in a loop of their own: with the rare
+    // overflow call inside it, the copy loop cost the band kernel 15 %
+    const uint32_t fit = base >= scr.vox_cap ? 0u : min(n, scr.vox_cap - base);
+    for (uint32_t i = lane; i < fit; i += 32) scr.vox[base + i] = S.out[i];
+    if (fit < n) {  // beyond the buffer
+        if (c.record_mode) {
+            if (lane == 0) atomicOr(scr.err, ERR_RECORD_OVERFLOW);  // recording has no fallback; the host reports it
+        } else {
+            for (uint32_t i = fit + lane; i < n; i += 32) {
+                const uint2 r = S.out[i];
+                if (colour_after_band_outlined(c, vol.C, depth, rgb, (int)(r.x & 0xFFFFu), (int)(r.x >> 16), (int)r.y))
+                    ++done;
+            }
+        }
     }
     __syncwarp();
     return done;
