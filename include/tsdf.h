@@ -357,27 +357,31 @@ void tsdf_adjoint_destroy(tsdf_adjoint* adj);
  * (culling only skips bricks that cannot change).  It needs no handle and
  * calls no cudaMalloc, cudaFree or other allocating routine: its scratch
  * (work counters, depth tiles, brick work list) is one fixed device array of
- * about 4.3 MB that every GPU loading the library holds until the process
- * exits.
+ * TSDF_STATIC_SCRATCH_BYTES = 256 + 4 * TSDF_STATIC_MAX_DEPTH_TILES +
+ * 4 * TSDF_STATIC_MAX_BRICKS = 5,243,136 bytes (5.0 MiB) that every GPU
+ * loading the library holds until the process exits.
  *   dims            voxels per axis (x, y, z), 1..4096, with at most
  *                   TSDF_STATIC_MAX_BRICKS bricks of 8^3 voxels
  *   voxel_size, mu, max_weight, origin   as in tsdf_create_ex
- *   tsdf_dev, w_dev device arrays of dims[0]*dims[1]*dims[2] floats / bytes,
+ *   tsdf_dev, w_dev device (or managed) arrays of dims[0]*dims[1]*dims[2] floats / bytes,
  *                   linear x-fastest, read and updated in place (start from
  *                   zeros for an empty volume)
  *   depth_dev       device uint16 millimetre depth image of dsz, at most
  *                   TSDF_STATIC_MAX_DEPTH_TILES tiles of 8x8 pixels
  *   K_depth, T_world_depth  host pointers, as in tsdf_integrate
  *   stream          cudaStream_t the kernels are queued on (NULL = legacy default)
- * Sizes beyond the maxima, NULL pointers and invalid K / T are rejected with
- * TSDF_ERR_INVALID_ARG before any work is queued.  The first call on a device
- * looks up the scratch array's device address there (cudaGetSymbolAddress),
- * so make it before any stream capture.  Every call shares the one scratch
+ * Sizes beyond the maxima, NULL or host pointers and invalid K / T are
+ * rejected with TSDF_ERR_INVALID_ARG before any work is queued.  The first
+ * call on a device looks up the scratch array's device address there
+ * (cudaGetSymbolAddress), so make it before any stream capture; the address
+ * is kept for the life of the process, so do not use the library across a
+ * cudaDeviceReset.  Every call shares the one scratch
  * array, which keeps the previous call's contents (the call clears what must
  * start at zero): calls whose work overlaps on the GPU race, so queue them on
  * one stream or wait between them.  Asynchronous with respect to the host. */
 #define TSDF_STATIC_MAX_BRICKS (1 << 20)     /* e.g. 512^3 voxels use 262,144 bricks */
 #define TSDF_STATIC_MAX_DEPTH_TILES 262144   /* e.g. 4096 x 4096 pixels use 262,144 tiles */
+#define TSDF_STATIC_SCRATCH_BYTES (256 + 4 * TSDF_STATIC_MAX_DEPTH_TILES + 4 * TSDF_STATIC_MAX_BRICKS)
 tsdf_status tsdf_integrate_geometry_static(const int32_t dims[3], float voxel_size, float mu, int32_t max_weight,
                                            const float origin[3], float* tsdf_dev, uint8_t* w_dev,
                                            const uint16_t* depth_dev, tsdf_image_size dsz, const float K_depth[9],

@@ -119,8 +119,9 @@ def _load():
         lib.orc_adj_cells.restype = None
         lib.orc_adj_eval.argtypes = [ctypes.POINTER(AdjProblem), vp, vp, vp, ctypes.c_int64, vp, vp, vp, vp, vp,
                                      ctypes.c_int64, vp]
-        lib.orc_adj_cells32.argtypes = [ctypes.POINTER(AdjProblem), vp, vp, vp]
-        lib.orc_adj_cells32.restype = None
+        lib.orc_hd_cells.argtypes = [ctypes.POINTER(ctypes.c_int32), ctypes.c_float, ctypes.POINTER(ctypes.c_float),
+                                     ctypes.c_int, vp, vp, vp, vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]
+        lib.orc_hd_cells.restype = None
         lib.orc_adj_eval.restype = ctypes.c_double
         lib.orc_sparse_frame.argtypes = [ctypes.POINTER(Params), vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int,
                                          ctypes.c_int, vp, vp, vp, vp, ctypes.c_int64, vp, vp, vp, ctypes.c_int64,
@@ -233,6 +234,8 @@ class Oracle:
         out = np.empty(cap, dtype=np.uint32)
         n = self.lib.orc_record_gates(ctypes.byref(self.p), self.F.ctypes.data, self.W.ctypes.data, depth.ctypes.data,
                                       dw, dh, Kd.ctypes.data, Twd.ctypes.data, out.ctypes.data, cap)
+        if n < 0:
+            raise MemoryError("orc_record_gates: no memory for the gate flags")
         return out[:n].copy()
 
     @property
@@ -312,12 +315,20 @@ class Adjoint:
         return cells
 
     def cells32(self, K4, T):
-        """Cells chosen in binary32 with the kernels' operation order, for
-        the binary32 camera K4 = (fx, fy, cx, cy) and 4x4 T."""
-        k4 = np.ascontiguousarray(K4, np.float32)
+        """Cells of the binary32 camera K4 = (fx, fy, cx, cy), 4x4 T: the
+        integer decision taken by the fusion oracle's own colour path (Eq. 5,
+        Eq. 3, Eq. 4 projection and the bilinear footprint test of oracle.c),
+        the same precision as the kernels."""
+        fx, fy, cx, cy = [float(v) for v in np.asarray(K4, np.float32)]
+        Kr = np.array([[fx, 0, cx], [0, fy, cy], [0, 0, 1]], np.float32).reshape(9)
         t = np.ascontiguousarray(np.asarray(T, np.float32).reshape(16))
         cells = np.empty(2 * len(self.idx), np.int32)
-        self.lib.orc_adj_cells32(ctypes.byref(self.p), k4.ctypes.data, t.ctypes.data, cells.ctypes.data)
+        n, H, W, _ = self.images.shape
+        nc = (ctypes.c_int32 * 3)(*self.p.nc)
+        org = (ctypes.c_float * 3)(*self.p.origin)
+        self.lib.orc_hd_cells(nc, ctypes.c_float(self.p.s_c), org, n, self.Rn.ctypes.data, self.tn.ctypes.data,
+                              self.offsets.ctypes.data, self.idx.ctypes.data, Kr.ctypes.data, t.ctypes.data, W, H,
+                              cells.ctypes.data)
         return cells
 
     def eval(self, theta, cells, target=None, grad=False, query=None):

@@ -269,46 +269,4 @@ double orc_adj_eval(const orc_adj* P, const double theta[10], const int32_t* cel
     return loss;
 }
 
-/* Bilinear cells chosen in binary32, in the kernels' operation order (the
- * cell is an integer decision, so both sides take it in the same precision):
- *   p = fmaf(k + 1/2, s_c, origin)                       voxel centre
- *   P_vc = R_n p + t_n, P = R P_vc + t  as fmaf(R0, x, fmaf(R1, y, fmaf(R2, z, t)))
- *   u = fmaf(fx, X * (1/Z), cx), v = fmaf(fy, Y * (1/Z), cy), (x0, y0) = floor
- * with K4 = (fx, fy, cx, cy) and T (row-major 4x4) the binary32 camera. */
-static void rigid32(const float* R, const float* t, float x, float y, float z, float o[3]) {
-    for (int r = 0; r < 3; ++r) o[r] = fmaf(R[r * 3], x, fmaf(R[r * 3 + 1], y, fmaf(R[r * 3 + 2], z, t[r])));
-}
-
-void orc_adj_cells32(const orc_adj* P, const float K4[4], const float T[16], int32_t* cells) {
-    float R[9], t[3];
-    for (int r = 0; r < 3; ++r) {
-        for (int c = 0; c < 3; ++c) R[r * 3 + c] = T[r * 4 + c];
-        t[r] = T[r * 4 + 3];
-    }
-    const int nx = P->nc[0], ny = P->nc[1];
-    for (int k = 0; k < P->n_frames; ++k)
-        for (int64_t i = P->offsets[k]; i < P->offsets[k + 1]; ++i) {
-            uint32_t vox = P->idx[i];
-            int x = (int)(vox % (uint32_t)nx), y = (int)((vox / (uint32_t)nx) % (uint32_t)ny),
-                z = (int)(vox / ((uint32_t)nx * ny));
-            float p[3] = {fmaf((float)x + 0.5f, P->s_c, P->origin[0]), fmaf((float)y + 0.5f, P->s_c, P->origin[1]),
-                          fmaf((float)z + 0.5f, P->s_c, P->origin[2])};
-            float Pc[3], Ph[3];
-            rigid32(P->Rn + 9 * k, P->tn + 3 * k, p[0], p[1], p[2], Pc);
-            rigid32(R, t, Pc[0], Pc[1], Pc[2], Ph);
-            int32_t x0 = INT32_MIN, y0 = INT32_MIN;
-            if (Ph[2] > 0.0f) {
-                float rz = 1.0f / Ph[2];
-                float u = fmaf(K4[0], Ph[0] * rz, K4[2]), v = fmaf(K4[1], Ph[1] * rz, K4[3]);
-                float fx0 = floorf(u), fy0 = floorf(v);
-                if (fx0 >= 0.0f && fx0 <= (float)(P->width - 2) && fy0 >= 0.0f && fy0 <= (float)(P->height - 2)) {
-                    x0 = (int32_t)fx0;
-                    y0 = (int32_t)fy0;
-                }
-            }
-            cells[2 * i] = x0;
-            cells[2 * i + 1] = y0;
-        }
-}
-
 int orc_adj_size(void) { return (int)sizeof(orc_adj); }

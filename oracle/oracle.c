@@ -28,6 +28,7 @@
  */
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 typedef struct {
@@ -224,6 +225,15 @@ static int trilinear(const orc_params* p, corner_fn corner, const void* ctx, con
     return 1;
 }
 
+/* Bilinear cell of HD position (u, v): the upper-left pixel (floor u,
+ * floor v) of the 2x2 footprint, which must lie inside the W x H image.
+ * Returns 0 when it does not (tested in float, so NaN fails). */
+static int bilinear_cell(float u, float v, int W, int H, float* x0, float* y0) {
+    *x0 = floorf(u);
+    *y0 = floorf(v);
+    return *x0 >= 0.0f && *x0 + 1.0f <= (float)(W - 1) && *y0 >= 0.0f && *y0 + 1.0f <= (float)(H - 1);
+}
+
 /* HD pixel value HD(x_hd, y_hd) (Eq. 9): nearest pixel, or bilinear over the
  * 2x2 neighbourhood (which must lie inside the image), rounded half-up. */
 static int sample_rgb(const orc_params* p, const orc_frame* fr, const uint8_t* rgb, float u, float v,
@@ -235,9 +245,8 @@ static int sample_rgb(const orc_params* p, const orc_frame* fr, const uint8_t* r
         for (int c = 0; c < 3; ++c) s[c] = px[c];
         return 1;
     }
-    float x0 = floorf(u), y0 = floorf(v);
-    if (!(x0 >= 0.0f && x0 + 1.0f <= (float)(fr->cw - 1) && y0 >= 0.0f && y0 + 1.0f <= (float)(fr->ch - 1)))
-        return 0;
+    float x0, y0;
+    if (!bilinear_cell(u, v, fr->cw, fr->ch, &x0, &y0)) return 0;
     float ax = u - x0, ay = v - y0;
     int ix = (int)x0, iy = (int)y0;
     const uint8_t* r0 = rgb + ((size_t)iy * fr->cw + ix) * 3;
@@ -304,6 +313,15 @@ static int colour_depth_gates(const orc_params* p, const orc_frame* fr, corner_f
     return 1;
 }
 
+/* Eq. 3-4: the voxel's point P_vc in the depth camera, moved to the HD camera
+ * (P_hd = R_calib P_vc + t_calib) and projected with K_hd.  Returns 0 behind
+ * the HD camera. */
+static int hd_position(const orc_frame* fr, const float Pc[3], float* uh, float* vh) {
+    float Ph[3];
+    rigid(fr->Rc, fr->tc, Pc[0], Pc[1], Pc[2], Ph);
+    return project(fr->Kr, Ph[0], Ph[1], Ph[2], uh, vh);
+}
+
 /* One colour voxel (x, y, z) whose packed colour is at *Cv; the band gate
  * reads the geometry through `corner`.  Returns 1 if it was updated. */
 static int colour_voxel(const orc_params* p, const orc_frame* fr, corner_fn corner, const void* ctx, uint32_t* Cv,
@@ -311,10 +329,8 @@ static int colour_voxel(const orc_params* p, const orc_frame* fr, corner_fn corn
     float Pc[3], Pd[3];
     int iu, iv;
     if (!colour_depth_gates(p, fr, corner, ctx, depth, x, y, z, Pc, &iu, &iv, Pd)) return 0;
-    float Ph[3];
-    rigid(fr->Rc, fr->tc, Pc[0], Pc[1], Pc[2], Ph);
     float uh, vh;
-    if (!project(fr->Kr, Ph[0], Ph[1], Ph[2], &uh, &vh)) return 0;
+    if (!hd_position(fr, Pc, &uh, &vh)) return 0;
     uint32_t s[3];
     if (!sample_rgb(p, fr, rgb, uh, vh, s)) return 0;
     if (p->colour_mode == 1) return orc_paper_normal_update(p, fr, depth, iu, iv, Pd, Pc, Cv, s);
@@ -450,17 +466,70 @@ long long orc_record_gates(const orc_params* p, float* F, uint8_t* W, const uint
     orc_geometry(p, &fr, F, W, depth);
     const int nx = p->nc[0], ny = p->nc[1], nz = p->nc[2];
     const dense_geo geo = {p, F, W};
-    long long n = 0;
+    /* the gates of every voxel (in parallel for timing runs), then the list in
+     * ascending order */
+    uint8_t* pass = (uint8_t*)malloc((size_t)nx * ny * nz);
+    if (!pass) return -1;
+#pragma omp parallel for num_threads(p->n_threads > 0 ? p->n_threads : 1) schedule(dynamic, 1)
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
                 float Pc[3], Pd[3];
                 int iu, iv;
-                if (!colour_depth_gates(p, &fr, dense_corner, &geo, depth, x, y, z, Pc, &iu, &iv, Pd)) continue;
-                if (n < cap) out[n] = (uint32_t)(((size_t)z * ny + y) * nx + x);
-                ++n;
+                pass[((size_t)z * ny + y) * nx + x] =
+                    (uint8_t)colour_depth_gates(p, &fr, dense_corner, &geo, depth, x, y, z, Pc, &iu, &iv, Pd);
             }
+    long long n = 0;
+    for (size_t i = 0; i < (size_t)nx * ny * nz; ++i)
+        if (pass[i]) {
+            if (n < cap) out[n] = (uint32_t)i;
+            ++n;
+        }
+    free(pass);
     return n;
+}
+
+/* Bilinear HD cells of the photometric loss (the integer decision of each
+ * sample): for every (frame k, colour voxel) pair, the voxel centre moved by
+ * frame k's depth-camera motion (R_n, t_n) (Eq. 5), then by the depth-to-HD
+ * extrinsic T (Eq. 3) and projected with K_hd (Eq. 4) -- the steps of the
+ * colour update above (hd_position) -- and the 2x2 footprint test of the
+ * bilinear sampling (bilinear_cell).  cells[2 i], cells[2 i + 1] = (x0, y0)
+ * of pair i, or INT32_MIN twice when the sample is behind the camera or its
+ * footprint leaves the cw x ch image.
+ *   nc, s_c, origin   the colour grid;  Rn, tn  n_frames x 9 / x 3
+ *   offsets, idx      pairs of frame k are idx[offsets[k] .. offsets[k+1])
+ *   Kr, Tdr           row-major 3x3 K_hd and 4x4 T_depth_rgb (binary32) */
+void orc_hd_cells(const int32_t nc[3], float s_c, const float origin[3], int n_frames, const float* Rn,
+                  const float* tn, const int64_t* offsets, const uint32_t* idx, const float Kr[9], const float Tdr[16],
+                  int cw, int ch, int32_t* cells) {
+    orc_frame fr;
+    memset(&fr, 0, sizeof fr);
+    memcpy(fr.Kr, Kr, sizeof fr.Kr);
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) fr.Rc[r * 3 + c] = Tdr[r * 4 + c];
+        fr.tc[r] = Tdr[r * 4 + 3];
+    }
+    fr.cw = cw;
+    fr.ch = ch;
+    const uint32_t nx = (uint32_t)nc[0], ny = (uint32_t)nc[1];
+    for (int k = 0; k < n_frames; ++k) {
+        memcpy(fr.R, Rn + 9 * k, sizeof fr.R);
+        memcpy(fr.t, tn + 3 * k, sizeof fr.t);
+        for (int64_t i = offsets[k]; i < offsets[k + 1]; ++i) {
+            const uint32_t v = idx[i];
+            const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / (nx * ny));
+            float Pc[3], uh, vh, x0, y0;
+            rigid(fr.R, fr.t, centre(origin[0], x, s_c), centre(origin[1], y, s_c), centre(origin[2], z, s_c), Pc);
+            int32_t cx = INT32_MIN, cy = INT32_MIN;
+            if (hd_position(&fr, Pc, &uh, &vh) && bilinear_cell(uh, vh, cw, ch, &x0, &y0)) {
+                cx = (int32_t)x0;
+                cy = (int32_t)y0;
+            }
+            cells[2 * i] = cx;
+            cells[2 * i + 1] = cy;
+        }
+    }
 }
 
 /* ---------------------------------------------------------- sampled ---- */

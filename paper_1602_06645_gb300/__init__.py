@@ -390,6 +390,17 @@ def tsdf_integrate_geometry_static(dims, voxel_size, mu, max_weight, origin, tsd
     """Allocation-free geometry fusion into caller-owned device arrays (see
     include/tsdf.h): `tsdf` / `w` are CUDA tensors of dims[2] x dims[1] x
     dims[0] float32 / uint8, `depth_mm` a CUDA tensor of the depth image."""
+    import torch
+
+    n = int(dims[0]) * int(dims[1]) * int(dims[2])
+    for name, x, dts in (("tsdf", tsdf, (torch.float32,)), ("w", w, (torch.uint8,)),
+                         ("depth_mm", depth_mm, (torch.int16, torch.uint16))):
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype in dts and x.is_contiguous()):
+            raise ValueError("%s must be a contiguous CUDA tensor of %s" % (name, " or ".join(map(str, dts))))
+    if tsdf.numel() != n or w.numel() != n:
+        raise ValueError("tsdf and w must hold dims[0] * dims[1] * dims[2] = %d elements" % n)
+    if depth_mm.dim() != 2:
+        raise ValueError("depth_mm must be a 2-D (height x width) tensor")
     keep = []
     dh, dw = _hw(depth_mm)
     org = np.ascontiguousarray(np.asarray(origin, dtype=np.float32).reshape(3))

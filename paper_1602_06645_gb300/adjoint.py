@@ -94,11 +94,18 @@ class ColourFusionFn(torch.autograd.Function):
     colour voxel at the camera K4 = (fx, fy, cx, cy), T = exp(xi^) T0.
 
     Gradients: images (float32, like images), K4 (4), and xi (6) as the
-    derivative with respect to a left perturbation of T(xi), exact at xi = 0."""
+    derivative with respect to a left perturbation of T(xi) = exp(xi^) T0.
+    That is the gradient with respect to xi only at xi = 0, so xi must be zero:
+    to move the camera, fold a step into T0 (T0 <- exp(step^) T0) and evaluate
+    again at xi = 0.  A non-zero xi raises ValueError."""
 
     @staticmethod
     def forward(ctx, images, K4, xi, adj: Adjoint, T0):
-        T = (se3_exp(xi.detach().cpu().numpy()) @ np.asarray(T0, np.float64)).astype(np.float32)
+        xi_np = xi.detach().cpu().numpy()
+        if np.any(xi_np != 0):
+            raise ValueError("ColourFusionFn is linearised at xi = 0: fold xi into T0 (T0 <- exp(xi^) T0) "
+                             "and pass xi = 0")
+        T = np.asarray(T0, np.float64).astype(np.float32)
         k4 = K4.detach().cpu().numpy().astype(np.float32)
         C, n = adj.forward(images.detach().contiguous(), k4, T)
         ctx.adj, ctx.T, ctx.k4 = adj, T, k4

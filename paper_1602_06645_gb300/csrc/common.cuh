@@ -183,6 +183,7 @@ cudaError_t launch_frame_post(const FrameConst& c, const Volumes& v, const Scrat
 cudaError_t launch_frame(const FrameConst& c, const Volumes& v, const Scratch& s, const uint16_t* depth,
                          const uint8_t* rgb, const LaunchGrids& g, cudaStream_t stream, cudaEvent_t* ev = nullptr);
 int geometry_blocks_per_sm();
+int geometry_linear_blocks_per_sm();  // k_geometry_linear (the allocation-free entry point)
 int colour_blocks_per_sm();
 int voxel_blocks_per_sm();
 

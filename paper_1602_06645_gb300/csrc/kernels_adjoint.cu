@@ -18,6 +18,7 @@
 
 #include "common.cuh"
 #include "device_math.cuh"
+#include "ffloat.cuh"
 
 namespace tsdf {
 namespace {
@@ -83,7 +84,10 @@ struct Sample {
 
 // HD sample position of voxel (centre p) in frame k at the linearisation
 // point: P_vc = R_n p + t_n (Eq. 5), P = R P_vc + t (Eq. 3), (u, v) = K P / Z
-// (Eq. 4); the bilinear footprint (x0..x0+1, y0..y0+1) must lie in the image.
+// (Eq. 4) with the operations of the colour update's projection
+// (xh = fmaf(fx, X, cx Z), u = xh * (1/Z)); the bilinear footprint
+// (x0..x0+1, y0..y0+1), x0 = floor(u), must lie in the image.  The cell is an
+// integer decision, taken exactly as the fusion's bilinear sampling takes it.
 __device__ __forceinline__ Sample hd_sample(const AdjCamera& cam, const AdjFrame& fr, float px, float py, float pz) {
     Sample s;
     float Xc, Yc, Zc;
@@ -92,23 +96,48 @@ __device__ __forceinline__ Sample hd_sample(const AdjCamera& cam, const AdjFrame
     s.valid = false;
     if (!(s.Z > 0.0f)) return s;
     const float rz = __frcp_rn(s.Z);
-    const float u = fmaf(cam.fx, s.X * rz, cam.cx), v = fmaf(cam.fy, s.Y * rz, cam.cy);
+    const float u = fmaf(cam.fx, s.X, cam.cx * s.Z) * rz, v = fmaf(cam.fy, s.Y, cam.cy * s.Z) * rz;
     const float fx0 = floorf(u), fy0 = floorf(v);
-    if (!(fx0 >= 0.0f && fx0 <= (float)(cam.width - 2) && fy0 >= 0.0f && fy0 <= (float)(cam.height - 2))) return s;
+    if (!(fx0 >= 0.0f && fx0 + 1.0f <= (float)(cam.width - 1) && fy0 >= 0.0f && fy0 + 1.0f <= (float)(cam.height - 1)))
+        return s;
     s.valid = true;
     s.x0 = (int)fx0;
     s.y0 = (int)fy0;
-    s.ax = u - fx0;
-    s.ay = v - fy0;
     return s;
 }
 
-__device__ __forceinline__ void voxel_centre(const AdjCamera& cam, uint32_t lin, float& px, float& py, float& pz) {
+// The bilinear fractions (u - x0, v - y0) of a valid sample, from the sample
+// position in float-float arithmetic: the voxel centre origin + (k + 1/2) s_c,
+// both rigid motions and the projection carry ~48 bits, so the fractions are
+// those of the exact position for the given binary32 constants to within a
+// few binary32 roundings (binary32 throughout would be ~1e-4 pixel off at
+// HD resolution, a visible colour error across a sharp image edge).
+__device__ __forceinline__ void hd_fractions(const AdjCamera& cam, const AdjFrame& fr, const int k[3], Sample& s) {
+    ff p[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) p[a] = ff_add(two_prod((float)k[a] + 0.5f, cam.s_c), cam.origin[a]);
+    ff c[3], h[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) c[r] = ff_row(fr.R + 3 * r, fr.t[r], p);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) h[r] = ff_row(cam.R + 3 * r, cam.t[r], c);
+    const ff qx = ff_div(h[0], h[2]), qy = ff_div(h[1], h[2]);
+    const ff u = ff_add(ff_mul(qx, cam.fx), cam.cx), v = ff_add(ff_mul(qy, cam.fy), cam.cy);
+    s.ax = (u.hi - (float)s.x0) + u.lo;  // the difference of the high parts is exact (Sterbenz)
+    s.ay = (v.hi - (float)s.y0) + v.lo;
+}
+
+__device__ __forceinline__ void voxel_index(const AdjCamera& cam, uint32_t lin, int k[3]) {
     const uint32_t nx = (uint32_t)cam.nc[0], ny = (uint32_t)cam.nc[1];
-    const int x = (int)(lin % nx), y = (int)((lin / nx) % ny), z = (int)(lin / (nx * ny));
-    px = fmaf((float)x + 0.5f, cam.s_c, cam.origin[0]);
-    py = fmaf((float)y + 0.5f, cam.s_c, cam.origin[1]);
-    pz = fmaf((float)z + 0.5f, cam.s_c, cam.origin[2]);
+    k[0] = (int)(lin % nx);
+    k[1] = (int)((lin / nx) % ny);
+    k[2] = (int)(lin / (nx * ny));
+}
+
+__device__ __forceinline__ void voxel_centre(const AdjCamera& cam, const int k[3], float& px, float& py, float& pz) {
+    px = fmaf((float)k[0] + 0.5f, cam.s_c, cam.origin[0]);
+    py = fmaf((float)k[1] + 0.5f, cam.s_c, cam.origin[1]);
+    pz = fmaf((float)k[2] + 0.5f, cam.s_c, cam.origin[2]);
 }
 
 // ------------------------------------------------------------ forward -----
@@ -117,16 +146,19 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_forward(AdjCamera cam, AdjB
                                                              int32_t* __restrict__ n_out) {
     const size_t plane = (size_t)cam.height * cam.width * 3;
     for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n_slots; s += gridDim.x * blockDim.x) {
+        int kv[3];
         float px, py, pz;
-        voxel_centre(cam, a.V[s], px, py, pz);
+        voxel_index(cam, a.V[s], kv);
+        voxel_centre(cam, kv, px, py, pz);
         const uint8_t* fl = a.slot_frames + (size_t)s * a.max_frames;
         const int m = min((int)a.slot_count[s], a.max_frames);
         float sum[3] = {0.0f, 0.0f, 0.0f};
         int n = 0;
         for (int j = 0; j < m; ++j) {
             const int k = fl[j];
-            const Sample smp = hd_sample(cam, a.frames[k], px, py, pz);
+            Sample smp = hd_sample(cam, a.frames[k], px, py, pz);
             if (!smp.valid) continue;
+            hd_fractions(cam, a.frames[k], kv, smp);
             const float* p00 = images + k * plane + ((size_t)smp.y0 * cam.width + smp.x0) * 3;
             const float* p01 = p00 + (size_t)cam.width * 3;
 #pragma unroll
@@ -161,14 +193,17 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_backward(AdjCamera cam, Adj
         const float inv = 1.0f / (float)n;
         const float g[3] = {grad_C[(size_t)s * 3] * inv, grad_C[(size_t)s * 3 + 1] * inv, grad_C[(size_t)s * 3 + 2] * inv};
         if (g[0] == 0.0f && g[1] == 0.0f && g[2] == 0.0f) continue;
+        int kv[3];
         float px, py, pz;
-        voxel_centre(cam, a.V[s], px, py, pz);
+        voxel_index(cam, a.V[s], kv);
+        voxel_centre(cam, kv, px, py, pz);
         const uint8_t* fl = a.slot_frames + (size_t)s * a.max_frames;
         const int m = min((int)a.slot_count[s], a.max_frames);
         for (int j = 0; j < m; ++j) {
             const int k = fl[j];
-            const Sample smp = hd_sample(cam, a.frames[k], px, py, pz);
+            Sample smp = hd_sample(cam, a.frames[k], px, py, pz);
             if (!smp.valid) continue;
+            hd_fractions(cam, a.frames[k], kv, smp);
             const size_t o00 = k * plane + ((size_t)smp.y0 * cam.width + smp.x0) * 3;
             const size_t o01 = o00 + (size_t)cam.width * 3;
             const float* p00 = images + o00;

@@ -1443,6 +1443,12 @@ int geometry_blocks_per_sm() {
     return n > 0 ? n : 1;
 }
 
+int geometry_linear_blocks_per_sm() {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_geometry_linear<true, true>, GEO_THREADS, 0);
+    return n > 0 ? n : 1;
+}
+
 size_t colour_smem_bytes() { return sizeof(ColourSlot) * (COL_THREADS / 32); }
 
 int colour_blocks_per_sm() {

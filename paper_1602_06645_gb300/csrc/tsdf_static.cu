@@ -13,6 +13,7 @@
 #include <mutex>
 
 #include "../../include/tsdf.h"
+#include "api_internal.h"
 #include "common.cuh"
 
 using namespace tsdf;
@@ -25,6 +26,7 @@ constexpr size_t COUNTERS_BYTES = 256;
 constexpr size_t TILES_BYTES = (size_t)STATIC_MAX_TILES * sizeof(uint32_t);
 constexpr size_t LIST_BYTES = (size_t)STATIC_MAX_BRICKS * sizeof(uint32_t);
 constexpr size_t SCRATCH_BYTES = COUNTERS_BYTES + TILES_BYTES + LIST_BYTES;
+static_assert(SCRATCH_BYTES == TSDF_STATIC_SCRATCH_BYTES, "the header states the scratch size");
 static_assert(sizeof(Counters) <= COUNTERS_BYTES, "counters do not fit their slot");
 
 // The shared scratch.  In host code this name is only a host-side stand-in;
@@ -62,6 +64,11 @@ extern "C" tsdf_status tsdf_integrate_geometry_static(const int32_t dims[3], flo
                                                       void* stream) {
     if (!dims || !origin || !tsdf_dev || !w_dev || !depth_dev || !K_depth || !T_world_depth)
         return TSDF_ERR_INVALID_ARG;
+    // the three arrays must be device memory (a host array would be read and
+    // written out of bounds by the kernels); this query allocates nothing
+    if (!tsdf_host::is_device_ptr(tsdf_dev) || !tsdf_host::is_device_ptr(w_dev) ||
+        !tsdf_host::is_device_ptr(depth_dev))
+        return TSDF_ERR_INVALID_ARG;
     int64_t nbt = 1;
     for (int a = 0; a < 3; ++a) {
         if (dims[a] < 1 || dims[a] > 4096) return TSDF_ERR_INVALID_ARG;
@@ -83,7 +90,9 @@ extern "C" tsdf_status tsdf_integrate_geometry_static(const int32_t dims[3], flo
     }
 
     // once per device, with that device current: the device address of the
-    // scratch array and the persistent grid size
+    // scratch array and the persistent grid size.  The address belongs to the
+    // device's primary context: after cudaDeviceReset the cached value is
+    // stale, so the library must not be used across a device reset.
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
         cudaGetLastError();
@@ -104,7 +113,7 @@ extern "C" tsdf_status tsdf_integrate_geometry_static(const int32_t dims[3], flo
                 cudaGetLastError();
                 return TSDF_ERR_CUDA;
             }
-            g_grid[dev] = sms * geometry_blocks_per_sm();
+            g_grid[dev] = sms * geometry_linear_blocks_per_sm();
             g_scratch_dev[dev] = p;
         }
         scratch = g_scratch_dev[dev];

@@ -188,3 +188,93 @@ def test_forward_of_linear_images_is_the_mean_projected_pixel(prob):
     assert (r["n"][ok] == cnt[ok]).mean() > 0.999
     same = ok & (r["n"] == cnt)
     np.testing.assert_allclose(r["C"][same], acc[same] / cnt[same, None], rtol=0, atol=1e-4)
+
+
+# ------------------------------------------------ bilinear cells (binary32) --
+def _cells64(adj, K4, T, W, H):
+    """Binary64 cells of every pair: the voxel centre moved by (R_n, t_n)
+    (Eq. 5) and by T (Eq. 3), projected with (fx, fy, cx, cy) (Eq. 4); the
+    footprint (x0..x0+1, y0..y0+1) must lie in the W x H image.  Also returns
+    the distance of u and v from the nearest integer (the near-tie margin)."""
+    nc = np.array(adj.p.nc, np.int64)
+    org = np.array(adj.p.origin, np.float64)
+    s = float(np.float32(adj.p.s_c))
+    fx, fy, cx, cy = [float(v) for v in np.asarray(K4, np.float32)]
+    T = np.asarray(T, np.float32).astype(np.float64)
+    x0 = np.full(len(adj.idx), np.iinfo(np.int32).min, np.int64)
+    y0 = x0.copy()
+    margin = np.full(len(adj.idx), np.inf)
+    for k in range(len(adj.offsets) - 1):
+        sl = slice(adj.offsets[k], adj.offsets[k + 1])
+        v = adj.idx[sl].astype(np.int64)
+        ijk = np.stack([v % nc[0], (v // nc[0]) % nc[1], v // (nc[0] * nc[1])], 1).astype(np.float64)
+        pw = org + (ijk + 0.5) * s
+        Pc = pw @ adj.Rn[k].reshape(3, 3).astype(np.float64).T + adj.tn[k].astype(np.float64)
+        Ph = Pc @ T[:3, :3].T + T[:3, 3]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            u = fx * Ph[:, 0] / Ph[:, 2] + cx
+            w = fy * Ph[:, 1] / Ph[:, 2] + cy
+        fu, fw = np.floor(u), np.floor(w)
+        ok = (Ph[:, 2] > 0) & (fu >= 0) & (fu <= W - 2) & (fw >= 0) & (fw <= H - 2)
+        x0[sl] = np.where(ok, fu, x0[sl])
+        y0[sl] = np.where(ok, fw, y0[sl])
+        margin[sl] = np.minimum(np.abs(u - np.round(u)), np.abs(w - np.round(w)))
+    return x0, y0, margin
+
+
+def test_cells_equal_binary64_cells_away_from_ties(prob):
+    """The binary32 cell decision (the fusion oracle's colour path) equals the
+    binary64 floor of the projected sample wherever u and v are farther than
+    1e-3 pixel from an integer."""
+    adj, th0, seq = prob["adj"], prob["th0"], prob["seq"]
+    _, H, W, _ = adj.images.shape
+    K4 = (th0[:4] - np.array([0.0, 0.0, 0.3 * W, 0.0])).astype(np.float32)  # part of the scan leaves the image
+    T = np.asarray(perturbed(seq.T_depth_rgb), np.float32)
+    cells = adj.cells32(K4, T)
+    x0, y0, margin = _cells64(adj, K4, T, W, H)
+    far = margin > 1e-3
+    assert far.mean() > 0.99
+    np.testing.assert_array_equal(cells[0::2][far], x0[far])
+    np.testing.assert_array_equal(cells[1::2][far], y0[far])
+    valid = cells[0::2] != np.iinfo(np.int32).min
+    assert valid.sum() > 1000 and (~valid).sum() > 10  # the case has samples on both sides of the border
+
+
+def test_cells_equal_binary64_cells_full_hd(prob):
+    """The same at the HD camera of the rig (1920 x 1080, f = 1050): most
+    samples now fall inside the image."""
+    seq, o, S = prob["seq"], prob["o"], prob["S"]
+    adj = prob["adj"]
+    n = len(S)
+    imgs = np.zeros((n, 1080, 1920, 3), np.float32)
+    big = oracle.Adjoint(imgs, adj.Rn, adj.tn, S, seq.dims_col, o.p.s_c, list(o.p.origin), np.eye(4))
+    K4 = np.array([1050.0, 1050.0, 959.5, 539.5], np.float32)
+    T = np.asarray(perturbed(seq.T_depth_rgb, seed=5), np.float32)
+    cells = big.cells32(K4, T)
+    x0, y0, margin = _cells64(big, K4, T, 1920, 1080)
+    far = margin > 1e-3
+    np.testing.assert_array_equal(cells[0::2][far], x0[far])
+    np.testing.assert_array_equal(cells[1::2][far], y0[far])
+    assert (cells[0::2] != np.iinfo(np.int32).min).mean() > 0.5
+
+
+def test_cells_at_the_image_edge():
+    """Samples placed exactly (dyadic values) on either side of the image
+    border: the 2x2 footprint (x0..x0+1, y0..y0+1) must lie inside the
+    16 x 12 image, x0 = floor(u) (not the nearest integer), u = fx X / Z + cx."""
+    Wd, Hd = 16, 12
+    fx, fy, cx, cy = 2.0, 2.0, 3.0, 1.0
+    # one colour voxel (centre (0.125, 0.125, 0.125)) seen in one frame per case
+    us = [(-0.25, 5.0), (0.0, 5.0), (0.75, 5.0), (14.0, 5.0), (15.0 - 2.0 ** -10, 5.0), (15.0, 5.0),
+          (5.0, -0.5), (5.0, 0.0), (5.0, 10.0), (5.0, 10.5), (5.0, 11.0), (3.25, 7.5)]
+    want = [None, (0, 5), (0, 5), (14, 5), (14, 5), None, None, (5, 0), (5, 10), (5, 10), None, (3, 7)]
+    n = len(us)
+    Rn = np.tile(np.eye(3, dtype=np.float32).reshape(9), (n, 1))
+    tn = np.array([[(u - cx) / fx - 0.125, (v - cy) / fy - 0.125, 1.0 - 0.125] for u, v in us], np.float32)
+    S = [np.zeros(1, np.uint32) for _ in range(n)]
+    imgs = np.zeros((n, Hd, Wd, 3), np.float32)
+    adj = oracle.Adjoint(imgs, Rn, tn, S, (1, 1, 1), 0.25, [0.0, 0.0, 0.0], np.eye(4))
+    cells = adj.cells32(np.array([fx, fy, cx, cy], np.float32), np.eye(4, dtype=np.float32))
+    none = np.iinfo(np.int32).min
+    got = [None if cells[2 * i] == none else (int(cells[2 * i]), int(cells[2 * i + 1])) for i in range(n)]
+    assert got == want

@@ -74,7 +74,18 @@ MESH_MUTANTS = {
     "tx_unobserved_colour_used": ("if ((c >> 24) == 0u) continue;", ""),
     "tx_size_truncated": ("float q = floorf(dist / size_pixel + 0.5f);", "float q = floorf(dist / size_pixel);"),
 }
+# Slips in the bilinear-cell decision of the photometric loss (oracle.c and the
+# camera built in oracle/__init__.py), caught by tests/test_adjoint_oracle.py.
+CELL_MUTANTS = {
+    "cell_round_not_floor": ("oracle.c", "    *x0 = floorf(u);\n", "    *x0 = floorf(u + 0.5f);\n"),
+    "cell_bound_w_minus_1": ("oracle.c", "*x0 + 1.0f <= (float)(W - 1) && *y0 >= 0.0f",
+                             "*x0 <= (float)(W - 1) && *y0 >= 0.0f"),
+    "cell_fx_cx_swapped": ("__init__.py", "Kr = np.array([[fx, 0, cx], [0, fy, cy], [0, 0, 1]], np.float32)",
+                           "Kr = np.array([[cx, 0, fx], [0, fy, cy], [0, 0, 1]], np.float32)"),
+    "cell_u_from_y": ("oracle.c", "    *x0 = floorf(u);\n    *y0 = floorf(v);", "    *x0 = floorf(v);\n    *y0 = floorf(u);"),
+}
 ALL = {**{k: ("oracle.c", "tests/test_oracle_pins.py") + v for k, v in MUTANTS.items()},
+       **{k: (v[0], "tests/test_adjoint_oracle.py") + v[1:] for k, v in CELL_MUTANTS.items()},
        **{k: ("raycast.c", "tests/test_raycast_oracle.py") + v for k, v in RAYCAST_MUTANTS.items()},
        **{k: ("mesh.c", "tests/test_mesh_oracle.py") + v for k, v in MESH_MUTANTS.items()}}
 

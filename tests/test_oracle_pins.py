@@ -122,6 +122,112 @@ def test_plane_tsdf_closed_form(oracle_lib, a, b):
     assert inside_hidden.sum() > 100
 
 
+def sphere_Z(K, iu, iv, c, r):
+    """Camera-frame Z of the first point where the ray through pixel (iu, iv)
+    meets the sphere |P - c| = r (closed form: P = Z d with d = K^-1 (iu, iv, 1)
+    scaled to d_z = 1, so Z^2 |d|^2 - 2 Z d.c + |c|^2 - r^2 = 0, smaller root);
+    NaN where the ray misses or the sphere is behind the camera."""
+    Ki = np.linalg.inv(np.asarray(K, np.float64))
+    d = [Ki[i, 0] * iu + Ki[i, 1] * iv + Ki[i, 2] for i in range(3)]
+    d = [d[0] / d[2], d[1] / d[2], np.ones_like(d[2])]
+    dd = d[0] ** 2 + d[1] ** 2 + d[2] ** 2
+    dc = d[0] * c[0] + d[1] * c[1] + d[2] * c[2]
+    disc = dc * dc - dd * (c[0] ** 2 + c[1] ** 2 + c[2] ** 2 - r * r)
+    with np.errstate(invalid="ignore"):
+        Z = (dc - np.sqrt(disc)) / dd
+    return np.where((disc >= 0) & (Z > 0), Z, np.nan)
+
+
+def expected_sphere_tsdf(dims, s, origin, T, K, W, H, mu, c, r):
+    """Closed-form single-frame TSDF of a sphere (centre c, radius r in the
+    camera frame): per voxel its nearest pixel, the mm-quantised depth of the
+    sphere along that pixel's ray (no depth where the ray misses),
+    sdf = D/1000 - Z, updated iff D > 0 and sdf >= -mu, F = min(1, sdf/mu).
+    Also returns the near-tie mask."""
+    X, Y, Z = world_to_cam(T, *centres_world(dims, s, origin))
+    K = np.asarray(K, np.float64)
+    u = K[0, 0] * X / Z + K[0, 2]
+    v = K[1, 1] * Y / Z + K[1, 2]
+    fu, fv = np.floor(u + 0.5), np.floor(v + 0.5)
+    inside = (Z > 0) & (fu >= 0) & (fu <= W - 1) & (fv >= 0) & (fv <= H - 1)
+    Zs = sphere_Z(K, fu, fv, c, r)
+    hit = np.isfinite(Zs)
+    D = np.where(hit, np.floor(np.nan_to_num(Zs) * 1000.0 + 0.5), 0.0)
+    sdf = D * 1e-3 - Z
+    upd = inside & (D > 0) & (sdf >= -mu)
+    F = np.where(upd, np.minimum(1.0, sdf / mu), 0.0)
+    tie = _round_tie(u) | _round_tie(v) | (np.abs(sdf + mu) < EPS_M)
+    return upd, F, tie, sdf
+
+
+def sphere_depth_image(K, W, H, c, r):
+    iv, iu = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    Z = sphere_Z(K, iu, iv, c, r)
+    return np.where(np.isfinite(Z), np.floor(np.nan_to_num(Z) * 1000.0 + 0.5), 0).astype(np.uint16)
+
+
+SPHERE = dict(c=(0.04, -0.03, 0.8), r=0.15)
+
+
+def test_sphere_tsdf_closed_form(oracle_lib):
+    """One frame of a sphere: every voxel's TSDF and weight equal the
+    projective closed form through its rounded pixel ray, including voxels
+    whose ray misses the sphere (no depth, not updated) and the silhouette."""
+    W, H = IMG
+    K = K_of(70.0, W, H)
+    T = pose(deg=35.0)
+    dims, s, mu = GEO["dims"], GEO["s"], GEO["mu"]
+    origin = box_in_front(T, dims, s, 0.8)
+    depth = sphere_depth_image(K, W, H, SPHERE["c"], SPHERE["r"])
+    assert (depth == 0).sum() > 100 and (depth > 0).sum() > 100
+    o = oracle.Oracle(dims, dims, s, mu, 10, origin=origin)
+    n = o.integrate_geometry(depth, K, T)
+    upd, F, tie, sdf = expected_sphere_tsdf(dims, s, origin, T, K, W, H, mu, SPHERE["c"], SPHERE["r"])
+    ok = ~tie
+    assert n == int(o.W.astype(bool).sum())
+    np.testing.assert_array_equal(o.W[ok], upd[ok].astype(np.uint8))
+    np.testing.assert_allclose(o.F[ok], F[ok].astype(np.float32), atol=1e-5, rtol=0)
+    assert (upd & ok & (np.abs(sdf) < mu)).sum() > 100  # the band around the curved surface
+    assert (upd & ok & (sdf > mu)).sum() > 100
+    assert (ok & ~upd & (sdf < -mu) & (F == 0)).sum() > 10  # hidden inside the sphere
+
+
+def test_sphere_tsdf_two_views_average(oracle_lib):
+    """Two frames of the same sphere from two camera poses: voxels updated in
+    both hold the mean of the two closed forms, in one the single value; the
+    weight counts the frames."""
+    W, H = IMG
+    K = K_of(70.0, W, H)
+    dims, s, mu = GEO["dims"], GEO["s"], GEO["mu"]
+    T1 = pose(deg=10.0, t=(0.0, 0.0, 0.0))
+    c_world = np.asarray(T1, np.float64) @ np.array([*SPHERE["c"], 1.0])
+    T2 = np.asarray(T1, np.float64).copy()
+    R2 = rot((0.0, 1.0, 0.0), 12.0)
+    # second camera: rotated about the sphere centre by 12 degrees
+    T2[:3, :3] = R2 @ T1[:3, :3]
+    T2[:3, 3] = c_world[:3] + R2 @ (T1[:3, 3] - c_world[:3])
+    T2 = T2.astype(np.float32)
+    origin = box_in_front(T1, dims, s, 0.8)
+    o = oracle.Oracle(dims, dims, s, mu, 10, origin=origin)
+    ups, Fs, ties = [], [], []
+    for Tk in (T1, T2):
+        Tk64 = np.asarray(Tk, np.float64)
+        c_cam = Tk64[:3, :3].T @ (c_world[:3] - Tk64[:3, 3])
+        depth = sphere_depth_image(K, W, H, c_cam, SPHERE["r"])
+        o.integrate_geometry(depth, K, Tk)
+        u, F, tie, _ = expected_sphere_tsdf(dims, s, origin, Tk, K, W, H, mu, c_cam, SPHERE["r"])
+        ups.append(u)
+        Fs.append(F)
+        ties.append(tie)
+    ok = ~(ties[0] | ties[1])
+    both = ups[0] & ups[1]
+    wexp = ups[0].astype(np.uint8) + ups[1].astype(np.uint8)
+    np.testing.assert_array_equal(o.W[ok], wexp[ok])
+    Fexp = np.where(both, 0.5 * (Fs[0] + Fs[1]), Fs[0] + Fs[1])
+    np.testing.assert_allclose(o.F[ok], Fexp[ok].astype(np.float32), atol=1e-5, rtol=0)
+    assert (both & ok).sum() > 500 and (ok & (wexp == 1)).sum() > 50
+
+
 @pytest.mark.parametrize("max_w", [1, 4, 255])
 def test_weight_counts_observing_frames(oracle_lib, max_w):
     """n identical frames: weight = min(n, max_weight) where observed, 0 elsewhere;
