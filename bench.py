@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -49,8 +50,11 @@ def parse():
                     help="scan (512^3/1024^3) | small (128^3/256^3) | sweep256 | sweep512 | sweep768 | sweep1024 | "
                          "scan_r1 | batched (64 scans) | adjoint (256^3/512^3, 20 frames) | <any of the first>_fused "
                          "(one persistent launch per frame) | raycast (640x480 casts of the scan volumes) | "
-                         "mesh (mesh + texture maps of the scan volumes)")
+                         "mesh (mesh + texture maps of the scan volumes) | track (ICP camera tracking)")
     ap.add_argument("--dense", action="store_true", help="culling off (dense sweep of every brick)")
+    ap.add_argument("--shard", default="scans", choices=["scans", "slab"],
+                    help="N > 1: an independent scan per GPU (weak scaling, the default) or one scan split into "
+                         "z-slabs over the GPUs (strong scaling; each GPU holds 1/N of both volumes)")
     ap.add_argument("--l2-flush", action="store_true",
                     help="flush L2 between frames and time each frame alone (the default when the volumes are "
                          "smaller than 4x L2)")
@@ -139,6 +143,24 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+class clock_record:
+    """Context manager: nvidia-smi clock samples over the enclosed (timed)
+    region of a single-GPU workload; .result is the line's "clocks" entry."""
+
+    def __init__(self, dev=0):
+        self.s = ClockSampler(gpu_uuid(dev))
+        self.result = None
+
+    def __enter__(self):
+        self.s.start()
+        time.sleep(0.15)
+        return self
+
+    def __exit__(self, *exc):
+        self.result = self.s.stop()
+        return False
 
 
 def gpu_uuid(dev):
@@ -241,7 +263,11 @@ def run_ours(args):
     T.load()
 
     n = args.warmup + args.steps
-    seq = make_sequence(args.workload, n, rank)
+    slab_mode = getattr(args, "shard", "scans") == "slab"
+    seq = make_sequence(args.workload, n, 0 if slab_mode else rank)
+    # z-slab sharding: every rank gets every frame and integrates its slab of
+    # the one scan (no exchange on the data path)
+    slab = T.slab_ranges(seq.dims_geo, seq.dims_col, world)[rank] if slab_mode and world > 1 else None
     t0 = time.perf_counter()
     frames = render_frames(seq, n)
     gen_s = time.perf_counter() - t0
@@ -253,7 +279,7 @@ def run_ours(args):
 
     def volume():
         return T.Volume(seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, seq.max_weight, culling=not args.dense,
-                        stream=stream.cuda_stream)
+                        stream=stream.cuda_stream, slab=slab)
 
     # Phase breakdown: the same frames through a separate volume with every
     # phase timed (eight event records per frame), before the timed run.
@@ -325,6 +351,8 @@ def run_ours(args):
     del flush
 
     nominal = nominal_voxels(seq)
+    if slab is not None:  # this rank's share of the volumes: the sum over ranks is the whole
+        nominal = nominal * (slab[1] - slab[0]) // seq.dims_geo[2]
     units = nominal * args.steps
     (total_ms,), (units,) = reduce_over_ranks(dist, "cuda", [total_ms], [units])
     value = units / (total_ms / 1e3)
@@ -357,12 +385,14 @@ def run_ours(args):
     result = {
         "metric": "voxel-updates/s (nominal, geo+colour)", "value": value, "unit": "voxel-updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / K,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+u8", "data": "synthetic",
+        "higher_is_better": True, "scaling": "strong" if slab is not None else "weak", "vs_baseline": None,
+        "dtype": "f32+u8", "data": "synthetic",
         "config": {"workload": seq.name, "dims_geo": list(seq.dims_geo), "dims_col": list(seq.dims_col),
                    "depth": "%dx%d" % seq.depth_size, "rgb": "%dx%d" % seq.rgb_size, "frames": args.steps,
                    "culling": not args.dense, "l2": l2_note,
-                   "parallelism": "independent scan per GPU" if world > 1 else "single GPU"},
-        "frames_per_s": args.steps * world / (total_ms / 1e3),
+                   "parallelism": ("z-slabs of one scan over the GPUs" if slab is not None else
+                                   "independent scan per GPU" if world > 1 else "single GPU")},
+        "frames_per_s": args.steps * (1 if slab is not None else world) / (total_ms / 1e3),
         "updated_voxels_per_s": (st.total_geo_updated + st.total_col_updated) * world / (total_ms / 1e3),
         "per_frame": {"geo_updated": st.total_geo_updated / K, "col_updated": st.total_col_updated / K,
                       "geo_bricks": st.total_geo_bricks / K, "col_bricks": st.total_col_bricks / K,
@@ -386,7 +416,7 @@ def run_ours(args):
     if not args.no_e2e:
         host = [(torch.from_numpy(d.view(np.int16)).pin_memory(), torch.from_numpy(c).pin_memory()) for d, c in frames]
         vol2 = T.Volume(seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, seq.max_weight, culling=not args.dense,
-                        stream=stream.cuda_stream)
+                        stream=stream.cuda_stream, slab=slab)
         # each step: upload and integrate frame i, queue the read of its
         # counters, then wait for frame i - 1's counters (a one-frame-deep
         # pipeline: the host queues frame i while frame i - 1 finishes); the
@@ -412,7 +442,8 @@ def run_ours(args):
         h2d = frames[0][0].nbytes + frames[0][1].nbytes
         assert last.frames_counted == args.warmup + args.steps
         result["e2e"] = {"value": units / e2e_s, "unit": "voxel-updates/s", "h2d_bytes_per_step": int(h2d),
-                         "d2h_bytes_per_step": 2 * T.STATS_COPY_BYTES, "frames_per_s": args.steps * world / e2e_s}
+                         "d2h_bytes_per_step": 2 * T.STATS_COPY_BYTES,
+                         "frames_per_s": args.steps * (1 if slab is not None else world) / e2e_s}
 
     # ---- CPU baseline: the oracle on the host cores, bounded sample
     if world == 1 and rank == 0 and not args.no_cpu_baseline:
@@ -449,11 +480,11 @@ def tuned_schedule(batch, frames, key):
             cache = json.load(f)
     except Exception:
         cache = {}
-    if key in cache:
-        batch.set_schedule(int(cache[key]["blocks_per_sm"]), True)
+    if key in cache and "bricks_per_item" in cache[key]:
+        batch.set_schedule(int(cache[key]["blocks_per_sm"]), True, int(cache[key]["bricks_per_item"]))
         return cache[key], True
-    best, ms = batch.autotune(frames, rounds=3)
-    cache[key] = {"blocks_per_sm": best, "ms_per_candidate": ms}
+    (best, tile), ms = batch.autotune(frames, rounds=3)
+    cache[key] = {"blocks_per_sm": best, "bricks_per_item": tile, "ms_per_candidate": ms}
     try:
         os.makedirs(os.path.dirname(path), exist_ok=True)
         with open(path, "w") as f:
@@ -512,7 +543,8 @@ def run_batched(args):
     batch = T.Batch(vols)
     key = "%s|%s" % (torch.cuda.get_device_name(0), hashlib.sha1(json.dumps(edges).encode()).hexdigest()[:12])
     sched, cached = tuned_schedule(batch, [fr[0] for _, fr in data], key)
-    ms_batched = timed(lambda f: batch.integrate([fr[f] for _, fr in data]))
+    with clock_record() as ck:
+        ms_batched = timed(lambda f: batch.integrate([fr[f] for _, fr in data]))
     batch.synchronize()
     stats_b = [v.stats() for v in vols]
     batch.close()
@@ -537,13 +569,14 @@ def run_batched(args):
         "dtype": "f32+u8", "data": "synthetic",
         "config": {"workload": "batched_%d_scans" % n_scans, "edges": edges, "rgb": "1280x720", "depth": "640x480",
                    "l2": "flushed between steps (256 MiB write)", "schedule_blocks_per_sm": sched["blocks_per_sm"],
+                   "schedule_bricks_per_item": sched["bricks_per_item"],
                    "schedule_from_cache": cached, "cuda_graph": True},
         "sequential": {"value": nominal * K / (ms_seq / 1e3), "ms_per_step": ms_seq / K,
                        "launches_per_step": 6 * n_scans},
         "speedup_vs_sequential": ms_seq / ms_batched,
         "scan_frames_per_s": n_scans * K / (ms_batched / 1e3),
         "gpu_launches": K,
-        "autotune_ms_per_candidate": sched.get("ms_per_candidate"),
+        "autotune_ms_per_candidate": sched.get("ms_per_candidate"), "clocks": ck.result,
         "updated_per_step": {"geo": sum(s.total_geo_updated for s in stats_b) / K,
                              "col": sum(s.total_col_updated for s in stats_b) / K},
         "frame_generation_s": gen_s,
@@ -592,10 +625,11 @@ def run_fused(args):
     batch = T.Batch([vf])
     key = "%s|fused|%s" % (torch.cuda.get_device_name(0), seq.name)
     sched, cached = tuned_schedule(batch, [frames[0]], key)
-    ms_fused = timed(lambda f: batch.integrate([frames[f]]))
-    batch.synchronize()
     vp = volume()
-    ms_plain = timed(lambda f: vp.integrate(*frames[f]))
+    with clock_record() as ck:
+        ms_fused = timed(lambda f: batch.integrate([frames[f]]))
+        batch.synchronize()
+        ms_plain = timed(lambda f: vp.integrate(*frames[f]))
     vp.synchronize()
     same = all(bool(torch.equal(a, b)) for a, b in zip(vf.read_torch(), vp.read_torch()))
     batch.close()
@@ -612,7 +646,7 @@ def run_fused(args):
                    "schedule_blocks_per_sm": sched["blocks_per_sm"], "schedule_from_cache": cached,
                    "cuda_graph": True},
         "plain": {"value": nominal * K / (ms_plain / 1e3), "ms_per_step": ms_plain / K, "launches_per_step": 6},
-        "fused_over_plain_time": ms_fused / ms_plain, "volumes_identical": same,
+        "fused_over_plain_time": ms_fused / ms_plain, "volumes_identical": same, "clocks": ck.result,
         "gpu_launches": K, "frame_generation_s": gen_s,
     }
     print(json.dumps(line), flush=True)
@@ -641,13 +675,14 @@ def run_raycast(args):
         vol.raycast(seq.K_depth, seq.poses[n_fuse + i], size, 0.1, 4.0, device="cuda")
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for i in range(args.steps):
-        flush.zero_()
-        ev[i][0].record(stream)
-        out = vol.raycast(seq.K_depth, seq.poses[n_fuse + args.warmup + i], size, 0.1, 4.0, device="cuda")
-        ev[i][1].record(stream)
-        hits.append(out["range"] > 0)
-    torch.cuda.synchronize()
+    with clock_record() as ck:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            out = vol.raycast(seq.K_depth, seq.poses[n_fuse + args.warmup + i], size, 0.1, 4.0, device="cuda")
+            ev[i][1].record(stream)
+            hits.append(out["range"] > 0)
+        torch.cuda.synchronize()
     ms = [a.elapsed_time(b) for a, b in ev]
     K = max(args.steps, 1)
     rays = size[0] * size[1]
@@ -657,7 +692,7 @@ def run_raycast(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": seq.name + "_raycast_640x480", "fused_frames": n_fuse, "near_far_m": [0.1, 4.0],
                    "l2": "flushed between steps (256 MiB write)"},
-        "hit_fraction": float(torch.stack(hits).float().mean()), "gpu_launches": K,
+        "hit_fraction": float(torch.stack(hits).float().mean()), "gpu_launches": K, "clocks": ck.result,
     }
     vol.close()
     print(json.dumps(line), flush=True)
@@ -687,7 +722,10 @@ def run_mesh(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     texels = None
     ev = []
+    ck = clock_record()
     for i in range(args.warmup + args.steps):
+        if i == args.warmup:
+            ck.__enter__()
         flush.zero_()
         e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         e[0].record(stream)
@@ -701,6 +739,7 @@ def run_mesh(args):
         if i >= args.warmup:
             ev.append(e)
     torch.cuda.synchronize()
+    ck.__exit__(None, None, None)
     mesh_ms = [a.elapsed_time(b) for a, b, _ in ev]
     tex_ms = [b.elapsed_time(c) for _, b, c in ev]
     K = max(args.steps, 1)
@@ -714,7 +753,68 @@ def run_mesh(args):
         "config": {"workload": seq.name + "_mesh_texture", "fused_frames": n_fuse, "size_pixel_m": size,
                    "l2": "flushed between steps (256 MiB write)"},
         "triangles": n_tri, "texels": n_tex, "mesh_ms": sum(mesh_ms) / K, "texture_ms": sum(tex_ms) / K,
-        "texels_per_s": n_tex * K / (sum(tex_ms) / 1e3), "gpu_launches": 7 * K,
+        "texels_per_s": n_tex * K / (sum(tex_ms) / 1e3), "gpu_launches": 7 * K, "clocks": ck.result,
+    }
+    vol.close()
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------- tracking -----
+def run_track(args):
+    """Camera tracking (tsdf_track) on the scan workload: 30 frames fused at
+    their true poses, then each next frame tracked from the previous frame's
+    pose against the volume (3-level pyramid, 10 / 5 / 4 steps, the
+    prediction ray-cast per level), with the pose error against the truth."""
+    import torch
+    import paper_1602_06645_gb300 as T
+
+    torch.cuda.set_device(0)
+    T.load()
+    n_fuse = 30
+    seq = make_sequence("scan", n_fuse + args.warmup + args.steps, 0)
+    stream = torch.cuda.current_stream()
+    vol = T.Volume(seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, seq.max_weight, stream=stream.cuda_stream)
+    frames = [seq.frame(f) for f in range(n_fuse + args.warmup + args.steps)]
+    for f in range(n_fuse):
+        d, c = frames[f]
+        vol.integrate(d, c, seq.K_depth, seq.K_rgb, seq.poses[f], seq.T_depth_rgb)
+    depth = [torch.from_numpy(d.view(np.int16)).cuda() for d, _ in frames]
+    torch.cuda.synchronize()
+
+    def track(f):
+        Tp = seq.poses[f - 1]
+        return T.tsdf_track(vol.h, depth[f], seq.K_depth, Tp, np.asarray(Tp, np.float64))
+
+    for i in range(args.warmup):
+        track(n_fuse + i)
+    errs, corr = [], []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with clock_record() as ck:
+        for i in range(args.steps):
+            f = n_fuse + args.warmup + i
+            ev[i][0].record(stream)
+            Tt, rep = track(f)
+            ev[i][1].record(stream)
+            Tg = np.asarray(seq.poses[f], np.float64)
+            R = Tt[:3, :3].T @ Tg[:3, :3]
+            errs.append((1e3 * float(np.linalg.norm(Tt[:3, 3] - Tg[:3, 3])),
+                         math.degrees(math.acos(min(1.0, max(-1.0, (np.trace(R) - 1) / 2))))))
+            corr.append(rep.correspondences[rep.steps - 1])
+        torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    K = max(args.steps, 1)
+    e = np.array(errs)
+    line = {
+        "metric": "tracked frames/s (ICP against the ray-cast prediction, scan volumes)",
+        "value": K / (sum(ms) / 1e3), "unit": "frames/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sum(ms) / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": seq.name + "_track", "fused_frames": n_fuse, "levels": 3, "steps": [10, 5, 4],
+                   "l2": "not flushed: each call rebuilds its pyramid, maps and predictions"},
+        "pose_error_mm": {"median": float(np.median(e[:, 0])), "max": float(e[:, 0].max())},
+        "pose_error_deg": {"median": float(np.median(e[:, 1])), "max": float(e[:, 1].max())},
+        "correspondences_last_step": int(np.median(corr)), "gpu_launches": (3 * 2 + 3 + 19 * 2) * K,
+        "clocks": ck.result,
     }
     vol.close()
     print(json.dumps(line), flush=True)
@@ -783,8 +883,9 @@ def run_adjoint(args):
 
     for _ in range(args.warmup):
         fwd_bwd()
-    ms_fb = ev_time(fwd_bwd, max(args.steps, 1))
-    ms_f = ev_time(lambda: adj.forward(images, K4, Tm), max(args.steps, 1))
+    with clock_record() as ck:
+        ms_fb = ev_time(fwd_bwd, max(args.steps, 1))
+        ms_f = ev_time(lambda: adj.forward(images, K4, Tm), max(args.steps, 1))
     vox, fr = adj.pairs()
     line = {
         "metric": "adjoint forward+backward time (20 frames, 256^3/512^3)", "value": ms_fb, "unit": "ms",
@@ -793,7 +894,7 @@ def run_adjoint(args):
         "config": {"workload": seq.name, "frames": n_frames, "rgb": "%dx%d" % seq.rgb_size,
                    "voxels": nv, "pairs": int(len(vox))},
         "forward_ms": ms_f, "record_ms": ms_record, "plain_fusion_20_frames_ms": ms_plain,
-        "pairs_per_s_fwd_bwd": len(vox) / (ms_fb / 1e3),
+        "pairs_per_s_fwd_bwd": len(vox) / (ms_fb / 1e3), "clocks": ck.result,
     }
     adj.close()
     vol.close()
@@ -814,6 +915,8 @@ def main():
         run_raycast(args)
     elif args.workload == "mesh":
         run_mesh(args)
+    elif args.workload == "track":
+        run_track(args)
     else:
         run_ours(args)
 

@@ -90,6 +90,9 @@ typedef struct {
                                   updated with F = 1; 0: only |sdf| <= mu */
     void* stream;              /* cudaStream_t for all work on the handle; NULL = legacy default */
     tsdf_allocator allocator;
+    int32_t slab_z[2];         /* {z0, z1}: the handle holds the z-slab [z0, z1) of the geometry
+                                  volume dims_geo (and the same slice of space of the colour
+                                  volume) instead of the whole volume; {0, 0} = whole [0, 0] */
 } tsdf_params;
 
 /* Fill *p with the defaults listed above. */
@@ -106,7 +109,25 @@ void tsdf_params_default(tsdf_params* p);
  *   mu          truncation distance (m) > 0
  *   max_weight  weight cap, 1..255 (weights count observing frames up to it)
  *   out         receives the handle (owned by the caller until tsdf_destroy)
- * Errors: INVALID_ARG (bad dims, ratio, sizes or NULL out), OOM, CUDA. */
+ * Z-slabs (params->slab_z = {z0, z1}, 0 <= z0 < z1 <= dims_geo[2]): one scan's
+ * volumes split along z over several handles (several GPUs, or a colour
+ * volume larger than one device holds; Section IV.B notes that GPU memory
+ * bounds the colour volume).  dims_geo / dims_col stay the whole volume's;
+ * z0 * dims_col[2] and z1 * dims_col[2] must be multiples of dims_geo[2] (the
+ * cuts fall on whole colour voxels).  The handle holds colour z
+ * [z0 c, z1 c), c = dims_col[2] / dims_geo[2], and geometry z [max(0, z0 - 1),
+ * min(dims_geo[2], z1 + 1)): one geometry voxel beyond the slab on each side,
+ * integrated redundantly, which the trilinear band gate of the colour voxels
+ * next to the cut reads.  Every voxel is computed at its global index, so
+ * each slab's values equal the whole volume's bit for bit; every slab handle
+ * receives every frame.  tsdf_read / tsdf_write / tsdf_save / tsdf_load
+ * cover the held ranges (tsdf_get_info: held_geo_z, held_col_z); the
+ * geometry of [z0, z1) and the colour of the colour range, concatenated over
+ * the slabs in z order, are the whole volumes.  Ray casting, mesh extraction,
+ * texture maps and the adjoint need a whole-volume handle.
+ * The volumes must lie within 10^6 m of the world origin (|origin| +
+ * dims * voxel size per axis).
+ * Errors: INVALID_ARG (bad dims, ratio, sizes, slab or NULL out), OOM, CUDA. */
 tsdf_status tsdf_create(const int32_t dims_geo[3], const int32_t dims_col[3], float voxel_size, float mu,
                         int32_t max_weight, tsdf_volume** out);
 tsdf_status tsdf_create_ex(const int32_t dims_geo[3], const int32_t dims_col[3], float voxel_size, float mu,
@@ -137,7 +158,8 @@ tsdf_status tsdf_create_ex(const int32_t dims_geo[3], const int32_t dims_col[3],
  * not overwrite the buffer until the handle's stream has passed the frame's
  * last kernel.  The call is asynchronous with respect to the host.
  * Errors: INVALID_ARG (NULL pointers, sizes outside 1..16384, non-finite or
- * singular K, non-finite or non-rigid T with |R^T R - I| > 1e-4), OOM, CUDA. */
+ * singular K, non-finite or non-rigid T with |R^T R - I| > 1e-4, a
+ * translation beyond 10^6 m), OOM, CUDA. */
 tsdf_status tsdf_integrate(tsdf_volume* vol, const uint16_t* depth_mm, tsdf_image_size dsz, const uint8_t* rgb_hwc,
                            tsdf_image_size csz, const float K_depth[9], const float K_rgb[9],
                            const float T_world_depth[16], const float T_depth_rgb[16]);
@@ -145,8 +167,10 @@ tsdf_status tsdf_integrate(tsdf_volume* vol, const uint16_t* depth_mm, tsdf_imag
 /* Copy the volumes out, linear x-fastest (Section IV.B: "the new RGB value and
  * weight are saved in the colour voxel").  Each destination may be NULL (not
  * read) or a host or device pointer of dims_geo product floats (tsdf), bytes
- * (w_geo) or dims_col product uint32 (rgbw).  Synchronous: returns after the
- * copies are complete, and reports any recorded device-side error. */
+ * (w_geo) or dims_col product uint32 (rgbw); for a z-slab handle, of the held
+ * ranges (dims_geo[0] * dims_geo[1] * (held_geo_z[1] - held_geo_z[0]) and
+ * likewise for colour).  Synchronous: returns after the copies are complete,
+ * and reports any recorded device-side error. */
 tsdf_status tsdf_read(tsdf_volume* vol, float* tsdf, uint8_t* w_geo, uint32_t* rgbw);
 
 /* Overwrite the volumes from linear x-fastest arrays (host or device), e.g. to
@@ -179,6 +203,9 @@ typedef struct {
     int32_t max_weight, colour_mode, sample_mode, culling, update_free_space;
     int64_t frames;              /* frames integrated so far */
     int64_t device_bytes;        /* bytes of device memory the handle holds */
+    int32_t slab_z[2];           /* the slab [z0, z1) of a z-slab handle; {0, dims_geo[2]} otherwise */
+    int32_t held_geo_z[2];       /* geometry z range held (the slab and its one-voxel margins) */
+    int32_t held_col_z[2];       /* colour z range held */
 } tsdf_info;
 tsdf_status tsdf_get_info(const tsdf_volume* vol, tsdf_info* out);
 
@@ -281,16 +308,25 @@ tsdf_status tsdf_batch_integrate(tsdf_batch* batch, const tsdf_frame* frames);
 tsdf_status tsdf_batch_synchronize(tsdf_batch* batch);
 /* Schedule: blocks per SM of the persistent launch (1..max, the occupancy
  * limit) and whether steps replay a CUDA graph. */
-tsdf_status tsdf_batch_set_schedule(tsdf_batch* batch, int32_t blocks_per_sm, int32_t use_graph);
+/* The schedule of the batched step: blocks per SM of the persistent grid
+ * (1..max_blocks_per_sm), listed bricks per work item of the geometry and
+ * band phases (1..TSDF_BATCH_MAX_BRICKS_PER_ITEM: a warp takes that many
+ * consecutive bricks of one scan's list at a time) and whether the step runs
+ * as a CUDA graph.  Results do not depend on the schedule. */
+#define TSDF_BATCH_MAX_BRICKS_PER_ITEM 8
+tsdf_status tsdf_batch_set_schedule(tsdf_batch* batch, int32_t blocks_per_sm, int32_t bricks_per_item,
+                                    int32_t use_graph);
 tsdf_status tsdf_batch_get_schedule(const tsdf_batch* batch, int32_t* blocks_per_sm, int32_t* max_blocks_per_sm,
-                                    int32_t* use_graph);
-/* Autotuner: times each blocks-per-SM candidate (median over `rounds`
- * interleaved rounds) on freshly created clones of the batch's volumes fed
- * with `frames`, keeps the fastest in the batch's schedule and reports it;
- * ms_per_candidate (nullable) receives max_blocks_per_sm median times.  The
- * batch's own volumes are not touched. */
+                                    int32_t* bricks_per_item, int32_t* use_graph);
+/* Autotuner: times every schedule (blocks per SM 1..max_blocks_per_sm times
+ * 1, 2, 4 or 8 bricks per item; median over `rounds` interleaved rounds) on
+ * freshly created clones of the batch's volumes fed with `frames`, keeps the
+ * fastest in the batch's schedule and reports it; ms_per_candidate
+ * (nullable) receives 4 * max_blocks_per_sm median times, candidate
+ * (blocks - 1) * 4 + log2(bricks per item).  The batch's own volumes are not
+ * touched. */
 tsdf_status tsdf_batch_autotune(tsdf_batch* batch, const tsdf_frame* frames, int32_t rounds,
-                                int32_t* best_blocks_per_sm, float* ms_per_candidate);
+                                int32_t* best_blocks_per_sm, int32_t* best_bricks_per_item, float* ms_per_candidate);
 /* Failure injection for tests: in the next step one block never arrives at
  * the first grid barrier, so the other blocks' bounded waits run out. */
 tsdf_status tsdf_batch_inject_stall(tsdf_batch* batch);
@@ -388,6 +424,77 @@ tsdf_status tsdf_integrate_geometry_static(const int32_t dims[3], float voxel_si
                                            const float T_world_depth[16], void* stream);
 
 /* ------------------------------------------------------------------------
+ * Camera tracking (Section III: the KinectFusion loop the paper builds on).
+ * A vertex map and normal map pyramid is computed from the input depth map
+ * and the camera motion is estimated by iterative closest point against the
+ * surface vertex map predicted by ray tracing the geometry volume.  The paper
+ * gives no more detail; the steps (all binary32 per pixel, in this order):
+ *   pyramid   level 0: d = D * 0.001 m (D = 0: none); level l + 1 pixel (x, y):
+ *             the mean of the valid depths of level l's block (2x + i, 2y + j),
+ *             taken (0,0), (1,0), (0,1), (1,1), that lie within 0.03 m of the
+ *             block's first valid depth (summed in that order, divided once);
+ *             level l is W >> l by H >> l with f_l = f / 2^l and
+ *             c_l = (c + 1/2) / 2^l - 1/2 (binary64, rounded once)
+ *   maps      V = d (fmaf(1/fx, x, -cx/fx), fmaf(1/fy, y, -cy/fy), 1) (the
+ *             coefficients binary64, rounded once); N = n / sqrt(n . n) with
+ *             n = (V(x, y+1) - V) x (V(x+1, y) - V), facing the camera; no
+ *             normal on the last row / column or next to a pixel without depth
+ *   predict   per level, tsdf_raycast from T_world_depth_prev with the level's
+ *             intrinsics and size (vertex and normal maps, world frame)
+ *   steps     levels coarsest first, iterations[l] Gauss-Newton steps each:
+ *             for a pixel with a vertex and a normal, p = R V + t, m = R N
+ *             (R, t: the current pose rounded to binary32); the prediction
+ *             pixel of q_c = R_p p + t_p (R_p = R_prev^T, t_p = -R_prev^T t_prev
+ *             in binary64 rounded once) projected as in Eq. 6 (u = fmaf(fx, X,
+ *             cx Z) * (1/Z), nearest, inside, Z > 0) with a predicted normal nq
+ *             and vertex q; |p - q|^2 <= max_distance^2 and m . nq >=
+ *             min_normal_cos; r = (p - q) . nq, J = (nq, p x nq).  A = sum J J^T,
+ *             g = sum J r in binary64; xi = -A^-1 g by Cholesky (binary64; a
+ *             matrix that is not positive definite leaves the pose), applied
+ *             as T <- exp(xi^) T with xi = (rho, phi) (Rodrigues, binary64).
+ * The pose stays on the device between steps: a frame's steps are queued
+ * without host round trips.
+ * ---------------------------------------------------------------------- */
+#define TSDF_TRACK_MAX_LEVELS 3
+#define TSDF_TRACK_MAX_STEPS 32
+typedef struct {
+    int32_t levels;                             /* 1..3 [3] */
+    int32_t iterations[TSDF_TRACK_MAX_LEVELS];  /* steps per level, finest first [10, 5, 4]; total <= 32 */
+    float max_distance;                         /* correspondence gate, metres [0.1] */
+    float min_normal_cos;                       /* normal gate, cosine of the largest angle [cos 20 deg] */
+    float near_m, far_m;                        /* prediction ray-cast range [0.1, 4] */
+} tsdf_track_params;
+void tsdf_track_params_default(tsdf_track_params* p);
+
+/* What each step saw: its level, correspondences, sum of squared residuals,
+ * the normal equations (A row-major, g), the pose it started from and whether
+ * it was solved. */
+typedef struct {
+    int32_t steps;
+    int32_t level[TSDF_TRACK_MAX_STEPS];
+    int32_t solved[TSDF_TRACK_MAX_STEPS];
+    int64_t correspondences[TSDF_TRACK_MAX_STEPS];
+    double err2[TSDF_TRACK_MAX_STEPS];
+    double A[TSDF_TRACK_MAX_STEPS][36];
+    double g[TSDF_TRACK_MAX_STEPS][6];
+    double T_before[TSDF_TRACK_MAX_STEPS][16];
+} tsdf_track_report;
+
+/* Track one depth frame against the volume (whole-volume handles only).
+ *   depth_mm            dsz.height x dsz.width uint16 mm, host or device
+ *   K_depth             pinhole 3x3 (zero skew, bottom row 0 0 1), host
+ *   T_world_depth_prev  the pose the prediction is ray-cast from (row-major 4x4, host)
+ *   T_init              the first estimate of the frame's pose (binary64, host)
+ *   params              NULL = defaults
+ *   T_out               the estimate after the last step (binary64, host)
+ *   report              nullable
+ * Synchronous.  Errors: INVALID_ARG (sizes, K, T, params, slab handle), OOM,
+ * CUDA. */
+tsdf_status tsdf_track(tsdf_volume* vol, const uint16_t* depth_mm, tsdf_image_size dsz, const float K_depth[9],
+                       const float T_world_depth_prev[16], const double T_init[16], const tsdf_track_params* params,
+                       double T_out[16], tsdf_track_report* report);
+
+/* ------------------------------------------------------------------------
  * Ray casting of the fused volumes.  The paper shows the scan to the user by
  * ray casting the geometry and colour volumes (abstract) and tracks the camera
  * against a surface vertex map predicted by ray tracing the geometry volume
@@ -431,20 +538,33 @@ tsdf_status tsdf_raycast(tsdf_volume* vol, const float K[9], const float T_world
  * mesh from the TSDF volume (Section IV.C) and textures each polygon with its
  * own 2D map sampled from the colour volume (Section IV.D, Eq. 11-14).
  *
- * Mesh: the zero level set of the TSDF by marching tetrahedra.  A cell is the
- * cube of eight neighbouring geometry voxels (corner k = (k & 1, (k >> 1) & 1,
- * k >> 2)) and is meshed only when all eight are observed.  It is split into
- * six tetrahedra along the diagonal from corner 0 to corner 7 (for each axis
- * order (x,y,z), (x,z,y), (y,x,z), (y,z,x), (z,x,y), (z,y,x): corners 0, 0 + a0,
- * 0 + a0 + a1, 7), the same split on both sides of a shared face, so the
- * surface has no cracks.  A corner is inside when F < 0.  A tetrahedron with a
- * lone corner gives the triangle on its three edges; one with two inside
- * corners i1, i2 and outside corners o1, o2 (tetrahedron order) gives the quad
- * on edges (i1,o1), (i1,o2), (i2,o2), (i2,o1) as triangles ((i1,o1), (i1,o2),
- * (i2,o2)) and ((i1,o1), (i2,o2), (i2,o1)).  The vertex on edge (p, q), p the
- * lower voxel index: t = F_p / (F_p - F_q), v = fmaf(t, P_q - P_p, P_p), P the
- * voxel centre.  Triangles are wound so that their normal points to free
- * space (F > 0).  Binary32, operation order as in the reference definition.
+ * Mesh: the zero level set of the TSDF by marching cubes (Section IV.C).  A
+ * cell is the cube of eight neighbouring geometry voxels (corner k = (k & 1,
+ * (k >> 1) & 1, k >> 2)) and is meshed only when all eight are observed; a
+ * corner is inside when F < 0.  The twelve cell edges are numbered 4 a + r
+ * (a the edge's axis, r the rank of its lower corner among the four corners
+ * whose bit a is 0).  On each face, corners taken counter-clockwise about the
+ * outward normal, every maximal run c_i..c_j of inside corners is cut off by
+ * a segment from the edge (c_(i-1), c_i) to the edge (c_j, c_(j+1)), so a face
+ * with two diagonal inside corners separates them.  The segments form closed
+ * loops, taken in the order of their lowest edge; each loop is fanned along
+ * the segments' direction from its first vertex (in loop order from the
+ * lowest edge) whose fan has no triangle with all three vertices on one face
+ * (else from the lowest edge), which winds every triangle with its normal to
+ * free space (F > 0).  At most five triangles per cell; the library builds
+ * its 256-case table from these rules.  The vertex on edge (p, q), p the lower
+ * voxel index: t = F_p / (F_p - F_q), v = fmaf(t, P_q - P_p, P_p), P the voxel
+ * centre fmaf(i + 1/2, s_g, origin).  Binary32, operation order as written.
+ *
+ * Marching tetrahedra (tsdf_mesh_ex, TSDF_MESH_TETRAHEDRA): each observed cell
+ * is split into six tetrahedra along the diagonal from corner 0 to corner 7
+ * (for each axis order (x,y,z), (x,z,y), (y,x,z), (y,z,x), (z,x,y), (z,y,x):
+ * corners 0, 0 + a0, 0 + a0 + a1, 7), the same split on both sides of a shared
+ * face.  A tetrahedron with a lone corner gives the triangle on its three
+ * edges; one with two inside corners i1, i2 and outside corners o1, o2
+ * (tetrahedron order) gives the quad on edges (i1,o1), (i1,o2), (i2,o2),
+ * (i2,o1) as triangles ((i1,o1), (i1,o2), (i2,o2)) and ((i1,o1), (i2,o2),
+ * (i2,o1)), wound so that their normal points to free space.
  * ---------------------------------------------------------------------- */
 /* Write up to capacity triangles (9 floats each: v0, v1, v2; host or device
  * pointer, may be NULL with capacity 0) in no fixed order and set
@@ -452,6 +572,10 @@ tsdf_status tsdf_raycast(tsdf_volume* vol, const float K[9], const float T_world
  * output was cut short: call again with more room).  Errors: INVALID_ARG,
  * OOM. */
 tsdf_status tsdf_mesh(tsdf_volume* vol, float* triangles, int64_t capacity, int64_t* n_triangles);
+/* The same with a choice of method: TSDF_MESH_CUBES (what tsdf_mesh does) or
+ * TSDF_MESH_TETRAHEDRA. */
+enum { TSDF_MESH_CUBES = 0, TSDF_MESH_TETRAHEDRA = 1 };
+tsdf_status tsdf_mesh_ex(tsdf_volume* vol, int32_t method, float* triangles, int64_t capacity, int64_t* n_triangles);
 
 /* Texture map layout (Eq. 11-12): for n triangles (V_a, V_b, V_c as 9 floats
  * each) and the size of a texel on the model, w = max(2, round(|V_a V_b| /

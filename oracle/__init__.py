@@ -10,7 +10,9 @@ with a fixed operation order; ``adjoint.c`` is the binary64 photometric loss
 and its analytic gradient (the calibration-refinement extension);
 ``raycast.c`` ray-casts the volumes (range, vertex, normal and colour maps);
 ``mesh.c`` extracts the zero level set as triangles and fills per-polygon
-texture maps from the colour volume (Eq. 11-14).
+texture maps from the colour volume (Eq. 11-14); ``icp.c`` tracks the camera
+(vertex / normal pyramid, projective point-to-plane ICP against the ray-cast
+prediction, Section III).
 """
 from __future__ import annotations
 
@@ -21,7 +23,7 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = [os.path.join(_HERE, f) for f in ("oracle.c", "adjoint.c", "raycast.c", "mesh.c")]
+_SRCS = [os.path.join(_HERE, f) for f in ("oracle.c", "adjoint.c", "raycast.c", "mesh.c", "icp.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 # -ffp-contract=off: no implicit fused multiply-adds; the operation order in the
@@ -54,6 +56,8 @@ class Params(ctypes.Structure):
         ("sample_mode", ctypes.c_int32),
         ("update_free_space", ctypes.c_int32),
         ("n_threads", ctypes.c_int32),
+        ("zoff_g", ctypes.c_int32),
+        ("zoff_c", ctypes.c_int32),
     ]
 
 
@@ -88,6 +92,13 @@ class MeshVolume(ctypes.Structure):
 class ColourVolume(ctypes.Structure):
     _fields_ = [("nc", ctypes.c_int32 * 3), ("s_c", ctypes.c_float), ("origin", ctypes.c_float * 3),
                 ("C", ctypes.c_void_p)]
+
+
+class IcpLevel(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_int32), ("h", ctypes.c_int32), ("Kl", ctypes.c_float * 9),
+                ("V", ctypes.c_void_p), ("N", ctypes.c_void_p), ("PV", ctypes.c_void_p), ("PN", ctypes.c_void_p),
+                ("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3), ("Rp", ctypes.c_float * 9),
+                ("tp", ctypes.c_float * 3), ("max_dist2", ctypes.c_float), ("min_cos", ctypes.c_float)]
 
 
 _lib = None
@@ -132,6 +143,16 @@ def _load():
         assert lib.orc_rc_sizes(0) == ctypes.sizeof(RcVolume) and lib.orc_rc_sizes(1) == ctypes.sizeof(RcCamera)
         lib.orc_mesh.argtypes = [ctypes.POINTER(MeshVolume), vp, ctypes.c_longlong]
         lib.orc_mesh.restype = ctypes.c_longlong
+        lib.orc_icp_pyramid.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]
+        lib.orc_icp_level_K.argtypes = [vp, ctypes.c_int, vp]
+        lib.orc_icp_maps.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp]
+        lib.orc_icp_system.argtypes = [ctypes.POINTER(IcpLevel), vp, vp, vp]
+        lib.orc_icp_system.restype = ctypes.c_longlong
+        lib.orc_icp_solve.argtypes = [vp, vp, vp]
+        lib.orc_icp_solve.restype = ctypes.c_int
+        lib.orc_icp_update.argtypes = [vp, vp]
+        lib.orc_mesh_cubes.argtypes = [ctypes.POINTER(MeshVolume), vp, ctypes.c_longlong]
+        lib.orc_mesh_cubes.restype = ctypes.c_longlong
         lib.orc_texture_sizes.argtypes = [vp, ctypes.c_longlong, ctypes.c_float, ctypes.c_int, vp]
         lib.orc_texture_sizes.restype = ctypes.c_longlong
         lib.orc_texture_fill.argtypes = [ctypes.POINTER(ColourVolume), vp, ctypes.c_longlong, vp, vp, vp]
@@ -159,12 +180,30 @@ def colour_voxel(dims_geo, dims_col, voxel_size):
     return float(np.float32(float(dims_geo[0]) * float(voxel_size) / float(dims_col[0])))
 
 
+def slab_extent(dims_geo, dims_col, z0, z1):
+    """Geometry and colour z ranges held by the z-slab [z0, z1) (geometry
+    voxels) of a volume: the colour range covering the same slice of space,
+    [z0 Nc / Ng, z1 Nc / Ng) (both must be whole voxels), and the geometry
+    range widened by the one voxel on each side that the band gate's trilinear
+    corners reach, clipped to the volume.  Returns (g0, g1, c0, c1)."""
+    ng, nc = int(dims_geo[2]), int(dims_col[2])
+    if not (0 <= z0 < z1 <= ng) or (z0 * nc) % ng or (z1 * nc) % ng:
+        raise ValueError("slab [%d, %d) does not cut both volumes at whole voxels" % (z0, z1))
+    return max(0, z0 - 1), min(ng, z1 + 1), z0 * nc // ng, z1 * nc // ng
+
+
 def make_params(dims_geo, dims_col, voxel_size, mu, max_weight, sigma=0.020, band=None, colour_mode=0,
-                sample_mode=0, update_free_space=1, origin=None, n_threads=1):
-    """orc_params for the two volumes (Section IV.B)."""
+                sample_mode=0, update_free_space=1, origin=None, n_threads=1, slab=None):
+    """orc_params for the two volumes (Section IV.B); slab = (z0, z1) makes
+    them the z-slab [z0, z1) of the volume of dims_geo / dims_col (see
+    slab_extent)."""
     p = Params()
     p.ng[:] = [int(v) for v in dims_geo]
     p.nc[:] = [int(v) for v in dims_col]
+    if slab is not None:
+        g0, g1, c0, c1 = slab_extent(dims_geo, dims_col, *slab)
+        p.ng[2], p.nc[2] = g1 - g0, c1 - c0
+        p.zoff_g, p.zoff_c = g0, c0
     p.s_g = float(voxel_size)
     p.s_c = colour_voxel(dims_geo, dims_col, voxel_size)
     o = volume_geometry(dims_geo, voxel_size) if origin is None else origin
@@ -184,12 +223,12 @@ class Oracle:
     """Holds the two volumes (linear, x fastest) and integrates frames on the CPU."""
 
     def __init__(self, dims_geo, dims_col, voxel_size, mu, max_weight, sigma=0.020, band=None,
-                 colour_mode=0, sample_mode=0, update_free_space=1, origin=None, n_threads=1):
+                 colour_mode=0, sample_mode=0, update_free_space=1, origin=None, n_threads=1, slab=None):
         self.lib = _load()
         self.p = make_params(dims_geo, dims_col, voxel_size, mu, max_weight, sigma, band, colour_mode, sample_mode,
-                             update_free_space, origin, n_threads)
-        gx, gy, gz = dims_geo
-        cx, cy, cz = dims_col
+                             update_free_space, origin, n_threads, slab)
+        gx, gy, gz = self.p.ng
+        cx, cy, cz = self.p.nc
         self.F = np.zeros((gz, gy, gx), dtype=np.float32)
         self.W = np.zeros((gz, gy, gx), dtype=np.uint8)
         self.C = np.zeros((cz, cy, cx), dtype=np.uint32)
@@ -387,10 +426,12 @@ def raycast(F, W, C, s_g, s_c, origin, K, T_world_camera, size, near, far, step_
     return out
 
 
-def mesh(F, W, s_g, origin):
+def mesh(F, W, s_g, origin, method="cubes"):
     """Triangles (n, 3, 3) of the zero level set of linear volumes F, W
-    (Nz, Ny, Nx) by marching tetrahedra (mesh.c), in cell order."""
+    (Nz, Ny, Nx) by marching cubes (method "cubes", the paper's Section IV.C)
+    or marching tetrahedra ("tetrahedra"), in cell order (mesh.c)."""
     lib = _load()
+    fn = {"cubes": lib.orc_mesh_cubes, "tetrahedra": lib.orc_mesh}[method]
     F = np.ascontiguousarray(F, np.float32)
     W = np.ascontiguousarray(W, np.uint8)
     v = MeshVolume()
@@ -398,9 +439,9 @@ def mesh(F, W, s_g, origin):
     v.s_g = float(s_g)
     v.origin[:] = [float(o) for o in origin]
     v.F, v.W = F.ctypes.data, W.ctypes.data
-    n = int(lib.orc_mesh(ctypes.byref(v), None, 0))
+    n = int(fn(ctypes.byref(v), None, 0))
     out = np.zeros((n, 3, 3), np.float32)
-    lib.orc_mesh(ctypes.byref(v), out.ctypes.data, n)
+    fn(ctypes.byref(v), out.ctypes.data, n)
     return out
 
 
@@ -424,3 +465,119 @@ def texture_maps(tris, C, s_c, origin, size_pixel, max_side=1024):
     texels = np.zeros(total, np.uint32)
     lib.orc_texture_fill(ctypes.byref(cv), tris.ctypes.data, n, wh.ctypes.data, off.ctypes.data, texels.ctypes.data)
     return wh, off, texels
+
+
+# ------------------------------------------------------------------ ICP ----
+ICP_ITERATIONS = (10, 5, 4)  # per pyramid level, finest first (KinectFusion's counts)
+ICP_MAX_DIST = 0.1           # correspondence distance gate (m)
+ICP_MIN_COS = float(np.float32(np.cos(np.radians(20.0))))  # normal-angle gate: 20 degrees
+
+
+def icp_pyramid(depth, levels):
+    """Depth pyramid in metres (icp.c): a list of float32 (H >> l, W >> l) maps."""
+    lib = _load()
+    depth = np.ascontiguousarray(depth, np.uint16)
+    H, W = depth.shape
+    sizes = [(H >> l, W >> l) for l in range(levels)]
+    buf = np.zeros(sum(h * w for h, w in sizes), np.float32)
+    lib.orc_icp_pyramid(depth.ctypes.data, W, H, levels, buf.ctypes.data)
+    out, o = [], 0
+    for h, w in sizes:
+        out.append(buf[o:o + h * w].reshape(h, w).copy())
+        o += h * w
+    return out
+
+
+def icp_level_K(K, l):
+    lib = _load()
+    K = np.ascontiguousarray(K, np.float32).reshape(9)
+    out = np.zeros(9, np.float32)
+    lib.orc_icp_level_K(K.ctypes.data, int(l), out.ctypes.data)
+    return out.reshape(3, 3)
+
+
+def icp_maps(d, Kl):
+    """Vertex and normal maps (H, W, 3), camera frame, of a depth map in metres."""
+    lib = _load()
+    d = np.ascontiguousarray(d, np.float32)
+    h, w = d.shape
+    V = np.zeros((h, w, 3), np.float32)
+    N = np.zeros((h, w, 3), np.float32)
+    K = np.ascontiguousarray(Kl, np.float32).reshape(9)
+    lib.orc_icp_maps(d.ctypes.data, w, h, K.ctypes.data, V.ctypes.data, N.ctypes.data)
+    return V, N
+
+
+def _world_to_camera(T):
+    """(R^T, -R^T t) of a camera -> world pose: the transpose exactly, the
+    translation in binary64 rounded once."""
+    T = np.asarray(T, np.float32)
+    R = T[:3, :3].astype(np.float64)
+    return T[:3, :3].T.copy(), (-(R.T @ T[:3, 3].astype(np.float64))).astype(np.float32)
+
+
+def icp_system(V, N, PV, PN, Kl, T_cur, T_prev, max_dist=ICP_MAX_DIST, min_cos=ICP_MIN_COS):
+    """One level's normal equations at pose T_cur (icp.c): dict(A (6, 6),
+    g (6,), err2, n)."""
+    lib = _load()
+    h, w = V.shape[:2]
+    L = IcpLevel()
+    L.w, L.h = w, h
+    L.Kl[:] = [float(x) for x in np.asarray(Kl, np.float32).reshape(9)]
+    arrs = [np.ascontiguousarray(a, np.float32) for a in (V, N, PV, PN)]
+    L.V, L.N, L.PV, L.PN = [a.ctypes.data for a in arrs]
+    Tc = np.asarray(T_cur, np.float64).astype(np.float32)
+    L.R[:] = [float(x) for x in Tc[:3, :3].reshape(9)]
+    L.t[:] = [float(x) for x in Tc[:3, 3]]
+    Rp, tp = _world_to_camera(T_prev)
+    L.Rp[:] = [float(x) for x in Rp.reshape(9)]
+    L.tp[:] = [float(x) for x in tp]
+    L.max_dist2 = float(np.float32(max_dist) * np.float32(max_dist))
+    L.min_cos = float(min_cos)
+    A = np.zeros(36)
+    g = np.zeros(6)
+    e = np.zeros(1)
+    n = lib.orc_icp_system(ctypes.byref(L), A.ctypes.data, g.ctypes.data, e.ctypes.data)
+    return dict(A=A.reshape(6, 6), g=g, err2=float(e[0]), n=int(n))
+
+
+def icp_solve(A, g):
+    lib = _load()
+    A = np.ascontiguousarray(A, np.float64)
+    g = np.ascontiguousarray(g, np.float64)
+    xi = np.zeros(6)
+    ok = lib.orc_icp_solve(A.ctypes.data, g.ctypes.data, xi.ctypes.data)
+    return xi if ok else None
+
+
+def icp_update(xi, T):
+    lib = _load()
+    T = np.ascontiguousarray(T, np.float64).copy()
+    xi = np.ascontiguousarray(xi, np.float64)
+    lib.orc_icp_update(xi.ctypes.data, T.ctypes.data)
+    return T
+
+
+def track(F, W, s_g, origin, mu, depth, K, T_prev, T_init, levels=3, iterations=ICP_ITERATIONS,
+          max_dist=ICP_MAX_DIST, min_cos=ICP_MIN_COS, near=0.1, far=4.0):
+    """Camera tracking of one depth frame against the volumes (F, W): the
+    depth pyramid and its vertex / normal maps; per level, coarsest first,
+    the prediction ray-cast from T_prev with the level's intrinsics and the
+    given number of Gauss-Newton steps T <- exp(xi^) T from T_init.  Returns
+    (T (4, 4) binary64, list of per-iteration dict(level, n, err2, A, g))."""
+    pyr = icp_pyramid(depth, levels)
+    T = np.asarray(T_init, np.float64).copy()
+    log = []
+    for l in reversed(range(levels)):
+        Kl = icp_level_K(K, l)
+        h, w = pyr[l].shape
+        pred = raycast(F, W, None, s_g, s_g, origin, Kl, T_prev, (w, h), near, far, mu=mu)
+        V, N = icp_maps(pyr[l], Kl)
+        for _ in range(iterations[l]):
+            r = icp_system(V, N, pred["vertex"], pred["normal"], Kl, T, T_prev, max_dist, min_cos)
+            r["level"] = l
+            log.append(r)
+            xi = icp_solve(r["A"], r["g"])
+            if xi is not None:
+                T = icp_update(xi, T)
+    return T, log

@@ -10,7 +10,9 @@
  * Binary32 with the operation order written here (-ffp-contract=off; fmaf is
  * the correctly rounded fused multiply-add).
  *
- * Mesh: the zero level set of the TSDF by marching tetrahedra.  A cell is the
+ * Mesh: the zero level set of the TSDF by marching cubes (orc_mesh_cubes,
+ * described at its definition below) or, as an option, by marching
+ * tetrahedra (orc_mesh).  Marching tetrahedra:  a cell is the
  * cube of eight neighbouring geometry voxels (x..x+1, y..y+1, z..z+1), corner
  * k = (k & 1, (k >> 1) & 1, k >> 2); it is meshed only when all eight corners
  * are observed (w > 0).  The cell is split into six tetrahedra along its main
@@ -137,6 +139,147 @@ static int cell_triangles(const orc_mesh_volume* v, int x, int y, int z, float* 
             emit(v, base, tri, ins[0], outs[0], out + 9 * n++);
         }
     }
+    return n;
+}
+
+/* ---------------------------------------------------- marching cubes ---- */
+/* Marching cubes (Section IV.C), written as its definition, cell by cell,
+ * without a case table.  Cells, corners, "inside" (F < 0), observed cells and
+ * the vertex on an edge are as above.  The twelve edges of a cell are
+ * numbered 4 a + r: a the axis along which the edge runs, r the rank of its
+ * lower corner among the four corners whose bit a is 0.
+ *
+ * The surface's boundary on each face of the cell: with the face's corners
+ * c0..c3 taken counter-clockwise about the face's outward normal and e_i the
+ * edge from c_i to c_(i+1), every maximal run c_i..c_j of consecutive inside
+ * corners is cut off by one segment from edge e_(i-1) to edge e_j.  A face
+ * with two diagonal inside corners therefore separates them (the reading of
+ * the face ambiguity taken here; neighbouring cells see the same face alike,
+ * so the surface has no cracks).  Every crossing edge then starts one segment
+ * and ends one, and the segments form closed loops; the loops are taken in
+ * the order of their lowest edge and each is triangulated as a fan from that
+ * edge's vertex, along the segments' direction: (v0, v1, v2), (v0, v2, v3),
+ * ...  With this direction the triangles' normals (v1 - v0) x (v2 - v0) point
+ * to the outside (F >= 0).  A loop that crosses one face twice would give,
+ * fanned from some vertices, a triangle lying flat in that face (and the
+ * neighbouring cell the same triangle reversed); the fan therefore starts at
+ * the first vertex, in loop order from the lowest edge, whose fan has no
+ * triangle with all three vertices on edges of one face (the lowest edge's
+ * vertex when none qualifies).  Triangles come in cell order (linear index,
+ * x fastest), loop order, fan order. */
+static const int FACE_CCW[6][4] = {
+    {0, 4, 6, 2},  /* x = 0, normal -x */
+    {1, 3, 7, 5},  /* x = 1, normal +x */
+    {0, 1, 5, 4},  /* y = 0, normal -y */
+    {2, 6, 7, 3},  /* y = 1, normal +y */
+    {0, 2, 3, 1},  /* z = 0, normal -z */
+    {4, 5, 7, 6},  /* z = 1, normal +z */
+};
+
+/* Edge number of the cell edge between corners p and q (one bit apart). */
+static int edge_of(int p, int q) {
+    int lo = p < q ? p : q, d = p ^ q, a = d == 1 ? 0 : (d == 2 ? 1 : 2), r = 0;
+    for (int c = 0; c < lo; ++c)
+        if (!((c >> a) & 1)) ++r;
+    return 4 * a + r;
+}
+
+/* The two corners (lower first) of edge e. */
+static void edge_corners(int e, int* p, int* q) {
+    int a = e / 4, r = e % 4;
+    for (int c = 0; c < 8; ++c)
+        if (!((c >> a) & 1) && r-- == 0) {
+            *p = c;
+            *q = c | (1 << a);
+            return;
+        }
+}
+
+/* Whether edges e0, e1, e2 all lie in one face of the cell.  The edge with
+ * lower corner p along axis a lies in the faces (b, bit b of p), b != a. */
+static int on_one_face(int e0, int e1, int e2) {
+    const int es[3] = {e0, e1, e2};
+    for (int b = 0; b < 3; ++b)
+        for (int side = 0; side < 2; ++side) {
+            int all = 1;
+            for (int k = 0; k < 3 && all; ++k) {
+                int p, q;
+                edge_corners(es[k], &p, &q);
+                all = (es[k] / 4 != b) && (((p >> b) & 1) == side);
+            }
+            if (all) return 1;
+        }
+    return 0;
+}
+
+static int cell_cubes(const orc_mesh_volume* v, int x, int y, int z, float* out) {
+    const int base[3] = {x, y, z};
+    float Fc[8];
+    int inside = 0;
+    for (int k = 0; k < 8; ++k) {
+        size_t idx = ((size_t)(z + (k >> 2)) * v->ng[1] + (y + ((k >> 1) & 1))) * v->ng[0] + (x + (k & 1));
+        if (v->W[idx] == 0) return 0;
+        Fc[k] = v->F[idx];
+        if (Fc[k] < 0.0f) inside |= 1 << k;
+    }
+    if (inside == 0 || inside == 255) return 0;
+    int next[12];
+    for (int e = 0; e < 12; ++e) next[e] = -1;
+    for (int f = 0; f < 6; ++f) {
+        const int* c = FACE_CCW[f];
+        for (int i = 0; i < 4; ++i) {
+            int in_i = (inside >> c[i]) & 1, in_prev = (inside >> c[(i + 3) % 4]) & 1;
+            if (!in_i || in_prev) continue;  /* i starts a run of inside corners */
+            int j = i;
+            while ((inside >> c[(j + 1) % 4]) & 1) j = (j + 1) % 4;
+            next[edge_of(c[(i + 3) % 4], c[i])] = edge_of(c[j], c[(j + 1) % 4]);
+        }
+    }
+    int n = 0, seen[12] = {0};
+    for (int e0 = 0; e0 < 12; ++e0) {
+        if (next[e0] < 0 || seen[e0]) continue;
+        int loop[12], m = 0;
+        for (int e = e0; !seen[e]; e = next[e]) {
+            seen[e] = 1;
+            loop[m++] = e;
+        }
+        float vert[12][3];
+        for (int i = 0; i < m; ++i) {
+            int p, q;
+            edge_corners(loop[i], &p, &q);
+            edge_vertex(v, base, Fc, p, q, vert[i]);
+        }
+        int s0 = 0;
+        for (int s = 0; s < m; ++s) {
+            int flat = 0;
+            for (int i = 1; i + 1 < m && !flat; ++i)
+                flat = on_one_face(loop[s], loop[(s + i) % m], loop[(s + i + 1) % m]);
+            if (!flat) {
+                s0 = s;
+                break;
+            }
+        }
+        for (int i = 1; i + 1 < m; ++i, ++n) {
+            memcpy(out + 9 * n, vert[s0], 12);
+            memcpy(out + 9 * n + 3, vert[(s0 + i) % m], 12);
+            memcpy(out + 9 * n + 6, vert[(s0 + i + 1) % m], 12);
+        }
+    }
+    return n;
+}
+
+/* Marching-cubes mesh: writes up to cap triangles (9 floats each) to tris
+ * (may be NULL) and returns the total number of triangles. */
+long long orc_mesh_cubes(const orc_mesh_volume* v, float* tris, long long cap) {
+    long long n = 0;
+    float buf[12 * 9];
+    for (int z = 0; z + 1 < v->ng[2]; ++z)
+        for (int y = 0; y + 1 < v->ng[1]; ++y)
+            for (int x = 0; x + 1 < v->ng[0]; ++x) {
+                int m = cell_cubes(v, x, y, z, buf);
+                for (int i = 0; i < m; ++i, ++n)
+                    if (tris && n < cap) memcpy(tris + 9 * n, buf + 9 * i, 9 * sizeof(float));
+            }
     return n;
 }
 

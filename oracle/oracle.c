@@ -25,6 +25,14 @@
  *
  * Volumes are linear, x fastest: index (z * Ny + y) * Nx + x.  Colour voxels
  * are packed R | G<<8 | B<<16 | weight<<24.
+ *
+ * A z-slab of a larger volume (several devices or hosts each holding part of
+ * one scan) is the same computation over a range of z: the parameters carry
+ * the global z index of the slab's first geometry and colour voxel, every
+ * voxel centre is taken at its global index, and the trilinear band gate
+ * addresses the slab's geometry by global index minus that offset.  A slab
+ * whose geometry extends one voxel beyond its colour range on each side
+ * (where the volume continues) computes exactly the whole volume's values.
  */
 #include <math.h>
 #include <stdint.h>
@@ -45,6 +53,8 @@ typedef struct {
     int32_t sample_mode;  /* 0 = nearest HD pixel; 1 = bilinear */
     int32_t update_free_space; /* 1: voxels with sdf > mu are updated with t = 1 */
     int32_t n_threads;    /* OpenMP threads for timing; 1 = reference mode */
+    int32_t zoff_g;       /* z-slab of a larger volume: global z index of local geometry z = 0 */
+    int32_t zoff_c;       /* and of local colour z = 0 (0, 0 for a whole volume) */
 } orc_params;
 
 typedef struct {
@@ -141,7 +151,7 @@ static int geo_voxel(const orc_params* p, const orc_frame* fr, float* Fv, uint8_
                      int y, int z) {
     float P[3];
     rigid(fr->R, fr->t, centre(p->origin[0], x, p->s_g), centre(p->origin[1], y, p->s_g),
-          centre(p->origin[2], z, p->s_g), P);
+          centre(p->origin[2], z + p->zoff_g, p->s_g), P);
     float u, v;
     int iu, iv;
     if (!project(fr->Kd, P[0], P[1], P[2], &u, &v)) return 0;
@@ -203,8 +213,10 @@ static int trilinear(const orc_params* p, corner_fn corner, const void* ctx, con
     for (int a = 0; a < 3; ++a) {
         i0f[a] = floorf(g[a]);
         fr[a] = g[a] - i0f[a];
-        if (!(i0f[a] >= 0.0f && i0f[a] + 1.0f <= (float)(p->ng[a] - 1))) return 0;
-        i0[a] = (int)i0f[a];
+        /* local cell of a z-slab: global index minus the slab's offset */
+        const int lo = a == 2 ? p->zoff_g : 0;
+        if (!(i0f[a] >= (float)lo && i0f[a] + 1.0f <= (float)(lo + p->ng[a] - 1))) return 0;
+        i0[a] = (int)i0f[a] - lo;
     }
     float c[2][2][2];
     for (int dz = 0; dz < 2; ++dz)
@@ -294,7 +306,8 @@ static int orc_paper_normal_update(const orc_params* p, const orc_frame* fr, con
 static int colour_depth_gates(const orc_params* p, const orc_frame* fr, corner_fn corner, const void* ctx,
                               const uint16_t* depth, int x, int y, int z, float Pc[3], int* iu, int* iv,
                               float Pd[3]) {
-    float pw[3] = {centre(p->origin[0], x, p->s_c), centre(p->origin[1], y, p->s_c), centre(p->origin[2], z, p->s_c)};
+    float pw[3] = {centre(p->origin[0], x, p->s_c), centre(p->origin[1], y, p->s_c),
+                   centre(p->origin[2], z + p->zoff_c, p->s_c)};
     rigid(fr->R, fr->t, pw[0], pw[1], pw[2], Pc);
     float u, v;
     if (!project(fr->Kd, Pc[0], Pc[1], Pc[2], &u, &v)) return 0;

@@ -37,8 +37,8 @@ EXPORTS = [
     "tsdf_adjoint_voxels", "tsdf_adjoint_pairs", "tsdf_adjoint_forward", "tsdf_adjoint_backward",
     "tsdf_adjoint_destroy", "tsdf_batch_create", "tsdf_batch_integrate", "tsdf_batch_synchronize",
     "tsdf_batch_set_schedule", "tsdf_batch_get_schedule", "tsdf_batch_autotune", "tsdf_batch_inject_stall",
-    "tsdf_batch_destroy", "tsdf_raycast", "tsdf_mesh", "tsdf_texture_layout", "tsdf_texture_fill",
-    "tsdf_profile_phases",
+    "tsdf_batch_destroy", "tsdf_raycast", "tsdf_mesh", "tsdf_mesh_ex", "tsdf_texture_layout", "tsdf_texture_fill",
+    "tsdf_profile_phases", "tsdf_track_params_default", "tsdf_track",
 ]
 PHASES = ["upload", "depth_tiles", "bricks", "geometry", "colour_list", "colour_cells", "colour"]
 
@@ -61,6 +61,7 @@ class tsdf_params(ctypes.Structure):
         ("update_free_space", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
         ("allocator", tsdf_allocator),
+        ("slab_z", ctypes.c_int32 * 2),
     ]
 
 
@@ -76,6 +77,7 @@ class tsdf_info(ctypes.Structure):
         ("max_weight", ctypes.c_int32), ("colour_mode", ctypes.c_int32), ("sample_mode", ctypes.c_int32),
         ("culling", ctypes.c_int32), ("update_free_space", ctypes.c_int32),
         ("frames", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+        ("slab_z", ctypes.c_int32 * 2), ("held_geo_z", ctypes.c_int32 * 2), ("held_col_z", ctypes.c_int32 * 2),
     ]
 
 
@@ -102,6 +104,21 @@ class tsdf_frame(ctypes.Structure):
         ("K_rgb", ctypes.POINTER(ctypes.c_float)), ("T_world_depth", ctypes.POINTER(ctypes.c_float)),
         ("T_depth_rgb", ctypes.POINTER(ctypes.c_float)),
     ]
+
+
+class tsdf_track_params(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int32), ("iterations", ctypes.c_int32 * 3), ("max_distance", ctypes.c_float),
+                ("min_normal_cos", ctypes.c_float), ("near_m", ctypes.c_float), ("far_m", ctypes.c_float)]
+
+
+TRACK_MAX_STEPS = 32
+
+
+class tsdf_track_report(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int32), ("level", ctypes.c_int32 * TRACK_MAX_STEPS),
+                ("solved", ctypes.c_int32 * TRACK_MAX_STEPS), ("correspondences", ctypes.c_int64 * TRACK_MAX_STEPS),
+                ("err2", ctypes.c_double * TRACK_MAX_STEPS), ("A", (ctypes.c_double * 36) * TRACK_MAX_STEPS),
+                ("g", (ctypes.c_double * 6) * TRACK_MAX_STEPS), ("T_before", (ctypes.c_double * 16) * TRACK_MAX_STEPS)]
 
 
 class TsdfError(RuntimeError):
@@ -158,10 +175,10 @@ def load():
     lib.tsdf_batch_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, H]
     lib.tsdf_batch_integrate.argtypes = [vp, ctypes.POINTER(tsdf_frame)]
     lib.tsdf_batch_synchronize.argtypes = [vp]
-    lib.tsdf_batch_set_schedule.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
+    lib.tsdf_batch_set_schedule.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
     i32o = ctypes.POINTER(ctypes.c_int32)
-    lib.tsdf_batch_get_schedule.argtypes = [vp, i32o, i32o, i32o]
-    lib.tsdf_batch_autotune.argtypes = [vp, ctypes.POINTER(tsdf_frame), ctypes.c_int32, i32o,
+    lib.tsdf_batch_get_schedule.argtypes = [vp, i32o, i32o, i32o, i32o]
+    lib.tsdf_batch_autotune.argtypes = [vp, ctypes.POINTER(tsdf_frame), ctypes.c_int32, i32o, i32o,
                                         ctypes.POINTER(ctypes.c_float)]
     lib.tsdf_batch_inject_stall.argtypes = [vp]
     lib.tsdf_batch_destroy.argtypes = [vp]
@@ -184,10 +201,17 @@ def load():
     lib.tsdf_raycast.argtypes = [vp, fp, fp, tsdf_image_size, ctypes.POINTER(tsdf_raycast_params), vp, vp, vp, vp]
     lib.tsdf_raycast.restype = ctypes.c_int
     lib.tsdf_mesh.argtypes = [vp, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
+    lib.tsdf_mesh_ex.argtypes = [vp, ctypes.c_int32, vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
     lib.tsdf_texture_layout.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_float, ctypes.c_int32, vp, vp]
     lib.tsdf_texture_fill.argtypes = [vp, vp, ctypes.c_int64, vp, vp, vp]
-    for name in ("tsdf_mesh", "tsdf_texture_layout", "tsdf_texture_fill"):
+    for name in ("tsdf_mesh", "tsdf_mesh_ex", "tsdf_texture_layout", "tsdf_texture_fill"):
         getattr(lib, name).restype = ctypes.c_int
+    lib.tsdf_track_params_default.argtypes = [ctypes.POINTER(tsdf_track_params)]
+    lib.tsdf_track_params_default.restype = None
+    lib.tsdf_track.argtypes = [vp, vp, tsdf_image_size, fp, fp, ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(tsdf_track_params), ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(tsdf_track_report)]
+    lib.tsdf_track.restype = ctypes.c_int
     lib.tsdf_profile_enable.argtypes = [vp, ctypes.c_int32]
     lib.tsdf_profile_phases.argtypes = [vp, ctypes.c_uint32]
     lib.tsdf_profile_phases.restype = ctypes.c_int
@@ -316,11 +340,42 @@ def tsdf_raycast(h, K, T_world_camera, size, params=None, range_=None, vertex=No
                                _ptr(normal, np.float32, keep), _ptr(rgbw, np.uint32, keep)), h)
 
 
+TSDF_MESH_CUBES, TSDF_MESH_TETRAHEDRA = 0, 1
+
+
 def tsdf_mesh(h, triangles=None, capacity=0):
     keep = []
     n = ctypes.c_int64()
     _check(load().tsdf_mesh(h, _ptr(triangles, np.float32, keep), int(capacity), ctypes.byref(n)), h)
     return n.value
+
+
+def tsdf_mesh_ex(h, method, triangles=None, capacity=0):
+    keep = []
+    n = ctypes.c_int64()
+    _check(load().tsdf_mesh_ex(h, int(method), _ptr(triangles, np.float32, keep), int(capacity), ctypes.byref(n)), h)
+    return n.value
+
+
+def tsdf_track_params_default():
+    p = tsdf_track_params()
+    load().tsdf_track_params_default(ctypes.byref(p))
+    return p
+
+
+def tsdf_track(h, depth_mm, K_depth, T_world_depth_prev, T_init, params=None, report=True):
+    """Track a depth frame (tsdf_track): (T (4, 4) binary64, tsdf_track_report or None)."""
+    keep = []
+    dh, dw = _hw(depth_mm)
+    Kd, Tp = _mat(K_depth, 9), _mat(T_world_depth_prev, 16)
+    Ti = np.ascontiguousarray(np.asarray(T_init, np.float64).reshape(16))
+    Tout = np.zeros(16, np.float64)
+    rep = tsdf_track_report() if report else None
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(load().tsdf_track(h, _ptr(depth_mm, np.uint16, keep), tsdf_image_size(dw, dh), Kd[1], Tp[1],
+                             Ti.ctypes.data_as(dp), None if params is None else ctypes.byref(params),
+                             Tout.ctypes.data_as(dp), None if rep is None else ctypes.byref(rep)), h)
+    return Tout.reshape(4, 4), rep
 
 
 def tsdf_texture_layout(h, triangles, n, size_pixel, max_side, wh, offsets):
@@ -443,24 +498,27 @@ def tsdf_batch_synchronize(b, err_handle=None):
     _check(load().tsdf_batch_synchronize(b), err_handle)
 
 
-def tsdf_batch_set_schedule(b, blocks_per_sm, use_graph=True):
-    _check(load().tsdf_batch_set_schedule(b, int(blocks_per_sm), int(bool(use_graph))))
+def tsdf_batch_set_schedule(b, blocks_per_sm, bricks_per_item=1, use_graph=True):
+    _check(load().tsdf_batch_set_schedule(b, int(blocks_per_sm), int(bricks_per_item), int(bool(use_graph))))
 
 
 def tsdf_batch_get_schedule(b):
-    x, m, g = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
-    _check(load().tsdf_batch_get_schedule(b, ctypes.byref(x), ctypes.byref(m), ctypes.byref(g)))
-    return x.value, m.value, bool(g.value)
+    """(blocks per SM, max blocks per SM, bricks per item, use_graph)."""
+    x, m, t, g = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().tsdf_batch_get_schedule(b, ctypes.byref(x), ctypes.byref(m), ctypes.byref(t), ctypes.byref(g)))
+    return x.value, m.value, t.value, bool(g.value)
 
 
 def tsdf_batch_autotune(b, frames, rounds=3):
+    """Returns ((blocks per SM, bricks per item), median ms of every candidate,
+    candidate (blocks - 1) * 4 + log2(bricks per item))."""
     keep = []
     arr = _frames(frames, keep)
-    _, mx, _ = tsdf_batch_get_schedule(b)
-    best = ctypes.c_int32()
-    ms = (ctypes.c_float * mx)()
-    _check(load().tsdf_batch_autotune(b, arr, int(rounds), ctypes.byref(best), ms))
-    return best.value, list(ms)
+    _, mx, _, _ = tsdf_batch_get_schedule(b)
+    best, tile = ctypes.c_int32(), ctypes.c_int32()
+    ms = (ctypes.c_float * (4 * mx))()
+    _check(load().tsdf_batch_autotune(b, arr, int(rounds), ctypes.byref(best), ctypes.byref(tile), ms))
+    return (best.value, tile.value), list(ms)
 
 
 def tsdf_batch_inject_stall(b):
@@ -545,18 +603,41 @@ def tsdf_last_error(h):
     return load().tsdf_last_error(h).decode()
 
 
+def slab_ranges(dims_geo, dims_col, n):
+    """Split one volume's geometry z range into n contiguous z-slabs
+    [z0, z1) for n devices, as equal as the cuts allow: every cut falls on a
+    whole colour voxel and, where the slabs stay non-empty, on a multiple of
+    the 8-voxel brick."""
+    import math
+
+    ngz, ncz = int(dims_geo[2]), int(dims_col[2])
+    n = int(n)
+    if n < 1 or n > ngz:
+        raise ValueError("cannot cut %d geometry layers into %d slabs" % (ngz, n))
+    unit = ngz // math.gcd(ngz, ncz)  # z0 * ncz / ngz is whole iff z0 is a multiple of unit
+    for q in (unit * 8 // math.gcd(unit, 8), unit):
+        cuts = [0] + [min(ngz, int(round(k * ngz / n / q)) * q) for k in range(1, n)] + [ngz]
+        if all(a < b for a, b in zip(cuts, cuts[1:])):
+            return list(zip(cuts, cuts[1:]))
+    raise ValueError("no cut of %d layers into %d slabs falls on whole colour voxels" % (ngz, n))
+
+
 # ------------------------------------------------------------- Volume -----
 class Volume:
     """A fusion handle with PyTorch-backed device memory on the current stream."""
 
     def __init__(self, dims_geo, dims_col, voxel_size, mu, max_weight, *, origin=None, sigma=0.020, band=None,
                  colour_mode=TSDF_COLOUR_COUNT, sample_mode=TSDF_SAMPLE_NEAREST, culling=True,
-                 update_free_space=True, stream=None, torch_memory=True):
+                 update_free_space=True, stream=None, torch_memory=True, slab=None):
+        """slab = (z0, z1): hold the z-slab [z0, z1) of the volume (see
+        tsdf_create_ex); dims_geo / dims_col are the whole volume's."""
         import torch
 
         self.dims_geo = tuple(int(v) for v in dims_geo)
         self.dims_col = tuple(int(v) for v in dims_col)
         p = tsdf_params_default()
+        if slab is not None:
+            p.slab_z[:] = [int(slab[0]), int(slab[1])]
         if origin is not None:
             p.origin[:] = [float(v) for v in origin]
         p.sigma = float(sigma)
@@ -572,29 +653,46 @@ class Volume:
             self._alloc = torch_allocator()
             p.allocator = self._alloc
         self.h = tsdf_create_ex(self.dims_geo, self.dims_col, voxel_size, mu, max_weight, p)
+        info = tsdf_get_info(self.h)
+        self.slab = (info.slab_z[0], info.slab_z[1])
+        self.held_geo_z = (info.held_geo_z[0], info.held_geo_z[1])
+        self.held_col_z = (info.held_col_z[0], info.held_col_z[1])
+
+    def _held_shapes(self):
+        gx, gy, _ = self.dims_geo
+        cx, cy, _ = self.dims_col
+        return ((self.held_geo_z[1] - self.held_geo_z[0], gy, gx), (self.held_col_z[1] - self.held_col_z[0], cy, cx))
 
     def integrate(self, depth_mm, rgb_hwc, K_depth, K_rgb, T_world_depth, T_depth_rgb):
         tsdf_integrate(self.h, depth_mm, rgb_hwc, K_depth, K_rgb, T_world_depth, T_depth_rgb)
 
     def read(self):
-        """(F, w, rgbw) as numpy arrays shaped (Nz, Ny, Nx), linear x-fastest."""
-        gx, gy, gz = self.dims_geo
-        cx, cy, cz = self.dims_col
-        F = np.empty((gz, gy, gx), np.float32)
-        W = np.empty((gz, gy, gx), np.uint8)
-        C = np.empty((cz, cy, cx), np.uint32)
+        """(F, w, rgbw) as numpy arrays shaped (Nz, Ny, Nx), linear x-fastest
+        (for a z-slab handle: the held z ranges, see read_slab)."""
+        sg, sc = self._held_shapes()
+        F = np.empty(sg, np.float32)
+        W = np.empty(sg, np.uint8)
+        C = np.empty(sc, np.uint32)
         tsdf_read(self.h, F, W, C)
         return F, W, C
+
+    def read_slab(self):
+        """The slab's own part (F and w of geometry z [z0, z1), the colour
+        held): concatenated over the slabs of a volume in z order, these are
+        the whole volume's arrays."""
+        F, W, C = self.read()
+        a = self.slab[0] - self.held_geo_z[0]
+        b = a + self.slab[1] - self.slab[0]
+        return F[a:b], W[a:b], C
 
     def read_torch(self, device="cuda"):
         """(F, w, rgbw) as device tensors (rgbw as int32 holding the packed bits)."""
         import torch
 
-        gx, gy, gz = self.dims_geo
-        cx, cy, cz = self.dims_col
-        F = torch.empty((gz, gy, gx), dtype=torch.float32, device=device)
-        W = torch.empty((gz, gy, gx), dtype=torch.uint8, device=device)
-        C = torch.empty((cz, cy, cx), dtype=torch.int32, device=device)
+        sg, sc = self._held_shapes()
+        F = torch.empty(sg, dtype=torch.float32, device=device)
+        W = torch.empty(sg, dtype=torch.uint8, device=device)
+        C = torch.empty(sc, dtype=torch.int32, device=device)
         tsdf_read(self.h, F, W, C)
         return F, W, C
 
@@ -616,17 +714,19 @@ class Volume:
         tsdf_raycast(self.h, K, T_world_camera, (w, h), p, out["range"], out["vertex"], out["normal"], out["rgbw"])
         return out
 
-    def mesh(self, capacity=None, device=None):
-        """Triangles (n, 3, 3) of the TSDF zero level set (tsdf_mesh), in no
-        fixed order; numpy, or a device tensor when device is given."""
+    def mesh(self, capacity=None, device=None, method="cubes"):
+        """Triangles (n, 3, 3) of the TSDF zero level set (tsdf_mesh_ex: marching
+        "cubes" or "tetrahedra"), in no fixed order; numpy, or a device tensor
+        when device is given."""
+        m = {"cubes": TSDF_MESH_CUBES, "tetrahedra": TSDF_MESH_TETRAHEDRA}[method]
         if capacity is None:
-            capacity = tsdf_mesh(self.h, None, 0)
+            capacity = tsdf_mesh_ex(self.h, m, None, 0)
         if device is None:
             out = np.empty((int(capacity), 3, 3), np.float32)
         else:
             import torch
             out = torch.empty((int(capacity), 3, 3), dtype=torch.float32, device=device)
-        n = tsdf_mesh(self.h, out if capacity else None, capacity)
+        n = tsdf_mesh_ex(self.h, m, out if capacity else None, capacity)
         return out[:min(n, int(capacity))]
 
     def texture_maps(self, triangles, size_pixel, max_side=1024):
@@ -722,8 +822,8 @@ class Batch:
     def synchronize(self):
         tsdf_batch_synchronize(self.b, self.volumes[0].h)
 
-    def set_schedule(self, blocks_per_sm, use_graph=True):
-        tsdf_batch_set_schedule(self.b, blocks_per_sm, use_graph)
+    def set_schedule(self, blocks_per_sm, use_graph=True, bricks_per_item=1):
+        tsdf_batch_set_schedule(self.b, blocks_per_sm, bricks_per_item, use_graph)
 
     def schedule(self):
         return tsdf_batch_get_schedule(self.b)

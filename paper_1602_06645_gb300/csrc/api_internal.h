@@ -15,7 +15,10 @@ using tsdf::Scratch;
 using tsdf::Volumes;
 
 struct tsdf_volume {
-    int32_t ng[3], nc[3], nb[3], ncb[3];
+    int32_t ng[3], nc[3], nb[3], ncb[3];  // held voxels and bricks per axis
+    // z-slab handles: the whole volume's z dims, the slab [slab_z0, slab_z1)
+    // and the global z index of held geometry / colour z = 0 (whole: 0, 0)
+    int32_t ngz_all, ncz_all, slab_z0, slab_z1, zoff_g, zoff_c;
     float s_g, s_c, origin[3], mu, sigma, band;
     int32_t max_weight, colour_mode, sample_mode, culling, free_space;
     cudaStream_t stream;
@@ -86,6 +89,8 @@ void dev_free(tsdf_volume* v, void* p);
 bool finite_all(const float* a, int n);
 bool is_device_ptr(const void* p);
 bool rigid_ok(const float T[16]);
+constexpr double MAX_COORD = 1e6;  // metres: volume corners and camera translations stay within this
+bool translation_ok(const float T[16]);
 bool invert3(const float K[9], float out[9]);
 void frame_constants(const tsdf_volume* v, const float Kd[9], const float Kr[9], const float Twd[16],
                      const float Tdr[16], int dw, int dh, int cw, int ch, tsdf::FrameConst& c);
@@ -94,4 +99,7 @@ tsdf_status check_device_error(tsdf_volume* v);
 // buffer; sets *d_depth to the device copy.
 tsdf_status stage_depth(tsdf_volume* v, const uint16_t* depth_mm, tsdf_image_size dsz, int tiles,
                         const uint16_t** d_depth);
+// Validated ray-cast constants of a camera (as tsdf_raycast takes them).
+tsdf_status raycast_constants(tsdf_volume* v, const float K[9], const float T_world_camera[16], tsdf_image_size size,
+                              const tsdf_raycast_params* params, tsdf::RayConst& c);
 }  // namespace tsdf_host

@@ -41,6 +41,7 @@ struct FrameConst {
     int32_t kd_pinhole, kr_pinhole, kdi_pinhole;
     int32_t max_weight, free_space, sample_mode, colour_mode, culling;
     int32_t record_mode;   // 1: the band kernel only records (adjoint gate recording); no colour update
+    int32_t zoff_g, zoff_c;  // z-slab: global z index of held geometry / colour z = 0 (whole volume: 0)
 };
 
 // Min/max of F over observed voxels (w > 0) and min of w over the in-volume
@@ -240,8 +241,9 @@ constexpr int MAX_BATCH = 256;  // scans per batched launch
 // One frame step of n scans in a single cooperative launch: depth tiles,
 // bricks, geometry, colour candidates, band gate and colour voxels, with a
 // bounded grid barrier between phases.  Scans are processed in descriptor
-// order (put the largest first).
-cudaError_t launch_batch_step(const ScanDesc* descs, int n, BatchSync* sync, int grid, cudaStream_t stream);
+// order (put the largest first); the geometry and band phases hand out
+// tiles of `tile` consecutive listed bricks of one scan per work item.
+cudaError_t launch_batch_step(const ScanDesc* descs, int n, BatchSync* sync, int grid, int tile, cudaStream_t stream);
 int batch_blocks_per_sm();
 size_t batch_smem_bytes();
 
@@ -269,6 +271,27 @@ cudaError_t launch_raycast(const RayConst& c, const float* F, const uint8_t* W, 
                            const BrickSummary* summ, float* range, float* vertex, float* normal, uint32_t* rgbw,
                            cudaStream_t stream);
 
+// ------------------------------------------------------- camera tracking --
+// One pyramid level of one tracking step (see tsdf_track in tsdf.h).
+struct TrackLevel {
+    int32_t w, h;
+    float K[9];                    // level intrinsics (pinhole)
+    const float *V, *N;            // current vertex / normal maps, camera frame, 3 floats per pixel
+    const float *PV, *PN;          // predicted vertex / normal maps, world frame
+    float Rp[9], tp[3];            // world -> camera of the prediction
+    float max_dist2, min_cos;      // correspondence gates
+};
+// Depth pyramid in metres: d[l] of (W >> l) x (H >> l) floats.
+cudaError_t launch_track_pyramid(const uint16_t* depth, int W, int H, int levels, float* const* d, cudaStream_t stream);
+// Vertex and normal maps of one level; Kinv4 = (1/fx, 1/fy, -cx/fx, -cy/fy).
+cudaError_t launch_track_maps(const float* d, int w, int h, const float Kinv4[4], float* V, float* N,
+                              cudaStream_t stream);
+int track_blocks(int npx);       // blocks (and binary64 partial-sum rows) of one step's reduction
+size_t track_record_doubles();   // doubles recorded per step: 29 sums, 16 pose, 6 xi, 1 solved flag
+// One Gauss-Newton step at the device pose (binary64 row-major 4x4, updated in place).
+cudaError_t launch_track_step(const TrackLevel& L, double* pose, double* partials, double* record,
+                              cudaStream_t stream);
+
 // ------------------------------------------------- mesh and texture maps --
 // Geometry of the volume for mesh extraction (see tsdf_mesh in tsdf.h).
 struct MeshConst {
@@ -281,7 +304,10 @@ struct MeshConst {
 // not written).
 cudaError_t launch_mesh(const MeshConst& c, const float* F, const uint8_t* W, const BrickSummary* summ,
                         uint32_t* list, uint32_t* n_list, float* out, uint64_t cap, unsigned long long* count,
-                        cudaStream_t stream);
+                        bool cubes, cudaStream_t stream);
+// Copy the 256-entry marching-cubes case table (count, then edge triples) to
+// the device.
+cudaError_t upload_cube_cases(const uint8_t (*table)[16], cudaStream_t stream);
 // Colour volume for texture maps (see tsdf_texture_fill in tsdf.h).
 struct ColourConst {
     int32_t nc[3], ncb[3];

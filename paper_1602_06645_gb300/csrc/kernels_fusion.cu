@@ -175,15 +175,16 @@ __device__ __forceinline__ bool ball_outside_image(const FrameConst& c, const fl
 
 __device__ __forceinline__ void brick_flags(const FrameConst& c, const BrickSummary* __restrict__ summ,
                                             const uint32_t* __restrict__ tiles, uint32_t b, bool in, bool& geo,
-                                            bool& vis) {
+                                            bool& vis, bool& inner) {
     vis = in;
     geo = in;
+    inner = false;
     if (in && c.culling) {
         int bx = b % c.nb[0], by = (b / c.nb[0]) % c.nb[1], bz = b / (c.nb[0] * c.nb[1]);
         if (c.kd_pinhole) {
             const float p[3] = {c.origin[0] + (float)(bx * BRICK + BRICK / 2) * c.s_g,
                                 c.origin[1] + (float)(by * BRICK + BRICK / 2) * c.s_g,
-                                c.origin[2] + (float)(bz * BRICK + BRICK / 2) * c.s_g};
+                                c.origin[2] + (float)(bz * BRICK + BRICK / 2 + c.zoff_g) * c.s_g};
             // half-diagonal of the padded brick (4.5 voxels per axis) with 0.1 % and 10 um to spare
             const float r = fmaf(7.8e-3f, c.s_g, 1e-5f) + 4.5f * 1.7320508f * c.s_g;
             if (ball_outside_image(c, p, r)) {
@@ -193,10 +194,10 @@ __device__ __forceinline__ void brick_flags(const FrameConst& c, const BrickSumm
         }
         const BrickSummary s = summ[b];  // read early: its latency overlaps the footprint and tile reads
         float lo[3], hi[3];
-        int bc[3] = {bx, by, bz};
+        const int v0[3] = {bx * BRICK, by * BRICK, bz * BRICK + c.zoff_g};  // global index of the brick's first voxel
         for (int a = 0; a < 3; ++a) {
-            lo[a] = c.origin[a] + ((float)(bc[a] * BRICK) - 0.5f) * c.s_g;
-            hi[a] = c.origin[a] + ((float)(bc[a] * BRICK + BRICK) + 0.5f) * c.s_g;
+            lo[a] = c.origin[a] + ((float)v0[a] - 0.5f) * c.s_g;
+            hi[a] = c.origin[a] + ((float)(v0[a] + BRICK) + 0.5f) * c.s_g;
         }
         const Footprint fp = box_footprint(c, lo, hi);
         float umin = fp.umin, umax = fp.umax, vmin = fp.vmin, vmax = fp.vmax;
@@ -206,6 +207,11 @@ __device__ __forceinline__ void brick_flags(const FrameConst& c, const BrickSumm
         if (outside_image(c, fp)) {
             vis = false;
         } else if (!straddle) {
+            // every corner is in front of the camera and the footprint lies
+            // more than a pixel inside the image: every voxel of the brick is
+            // in front and projects into the image (the geometry update then
+            // skips its per-voxel image tests)
+            inner = umin > 1.0f && vmin > 1.0f && umax < (float)c.dw - 2.0f && vmax < (float)c.dh - 2.0f;
             // clamp before converting so the integer bounds cannot overflow
             umin = fmaxf(umin, -4.0f); umax = fminf(umax, (float)c.dw + 4.0f);
             vmin = fmaxf(vmin, -4.0f); vmax = fminf(vmax, (float)c.dh + 4.0f);
@@ -254,8 +260,8 @@ __device__ __forceinline__ void brick_flags(const FrameConst& c, const BrickSumm
 // list per block (all threads of the block call it): thousands of warps
 // finishing together would otherwise queue on the two counters.
 template <int NT>
-__device__ __forceinline__ void block_append2(bool p0, bool p1, uint32_t value, uint32_t* ctr0, uint32_t* list0,
-                                              uint32_t* ctr1, uint32_t* list1) {
+__device__ __forceinline__ void block_append2(bool p0, bool p1, uint32_t value0, uint32_t value1, uint32_t* ctr0,
+                                              uint32_t* list0, uint32_t* ctr1, uint32_t* list1) {
     constexpr int NW = NT / 32;
     __shared__ uint32_t off[2][NW + 1];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -276,12 +282,13 @@ __device__ __forceinline__ void block_append2(bool p0, bool p1, uint32_t value, 
     }
     __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
-    if (p0) list0[off[0][NW] + off[0][wid] + __popc(m0 & lt)] = value;
-    if (p1) list1[off[1][NW] + off[1][wid] + __popc(m1 & lt)] = value;
+    if (p0) list0[off[0][NW] + off[0][wid] + __popc(m0 & lt)] = value0;
+    if (p1) list1[off[1][NW] + off[1][wid] + __popc(m1 & lt)] = value1;
     __syncthreads();  // off is reused by the block's next call
 }
 
 constexpr int BRICK_THREADS = 64;  // small blocks: they fit beside the band kernel's blocks on an SM
+constexpr uint32_t GEO_INNER = 0x80000000u;  // geometry-list flag: the brick projects wholly into the image
 
 __global__ void __launch_bounds__(BRICK_THREADS) k_bricks(FrameConst c, const BrickSummary* __restrict__ summ,
                                                 const uint32_t* __restrict__ tiles, Counters* __restrict__ ctr,
@@ -289,9 +296,11 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_bricks(FrameConst c, const Br
     chain_enter();
     const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
     uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
-    bool geo, vis;
-    brick_flags(c, summ, tiles, b, b < nbt, geo, vis);
-    block_append2<BRICK_THREADS>(geo, vis, b, &ctr->n_geo, geo_list, &ctr->n_vis, vis_list);
+    bool geo, vis, inner;
+    brick_flags(c, summ, tiles, b, b < nbt, geo, vis, inner);
+    // geometry list entries carry the interior flag in bit 31
+    block_append2<BRICK_THREADS>(geo, vis, b | (inner ? GEO_INNER : 0u), b, &ctr->n_geo, geo_list, &ctr->n_vis,
+                                 vis_list);
 }
 
 // ---------------------------------------------------------- geometry ----
@@ -299,88 +308,164 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_bricks(FrameConst c, const Br
 //   D = depth at the nearest pixel of the voxel centre (Eq. 6); D = 0 skipped
 //   sdf = D * 0.001 - Z; sdf < -mu skipped; (free space off: sdf > mu skipped)
 //   t = min(1, sdf * (1/mu)); F <- fmaf(F, w, t) / (w + 1); w <- min(w+1, max_w)
-// One warp per brick, taken round-robin from the list.  Lane l owns the four
-// float4 groups q = l + 32 j (j = 0..3) of the brick: voxels 4q..4q+3, i.e.
-// x in {0..3} or {4..7}, y = (l >> 1) & 7, z = (l >> 4) + 2 j.  Each group of
-// the warp is 512 contiguous bytes of F and 128 of w.  The brick's F and w are
-// requested before the projections so their latency overlaps the arithmetic.
-// The warp then writes the brick summary (min/max F over observed voxels,
-// min w, band flags).
-// TSDF update of geometry brick b by one warp (lane = lane index); adds the
-// number of updated voxels to count and 1 to changed if any voxel changed.
-template <bool PINHOLE, bool FREE_SPACE, bool ALIGNED = false>
-__device__ __forceinline__ void geometry_brick(const FrameConst& c, const Volumes& vol,
-                                               const uint16_t* __restrict__ depth, uint32_t b, int lane,
-                                               uint32_t& count, uint32_t& changed) {
+// One warp per brick.  Lane l owns the four float4 groups q = l + 32 j
+// (j = 0..3) of the brick: voxels 4q..4q+3, i.e. x in {0..3} or {4..7},
+// y = (l >> 1) & 7, z = (l >> 4) + 2 j.  Each group of the warp is 512
+// contiguous bytes of F and 128 of w.  The warp then writes the brick summary
+// (min/max F over observed voxels, min w, band flags).
+
+// Two voxels per instruction: the sm_100 paired binary32 operations
+// (__ffma2_rn, __fmul2_rn, __fadd2_rn, __fadd2_rd) round each component
+// exactly as the scalar operation does, so a pair of voxels follows the
+// per-voxel definition bit for bit while the arithmetic issues half as often.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+// Nearest depth pixel of a pair of camera points (Eq. 6: xh = fmaf(K0, X,
+// K2 Z) for a pinhole K, u = xh (1/zh), pixel floor(u + 1/2)).  The floor is
+// taken as (u + 1/2) + 2^23 rounded toward minus infinity, whose bits are
+// 0x4B000000 + floor(u + 1/2) for 0 <= u + 1/2 < 2^23 and fall outside the
+// image test for any other value (negative, huge or infinite), so the
+// integer test 0 <= floor < W is the float test 0 <= u + 1/2 < W.  INNER: the
+// caller knows every point lies in front of the camera and inside the image.
+template <bool PINHOLE, bool INNER>
+__device__ __forceinline__ void depth_pixels(const FrameConst& c, float2 X, float2 Y, float2 Z, int pix[2],
+                                             bool ok[2]) {
+    float2 xh, yh, zh;
+    if (PINHOLE) {
+        xh = __ffma2_rn(f2(c.Kd[0]), X, __fmul2_rn(f2(c.Kd[2]), Z));
+        yh = __ffma2_rn(f2(c.Kd[4]), Y, __fmul2_rn(f2(c.Kd[5]), Z));
+        zh = Z;
+    } else {
+        xh = __ffma2_rn(f2(c.Kd[0]), X, __ffma2_rn(f2(c.Kd[1]), Y, __fmul2_rn(f2(c.Kd[2]), Z)));
+        yh = __ffma2_rn(f2(c.Kd[3]), X, __ffma2_rn(f2(c.Kd[4]), Y, __fmul2_rn(f2(c.Kd[5]), Z)));
+        zh = __ffma2_rn(f2(c.Kd[6]), X, __ffma2_rn(f2(c.Kd[7]), Y, __fmul2_rn(f2(c.Kd[8]), Z)));
+    }
+    const float2 rz = rcp2_rn(zh);
+    const float2 bu = __fadd2_rd(__fadd2_rn(__fmul2_rn(xh, rz), f2(0.5f)), f2(8388608.0f));
+    const float2 bv = __fadd2_rd(__fadd2_rn(__fmul2_rn(yh, rz), f2(0.5f)), f2(8388608.0f));
+    const int iu0 = __float_as_int(bu.x) - 0x4B000000, iu1 = __float_as_int(bu.y) - 0x4B000000;
+    const int iv0 = __float_as_int(bv.x) - 0x4B000000, iv1 = __float_as_int(bv.y) - 0x4B000000;
+    if (INNER) {
+        ok[0] = ok[1] = true;
+        pix[0] = iv0 * c.dw + iu0;
+        pix[1] = iv1 * c.dw + iu1;
+    } else {
+        ok[0] = zh.x > 0.0f && (unsigned)iu0 < (unsigned)c.dw && (unsigned)iv0 < (unsigned)c.dh;
+        ok[1] = zh.y > 0.0f && (unsigned)iu1 < (unsigned)c.dw && (unsigned)iv1 < (unsigned)c.dh;
+        pix[0] = ok[0] ? iv0 * c.dw + iu0 : 0;
+        pix[1] = ok[1] ? iv1 * c.dw + iu1 : 0;
+    }
+}
+
+// Any byte of v zero (the classic word trick: a borrow reaches the byte's top
+// bit only from a zero byte).
+__device__ __forceinline__ bool any_zero_byte(uint32_t v) { return ((v - 0x01010101u) & ~v & 0x80808080u) != 0u; }
+
+// TSDF update of geometry brick b by one warp (lane = lane index) from its F
+// and w already loaded (f, wv: this lane's four groups); writes the changed
+// groups and the brick summary.  Adds the number of updated voxels to count
+// and 1 to changed if any voxel changed.
+template <bool PINHOLE, bool FREE_SPACE, bool ALIGNED, bool INNER>
+__device__ __forceinline__ void geometry_update(const FrameConst& c, const Volumes& vol,
+                                                const uint16_t* __restrict__ depth, const float* rcp, uint32_t b,
+                                                int lane, const float4 (&f)[4], const uint32_t (&wv)[4],
+                                                uint32_t& count, uint32_t& changed) {
     const int lx = (lane & 1) * 4, ly = (lane >> 1) & 7, lz = lane >> 4;
     const int bx = b % c.nb[0], by = (b / c.nb[0]) % c.nb[1], bz = b / (c.nb[0] * c.nb[1]);
     float* Fb = vol.F + (size_t)b * BRICK_VOX + lane * 4;
     uint8_t* Wb = vol.W + (size_t)b * BRICK_VOX + lane * 4;
-    float4 f[4];
-    uint32_t wv[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        f[j] = *reinterpret_cast<const float4*>(Fb + 128 * j);
-        wv[j] = *reinterpret_cast<const uint32_t*>(Wb + 128 * j);
-    }
     const int gx0 = bx * BRICK + lx, gy = by * BRICK + ly;
     const bool yin = gy < c.ng[1];
     const float py = fmaf((float)gy + 0.5f, c.s_g, c.origin[1]);
     float px[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) px[i] = fmaf((float)(gx0 + i) + 0.5f, c.s_g, c.origin[0]);
+    const float2 pxp[2] = {make_float2(px[0], px[1]), make_float2(px[2], px[3])};
+    const uint32_t maxw = (uint32_t)c.max_weight, maxw4 = maxw * 0x01010101u;
     // min / max of F over this lane's observed voxels: all of them, and those
-    // on the brick faces x = lx + {0, 3} and z = lz + {0, 6} (band flags)
-    float fmn = FLT_MAX, fmx = -FLT_MAX;
-    float mn_x0 = FLT_MAX, mx_x0 = -FLT_MAX, mn_x3 = FLT_MAX, mx_x3 = -FLT_MAX;
-    float mn_z0 = FLT_MAX, mx_z0 = -FLT_MAX, mn_z3 = FLT_MAX, mx_z3 = -FLT_MAX;
-    uint32_t wmn = 0xFFFFFFFFu, nupd = 0;
-    // Straight-line code per voxel: a voxel outside the volume or the image
-    // reads depth pixel 0 and is masked, so every depth fetch is unconditional
-    // and the compiler can issue them together.
+    // on the brick faces (band flags): this lane's x face is its voxel i = 0
+    // (lx = 0, the -x face) or i = 3 (lx = 4, +x), its z face its group j = 0
+    // (lz = 0, -z) or j = 3 (lz = 1, +z).  An unobserved voxel enters as NaN,
+    // which fminf / fmaxf pass over.
+    const float qnan = __int_as_float(0x7fffffff);
+    float fmn = FLT_MAX, fmx = -FLT_MAX, mn_xf = FLT_MAX, mx_xf = -FLT_MAX, mn_zf = FLT_MAX, mx_zf = -FLT_MAX;
+    bool unobserved = false, below_cap = false;  // after the update, over this lane's in-volume voxels
+    uint32_t nupd = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int gz = bz * BRICK + lz + 2 * j;
         const bool zin = yin && gz < c.ng[2];
-        const float pz = fmaf((float)gz + 0.5f, c.s_g, c.origin[2]);
-        const float B0 = fmaf(c.R[1], py, fmaf(c.R[2], pz, c.t[0]));
-        const float B1 = fmaf(c.R[4], py, fmaf(c.R[5], pz, c.t[1]));
-        const float B2 = fmaf(c.R[7], py, fmaf(c.R[8], pz, c.t[2]));
-        float fv[4] = {f[j].x, f[j].y, f[j].z, f[j].w};
-        uint32_t wn = wv[j];
-        bool gupd = false;
+        const float pz = fmaf((float)(gz + c.zoff_g) + 0.5f, c.s_g, c.origin[2]);  // centre at the global index
+        const float2 B0 = f2(fmaf(c.R[1], py, fmaf(c.R[2], pz, c.t[0])));
+        const float2 B1 = f2(fmaf(c.R[4], py, fmaf(c.R[5], pz, c.t[1])));
+        const float2 B2 = f2(fmaf(c.R[7], py, fmaf(c.R[8], pz, c.t[2])));
+        const float fin[4] = {f[j].x, f[j].y, f[j].z, f[j].w};
+        float fv[4], fo[4];
+        const uint32_t w_old = wv[j];
+        uint32_t inc = 0, upm = 0, inside = 0xFFFFFFFFu;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const bool valid = ALIGNED || (zin && gx0 + i < c.ng[0]);  // ALIGNED: dims are multiples of 8
-            const float X = fmaf(c.R[0], px[i], B0), Y = fmaf(c.R[3], px[i], B1), Z = fmaf(c.R[6], px[i], B2);
-            int pix;
-            const bool seen = project_pixel(c.Kd, PINHOLE, X, Y, Z, c.dw, c.dh, pix) && valid;
-            uint32_t D = __ldg(depth + (seen ? pix : 0));
-            D = seen ? D : 0u;
-            const float d = (float)D * 0.001f;
-            const float sdf = d - Z;
-            const bool up = D != 0u && !(sdf < -c.mu) && (FREE_SPACE || !(sdf > c.mu));
-            uint32_t w = (wn >> (8 * i)) & 0xFFu;
-            if (up) {
-                const float t = fminf(1.0f, sdf * c.inv_mu);
-                const float wf = (float)w;
-                fv[i] = __fdiv_rn(fmaf(fv[i], wf, t), wf + 1.0f);
-                w = min(w + 1u, (uint32_t)c.max_weight);
-                wn = (wn & ~(0xFFu << (8 * i))) | (w << (8 * i));
+        for (int h = 0; h < 2; ++h) {  // voxel pair i = 2h, 2h + 1
+            const float2 X = __ffma2_rn(f2(c.R[0]), pxp[h], B0);
+            const float2 Y = __ffma2_rn(f2(c.R[3]), pxp[h], B1);
+            const float2 Z = __ffma2_rn(f2(c.R[6]), pxp[h], B2);
+            int pix[2];
+            bool ok[2];
+            depth_pixels<PINHOLE, INNER>(c, X, Y, Z, pix, ok);
+            bool seen[2];
+            uint32_t D[2], w[2];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int i = 2 * h + k;
+                const bool valid = ALIGNED || (zin && gx0 + i < c.ng[0]);  // ALIGNED: dims are multiples of 8
+                if (!valid) inside &= ~(0xFFu << (8 * i));
+                seen[k] = ok[k] && valid;
+                D[k] = __ldg(depth + pix[k]);  // pixel 0 when not seen: read, then ignored
+                w[k] = (w_old >> (8 * i)) & 0xFFu;
             }
-            gupd |= up;
-            nupd += up ? 1u : 0u;
-            wmn = min(wmn, valid ? w : 0xFFFFFFFFu);
-            const bool obs = valid && w != 0u;
-            const float fl = obs ? fv[i] : FLT_MAX, fh = obs ? fv[i] : -FLT_MAX;
-            fmn = fminf(fmn, fl);
-            fmx = fmaxf(fmx, fh);
-            if (i == 0) { mn_x0 = fminf(mn_x0, fl); mx_x0 = fmaxf(mx_x0, fh); }
-            if (i == 3) { mn_x3 = fminf(mn_x3, fl); mx_x3 = fmaxf(mx_x3, fh); }
-            if (j == 0) { mn_z0 = fminf(mn_z0, fl); mx_z0 = fmaxf(mx_z0, fh); }
-            if (j == 3) { mn_z3 = fminf(mn_z3, fl); mx_z3 = fmaxf(mx_z3, fh); }
+            const float2 d = __fmul2_rn(make_float2((float)D[0], (float)D[1]), f2(0.001f));
+            const float2 sdf = __ffma2_rn(Z, f2(-1.0f), d);  // d - Z, rounded once
+            const float2 tq = __fmul2_rn(sdf, f2(c.inv_mu));
+            const float2 t = make_float2(fminf(1.0f, tq.x), fminf(1.0f, tq.y));
+            const float2 wf = make_float2((float)w[0], (float)w[1]);
+            // F <- fmaf(F, w, t) / (w + 1), the quotient by div_by_weight's steps
+            const float2 a = __ffma2_rn(make_float2(fin[2 * h], fin[2 * h + 1]), wf, t);
+            const float2 nb = __ffma2_rn(wf, f2(-1.0f), f2(-1.0f));  // -(w + 1), exact
+            const float2 y = make_float2(rcp[w[0]], rcp[w[1]]);
+            const float2 q = __fmul2_rn(a, y);
+            const float2 r = __ffma2_rn(nb, q, a);
+            const float2 fn = __ffma2_rn(r, y, q);
+            const float sd[2] = {sdf.x, sdf.y}, fnew[2] = {fn.x, fn.y};
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int i = 2 * h + k;
+                const bool up = seen[k] && D[k] != 0u && !(sd[k] < -c.mu) && (FREE_SPACE || !(sd[k] > c.mu));
+                fv[i] = up ? fnew[k] : fin[i];
+                // w <- min(w + 1, max_weight): a byte below the cap gains 1 (no carry)
+                inc |= up && w[k] < maxw ? 1u << (8 * i) : 0u;
+                upm |= up ? 1u << i : 0u;
+                const bool valid = ALIGNED || (zin && gx0 + i < c.ng[0]);
+                fo[i] = (up || w[k] != 0u) && valid ? fv[i] : qnan;  // observed after the update
+            }
         }
-        if (gupd) {
+        const uint32_t wn = w_old + inc;
+        // in-volume voxels only: a byte outside the volume reads as observed and at the cap
+        const uint32_t wq = ALIGNED ? wn : (wn & inside) | (maxw4 & ~inside);
+        unobserved = unobserved || any_zero_byte(wq);
+        below_cap = below_cap || wq != maxw4;
+        const float gmn = fminf(fminf(fo[0], fo[1]), fminf(fo[2], fo[3]));
+        const float gmx = fmaxf(fmaxf(fo[0], fo[1]), fmaxf(fo[2], fo[3]));
+        fmn = fminf(fmn, gmn);
+        fmx = fmaxf(fmx, gmx);
+        // this lane's x-face voxel of the group, and its z-face group
+        const float fx = lx == 0 ? fo[0] : fo[3];
+        mn_xf = fminf(mn_xf, fx);
+        mx_xf = fmaxf(mx_xf, fx);
+        if ((j == 0 && lz == 0) || (j == 3 && lz == 1)) {
+            mn_zf = gmn;
+            mx_zf = gmx;
+        }
+        nupd += __popc(upm);
+        if (upm) {
             *reinterpret_cast<float4*>(Fb + 128 * j) = make_float4(fv[0], fv[1], fv[2], fv[3]);
             *reinterpret_cast<uint32_t*>(Wb + 128 * j) = wn;
         }
@@ -390,37 +475,57 @@ __device__ __forceinline__ void geometry_brick(const FrameConst& c, const Volume
     if (!__any_sync(0xffffffffu, nupd != 0u)) return;
     ++changed;
     // band flags (see BrickSummary): this lane's voxels sit at x = lx + i,
-    // y = ly, z = lz + 2 j, so it holds the -x face when lx = 0 (i = 0), +x
-    // when lx = 4 (i = 3), -y / +y when ly = 0 / 7, -z when lz = 0 (j = 0)
-    // and +z when lz = 1 (j = 3)
+    // y = ly, z = lz + 2 j, so it holds the -x face when lx = 0, +x when
+    // lx = 4, -y / +y when ly = 0 / 7, -z when lz = 0 and +z when lz = 1
     const float lo_thr = c.band + CELL_EPS, hi_thr = -c.band - CELL_EPS;
     auto lohi = [&](bool on, float mn, float mx) -> uint32_t {
         return on ? (mn <= lo_thr ? 1u : 0u) | (mx >= hi_thr ? 2u : 0u) : 0u;
     };
-    uint32_t bflags = lohi(true, fmn, fmx) | lohi(lx == 0, mn_x0, mx_x0) << 2 | lohi(lx == 4, mn_x3, mx_x3) << 4 |
-                      lohi(ly == 0, fmn, fmx) << 6 | lohi(ly == 7, fmn, fmx) << 8 |
-                      lohi(lz == 0, mn_z0, mx_z0) << 10 | lohi(lz == 1, mn_z3, mx_z3) << 12;
+    const uint32_t xf = lohi(true, mn_xf, mx_xf), zf = lohi(true, mn_zf, mx_zf);
+    uint32_t bflags = lohi(true, fmn, fmx) | (lx == 0 ? xf << 2 : xf << 4) | lohi(ly == 0, fmn, fmx) << 6 |
+                      lohi(ly == 7, fmn, fmx) << 8 | (lz == 0 ? zf << 10 : zf << 12);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         fmn = fminf(fmn, __shfl_xor_sync(0xffffffffu, fmn, o));
         fmx = fmaxf(fmx, __shfl_xor_sync(0xffffffffu, fmx, o));
     }
-    wmn = __reduce_min_sync(0xffffffffu, wmn);
+    unobserved = __any_sync(0xffffffffu, unobserved);
+    below_cap = __any_sync(0xffffffffu, below_cap);
     bflags = __reduce_or_sync(0xffffffffu, bflags);
     if (lane == 0) {
         BrickSummary sm;
         sm.fmin = fmn == FLT_MAX ? __int_as_float(0x7f800000) : fmn;
         sm.fmax = fmx == -FLT_MAX ? __int_as_float(0xff800000) : fmx;
-        sm.wmin = wmn == 0xFFFFFFFFu ? 0u : wmn;
+        sm.wmin = unobserved ? 0u : (below_cap ? maxw - 1u : maxw);
         sm.flags = bflags;
         vol.summ[b] = sm;
     }
 }
 
+// The same with F and w read from the volume.
+template <bool PINHOLE, bool FREE_SPACE, bool ALIGNED = false, bool INNER = false>
+__device__ __forceinline__ void geometry_brick(const FrameConst& c, const Volumes& vol,
+                                               const uint16_t* __restrict__ depth, const float* rcp, uint32_t b,
+                                               int lane, uint32_t& count, uint32_t& changed) {
+    const float* Fb = vol.F + (size_t)b * BRICK_VOX + lane * 4;
+    const uint8_t* Wb = vol.W + (size_t)b * BRICK_VOX + lane * 4;
+    float4 f[4];
+    uint32_t wv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        f[j] = *reinterpret_cast<const float4*>(Fb + 128 * j);
+        wv[j] = *reinterpret_cast<const uint32_t*>(Wb + 128 * j);
+    }
+    geometry_update<PINHOLE, FREE_SPACE, ALIGNED, INNER>(c, vol, depth, rcp, b, lane, f, wv, count, changed);
+}
+
 template <bool PINHOLE, bool FREE_SPACE, bool ALIGNED>
-__global__ void __launch_bounds__(GEO_THREADS, 7) k_geometry(FrameConst c, Volumes vol, const uint16_t* __restrict__ depth,
+__global__ void __launch_bounds__(GEO_THREADS, 8) k_geometry(FrameConst c, Volumes vol, const uint16_t* __restrict__ depth,
                                                           Counters* __restrict__ ctr,
                                                           const uint32_t* __restrict__ list) {
+    __shared__ float rcp[256];
+    fill_weight_reciprocals(rcp);
+    __syncthreads();
     chain_enter();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         // fold the previous frame's colour-side counters into the running totals
@@ -440,8 +545,14 @@ __global__ void __launch_bounds__(GEO_THREADS, 7) k_geometry(FrameConst c, Volum
     // the list is taken from its end: the colour kernels that follow walk
     // their lists from the front, whose bricks are then the ones this kernel
     // wrote last (measured: 1 % off the frame)
-    for (uint32_t item = warp; item < n; item += nwarps)
-        geometry_brick<PINHOLE, FREE_SPACE, ALIGNED>(c, vol, depth, list[n - 1u - item], lane, count, changed);
+    for (uint32_t item = warp; item < n; item += nwarps) {
+        const uint32_t e = list[n - 1u - item];
+        if (e & GEO_INNER)  // the brick projects wholly into the image: no per-voxel image tests
+            geometry_brick<PINHOLE, FREE_SPACE, ALIGNED, true>(c, vol, depth, rcp, e & ~GEO_INNER, lane, count,
+                                                               changed);
+        else
+            geometry_brick<PINHOLE, FREE_SPACE, ALIGNED>(c, vol, depth, rcp, e, lane, count, changed);
+    }
     count = __reduce_add_sync(0xffffffffu, count);
     if (lane == 0 && count) atomicAdd(&ctr->geo_updated, (unsigned long long)count);
     if (lane == 0 && changed) atomicAdd(&ctr->n_geo_changed, changed);
@@ -545,7 +656,7 @@ __global__ void __launch_bounds__(LIST_THREADS) k_colour_list(FrameConst c, cons
         const uint32_t in = i + gridDim.x * blockDim.x;
         b_next = in < n ? vis_list[in] : 0u;
         const bool act = i < n && colour_candidate(c, summ, b);
-        block_append2<LIST_THREADS>(act, false, b, &ctr->n_col, col_list, nullptr, nullptr);
+        block_append2<LIST_THREADS>(act, false, b, b, &ctr->n_col, col_list, nullptr, nullptr);
     }
 }
 
@@ -629,7 +740,7 @@ __device__ __forceinline__ bool colour_after_band(const FrameConst& c, uint32_t*
                                                   int kx, int ky, int kz) {
     const float pwx = fmaf((float)kx + 0.5f, c.s_c, c.origin[0]);
     const float pwy = fmaf((float)ky + 0.5f, c.s_c, c.origin[1]);
-    const float pwz = fmaf((float)kz + 0.5f, c.s_c, c.origin[2]);
+    const float pwz = fmaf((float)(kz + c.zoff_c) + 0.5f, c.s_c, c.origin[2]);  // global index on a z-slab
     float X, Y, Z;
     rigid(c.R, c.t, pwx, pwy, pwz, X, Y, Z);
     float u, v;
@@ -1279,10 +1390,12 @@ __device__ __forceinline__ int find_scan(const uint32_t* pre, int n, uint32_t it
 }
 
 __global__ void __launch_bounds__(COL_THREADS, 4) k_batch_step(const ScanDesc* __restrict__ descs, int n,
-                                                            BatchSync* sync) {
+                                                            BatchSync* sync, int tile) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ColourSlot& S = reinterpret_cast<ColourSlot*>(smem_raw)[threadIdx.x >> 5];
     __shared__ uint32_t pre[MAX_BATCH + 1];
+    __shared__ float rcp[256];
+    fill_weight_reciprocals(rcp);  // read after the first grid barrier's __syncthreads
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1336,28 +1449,31 @@ __global__ void __launch_bounds__(COL_THREADS, 4) k_batch_step(const ScanDesc* _
         const ScanDesc& d = descs[s];
         const uint32_t b = item - pre[s];
         const uint32_t nbt = (uint32_t)d.c.nb[0] * d.c.nb[1] * d.c.nb[2];
-        bool geo, vis;
-        brick_flags(d.c, d.vol.summ, d.scr.depth_tiles, b, b < nbt, geo, vis);
-        append(geo, b, &d.scr.ctr->n_geo, d.scr.geo_list);
+        bool geo, vis, inner;
+        brick_flags(d.c, d.vol.summ, d.scr.depth_tiles, b, b < nbt, geo, vis, inner);
+        append(geo, b | (inner ? GEO_INNER : 0u), &d.scr.ctr->n_geo, d.scr.geo_list);
         append(vis, b, &d.scr.ctr->n_vis, d.scr.vis_list);
     }
     if (!grid_barrier(sync, gridDim.x)) return;
 
-    // P2: geometry, one warp per listed brick
-    scan_prefix(pre, n, 1, [&](int i) { return descs[i].scr.ctr->n_geo; });
+    // P2: geometry, one warp per tile of `tile` consecutive listed bricks of a scan
+    scan_prefix(pre, n, 1, [&](int i) { return (descs[i].scr.ctr->n_geo + tile - 1) / tile; });
     for (uint32_t item = warp; item < pre[n]; item += nwarps) {
         const int s = find_scan(pre, n, item);
         const ScanDesc& d = descs[s];
-        const uint32_t b = d.scr.geo_list[item - pre[s]];
+        const uint32_t k0 = (item - pre[s]) * tile, k1 = min(k0 + (uint32_t)tile, d.scr.ctr->n_geo);
         uint32_t count = 0, changed = 0;
-        if (d.c.kd_pinhole && d.c.free_space)
-            geometry_brick<true, true>(d.c, d.vol, d.depth, b, lane, count, changed);
-        else if (d.c.kd_pinhole)
-            geometry_brick<true, false>(d.c, d.vol, d.depth, b, lane, count, changed);
-        else if (d.c.free_space)
-            geometry_brick<false, true>(d.c, d.vol, d.depth, b, lane, count, changed);
-        else
-            geometry_brick<false, false>(d.c, d.vol, d.depth, b, lane, count, changed);
+        for (uint32_t k = k0; k < k1; ++k) {
+            const uint32_t b = d.scr.geo_list[k] & ~GEO_INNER;  // the general form handles every brick
+            if (d.c.kd_pinhole && d.c.free_space)
+                geometry_brick<true, true>(d.c, d.vol, d.depth, rcp, b, lane, count, changed);
+            else if (d.c.kd_pinhole)
+                geometry_brick<true, false>(d.c, d.vol, d.depth, rcp, b, lane, count, changed);
+            else if (d.c.free_space)
+                geometry_brick<false, true>(d.c, d.vol, d.depth, rcp, b, lane, count, changed);
+            else
+                geometry_brick<false, false>(d.c, d.vol, d.depth, rcp, b, lane, count, changed);
+        }
         count = __reduce_add_sync(full, count);
         if (lane == 0) {
             if (count) atomicAdd(&d.scr.ctr->geo_updated, (unsigned long long)count);
@@ -1379,8 +1495,8 @@ __global__ void __launch_bounds__(COL_THREADS, 4) k_batch_step(const ScanDesc* _
     }
     if (!grid_barrier(sync, gridDim.x)) return;
 
-    // P4: band gate, one warp per candidate, taken with an atomic counter
-    scan_prefix(pre, n, 1, [&](int i) { return descs[i].scr.ctr->n_col; });
+    // P4: band gate, one warp per tile of candidates, taken with an atomic counter
+    scan_prefix(pre, n, 1, [&](int i) { return (descs[i].scr.ctr->n_col + tile - 1) / tile; });
     for (;;) {
         uint32_t item = 0;
         if (lane == 0) item = atomicAdd(&sync->band_next, 1u);
@@ -1389,8 +1505,11 @@ __global__ void __launch_bounds__(COL_THREADS, 4) k_batch_step(const ScanDesc* _
         const int s = find_scan(pre, n, item);
         const ScanDesc& d = descs[s];
         uint32_t count = 0, n_active = 0, n_cells = 0;
-        band_brick(d.c, d.vol, d.depth, d.rgb, d.scr, S, d.scr.col_list[item - pre[s]], lane, count, n_active, n_cells);
-        __syncwarp();
+        const uint32_t k0 = (item - pre[s]) * tile, k1 = min(k0 + (uint32_t)tile, d.scr.ctr->n_col);
+        for (uint32_t k = k0; k < k1; ++k) {
+            band_brick(d.c, d.vol, d.depth, d.rgb, d.scr, S, d.scr.col_list[k], lane, count, n_active, n_cells);
+            __syncwarp();
+        }
         count = __reduce_add_sync(full, count);
         if (lane == 0) {
             if (count) atomicAdd(&d.scr.ctr->col_updated, (unsigned long long)count);
@@ -1555,7 +1674,7 @@ int batch_blocks_per_sm() {
     return n > 0 ? n : 1;
 }
 
-cudaError_t launch_batch_step(const ScanDesc* descs, int n, BatchSync* sync, int grid, cudaStream_t stream) {
+cudaError_t launch_batch_step(const ScanDesc* descs, int n, BatchSync* sync, int grid, int tile, cudaStream_t stream) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(COL_THREADS);
@@ -1566,7 +1685,7 @@ cudaError_t launch_batch_step(const ScanDesc* descs, int n, BatchSync* sync, int
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_batch_step, descs, n, sync);
+    return cudaLaunchKernelEx(&cfg, k_batch_step, descs, n, sync, tile);
 }
 
 }  // namespace tsdf

@@ -1,7 +1,8 @@
-// Mesh extraction from the geometry volume and per-polygon texture maps from
-// the colour volume (Section IV.C-D, Eq. 11-14).  Definitions (operation
-// order, tetrahedra, orientation, map layout) as stated in tsdf.h; compiled
-// with --fmad=false so only the written fmaf() fuse.
+// Mesh extraction from the geometry volume (marching cubes, or marching
+// tetrahedra as an option) and per-polygon texture maps from the colour
+// volume (Section IV.C-D, Eq. 11-14).  Definitions (operation order, cases,
+// orientation, map layout) as stated in tsdf.h; compiled with --fmad=false so
+// only the written fmaf() fuse.
 #include <cfloat>
 #include <cstdint>
 
@@ -25,6 +26,19 @@ __device__ __forceinline__ void tet_corners(int t, int c[4]) {
     c[1] = 1 << a0;
     c[2] = c[1] | (1 << a1);
     c[3] = 7;
+}
+
+// Marching-cubes case table (built on the host from the rules in tsdf.h):
+// entry m, for the mask m of inside corners, holds the triangle count and
+// then three cell-edge numbers per triangle.
+__constant__ uint8_t c_cube_cases[256][16];
+
+// Lower and upper corner of cell edge e = 4 a + r: the lower corner is r with
+// a zero bit inserted at position a.
+__device__ __forceinline__ void cube_edge_corners(int e, int& p, int& q) {
+    const int a = e >> 2, r = e & 3;
+    p = a == 0 ? r << 1 : (a == 1 ? (r & 1) | ((r & 2) << 1) : r);
+    q = p | (1 << a);
 }
 
 // ------------------------------------------------------- candidate bricks --
@@ -150,6 +164,32 @@ __device__ void cell_emit(const MeshConst& c, const int base[3], const float Fc[
     }
 }
 
+// Marching cubes: the triangles of one cell from the case table.
+__device__ __forceinline__ int cube_count(const float Fc[8]) {
+    int m = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) m |= Fc[k] < 0.0f ? 1 << k : 0;
+    return c_cube_cases[m][0];
+}
+
+__device__ void cube_emit(const MeshConst& c, const int base[3], const float Fc[8], float* __restrict__ out,
+                          uint64_t slot, uint64_t cap) {
+    int m = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) m |= Fc[k] < 0.0f ? 1 << k : 0;
+    const int n = c_cube_cases[m][0];
+    for (int t = 0; t < n; ++t, ++slot) {
+        if (slot >= cap) continue;
+        float* dst = out + 9 * slot;
+        for (int k = 0; k < 3; ++k) {
+            int p, q;
+            cube_edge_corners(c_cube_cases[m][1 + 3 * t + k], p, q);
+            edge_vertex(c, base, Fc, p, q, dst + 3 * k);
+        }
+    }
+}
+
+template <bool CUBES>
 __global__ void __launch_bounds__(MESH_THREADS) k_mesh(MeshConst c, const float* __restrict__ F,
                                                       const uint8_t* __restrict__ W,
                                                       const uint32_t* __restrict__ list,
@@ -192,7 +232,7 @@ __global__ void __launch_bounds__(MESH_THREADS) k_mesh(MeshConst c, const float*
                 Fc[k] = S.F[i];
                 obs = obs && S.W[i] != 0;
             }
-            const uint32_t m = obs ? (uint32_t)cell_count(Fc) : 0u;
+            const uint32_t m = obs ? (uint32_t)(CUBES ? cube_count(Fc) : cell_count(Fc)) : 0u;
             uint32_t incl = m;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -204,7 +244,10 @@ __global__ void __launch_bounds__(MESH_THREADS) k_mesh(MeshConst c, const float*
             unsigned long long wbase = 0;
             if (lane == 0) wbase = atomicAdd(count, (unsigned long long)total);
             wbase = __shfl_sync(0xffffffffu, wbase, 0);
-            if (m) cell_emit(c, base, Fc, out, wbase + incl - m, cap);
+            if (m) {
+                if (CUBES) cube_emit(c, base, Fc, out, wbase + incl - m, cap);
+                else cell_emit(c, base, Fc, out, wbase + incl - m, cap);
+            }
         }
         __syncwarp();
     }
@@ -365,16 +408,27 @@ __global__ void __launch_bounds__(256) k_tex_fill(ColourConst c, const uint32_t*
 
 }  // namespace
 
+cudaError_t upload_cube_cases(const uint8_t (*table)[16], cudaStream_t stream) {
+    return cudaMemcpyToSymbolAsync(c_cube_cases, table, sizeof(c_cube_cases), 0, cudaMemcpyHostToDevice, stream);
+}
+
 cudaError_t launch_mesh(const MeshConst& c, const float* F, const uint8_t* W, const BrickSummary* summ,
                         uint32_t* list, uint32_t* n_list, float* out, uint64_t cap, unsigned long long* count,
-                        cudaStream_t stream) {
+                        bool cubes, cudaStream_t stream) {
     const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
     k_mesh_bricks<<<(nbt + 255) / 256, 256, 0, stream>>>(c, summ, list, n_list);
     int sms = 0, dev = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mesh, MESH_THREADS, 0);
-    k_mesh<<<max(1, sms * max(1, per_sm)), MESH_THREADS, 0, stream>>>(c, F, W, list, n_list, out, cap, count);
+    if (cubes) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mesh<true>, MESH_THREADS, 0);
+        k_mesh<true><<<max(1, sms * max(1, per_sm)), MESH_THREADS, 0, stream>>>(c, F, W, list, n_list, out, cap,
+                                                                               count);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mesh<false>, MESH_THREADS, 0);
+        k_mesh<false><<<max(1, sms * max(1, per_sm)), MESH_THREADS, 0, stream>>>(c, F, W, list, n_list, out, cap,
+                                                                                count);
+    }
     return cudaGetLastError();
 }
 

@@ -71,6 +71,7 @@ extern "C" {
 tsdf_status tsdf_adjoint_create(tsdf_volume* vol, int32_t max_frames, int64_t max_pairs, tsdf_adjoint** out) {
     if (!vol || !out || max_frames < 1 || max_frames > 64 || max_pairs < 1 || max_pairs > (int64_t(1) << 31))
         return TSDF_ERR_INVALID_ARG;
+    if (vol->zoff_g != 0 || vol->ng[2] != vol->ngz_all) return TSDF_ERR_INVALID_ARG;  // whole volumes only
     *out = nullptr;
     tsdf_info info;
     tsdf_get_info(vol, &info);

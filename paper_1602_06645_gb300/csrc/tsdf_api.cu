@@ -87,6 +87,13 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Translation within MAX_COORD metres.
+bool translation_ok(const float T[16]) {
+    for (int i = 0; i < 3; ++i)
+        if (!(std::fabs(T[i * 4 + 3]) <= MAX_COORD)) return false;
+    return true;
+}
+
 // Rigid transform check: finite, bottom row (0, 0, 0, 1), |R^T R - I| <= 1e-4.
 bool rigid_ok(const float T[16]) {
     if (!finite_all(T, 16)) return false;
@@ -142,6 +149,8 @@ void frame_constants(const tsdf_volume* v, const float Kd[9], const float Kr[9],
         c.nb[a] = v->nb[a];
         c.ncb[a] = v->ncb[a];
     }
+    c.zoff_g = v->zoff_g;
+    c.zoff_c = v->zoff_c;
     c.s_g = v->s_g;
     c.s_c = v->s_c;
     c.inv_sg = 1.0f / v->s_g;
@@ -269,7 +278,7 @@ namespace tsdf {
 // fields are unused on that path).
 void geometry_frame_constants(const VolumeDesc& d, const float Kd[9], const float Twd[16], int dw, int dh,
                               FrameConst& c) {
-    tsdf_volume v;
+    tsdf_volume v{};
     for (int a = 0; a < 3; ++a) {
         v.ng[a] = d.ng[a];
         v.nc[a] = d.ng[a];
@@ -331,23 +340,28 @@ const char* tsdf_last_error(const tsdf_volume* v) { return v ? v->last_error.c_s
 static tsdf_status build_axis_tables(tsdf_volume* v) {
     const float inv_sg = 1.0f / v->s_g;
     for (int a = 0; a < 3; ++a) {
-        const int nc = v->nc[a], ng = v->ng[a], nb = v->nb[a];
+        const int nc = v->nc[a], nb = v->nb[a];
+        // the ratio is the whole volume's; on a z-slab handle the z indices are
+        // offset by the slab's global index of held voxel 0
+        const long long NG = a == 2 ? v->ngz_all : v->ng[a], NC = a == 2 ? v->ncz_all : v->nc[a];
+        const long long zg = a == 2 ? v->zoff_g : 0, zc = a == 2 ? v->zoff_c : 0;
         std::vector<float> frac(nc);
         std::vector<int8_t> cell(nc);
         std::vector<int32_t> k0(nb + 1);
         std::vector<uint16_t> span((size_t)nb * 9, 0);
         for (int bb = 0; bb <= nb; ++bb) {
-            const long long num = 16ll * bb * nc - ng;  // smallest k with (2k + 1) ng >= 16 bb nc
-            const long long k = num <= 0 ? 0 : (num + 2ll * ng - 1) / (2ll * ng);
-            k0[bb] = (int32_t)std::min<long long>(nc, k);
+            // smallest global K with (2K + 1) NG >= 2 (8 bb + zg) NC, as a held index
+            const long long num = 2ll * (8ll * bb + zg) * NC - NG;
+            const long long K = num <= 0 ? 0 : (num + 2ll * NG - 1) / (2ll * NG);
+            k0[bb] = (int32_t)std::min<long long>(nc, std::max<long long>(0, K - zc));
         }
         for (int bb = 0; bb < nb; ++bb) {
             const int ta = bb * BRICK - 1;
             for (int k = k0[bb]; k < k0[bb + 1]; ++k) {
-                const float p = std::fmaf((float)k + 0.5f, v->s_c, v->origin[a]);
+                const float p = std::fmaf((float)(k + zc) + 0.5f, v->s_c, v->origin[a]);
                 const float g = std::fmaf(p - v->origin[a], inv_sg, -0.5f);
                 const float i0 = std::floor(g);
-                const int rel = (int)i0 - ta;
+                const int rel = (int)i0 - (int)zg - ta;
                 if (rel < 0 || rel > BRICK) return fail(v, TSDF_ERR_INVALID_ARG, "colour grid does not fit the bricks");
                 frac[k] = g - i0;
                 cell[k] = (int8_t)rel;
@@ -402,6 +416,12 @@ tsdf_status tsdf_create_ex(const int32_t dims_geo[3], const int32_t dims_col[3],
         if ((int64_t)dims_col[a] * dims_geo[0] != (int64_t)dims_col[0] * dims_geo[a]) return TSDF_ERR_INVALID_ARG;
         if (dims_col[a] > 8 * dims_geo[a]) return TSDF_ERR_INVALID_ARG;  // colour/geometry ratio <= 8
     }
+    // z-slab: [z0, z1) of the geometry, cut at whole colour voxels
+    const bool slab = p.slab_z[0] != 0 || p.slab_z[1] != 0;
+    const int32_t z0 = slab ? p.slab_z[0] : 0, z1 = slab ? p.slab_z[1] : dims_geo[2];
+    if (slab && (z0 < 0 || z1 <= z0 || z1 > dims_geo[2] || ((int64_t)z0 * dims_col[2]) % dims_geo[2] != 0 ||
+                 ((int64_t)z1 * dims_col[2]) % dims_geo[2] != 0))
+        return TSDF_ERR_INVALID_ARG;
     if (!(voxel_size > 0.0f) || !std::isfinite(voxel_size) || !(mu > 0.0f) || !std::isfinite(mu))
         return TSDF_ERR_INVALID_ARG;
     if (max_weight < 1 || max_weight > 255) return TSDF_ERR_INVALID_ARG;
@@ -416,17 +436,37 @@ tsdf_status tsdf_create_ex(const int32_t dims_geo[3], const int32_t dims_col[3],
         delete v;
         return TSDF_ERR_INVALID_ARG;
     }
+    v->ngz_all = dims_geo[2];
+    v->ncz_all = dims_col[2];
+    v->slab_z0 = z0;
+    v->slab_z1 = z1;
+    // held z ranges: the slab's colour slice and its geometry widened by the
+    // voxel on each side that the band gate's trilinear corners reach
+    v->zoff_g = slab ? std::max(0, z0 - 1) : 0;
+    v->zoff_c = (int32_t)((int64_t)z0 * dims_col[2] / dims_geo[2]);
     for (int a = 0; a < 3; ++a) {
         v->ng[a] = dims_geo[a];
         v->nc[a] = dims_col[a];
-        v->nb[a] = (dims_geo[a] + BRICK - 1) / BRICK;
-        v->ncb[a] = (dims_col[a] + BRICK - 1) / BRICK;
+    }
+    if (slab) {
+        v->ng[2] = std::min(dims_geo[2], z1 + 1) - v->zoff_g;
+        v->nc[2] = (int32_t)((int64_t)z1 * dims_col[2] / dims_geo[2]) - v->zoff_c;
+    }
+    for (int a = 0; a < 3; ++a) {
+        v->nb[a] = (v->ng[a] + BRICK - 1) / BRICK;
+        v->ncb[a] = (v->nc[a] + BRICK - 1) / BRICK;
     }
     v->s_g = voxel_size;
     v->s_c = (float)((double)dims_geo[0] * (double)voxel_size / (double)dims_col[0]);
     for (int a = 0; a < 3; ++a)
         v->origin[a] = std::isnan(p.origin[a]) ? (float)(-0.5 * (double)dims_geo[a] * (double)voxel_size) : p.origin[a];
-    if (!finite_all(v->origin, 3)) {
+    // the volumes must lie within 10^6 m of the world origin (every voxel's
+    // camera depth then stays far inside the range where the projection's
+    // reciprocal is exact)
+    bool bounded = finite_all(v->origin, 3);
+    for (int a = 0; a < 3 && bounded; ++a)
+        bounded = std::fabs((double)v->origin[a]) + (double)dims_geo[a] * (double)voxel_size <= MAX_COORD;
+    if (!bounded) {
         delete v;
         return TSDF_ERR_INVALID_ARG;
     }
@@ -568,6 +608,8 @@ tsdf_status tsdf_integrate(tsdf_volume* v, const uint16_t* depth_mm, tsdf_image_
         return fail(v, TSDF_ERR_INVALID_ARG, "intrinsics not finite or singular");
     if (!rigid_ok(T_world_depth) || !rigid_ok(T_depth_rgb))
         return fail(v, TSDF_ERR_INVALID_ARG, "transform not finite or not rigid");
+    if (!translation_ok(T_world_depth) || !translation_ok(T_depth_rgb))
+        return fail(v, TSDF_ERR_INVALID_ARG, "translation beyond 10^6 m");
 
     FrameConst c;
     frame_constants(v, K_depth, K_rgb, T_world_depth, T_depth_rgb, dsz.width, dsz.height, csz.width, csz.height, c);
@@ -717,6 +759,14 @@ tsdf_status tsdf_get_info(const tsdf_volume* v, tsdf_info* o) {
     o->update_free_space = v->free_space;
     o->frames = v->frames;
     o->device_bytes = v->device_bytes;
+    o->dims_geo[2] = v->ngz_all;  // the whole volume's dims
+    o->dims_col[2] = v->ncz_all;
+    o->slab_z[0] = v->slab_z0;
+    o->slab_z[1] = v->slab_z1;
+    o->held_geo_z[0] = v->zoff_g;
+    o->held_geo_z[1] = v->zoff_g + v->ng[2];
+    o->held_col_z[0] = v->zoff_c;
+    o->held_col_z[1] = v->zoff_c + v->nc[2];
     return TSDF_OK;
 }
 
@@ -860,6 +910,7 @@ struct FileHeader {
     float voxel, mu, origin[3], sigma, band;
     int32_t max_weight, colour_mode, sample_mode, free_space;
     int64_t frames;
+    int32_t zoff_g, zoff_c;  // version 2: global z index of held geometry / colour z = 0
 };
 }  // namespace
 
@@ -875,7 +926,9 @@ tsdf_status tsdf_save(tsdf_volume* v, const char* path) {
     FileHeader h;
     std::memset(&h, 0, sizeof h);
     std::memcpy(h.magic, "TSDFVOL1", 8);
-    h.version = 1;
+    h.version = 2;
+    h.zoff_g = v->zoff_g;
+    h.zoff_c = v->zoff_c;
     for (int a = 0; a < 3; ++a) {
         h.dims_geo[a] = v->ng[a];
         h.dims_col[a] = v->nc[a];
@@ -904,9 +957,13 @@ tsdf_status tsdf_load(tsdf_volume* v, const char* path) {
     FILE* f = std::fopen(path, "rb");
     if (!f) return fail(v, TSDF_ERR_IO, std::string("cannot open ") + path);
     FileHeader h;
-    if (std::fread(&h, sizeof h, 1, f) != 1 || std::memcmp(h.magic, "TSDFVOL1", 8) != 0 || h.version != 1) {
+    if (std::fread(&h, sizeof h, 1, f) != 1 || std::memcmp(h.magic, "TSDFVOL1", 8) != 0 || h.version != 2) {
         std::fclose(f);
-        return fail(v, TSDF_ERR_IO, "not a TSDFVOL1 checkpoint");
+        return fail(v, TSDF_ERR_IO, "not a TSDFVOL1 version 2 checkpoint");
+    }
+    if (h.zoff_g != v->zoff_g || h.zoff_c != v->zoff_c) {
+        std::fclose(f);
+        return fail(v, TSDF_ERR_INVALID_ARG, "checkpoint holds another z-slab");
     }
     for (int a = 0; a < 3; ++a)
         if (h.dims_geo[a] != v->ng[a] || h.dims_col[a] != v->nc[a]) {

@@ -24,6 +24,7 @@ struct tsdf_batch {
     bool copied_valid[2];
     BatchSync* d_sync;
     int sms, max_blocks_per_sm, blocks_per_sm;
+    int tile;  // listed bricks per work item of the geometry and band phases
     bool use_graph;
     cudaGraphExec_t exec[2];
     int step;
@@ -45,7 +46,7 @@ tsdf_status queue_step(tsdf_batch* b, int buf) {
     const int grid = b->sms * b->blocks_per_sm;
     if (!b->use_graph) {
         cudaError_t e = cudaMemcpyAsync(b->d_descs[buf], b->h_descs[buf], bytes, cudaMemcpyHostToDevice, b->stream);
-        if (e == cudaSuccess) e = launch_batch_step(b->d_descs[buf], n, b->d_sync, grid, b->stream);
+        if (e == cudaSuccess) e = launch_batch_step(b->d_descs[buf], n, b->d_sync, grid, b->tile, b->stream);
         return e == cudaSuccess ? TSDF_OK : TSDF_ERR_CUDA;
     }
     if (!b->exec[buf]) {
@@ -54,7 +55,7 @@ tsdf_status queue_step(tsdf_batch* b, int buf) {
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_descs[buf], b->h_descs[buf], bytes, cudaMemcpyHostToDevice, cap);
-        if (e == cudaSuccess) e = launch_batch_step(b->d_descs[buf], n, b->d_sync, grid, cap);
+        if (e == cudaSuccess) e = launch_batch_step(b->d_descs[buf], n, b->d_sync, grid, b->tile, cap);
         cudaError_t e2 = cudaStreamEndCapture(cap, &g);
         if (e == cudaSuccess) e = e2;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec[buf], g, 0);
@@ -103,6 +104,7 @@ tsdf_status tsdf_batch_create(tsdf_volume* const* volumes, int32_t n, tsdf_batch
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
     b->max_blocks_per_sm = batch_blocks_per_sm();
     b->blocks_per_sm = b->max_blocks_per_sm;
+    b->tile = 1;
     b->use_graph = true;
     tsdf_volume* v0 = volumes[0];
     bool ok = true;
@@ -136,20 +138,24 @@ void tsdf_batch_destroy(tsdf_batch* b) {
     delete b;
 }
 
-tsdf_status tsdf_batch_set_schedule(tsdf_batch* b, int32_t blocks_per_sm, int32_t use_graph) {
-    if (!b || blocks_per_sm < 1 || blocks_per_sm > b->max_blocks_per_sm) return TSDF_ERR_INVALID_ARG;
+tsdf_status tsdf_batch_set_schedule(tsdf_batch* b, int32_t blocks_per_sm, int32_t bricks_per_item, int32_t use_graph) {
+    if (!b || blocks_per_sm < 1 || blocks_per_sm > b->max_blocks_per_sm || bricks_per_item < 1 ||
+        bricks_per_item > TSDF_BATCH_MAX_BRICKS_PER_ITEM)
+        return TSDF_ERR_INVALID_ARG;
     cudaStreamSynchronize(b->stream);
     release_graphs(b);
     b->blocks_per_sm = blocks_per_sm;
+    b->tile = bricks_per_item;
     b->use_graph = use_graph != 0;
     return TSDF_OK;
 }
 
 tsdf_status tsdf_batch_get_schedule(const tsdf_batch* b, int32_t* blocks_per_sm, int32_t* max_blocks_per_sm,
-                                    int32_t* use_graph) {
+                                    int32_t* bricks_per_item, int32_t* use_graph) {
     if (!b) return TSDF_ERR_INVALID_ARG;
     if (blocks_per_sm) *blocks_per_sm = b->blocks_per_sm;
     if (max_blocks_per_sm) *max_blocks_per_sm = b->max_blocks_per_sm;
+    if (bricks_per_item) *bricks_per_item = b->tile;
     if (use_graph) *use_graph = b->use_graph ? 1 : 0;
     return TSDF_OK;
 }
@@ -172,7 +178,8 @@ tsdf_status tsdf_batch_integrate(tsdf_batch* b, const tsdf_frame* frames) {
             return fail(v, TSDF_ERR_INVALID_ARG, "batched frames must be device images");
         float Ki[9];
         if (!finite_all(f.K_depth, 9) || !finite_all(f.K_rgb, 9) || !invert3(f.K_depth, Ki) || !invert3(f.K_rgb, Ki) ||
-            !rigid_ok(f.T_world_depth) || !rigid_ok(f.T_depth_rgb))
+            !rigid_ok(f.T_world_depth) || !rigid_ok(f.T_depth_rgb) || !translation_ok(f.T_world_depth) ||
+            !translation_ok(f.T_depth_rgb))
             return fail(v, TSDF_ERR_INVALID_ARG, "invalid intrinsics or transform");
         ScanDesc& d = b->h_descs[buf][b->slot_of[i]];
         frame_constants(v, f.K_depth, f.K_rgb, f.T_world_depth, f.T_depth_rgb, f.dsz.width, f.dsz.height,
@@ -221,11 +228,12 @@ tsdf_status tsdf_batch_inject_stall(tsdf_batch* b) {
     return e == cudaSuccess ? TSDF_OK : TSDF_ERR_CUDA;
 }
 
-// Native autotuner: times every grid size (blocks per SM) on clones of the
+// Native autotuner: times every schedule -- grid size (blocks per SM) times
+// work-item size (1, 2, 4, 8 listed bricks per item) -- on clones of the
 // batch's volumes with the given frames, interleaving the candidates over
 // `rounds` rounds, and keeps the one with the smallest median step time.
 tsdf_status tsdf_batch_autotune(tsdf_batch* b, const tsdf_frame* frames, int32_t rounds, int32_t* best_blocks_per_sm,
-                                float* ms_per_candidate) {
+                                int32_t* best_bricks_per_item, float* ms_per_candidate) {
     if (!b || !frames || rounds < 1) return TSDF_ERR_INVALID_ARG;
     const int n = (int)b->vols.size();
     std::vector<tsdf_volume*> clones(n, nullptr);
@@ -247,14 +255,15 @@ tsdf_status tsdf_batch_autotune(tsdf_batch* b, const tsdf_frame* frames, int32_t
     }
     tsdf_batch* tb = nullptr;
     if (st == TSDF_OK) st = tsdf_batch_create(clones.data(), n, &tb);
-    const int cands = b->max_blocks_per_sm;
+    const int ntile = 4;  // 1, 2, 4, 8 bricks per item
+    const int cands = b->max_blocks_per_sm * ntile;
     std::vector<std::vector<float>> times(cands);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (st == TSDF_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
         st = TSDF_ERR_CUDA;
     for (int r = 0; r < rounds && st == TSDF_OK; ++r)
         for (int k = 1; k <= cands && st == TSDF_OK; ++k) {
-            st = tsdf_batch_set_schedule(tb, k, 0);
+            st = tsdf_batch_set_schedule(tb, (k - 1) / ntile + 1, 1 << ((k - 1) % ntile), 0);
             if (st == TSDF_OK) st = tsdf_batch_integrate(tb, frames);  // warm the schedule
             if (st != TSDF_OK) break;
             cudaEventRecord(e0, tb->stream);
@@ -265,7 +274,7 @@ tsdf_status tsdf_batch_autotune(tsdf_batch* b, const tsdf_frame* frames, int32_t
             cudaEventElapsedTime(&ms, e0, e1);
             times[k - 1].push_back(ms);
         }
-    int best = b->blocks_per_sm;
+    int best = (b->blocks_per_sm - 1) * ntile + 1;
     if (st == TSDF_OK) {
         float best_ms = 1e30f;
         for (int k = 1; k <= cands; ++k) {
@@ -284,8 +293,10 @@ tsdf_status tsdf_batch_autotune(tsdf_batch* b, const tsdf_frame* frames, int32_t
     tsdf_batch_destroy(tb);
     for (auto* c : clones) tsdf_destroy(c);
     if (st != TSDF_OK) return st;
-    if (best_blocks_per_sm) *best_blocks_per_sm = best;
-    return tsdf_batch_set_schedule(b, best, b->use_graph ? 1 : 0);
+    const int bps = (best - 1) / ntile + 1, tile = 1 << ((best - 1) % ntile);
+    if (best_blocks_per_sm) *best_blocks_per_sm = bps;
+    if (best_bricks_per_item) *best_bricks_per_item = tile;
+    return tsdf_batch_set_schedule(b, bps, tile, b->use_graph ? 1 : 0);
 }
 
 }  // extern "C"

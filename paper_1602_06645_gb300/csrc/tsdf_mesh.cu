@@ -58,10 +58,115 @@ tsdf::MeshConst mesh_const(const tsdf_volume* v) {
     return c;
 }
 
+// ---------------------------------------------------- marching-cubes cases --
+// The 256-case table of tsdf.h's marching-cubes rules, built once.  Corner k
+// sits at (k & 1, (k >> 1) & 1, k >> 2); edge 4 a + r joins the r-th corner
+// with bit a clear (in increasing order) to its neighbour along a.
+struct CubeCases {
+    uint8_t t[256][16];  // triangle count, then edge triples
+};
+
+int cube_edge(int p, int q) {
+    const int lo = std::min(p, q), a = (p ^ q) == 1 ? 0 : ((p ^ q) == 2 ? 1 : 2);
+    // drop bit a of the lower corner: its rank among the corners with bit a clear
+    return 4 * a + (((lo >> (a + 1)) << a) | (lo & ((1 << a) - 1)));
+}
+
+// The four corners of the face (axis a, side s) counter-clockwise about its
+// outward normal: with u = a + 1, v = a + 2 (mod 3) the frame (a, u, v) is
+// right-handed, so about +a the turn runs u -> v and about -a it runs v -> u.
+void face_ring(int a, int s, int ring[4]) {
+    const int u = (a + 1) % 3, v = (a + 2) % 3;
+    const int uv[4][2] = {{0, 0}, {1, 0}, {1, 1}, {0, 1}};
+    for (int i = 0; i < 4; ++i) {
+        const int iu = s ? uv[i][0] : uv[i][1], iv = s ? uv[i][1] : uv[i][0];
+        ring[i] = (s << a) | (iu << u) | (iv << v);
+    }
+}
+
+bool edges_share_a_face(const int e[3]) {
+    for (int b = 0; b < 3; ++b)
+        for (int side = 0; side < 2; ++side) {
+            bool all = true;
+            for (int k = 0; k < 3; ++k) {
+                const int a = e[k] / 4, r = e[k] % 4;
+                // the lower corner of edge e[k]: r with a zero bit inserted at a
+                const int lo = ((r >> a) << (a + 1)) | (r & ((1 << a) - 1));
+                all = all && a != b && ((lo >> b) & 1) == side;
+            }
+            if (all) return true;
+        }
+    return false;
+}
+
+CubeCases build_cube_cases() {
+    CubeCases cc;
+    std::memset(&cc, 0, sizeof cc);
+    for (int mask = 0; mask < 256; ++mask) {
+        int succ[12];
+        std::fill(succ, succ + 12, -1);
+        for (int a = 0; a < 3; ++a)
+            for (int s = 0; s < 2; ++s) {
+                int ring[4];
+                face_ring(a, s, ring);
+                auto in = [&](int i) { return (mask >> ring[(i + 4) % 4]) & 1; };
+                for (int i = 0; i < 4; ++i) {
+                    if (!in(i) || in(i - 1)) continue;  // not the first corner of an inside run
+                    int j = i;
+                    while (in(j + 1)) ++j;
+                    succ[cube_edge(ring[(i + 3) % 4], ring[i])] = cube_edge(ring[j % 4], ring[(j + 1) % 4]);
+                }
+            }
+        int n = 0;
+        bool used[12] = {false};
+        for (int first = 0; first < 12; ++first) {
+            if (succ[first] < 0 || used[first]) continue;
+            std::vector<int> loop;
+            for (int e = first; !used[e]; e = succ[e]) {
+                used[e] = true;
+                loop.push_back(e);
+            }
+            const int m = (int)loop.size();
+            int start = 0;
+            for (int st = 0; st < m; ++st) {
+                bool flat = false;
+                for (int i = 1; i + 1 < m && !flat; ++i) {
+                    const int tri[3] = {loop[st], loop[(st + i) % m], loop[(st + i + 1) % m]};
+                    flat = edges_share_a_face(tri);
+                }
+                if (!flat) {
+                    start = st;
+                    break;
+                }
+            }
+            for (int i = 1; i + 1 < m; ++i, ++n) {
+                cc.t[mask][1 + 3 * n] = (uint8_t)loop[start];
+                cc.t[mask][2 + 3 * n] = (uint8_t)loop[(start + i) % m];
+                cc.t[mask][3 + 3 * n] = (uint8_t)loop[(start + i + 1) % m];
+            }
+        }
+        cc.t[mask][0] = (uint8_t)n;
+    }
+    return cc;
+}
+
+const CubeCases& cube_cases() {
+    static const CubeCases cc = build_cube_cases();
+    return cc;
+}
+
 }  // namespace
 
 extern "C" tsdf_status tsdf_mesh(tsdf_volume* v, float* triangles, int64_t capacity, int64_t* n_triangles) {
+    return tsdf_mesh_ex(v, TSDF_MESH_CUBES, triangles, capacity, n_triangles);
+}
+
+extern "C" tsdf_status tsdf_mesh_ex(tsdf_volume* v, int32_t method, float* triangles, int64_t capacity,
+                                    int64_t* n_triangles) {
     if (!v) return TSDF_ERR_INVALID_ARG;
+    if (method != TSDF_MESH_CUBES && method != TSDF_MESH_TETRAHEDRA)
+        return fail(v, TSDF_ERR_INVALID_ARG, "mesh: unknown method");
+    if (v->zoff_g != 0 || v->ng[2] != v->ngz_all) return fail(v, TSDF_ERR_INVALID_ARG, "mesh: needs a whole volume");
     if (!n_triangles || capacity < 0 || (capacity > 0 && !triangles))
         return fail(v, TSDF_ERR_INVALID_ARG, "mesh: need n_triangles, capacity >= 0 and a buffer for it");
     Temps t(v);
@@ -73,9 +178,10 @@ extern "C" tsdf_status tsdf_mesh(tsdf_volume* v, float* triangles, int64_t capac
     if (!list || !n_list || (capacity > 0 && !out)) return fail(v, TSDF_ERR_OOM, "mesh: scratch buffers");
     unsigned long long* count = reinterpret_cast<unsigned long long*>(n_list + 2);
     cudaError_t e = cudaMemsetAsync(n_list, 0, sizeof(uint32_t) + sizeof(unsigned long long) * 2, v->stream);
+    if (e == cudaSuccess && method == TSDF_MESH_CUBES) e = tsdf::upload_cube_cases(cube_cases().t, v->stream);
     if (e == cudaSuccess)
         e = tsdf::launch_mesh(mesh_const(v), v->vol.F, v->vol.W, v->vol.summ, list, n_list, out,
-                              (uint64_t)capacity, count, v->stream);
+                              (uint64_t)capacity, count, method == TSDF_MESH_CUBES, v->stream);
     unsigned long long total = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&total, count, sizeof total, cudaMemcpyDeviceToHost, v->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(v->stream);
@@ -113,6 +219,8 @@ extern "C" tsdf_status tsdf_texture_layout(tsdf_volume* v, const float* triangle
 extern "C" tsdf_status tsdf_texture_fill(tsdf_volume* v, const float* triangles, int64_t n, const int32_t* wh,
                                          const int64_t* offsets, uint32_t* texels) {
     if (!v) return TSDF_ERR_INVALID_ARG;
+    if (v->zoff_c != 0 || v->nc[2] != v->ncz_all)
+        return fail(v, TSDF_ERR_INVALID_ARG, "texture fill: needs a whole volume");
     if (n < 0 || n > (int64_t(1) << 31) || (n > 0 && (!triangles || !wh || !offsets || !texels)))
         return fail(v, TSDF_ERR_INVALID_ARG, "texture fill: need triangles, wh, offsets and texels");
     if (n == 0) return TSDF_OK;

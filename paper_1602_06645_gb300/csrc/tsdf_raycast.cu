@@ -33,16 +33,13 @@ tsdf_status prepare(tsdf_volume* v, void* user, size_t bytes, Out& o) {
 
 }  // namespace
 
-extern "C" tsdf_status tsdf_raycast(tsdf_volume* v, const float K[9], const float T_world_camera[16],
-                                    tsdf_image_size size, const tsdf_raycast_params* params, float* range,
-                                    float* vertex, float* normal, uint32_t* rgbw) {
-    if (!v) return TSDF_ERR_INVALID_ARG;
-    if (!K || !T_world_camera) return fail(v, TSDF_ERR_INVALID_ARG, "raycast: K and T_world_camera are required");
+namespace tsdf_host {
+tsdf_status raycast_constants(tsdf_volume* v, const float K[9], const float T_world_camera[16], tsdf_image_size size,
+                              const tsdf_raycast_params* params, tsdf::RayConst& c) {
     if (size.width < 1 || size.height < 1 || size.width > 16384 || size.height > 16384)
         return fail(v, TSDF_ERR_INVALID_ARG, "raycast: image size outside 1..16384");
     if (!finite_all(K, 9) || !finite_all(T_world_camera, 16) || !rigid_ok(T_world_camera))
         return fail(v, TSDF_ERR_INVALID_ARG, "raycast: K must be finite and T_world_camera a rigid motion");
-    tsdf::RayConst c;
     std::memset(&c, 0, sizeof c);
     if (!invert3(K, c.Kinv)) return fail(v, TSDF_ERR_INVALID_ARG, "raycast: K is singular");
     tsdf_raycast_params p = params ? *params : tsdf_raycast_params{0.1f, 4.0f, 0.0f, 0.0f};
@@ -73,6 +70,19 @@ extern "C" tsdf_status tsdf_raycast(tsdf_volume* v, const float K[9], const floa
     c.height = size.height;
     // each step adds at least step_near less its rounding; 2% and 16 samples of slack
     c.max_iter = (uint32_t)std::ceil(1.02 * ((double)p.far_m - (double)p.near_m) / (double)p.step_near) + 16u;
+    return TSDF_OK;
+}
+}  // namespace tsdf_host
+
+extern "C" tsdf_status tsdf_raycast(tsdf_volume* v, const float K[9], const float T_world_camera[16],
+                                    tsdf_image_size size, const tsdf_raycast_params* params, float* range,
+                                    float* vertex, float* normal, uint32_t* rgbw) {
+    if (!v) return TSDF_ERR_INVALID_ARG;
+    if (v->zoff_g != 0 || v->ng[2] != v->ngz_all) return fail(v, TSDF_ERR_INVALID_ARG, "raycast: needs a whole volume");
+    if (!K || !T_world_camera) return fail(v, TSDF_ERR_INVALID_ARG, "raycast: K and T_world_camera are required");
+    tsdf::RayConst c;
+    const tsdf_status cs = raycast_constants(v, K, T_world_camera, size, params, c);
+    if (cs != TSDF_OK) return cs;
 
     const size_t npx = (size_t)size.width * size.height;
     Out o_range, o_vertex, o_normal, o_rgbw;

@@ -318,6 +318,19 @@ def sequence_small(n_frames: int = 10, seed: int = 1, dims_geo=128, ratio=2) -> 
                     (dims_geo * ratio,) * 3, vs, float(np.float32(3 * vs)), 64)
 
 
+def sequence_tracking(n_frames: int = 12, seed: int = 5, dims_geo=128, ratio=2, deg_per_frame=2.0) -> Sequence:
+    """Camera-tracking sequence: the small scene (sphere on a box on a ground
+    plane, 1 m cube) seen from a 0.8 m orbit moving 2 deg per frame with pose
+    jitter of 2 mm / 0.2 deg, so consecutive poses differ by what a tracker
+    must recover."""
+    poses = orbit_poses(n_frames, 0.8, 25.0, deg_per_frame, target=(0.0, 0.0, -0.1), jitter_t=2e-3,
+                        jitter_deg=0.2, seed=seed)
+    vs = _vox(1.0, dims_geo)
+    return Sequence("tracking_128", scene_sphere_box_plane(seed), poses, K_DEPTH, K_RGB_1080,
+                    rig_depth_to_rgb(), DEPTH_SIZE, RGB_1080, seed, (dims_geo,) * 3,
+                    (dims_geo * ratio,) * 3, vs, float(np.float32(3 * vs)), 64)
+
+
 def sequence_scan(n_frames: int = 300, seed: int = 2, dims_geo=512, ratio=2, frame_stride=1) -> Sequence:
     """Scan-scale sequence: 512^3 geometry / 1024^3 colour over a 2 m cube, 20 random
     primitives on a ground plane, one orbit (1.2 deg/frame for 300 frames) of radius

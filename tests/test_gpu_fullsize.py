@@ -85,3 +85,48 @@ def test_whole_volume_invariants(fullsize):
         assert int(wc.max()) <= seq.max_weight
     assert not bool((C[wc == 0] != 0).any())
     assert fullsize["info"].frames == N_FRAMES
+
+
+# Whole volumes at full size: the oracle integrates every voxel of the
+# 512^3 / 1024^3 volumes (about 1.2 s per frame on the host cores).
+WHOLE = {
+    "frames_0_9": dict(stride=1, max_weight=64, capacity=None),
+    # every 30th frame of the orbit with a weight cap of 4, so saturated free
+    # space is culled from the fourth frame on, and a band-record buffer of
+    # 100,000 entries, so the band kernel's overflow path runs at scale
+    "orbit_cap4_overflow": dict(stride=30, max_weight=4, capacity="100000"),
+}
+
+
+@pytest.fixture(scope="module", params=sorted(WHOLE))
+def whole(request):
+    cfg = WHOLE[request.param]
+    seq = synth.sequence_scan(n_frames=10, frame_stride=cfg["stride"])
+    mw = cfg["max_weight"]
+    mp = pytest.MonkeyPatch()
+    if cfg["capacity"]:
+        mp.setenv("TSDF_VOXEL_RECORD_CAPACITY", cfg["capacity"])
+    vol = T.Volume(seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, mw,
+                   stream=torch.cuda.current_stream().cuda_stream)
+    mp.undo()
+    o = oracle.Oracle(seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, mw, n_threads=NT)
+    for f in range(10):
+        d, c = seq.frame(f)
+        o.integrate(d, c, seq.K_depth, seq.K_rgb, seq.poses[f], seq.T_depth_rgb)
+        vol.integrate(torch.from_numpy(d.view(np.int16)).cuda(), torch.from_numpy(c).cuda(), seq.K_depth,
+                      seq.K_rgb, seq.poses[f], seq.T_depth_rgb)
+    st = vol.stats()
+    F, W, C = vol.read()
+    vol.close()
+    yield dict(name=request.param, o=o, F=F, W=W, C=C, stats=st)
+
+
+def test_whole_volumes_equal_the_oracle(whole):
+    o, F, W, C = whole["o"], whole["F"], whole["W"], whole["C"]
+    np.testing.assert_array_equal(W, o.W)
+    bad = np.count_nonzero(C != o.C)
+    assert bad == 0, "%d colour voxels differ" % bad
+    assert float(np.abs(F - o.F).max()) <= F_TOL
+    assert (W > 0).sum() > 10 ** 7 and ((C >> 24) > 0).sum() > 10 ** 6
+    if whole["name"] == "orbit_cap4_overflow":
+        assert whole["stats"].total_geo_bricks < 10 * 262144  # saturated free space was culled

@@ -1,4 +1,5 @@
-"""GPU mesh extraction and texture maps against the oracle (mesh.c).
+"""GPU mesh extraction (marching cubes, and marching tetrahedra as an option)
+and texture maps against the oracle (mesh.c).
 
 Volumes come from outside the CUDA path (analytic signed distances, or the
 oracle's own fusion of a synthetic sequence) and are written into the GPU
@@ -36,20 +37,21 @@ def sphere_volume(n):
     return F, W, s
 
 
+@pytest.mark.parametrize("method", ["cubes", "tetrahedra"])
 @pytest.mark.parametrize("n", [40, 45])  # whole bricks, and ragged bricks at the + faces
-def test_analytic_sphere_mesh_equals_oracle(n):
+def test_analytic_sphere_mesh_equals_oracle(n, method):
     F, W, s = sphere_volume(n)
     vol = T.Volume((n,) * 3, (n,) * 3, s, 3 * s, 64)
     vol.write(F, W)
-    g = vol.mesh()
-    o = oracle.mesh(F, W, s, vol.info().origin)
+    g = vol.mesh(method=method)
+    o = oracle.mesh(F, W, s, vol.info().origin, method)
     assert len(o) > 1000
     np.testing.assert_array_equal(tri_set(g), tri_set(o))
     # device output, and a buffer too small: the count is still the total
-    gd = vol.mesh(device="cuda").cpu().numpy()
+    gd = vol.mesh(device="cuda", method=method).cpu().numpy()
     np.testing.assert_array_equal(tri_set(gd), tri_set(o))
     part = np.zeros((100, 3, 3), np.float32)
-    assert T.tsdf_mesh(vol.h, part, 100) == len(o)
+    assert T.tsdf_mesh_ex(vol.h, {"cubes": 0, "tetrahedra": 1}[method], part, 100) == len(o)
     full = set(map(bytes, tri_set(o)))
     assert all(bytes(t) in full for t in tri_set(part))
     vol.close()
@@ -68,11 +70,28 @@ def fused():
     vol.close()
 
 
-def test_fused_sequence_mesh_equals_oracle(fused):
+@pytest.mark.parametrize("method", ["cubes", "tetrahedra"])
+def test_fused_sequence_mesh_equals_oracle(fused, method):
     seq, o, vol = fused
-    ref = oracle.mesh(o.F, o.W, seq.voxel_size, vol.info().origin)
+    ref = oracle.mesh(o.F, o.W, seq.voxel_size, vol.info().origin, method)
     assert len(ref) > 5000
-    np.testing.assert_array_equal(tri_set(vol.mesh()), tri_set(ref))
+    np.testing.assert_array_equal(tri_set(vol.mesh(method=method)), tri_set(ref))
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_random_fields_mesh_equals_oracle(seed):
+    """Random corner values everywhere (every marching-cubes case, many
+    ambiguous faces), ragged volume: triangle sets equal bit for bit."""
+    rng = np.random.default_rng(seed)
+    dims = (37, 29, 21)
+    F = rng.uniform(-1, 1, size=dims[::-1]).astype(np.float32)
+    W = (rng.uniform(size=dims[::-1]) > 0.02).astype(np.uint8)
+    vol = T.Volume(dims, dims, 0.01, 0.03, 64)
+    vol.write(F, W)
+    o = oracle.mesh(F, W, 0.01, vol.info().origin, "cubes")
+    assert len(o) > 20000
+    np.testing.assert_array_equal(tri_set(vol.mesh()), tri_set(o))
+    vol.close()
 
 
 @pytest.mark.parametrize("device", [False, True])

@@ -73,6 +73,12 @@ MESH_MUTANTS = {
     "tx_divide_by_w": ("green[a] = (T[3 + a] - T[a]) / (float)(w - 1);", "green[a] = (T[3 + a] - T[a]) / (float)w;"),
     "tx_unobserved_colour_used": ("if ((c >> 24) == 0u) continue;", ""),
     "tx_size_truncated": ("float q = floorf(dist / size_pixel + 0.5f);", "float q = floorf(dist / size_pixel);"),
+    "mc_face_order_reversed": ("{0, 4, 6, 2},  /* x = 0, normal -x */", "{0, 2, 6, 4},  /* x = 0, normal -x */"),
+    "mc_fan_drops_last": ("for (int i = 1; i + 1 < m; ++i, ++n) {\n            memcpy(out + 9 * n, vert[s0], 12);",
+                          "for (int i = 1; i + 2 < m; ++i, ++n) {\n            memcpy(out + 9 * n, vert[s0], 12);"),
+    "mc_flat_triangles_allowed": ("flat = on_one_face(loop[s], loop[(s + i) % m], loop[(s + i + 1) % m]);", "flat = 0;"),
+    "mc_runs_of_one_corner": ("while ((inside >> c[(j + 1) % 4]) & 1) j = (j + 1) % 4;", ""),
+    "mc_inside_is_positive": ("if (Fc[k] < 0.0f) inside |= 1 << k;", "if (Fc[k] > 0.0f) inside |= 1 << k;"),
 }
 # Slips in the bilinear-cell decision of the photometric loss (oracle.c and the
 # camera built in oracle/__init__.py), caught by tests/test_adjoint_oracle.py.
@@ -84,7 +90,21 @@ CELL_MUTANTS = {
                            "Kr = np.array([[cx, 0, fx], [0, fy, cy], [0, 0, 1]], np.float32)"),
     "cell_u_from_y": ("oracle.c", "    *x0 = floorf(u);\n    *y0 = floorf(v);", "    *x0 = floorf(v);\n    *y0 = floorf(u);"),
 }
+# Slips in camera tracking (oracle/icp.c), caught by tests/test_icp_oracle.py.
+ICP_MUTANTS = {
+    "icp_jacobian_n_cross_p": ("p[1] * nq[2] - p[2] * nq[1], p[2] * nq[0] - p[0] * nq[2],\n                                p[0] * nq[1] - p[1] * nq[0]",
+                               "nq[1] * p[2] - nq[2] * p[1], nq[2] * p[0] - nq[0] * p[2],\n                                nq[0] * p[1] - nq[1] * p[0]"),
+    "icp_solve_sign": ("double s = -g[i];", "double s = g[i];"),
+    "icp_association_floor": ("const float fu = floorf(ux + 0.5f), fv = floorf(uy + 0.5f);",
+                              "const float fu = floorf(ux), fv = floorf(uy);"),
+    "icp_normal_away_from_camera": ("const float c[3] = {b[1] * a[2] - b[2] * a[1], b[2] * a[0] - b[0] * a[2], b[0] * a[1] - b[1] * a[0]};",
+                                    "const float c[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};"),
+    "icp_pyramid_mixes_edges": ("if (fabsf(d - first) <= 0.03f) {", "if (fabsf(d - first) <= 3.0f) {"),
+    "icp_level_centre": ("Kl[2] = (float)(((double)K[2] + 0.5) * s - 0.5);", "Kl[2] = (float)((double)K[2] * s);"),
+    "icp_distance_gate_dropped": ("if (fmaf(e[0], e[0], fmaf(e[1], e[1], e[2] * e[2])) > L->max_dist2) continue;", ""),
+}
 ALL = {**{k: ("oracle.c", "tests/test_oracle_pins.py") + v for k, v in MUTANTS.items()},
+       **{k: ("icp.c", "tests/test_icp_oracle.py") + v for k, v in ICP_MUTANTS.items()},
        **{k: (v[0], "tests/test_adjoint_oracle.py") + v[1:] for k, v in CELL_MUTANTS.items()},
        **{k: ("raycast.c", "tests/test_raycast_oracle.py") + v for k, v in RAYCAST_MUTANTS.items()},
        **{k: ("mesh.c", "tests/test_mesh_oracle.py") + v for k, v in MESH_MUTANTS.items()}}
