@@ -218,8 +218,27 @@ def oracle_sample(seq, frames, n_threads):
     return nvox * len(frames) / dt, dt, desc
 
 
+def scan_config(seq, args, world, sliced):
+    """Whether the scan frames are timed one by one with L2 flushed, and the
+    config of the plain-scan line; both arms print this config."""
+    vol_bytes = 5 * int(np.prod(seq.dims_geo)) + 4 * int(np.prod(seq.dims_col))
+    per_step_flush = args.l2_flush or vol_bytes < 4 * L2_BYTES
+    if per_step_flush:
+        l2_note = "flushed between steps (256 MiB write), each step between its own events"
+    else:
+        l2_note = ("not flushed: inputs larger than L2 (volumes %.2f GB, L2 129 MB); the K frames back to back "
+                   "between two events" % (vol_bytes / 1e9))
+    return per_step_flush, {
+        "workload": seq.name, "dims_geo": list(seq.dims_geo), "dims_col": list(seq.dims_col),
+        "depth": "%dx%d" % seq.depth_size, "rgb": "%dx%d" % seq.rgb_size, "frames": args.steps,
+        "culling": not args.dense, "l2": l2_note,
+        "parallelism": ("z-slabs of one scan over the GPUs" if sliced else
+                        "independent scan per GPU" if world > 1 else "single GPU")}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return
     n = args.warmup + args.steps
@@ -236,8 +255,7 @@ def run_reference(args):
         "unit": "voxel-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / max(args.steps, 1), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+u8", "data": "synthetic",
-        "config": {"workload": seq.name, "dims_geo": list(seq.dims_geo), "dims_col": list(seq.dims_col),
-                   "sample": "central 1/8 of both volumes"},
+        "config": scan_config(seq, args, world, args.shard == "slab" and world > 1)[1],
         "cpu_baseline": {"value": v, "unit": "voxel-updates/s", "cores": cores, "kind": "oracle", "sample": desc},
         "e2e": {"value": v, "unit": "voxel-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -312,8 +330,7 @@ def run_ours(args):
     if sampler:
         sampler.start()
         time.sleep(0.15)
-    vol_bytes = 5 * int(np.prod(seq.dims_geo)) + 4 * int(np.prod(seq.dims_col))
-    per_step_flush = args.l2_flush or vol_bytes < 4 * L2_BYTES
+    per_step_flush, config = scan_config(seq, args, world, slab is not None)
     if per_step_flush:
         # each frame alone between its own events, L2 flushed in between; the
         # second stream's depth tiles and culling of a frame then wait for
@@ -325,7 +342,6 @@ def run_ours(args):
             ev[i][0].record(stream)
             vol.integrate(d, c, seq.K_depth, seq.K_rgb, seq.poses[f], seq.T_depth_rgb)
             ev[i][1].record(stream)
-        l2_note = "flushed between steps (256 MiB write), each step between its own events"
     else:
         # the volumes are far larger than L2: the K frames run back to back
         # between two events, so every kernel of every frame (both streams)
@@ -336,8 +352,6 @@ def run_ours(args):
             d, c = dev_frames[f]
             vol.integrate(d, c, seq.K_depth, seq.K_rgb, seq.poses[f], seq.T_depth_rgb)
         ev[0][1].record(stream)
-        l2_note = ("not flushed: inputs larger than L2 (volumes %.2f GB, L2 129 MB); the K frames back to back "
-                   "between two events" % (vol_bytes / 1e9))
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -387,11 +401,7 @@ def run_ours(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / K,
         "higher_is_better": True, "scaling": "strong" if slab is not None else "weak", "vs_baseline": None,
         "dtype": "f32+u8", "data": "synthetic",
-        "config": {"workload": seq.name, "dims_geo": list(seq.dims_geo), "dims_col": list(seq.dims_col),
-                   "depth": "%dx%d" % seq.depth_size, "rgb": "%dx%d" % seq.rgb_size, "frames": args.steps,
-                   "culling": not args.dense, "l2": l2_note,
-                   "parallelism": ("z-slabs of one scan over the GPUs" if slab is not None else
-                                   "independent scan per GPU" if world > 1 else "single GPU")},
+        "config": config,
         "frames_per_s": args.steps * (1 if slab is not None else world) / (total_ms / 1e3),
         "updated_voxels_per_s": (st.total_geo_updated + st.total_col_updated) * world / (total_ms / 1e3),
         "per_frame": {"geo_updated": st.total_geo_updated / K, "col_updated": st.total_col_updated / K,
@@ -524,11 +534,13 @@ def run_batched(args):
     nominal = sum(int(np.prod(s.dims_geo)) + int(np.prod(s.dims_col)) for s, _ in data)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
-    def timed(step_fn):
+    def timed(step_fn, after_warmup=None):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         for f in range(args.warmup):
             step_fn(f)
         torch.cuda.synchronize()
+        if after_warmup:
+            after_warmup()
         for i in range(args.steps):
             flush.zero_()
             ev[i][0].record(stream)
@@ -543,10 +555,25 @@ def run_batched(args):
     batch = T.Batch(vols)
     key = "%s|%s" % (torch.cuda.get_device_name(0), hashlib.sha1(json.dumps(edges).encode()).hexdigest()[:12])
     sched, cached = tuned_schedule(batch, [fr[0] for _, fr in data], key)
+    warm = []
     with clock_record() as ck:
-        ms_batched = timed(lambda f: batch.integrate([fr[f] for _, fr in data]))
+        ms_batched = timed(lambda f: batch.integrate([fr[f] for _, fr in data]),
+                           lambda: warm.extend(v.stats() for v in vols))
     batch.synchronize()
     stats_b = [v.stats() for v in vols]
+
+    def per_step(field):  # over the timed steps only
+        return sum(getattr(a, field) - getattr(w, field) for a, w in zip(stats_b, warm)) / max(args.steps, 1)
+
+    geo_upd, col_upd, col_bricks = per_step("total_geo_updated"), per_step("total_col_updated"), \
+        per_step("total_col_bricks")
+    # algorithmic bytes of the step: F and w read and written per updated
+    # geometry voxel, the 10^3 geometry tile (F and w) per colour-candidate
+    # brick, the packed colour read and written per updated colour voxel
+    step_bytes = 10.0 * geo_upd + 5.0 * 1000 * col_bricks + 8.0 * col_upd
+    peaks, peak_kind = measured_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    achieved = step_bytes / (ms_batched / max(args.steps, 1) / 1e3) / 1e9
     batch.close()
     for v in vols:
         v.close()
@@ -577,8 +604,12 @@ def run_batched(args):
         "scan_frames_per_s": n_scans * K / (ms_batched / 1e3),
         "gpu_launches": K,
         "autotune_ms_per_candidate": sched.get("ms_per_candidate"), "clocks": ck.result,
-        "updated_per_step": {"geo": sum(s.total_geo_updated for s in stats_b) / K,
-                             "col": sum(s.total_col_updated for s in stats_b) / K},
+        "updated_per_step": {"geo": geo_upd, "col": col_upd, "colour_candidate_bricks": col_bricks},
+        "roofline": {"kernel": "k_batch_step (whole step, one launch)", "bound": "hbm",
+                     "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                     "bytes_per_launch": step_bytes,
+                     "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                     else "fallback 6.8 TB/s"},
         "frame_generation_s": gen_s,
     }
     print(json.dumps(line), flush=True)

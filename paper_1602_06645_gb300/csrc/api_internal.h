@@ -99,6 +99,9 @@ tsdf_status check_device_error(tsdf_volume* v);
 // buffer; sets *d_depth to the device copy.
 tsdf_status stage_depth(tsdf_volume* v, const uint16_t* depth_mm, tsdf_image_size dsz, int tiles,
                         const uint16_t** d_depth);
+// The frame's depth-tile buffer: the 8x8 tiles, then (16-byte aligned) the
+// depth in metres, W * H floats; grown when a larger frame arrives.
+tsdf_status depth_scratch(tsdf_volume* v, size_t tiles, tsdf_image_size dsz);
 // Validated ray-cast constants of a camera (as tsdf_raycast takes them).
 tsdf_status raycast_constants(tsdf_volume* v, const float K[9], const float T_world_camera[16], tsdf_image_size size,
                               const tsdf_raycast_params* params, tsdf::RayConst& c);

@@ -42,6 +42,7 @@ struct FrameConst {
     int32_t max_weight, free_space, sample_mode, colour_mode, culling;
     int32_t record_mode;   // 1: the band kernel only records (adjoint gate recording); no colour update
     int32_t zoff_g, zoff_c;  // z-slab: global z index of held geometry / colour z = 0 (whole volume: 0)
+    uint32_t pix_bias;       // 0x4B000000 (dw + 1) mod 2^32: pixel index from the bits of u + 2^23, v + 2^23
 };
 
 // Min/max of F over observed voxels (w > 0) and min of w over the in-volume
@@ -134,6 +135,7 @@ struct Scratch {
     uint32_t* vis_list;
     uint32_t* col_list;
     uint32_t* depth_tiles;  // per 8x8 tile: min valid depth | max valid depth << 16
+    float* depth_m;         // per pixel RN(D * 0.001) metres, -inf where D = 0
     uint32_t* err;
     uint2* vox;           // colour voxels that passed the band gate this frame: x | y << 16, z
     uint32_t vox_cap;

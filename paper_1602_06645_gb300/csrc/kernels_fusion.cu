@@ -15,6 +15,8 @@
 #include <cfloat>
 #include <cstdint>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "device_math.cuh"
 
@@ -29,8 +31,12 @@ constexpr int CELLS = BRICK + 1;           // trilinear cells whose corners lie 
 constexpr int CELLS3 = CELLS * CELLS * CELLS;
 
 // ------------------------------------------------------- depth tiles ----
+// Per 8x8-pixel tile the min / max valid depth (mm); with depth_m, also the
+// depth in metres per pixel as the geometry update reads it: RN(D * 0.001),
+// -inf where D = 0.
 __global__ void __launch_bounds__(256) k_depth_tiles(FrameConst c, const uint16_t* __restrict__ depth,
-                                                     uint32_t* __restrict__ tiles, Counters* __restrict__ ctr) {
+                                                     uint32_t* __restrict__ tiles, Counters* __restrict__ ctr,
+                                                     float* __restrict__ depth_m) {
     chain_enter();
     static_assert(TILE_BLOCK_PX == 2 * TILE_PX && TILE_PX == 8, "the lane layout below assumes 8x8 tiles");
     // a 16x16-pixel block; warp w holds pixel rows 2w and 2w + 1, lane bit 3
@@ -38,7 +44,12 @@ __global__ void __launch_bounds__(256) k_depth_tiles(FrameConst c, const uint16_
     // half hx of warps 4 hy .. 4 hy + 3
     __shared__ uint32_t s_min[8][2], s_max[8][2];
     const int px = blockIdx.x * TILE_BLOCK_PX + threadIdx.x, py = blockIdx.y * TILE_BLOCK_PX + threadIdx.y;
-    const uint32_t D = (px < c.dw && py < c.dh) ? depth[(size_t)py * c.dw + px] : 0u;
+    const bool in = px < c.dw && py < c.dh;
+    const uint32_t D = in ? depth[(size_t)py * c.dw + px] : 0u;
+    if (depth_m) {
+        const float ninf = __int_as_float(0xff800000);
+        if (in) depth_m[(size_t)py * c.dw + px] = D ? (float)D * 0.001f : ninf;
+    }
     uint32_t mn = D ? D : 0xFFFFu, mx = D;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -287,8 +298,29 @@ __device__ __forceinline__ void block_append2(bool p0, bool p1, uint32_t value0,
     __syncthreads();  // off is reused by the block's next call
 }
 
+// Geometry work-list entry: the brick's coordinates (10 bits per axis; the
+// volume has at most 4096 voxels = 512 bricks per axis) and, in bit 31, the
+// interior flag (the brick projects wholly into the image).
+constexpr uint32_t GEO_INNER = 0x80000000u;
+__device__ __forceinline__ uint32_t geo_entry(const FrameConst& c, uint32_t b, bool inner) {
+    const uint32_t nb0 = (uint32_t)c.nb[0], nb1 = (uint32_t)c.nb[1];
+    const uint32_t bx = b % nb0, r = b / nb0, by = r % nb1, bz = r / nb1;
+    return bx | by << 10 | bz << 20 | (inner ? GEO_INNER : 0u);
+}
+struct BrickAt {
+    uint32_t b;
+    int bx, by, bz;
+};
+__device__ __forceinline__ BrickAt geo_brick(const FrameConst& c, uint32_t e) {
+    BrickAt a;
+    a.bx = (int)(e & 1023u);
+    a.by = (int)((e >> 10) & 1023u);
+    a.bz = (int)((e >> 20) & 1023u);
+    a.b = (uint32_t)a.bx + (uint32_t)c.nb[0] * ((uint32_t)a.by + (uint32_t)c.nb[1] * (uint32_t)a.bz);
+    return a;
+}
+
 constexpr int BRICK_THREADS = 64;  // small blocks: they fit beside the band kernel's blocks on an SM
-constexpr uint32_t GEO_INNER = 0x80000000u;  // geometry-list flag: the brick projects wholly into the image
 
 __global__ void __launch_bounds__(BRICK_THREADS) k_bricks(FrameConst c, const BrickSummary* __restrict__ summ,
                                                 const uint32_t* __restrict__ tiles, Counters* __restrict__ ctr,
@@ -299,7 +331,7 @@ __global__ void __launch_bounds__(BRICK_THREADS) k_bricks(FrameConst c, const Br
     bool geo, vis, inner;
     brick_flags(c, summ, tiles, b, b < nbt, geo, vis, inner);
     // geometry list entries carry the interior flag in bit 31
-    block_append2<BRICK_THREADS>(geo, vis, b | (inner ? GEO_INNER : 0u), b, &ctr->n_geo, geo_list, &ctr->n_vis,
+    block_append2<BRICK_THREADS>(geo, vis, geo_entry(c, b, inner), b, &ctr->n_geo, geo_list, &ctr->n_vis,
                                  vis_list);
 }
 
@@ -325,10 +357,13 @@ __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 // taken as (u + 1/2) + 2^23 rounded toward minus infinity, whose bits are
 // 0x4B000000 + floor(u + 1/2) for 0 <= u + 1/2 < 2^23 and fall outside the
 // image test for any other value (negative, huge or infinite), so the
-// integer test 0 <= floor < W is the float test 0 <= u + 1/2 < W.  INNER: the
-// caller knows every point lies in front of the camera and inside the image.
+// integer test 0 <= floor < W is the float test 0 <= u + 1/2 < W.  The pixel
+// index iv W + iu is then (bits of v) W + (bits of u) - 0x4B000000 (W + 1),
+// modulo 2^32.  INNER: the caller knows every point lies in front of the
+// camera and inside the image.  Otherwise a point outside the image gets
+// pixel 0 and ok = false.
 template <bool PINHOLE, bool INNER>
-__device__ __forceinline__ void depth_pixels(const FrameConst& c, float2 X, float2 Y, float2 Z, int pix[2],
+__device__ __forceinline__ void depth_pixels(const FrameConst& c, float2 X, float2 Y, float2 Z, uint32_t pix[2],
                                              bool ok[2]) {
     float2 xh, yh, zh;
     if (PINHOLE) {
@@ -343,17 +378,18 @@ __device__ __forceinline__ void depth_pixels(const FrameConst& c, float2 X, floa
     const float2 rz = rcp2_rn(zh);
     const float2 bu = __fadd2_rd(__fadd2_rn(__fmul2_rn(xh, rz), f2(0.5f)), f2(8388608.0f));
     const float2 bv = __fadd2_rd(__fadd2_rn(__fmul2_rn(yh, rz), f2(0.5f)), f2(8388608.0f));
-    const int iu0 = __float_as_int(bu.x) - 0x4B000000, iu1 = __float_as_int(bu.y) - 0x4B000000;
-    const int iv0 = __float_as_int(bv.x) - 0x4B000000, iv1 = __float_as_int(bv.y) - 0x4B000000;
+    const uint32_t u0 = __float_as_uint(bu.x), u1 = __float_as_uint(bu.y);
+    const uint32_t v0 = __float_as_uint(bv.x), v1 = __float_as_uint(bv.y);
+    const uint32_t dw = (uint32_t)c.dw;
+    pix[0] = v0 * dw + u0 - c.pix_bias;
+    pix[1] = v1 * dw + u1 - c.pix_bias;
     if (INNER) {
         ok[0] = ok[1] = true;
-        pix[0] = iv0 * c.dw + iu0;
-        pix[1] = iv1 * c.dw + iu1;
     } else {
-        ok[0] = zh.x > 0.0f && (unsigned)iu0 < (unsigned)c.dw && (unsigned)iv0 < (unsigned)c.dh;
-        ok[1] = zh.y > 0.0f && (unsigned)iu1 < (unsigned)c.dw && (unsigned)iv1 < (unsigned)c.dh;
-        pix[0] = ok[0] ? iv0 * c.dw + iu0 : 0;
-        pix[1] = ok[1] ? iv1 * c.dw + iu1 : 0;
+        ok[0] = zh.x > 0.0f && u0 - 0x4B000000u < dw && v0 - 0x4B000000u < (uint32_t)c.dh;
+        ok[1] = zh.y > 0.0f && u1 - 0x4B000000u < dw && v1 - 0x4B000000u < (uint32_t)c.dh;
+        if (!ok[0]) pix[0] = 0u;
+        if (!ok[1]) pix[1] = 0u;
     }
 }
 
@@ -361,26 +397,63 @@ __device__ __forceinline__ void depth_pixels(const FrameConst& c, float2 X, floa
 // bit only from a zero byte).
 __device__ __forceinline__ bool any_zero_byte(uint32_t v) { return ((v - 0x01010101u) & ~v & 0x80808080u) != 0u; }
 
-// TSDF update of geometry brick b by one warp (lane = lane index) from its F
-// and w already loaded (f, wv: this lane's four groups); writes the changed
+// 0x01 in each byte of v that is zero, 0x00 in the others (exact per byte:
+// (b & 0x7F) + 0x7F carries into bit 7 iff b & 0x7F != 0, and never out of the byte).
+__device__ __forceinline__ uint32_t zero_bytes(uint32_t v) {
+    return ~(((v & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | v | 0x7F7F7F7Fu) >> 7;
+}
+
+// Minimum / maximum of a float over the warp (sm_100 warp reduction; no NaN
+// reaches it here).
+__device__ __forceinline__ float warp_min(float v) {
+    float r;
+    asm volatile("redux.sync.min.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ float warp_max(float v) {
+    float r;
+    asm volatile("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+// Depth sources of the update.  The frame's depth image in mm (D = 0: no
+// measurement), or the same in metres as the depth-tile kernel writes it
+// (RN(D * 0.001), -inf where D = 0): a -inf depth gives sdf = -inf < -mu,
+// which the update skips as it skips D = 0.
+struct DepthMm {
+    const uint16_t* __restrict__ p;
+};
+struct DepthM {
+    const float* __restrict__ p;
+};
+
+// TSDF update of geometry brick `at` by one warp (lane = lane index) from its
+// F and w already loaded (f, wv: this lane's four groups); writes the changed
 // groups and the brick summary.  Adds the number of updated voxels to count
 // and 1 to changed if any voxel changed.
-template <bool PINHOLE, bool FREE_SPACE, bool ALIGNED, bool INNER>
-__device__ __forceinline__ void geometry_update(const FrameConst& c, const Volumes& vol,
-                                                const uint16_t* __restrict__ depth, const float* rcp, uint32_t b,
-                                                int lane, const float4 (&f)[4], const uint32_t (&wv)[4],
-                                                uint32_t& count, uint32_t& changed) {
+//   D = depth at the nearest pixel of the voxel centre (Eq. 6); D = 0 skipped
+//   sdf = D * 0.001 - Z; sdf < -mu skipped; (free space off: sdf > mu skipped)
+//   t = min(1, sdf * (1/mu)); F <- fmaf(F, w, t) / (w + 1); w <- min(w+1, max_w)
+// One warp per brick.  Lane l owns the four float4 groups q = l + 32 j
+// (j = 0..3) of the brick: voxels 4q..4q+3, i.e. x in {0..3} or {4..7},
+// y = (l >> 1) & 7, z = (l >> 4) + 2 j.  Each group of the warp is 512
+// contiguous bytes of F and 128 of w.
+template <bool PINHOLE, bool FREE_SPACE, bool ALIGNED, bool INNER, typename Depth>
+__device__ __forceinline__ void geometry_update(const FrameConst& c, const Volumes& vol, Depth depth, const float* rcp,
+                                                const BrickAt& at, int lane, const float4 (&f)[4],
+                                                const uint32_t (&wv)[4], uint32_t& count, uint32_t& changed) {
+    constexpr bool METRES = std::is_same<Depth, DepthM>::value;
     const int lx = (lane & 1) * 4, ly = (lane >> 1) & 7, lz = lane >> 4;
-    const int bx = b % c.nb[0], by = (b / c.nb[0]) % c.nb[1], bz = b / (c.nb[0] * c.nb[1]);
-    float* Fb = vol.F + (size_t)b * BRICK_VOX + lane * 4;
-    uint8_t* Wb = vol.W + (size_t)b * BRICK_VOX + lane * 4;
-    const int gx0 = bx * BRICK + lx, gy = by * BRICK + ly;
+    float* Fb = vol.F + (size_t)at.b * BRICK_VOX + lane * 4;
+    uint8_t* Wb = vol.W + (size_t)at.b * BRICK_VOX + lane * 4;
+    const int gx0 = at.bx * BRICK + lx, gy = at.by * BRICK + ly;
     const bool yin = gy < c.ng[1];
     const float py = fmaf((float)gy + 0.5f, c.s_g, c.origin[1]);
-    float px[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) px[i] = fmaf((float)(gx0 + i) + 0.5f, c.s_g, c.origin[0]);
-    const float2 pxp[2] = {make_float2(px[0], px[1]), make_float2(px[2], px[3])};
+    // voxel centres (index + 1/2) s + origin; the integer + 1/2 sums below are exact
+    const float gxf = (float)gx0;
+    const float2 pxp[2] = {make_float2(fmaf(gxf + 0.5f, c.s_g, c.origin[0]), fmaf(gxf + 1.5f, c.s_g, c.origin[0])),
+                           make_float2(fmaf(gxf + 2.5f, c.s_g, c.origin[0]), fmaf(gxf + 3.5f, c.s_g, c.origin[0]))};
+    const float gzf = (float)(at.bz * BRICK + lz + c.zoff_g) + 0.5f;  // centre at the global index
     const uint32_t maxw = (uint32_t)c.max_weight, maxw4 = maxw * 0x01010101u;
     // min / max of F over this lane's observed voxels: all of them, and those
     // on the brick faces (band flags): this lane's x face is its voxel i = 0
@@ -390,64 +463,77 @@ __device__ __forceinline__ void geometry_update(const FrameConst& c, const Volum
     const float qnan = __int_as_float(0x7fffffff);
     float fmn = FLT_MAX, fmx = -FLT_MAX, mn_xf = FLT_MAX, mx_xf = -FLT_MAX, mn_zf = FLT_MAX, mx_zf = -FLT_MAX;
     bool unobserved = false, below_cap = false;  // after the update, over this lane's in-volume voxels
-    uint32_t nupd = 0;
+    uint32_t upd = 0;                            // updated voxels of this lane, bit 4 j + i
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const int gz = bz * BRICK + lz + 2 * j;
+        const int gz = at.bz * BRICK + lz + 2 * j;
         const bool zin = yin && gz < c.ng[2];
-        const float pz = fmaf((float)(gz + c.zoff_g) + 0.5f, c.s_g, c.origin[2]);  // centre at the global index
+        const float pz = fmaf(gzf + (float)(2 * j), c.s_g, c.origin[2]);
         const float2 B0 = f2(fmaf(c.R[1], py, fmaf(c.R[2], pz, c.t[0])));
         const float2 B1 = f2(fmaf(c.R[4], py, fmaf(c.R[5], pz, c.t[1])));
         const float2 B2 = f2(fmaf(c.R[7], py, fmaf(c.R[8], pz, c.t[2])));
         const float fin[4] = {f[j].x, f[j].y, f[j].z, f[j].w};
         float fv[4], fo[4];
         const uint32_t w_old = wv[j];
-        uint32_t inc = 0, upm = 0, inside = 0xFFFFFFFFu;
+        uint32_t upm = 0, inside = 0xFFFFFFFFu;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {  // voxel pair i = 2h, 2h + 1
             const float2 X = __ffma2_rn(f2(c.R[0]), pxp[h], B0);
             const float2 Y = __ffma2_rn(f2(c.R[3]), pxp[h], B1);
             const float2 Z = __ffma2_rn(f2(c.R[6]), pxp[h], B2);
-            int pix[2];
-            bool ok[2];
+            uint32_t pix[2];
+            bool ok[2], valid[2];
             depth_pixels<PINHOLE, INNER>(c, X, Y, Z, pix, ok);
-            bool seen[2];
-            uint32_t D[2], w[2];
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 const int i = 2 * h + k;
-                const bool valid = ALIGNED || (zin && gx0 + i < c.ng[0]);  // ALIGNED: dims are multiples of 8
-                if (!valid) inside &= ~(0xFFu << (8 * i));
-                seen[k] = ok[k] && valid;
-                D[k] = __ldg(depth + pix[k]);  // pixel 0 when not seen: read, then ignored
-                w[k] = (w_old >> (8 * i)) & 0xFFu;
+                valid[k] = ALIGNED || (zin && gx0 + i < c.ng[0]);  // ALIGNED: dims are multiples of 8
+                if (!valid[k]) inside &= ~(0xFFu << (8 * i));
             }
-            const float2 d = __fmul2_rn(make_float2((float)D[0], (float)D[1]), f2(0.001f));
+            float2 d;
+            bool has[2];  // a depth the update may use (the metres image holds -inf where D = 0)
+            if constexpr (METRES) {
+                d = make_float2(__ldg(depth.p + pix[0]), __ldg(depth.p + pix[1]));
+                has[0] = ok[0] && valid[0];
+                has[1] = ok[1] && valid[1];
+            } else {
+                // RN(D * 0.001) as fmaf(2^23 + D, 0.001, -2^23 * 0.001): the product is exact
+                // inside the fma and 2^23 * 0.001f is a power-of-two scaling, so one rounding
+                const uint32_t D0 = __ldg(depth.p + pix[0]), D1 = __ldg(depth.p + pix[1]);
+                d = __ffma2_rn(make_float2(__uint_as_float(0x4B000000u | D0), __uint_as_float(0x4B000000u | D1)),
+                               f2(0.001f), f2(-8388608.0f * 0.001f));
+                has[0] = ok[0] && valid[0] && D0 != 0u;
+                has[1] = ok[1] && valid[1] && D1 != 0u;
+            }
             const float2 sdf = __ffma2_rn(Z, f2(-1.0f), d);  // d - Z, rounded once
             const float2 tq = __fmul2_rn(sdf, f2(c.inv_mu));
             const float2 t = make_float2(fminf(1.0f, tq.x), fminf(1.0f, tq.y));
-            const float2 wf = make_float2((float)w[0], (float)w[1]);
+            // w as binary32 from its byte: the bits 0x4B0000ww are 2^23 + w
+            const uint32_t wb0 = __byte_perm(w_old, 0x4B000000u, 0x7440u + 2 * h);
+            const uint32_t wb1 = __byte_perm(w_old, 0x4B000000u, 0x7441u + 2 * h);
+            const float2 wbf = make_float2(__uint_as_float(wb0), __uint_as_float(wb1));
+            const float2 wf = __fadd2_rn(wbf, f2(-8388608.0f));               // w, exact
+            const float2 nb = __ffma2_rn(wbf, f2(-1.0f), f2(8388607.0f));     // -(w + 1), exact
+            const float2 y = make_float2(rcp[wb0 & 0xFFu], rcp[wb1 & 0xFFu]);  // RN(1 / (w + 1))
             // F <- fmaf(F, w, t) / (w + 1), the quotient by div_by_weight's steps
             const float2 a = __ffma2_rn(make_float2(fin[2 * h], fin[2 * h + 1]), wf, t);
-            const float2 nb = __ffma2_rn(wf, f2(-1.0f), f2(-1.0f));  // -(w + 1), exact
-            const float2 y = make_float2(rcp[w[0]], rcp[w[1]]);
             const float2 q = __fmul2_rn(a, y);
             const float2 r = __ffma2_rn(nb, q, a);
             const float2 fn = __ffma2_rn(r, y, q);
             const float sd[2] = {sdf.x, sdf.y}, fnew[2] = {fn.x, fn.y};
+            const uint32_t wb[2] = {wb0, wb1};
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 const int i = 2 * h + k;
-                const bool up = seen[k] && D[k] != 0u && !(sd[k] < -c.mu) && (FREE_SPACE || !(sd[k] > c.mu));
+                const bool up = has[k] && !(sd[k] < -c.mu) && (FREE_SPACE || !(sd[k] > c.mu));
                 fv[i] = up ? fnew[k] : fin[i];
-                // w <- min(w + 1, max_weight): a byte below the cap gains 1 (no carry)
-                inc |= up && w[k] < maxw ? 1u << (8 * i) : 0u;
                 upm |= up ? 1u << i : 0u;
-                const bool valid = ALIGNED || (zin && gx0 + i < c.ng[0]);
-                fo[i] = (up || w[k] != 0u) && valid ? fv[i] : qnan;  // observed after the update
+                fo[i] = (up || wb[k] != 0x4B000000u) && valid[k] ? fv[i] : qnan;  // observed after the update
             }
         }
-        const uint32_t wn = w_old + inc;
+        // w <- min(w + 1, max_weight): +1 in the updated bytes that are below the cap
+        const uint32_t upb = (upm * 0x00204081u) & 0x01010101u;  // bit i of upm -> byte i
+        const uint32_t wn = w_old + (upb & ~zero_bytes(w_old ^ maxw4));
         // in-volume voxels only: a byte outside the volume reads as observed and at the cap
         const uint32_t wq = ALIGNED ? wn : (wn & inside) | (maxw4 & ~inside);
         unobserved = unobserved || any_zero_byte(wq);
@@ -464,15 +550,15 @@ __device__ __forceinline__ void geometry_update(const FrameConst& c, const Volum
             mn_zf = gmn;
             mx_zf = gmx;
         }
-        nupd += __popc(upm);
+        upd |= upm << (4 * j);
         if (upm) {
             *reinterpret_cast<float4*>(Fb + 128 * j) = make_float4(fv[0], fv[1], fv[2], fv[3]);
             *reinterpret_cast<uint32_t*>(Wb + 128 * j) = wn;
         }
     }
-    count += nupd;
+    count += __popc(upd);
     // bricks where nothing changed keep their summary
-    if (!__any_sync(0xffffffffu, nupd != 0u)) return;
+    if (!__any_sync(0xffffffffu, upd != 0u)) return;
     ++changed;
     // band flags (see BrickSummary): this lane's voxels sit at x = lx + i,
     // y = ly, z = lz + 2 j, so it holds the -x face when lx = 0, +x when
@@ -484,11 +570,8 @@ __device__ __forceinline__ void geometry_update(const FrameConst& c, const Volum
     const uint32_t xf = lohi(true, mn_xf, mx_xf), zf = lohi(true, mn_zf, mx_zf);
     uint32_t bflags = lohi(true, fmn, fmx) | (lx == 0 ? xf << 2 : xf << 4) | lohi(ly == 0, fmn, fmx) << 6 |
                       lohi(ly == 7, fmn, fmx) << 8 | (lz == 0 ? zf << 10 : zf << 12);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        fmn = fminf(fmn, __shfl_xor_sync(0xffffffffu, fmn, o));
-        fmx = fmaxf(fmx, __shfl_xor_sync(0xffffffffu, fmx, o));
-    }
+    fmn = warp_min(fmn);
+    fmx = warp_max(fmx);
     unobserved = __any_sync(0xffffffffu, unobserved);
     below_cap = __any_sync(0xffffffffu, below_cap);
     bflags = __reduce_or_sync(0xffffffffu, bflags);
@@ -498,17 +581,18 @@ __device__ __forceinline__ void geometry_update(const FrameConst& c, const Volum
         sm.fmax = fmx == -FLT_MAX ? __int_as_float(0xff800000) : fmx;
         sm.wmin = unobserved ? 0u : (below_cap ? maxw - 1u : maxw);
         sm.flags = bflags;
-        vol.summ[b] = sm;
+        vol.summ[at.b] = sm;
     }
 }
 
-// The same with F and w read from the volume.
-template <bool PINHOLE, bool FREE_SPACE, bool ALIGNED = false, bool INNER = false>
-__device__ __forceinline__ void geometry_brick(const FrameConst& c, const Volumes& vol,
-                                               const uint16_t* __restrict__ depth, const float* rcp, uint32_t b,
-                                               int lane, uint32_t& count, uint32_t& changed) {
-    const float* Fb = vol.F + (size_t)b * BRICK_VOX + lane * 4;
-    const uint8_t* Wb = vol.W + (size_t)b * BRICK_VOX + lane * 4;
+// The same with F and w read from the volume: all four groups' loads are
+// issued before the first update (the stores of a group could otherwise hold
+// back the next group's loads).
+template <bool PINHOLE, bool FREE_SPACE, bool ALIGNED = false, bool INNER = false, typename Depth>
+__device__ __forceinline__ void geometry_brick(const FrameConst& c, const Volumes& vol, Depth depth, const float* rcp,
+                                               const BrickAt& at, int lane, uint32_t& count, uint32_t& changed) {
+    const float* Fb = vol.F + (size_t)at.b * BRICK_VOX + lane * 4;
+    const uint8_t* Wb = vol.W + (size_t)at.b * BRICK_VOX + lane * 4;
     float4 f[4];
     uint32_t wv[4];
 #pragma unroll
@@ -516,11 +600,11 @@ __device__ __forceinline__ void geometry_brick(const FrameConst& c, const Volume
         f[j] = *reinterpret_cast<const float4*>(Fb + 128 * j);
         wv[j] = *reinterpret_cast<const uint32_t*>(Wb + 128 * j);
     }
-    geometry_update<PINHOLE, FREE_SPACE, ALIGNED, INNER>(c, vol, depth, rcp, b, lane, f, wv, count, changed);
+    geometry_update<PINHOLE, FREE_SPACE, ALIGNED, INNER>(c, vol, depth, rcp, at, lane, f, wv, count, changed);
 }
 
 template <bool PINHOLE, bool FREE_SPACE, bool ALIGNED>
-__global__ void __launch_bounds__(GEO_THREADS, 8) k_geometry(FrameConst c, Volumes vol, const uint16_t* __restrict__ depth,
+__global__ void __launch_bounds__(GEO_THREADS, 8) k_geometry(FrameConst c, Volumes vol, const float* __restrict__ depth_m,
                                                           Counters* __restrict__ ctr,
                                                           const uint32_t* __restrict__ list) {
     __shared__ float rcp[256];
@@ -541,17 +625,18 @@ __global__ void __launch_bounds__(GEO_THREADS, 8) k_geometry(FrameConst c, Volum
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t n = ctr->n_geo;
+    const DepthM depth{depth_m};
     uint32_t count = 0, changed = 0;
     // the list is taken from its end: the colour kernels that follow walk
     // their lists from the front, whose bricks are then the ones this kernel
     // wrote last (measured: 1 % off the frame)
     for (uint32_t item = warp; item < n; item += nwarps) {
         const uint32_t e = list[n - 1u - item];
+        const BrickAt at = geo_brick(c, e);
         if (e & GEO_INNER)  // the brick projects wholly into the image: no per-voxel image tests
-            geometry_brick<PINHOLE, FREE_SPACE, ALIGNED, true>(c, vol, depth, rcp, e & ~GEO_INNER, lane, count,
-                                                               changed);
+            geometry_brick<PINHOLE, FREE_SPACE, ALIGNED, true>(c, vol, depth, rcp, at, lane, count, changed);
         else
-            geometry_brick<PINHOLE, FREE_SPACE, ALIGNED>(c, vol, depth, rcp, e, lane, count, changed);
+            geometry_brick<PINHOLE, FREE_SPACE, ALIGNED, false>(c, vol, depth, rcp, at, lane, count, changed);
     }
     count = __reduce_add_sync(0xffffffffu, count);
     if (lane == 0 && count) atomicAdd(&ctr->geo_updated, (unsigned long long)count);
@@ -578,13 +663,13 @@ cudaError_t launch_chained(void (*kernel)(Params...), dim3 grid, dim3 block, siz
 
 // Launch the k_geometry instance for this frame's camera model, free-space
 // mode and volume shape (every dimension a multiple of 8: no bounds tests).
-cudaError_t launch_k_geometry(const FrameConst& c, const Volumes& v, const Scratch& s, const uint16_t* depth,
-                              int grid, cudaStream_t stream) {
+// It reads the depth in metres that this frame's k_depth_tiles wrote.
+cudaError_t launch_k_geometry(const FrameConst& c, const Volumes& v, const Scratch& s, int grid, cudaStream_t stream) {
     const bool aligned = c.ng[0] % BRICK == 0 && c.ng[1] % BRICK == 0 && c.ng[2] % BRICK == 0;
     const int key = (c.kd_pinhole ? 4 : 0) | (c.free_space ? 2 : 0) | (aligned ? 1 : 0);
     switch (key) {
 #define TSDF_GEO_CASE(k, P, F, A) \
-    case k: return launch_chained(k_geometry<P, F, A>, dim3(grid), dim3(GEO_THREADS), 0, stream, c, v, depth, \
+    case k: return launch_chained(k_geometry<P, F, A>, dim3(grid), dim3(GEO_THREADS), 0, stream, c, v, s.depth_m, \
                                   s.ctr, s.geo_list);
         TSDF_GEO_CASE(0, false, false, false)
         TSDF_GEO_CASE(1, false, false, true)
@@ -1451,7 +1536,7 @@ __global__ void __launch_bounds__(COL_THREADS, 4) k_batch_step(const ScanDesc* _
         const uint32_t nbt = (uint32_t)d.c.nb[0] * d.c.nb[1] * d.c.nb[2];
         bool geo, vis, inner;
         brick_flags(d.c, d.vol.summ, d.scr.depth_tiles, b, b < nbt, geo, vis, inner);
-        append(geo, b | (inner ? GEO_INNER : 0u), &d.scr.ctr->n_geo, d.scr.geo_list);
+        append(geo, geo_entry(d.c, b, inner), &d.scr.ctr->n_geo, d.scr.geo_list);
         append(vis, b, &d.scr.ctr->n_vis, d.scr.vis_list);
     }
     if (!grid_barrier(sync, gridDim.x)) return;
@@ -1464,15 +1549,16 @@ __global__ void __launch_bounds__(COL_THREADS, 4) k_batch_step(const ScanDesc* _
         const uint32_t k0 = (item - pre[s]) * tile, k1 = min(k0 + (uint32_t)tile, d.scr.ctr->n_geo);
         uint32_t count = 0, changed = 0;
         for (uint32_t k = k0; k < k1; ++k) {
-            const uint32_t b = d.scr.geo_list[k] & ~GEO_INNER;  // the general form handles every brick
+            const BrickAt at = geo_brick(d.c, d.scr.geo_list[k]);  // the general form handles every brick
+            const DepthMm dm{d.depth};
             if (d.c.kd_pinhole && d.c.free_space)
-                geometry_brick<true, true>(d.c, d.vol, d.depth, rcp, b, lane, count, changed);
+                geometry_brick<true, true>(d.c, d.vol, dm, rcp, at, lane, count, changed);
             else if (d.c.kd_pinhole)
-                geometry_brick<true, false>(d.c, d.vol, d.depth, rcp, b, lane, count, changed);
+                geometry_brick<true, false>(d.c, d.vol, dm, rcp, at, lane, count, changed);
             else if (d.c.free_space)
-                geometry_brick<false, true>(d.c, d.vol, d.depth, rcp, b, lane, count, changed);
+                geometry_brick<false, true>(d.c, d.vol, dm, rcp, at, lane, count, changed);
             else
-                geometry_brick<false, false>(d.c, d.vol, d.depth, rcp, b, lane, count, changed);
+                geometry_brick<false, false>(d.c, d.vol, dm, rcp, at, lane, count, changed);
         }
         count = __reduce_add_sync(full, count);
         if (lane == 0) {
@@ -1590,7 +1676,7 @@ cudaError_t launch_frame_pre(const FrameConst& c, const Volumes& v, const Scratc
     mark(0);
     const dim3 tg((c.tiles_x + 1) / 2, (c.tiles_y + 1) / 2);
     cudaError_t e = launch_chained(k_depth_tiles, tg, dim3(TILE_BLOCK_PX, TILE_BLOCK_PX), 0, stream, c, depth, s.depth_tiles,
-                                   s.ctr);
+                                   s.ctr, s.depth_m);
     mark(1);
     const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
     if (e == cudaSuccess)
@@ -1607,7 +1693,7 @@ cudaError_t launch_frame_post(const FrameConst& c, const Volumes& v, const Scrat
         if (ev && ev[i]) cudaEventRecord(ev[i], stream);
     };
     const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
-    cudaError_t e = launch_k_geometry(c, v, s, depth, g.geo, stream);
+    cudaError_t e = launch_k_geometry(c, v, s, g.geo, stream);
     mark(3);
     unsigned gl = (nbt + LIST_THREADS - 1) / LIST_THREADS;
     if (gl > 1024u) gl = 1024u;
@@ -1636,7 +1722,7 @@ cudaError_t launch_frame(const FrameConst& c, const Volumes& v, const Scratch& s
 cudaError_t launch_geometry_static(const FrameConst& c, float* F, uint8_t* W, const uint16_t* depth, Counters* ctr,
                                    uint32_t* tiles, uint32_t* geo_list, int grid_geo, cudaStream_t stream) {
     const dim3 tg((c.tiles_x + 1) / 2, (c.tiles_y + 1) / 2);
-    k_depth_tiles<<<tg, dim3(TILE_BLOCK_PX, TILE_BLOCK_PX), 0, stream>>>(c, depth, tiles, ctr);
+    k_depth_tiles<<<tg, dim3(TILE_BLOCK_PX, TILE_BLOCK_PX), 0, stream>>>(c, depth, tiles, ctr, nullptr);
     const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
     k_bricks_static<<<(nbt + 255) / 256, 256, 0, stream>>>(c, tiles, ctr, geo_list);
     if (c.kd_pinhole && c.free_space)
@@ -1653,11 +1739,11 @@ cudaError_t launch_geometry_static(const FrameConst& c, float* F, uint8_t* W, co
 cudaError_t launch_frame_record(const FrameConst& c, const Volumes& v, const Scratch& s, const uint16_t* depth,
                                 const LaunchGrids& g, const AdjBuffers& a, int frame, cudaStream_t stream) {
     const dim3 tg((c.tiles_x + 1) / 2, (c.tiles_y + 1) / 2);
-    k_depth_tiles<<<tg, dim3(TILE_BLOCK_PX, TILE_BLOCK_PX), 0, stream>>>(c, depth, s.depth_tiles, s.ctr);
+    k_depth_tiles<<<tg, dim3(TILE_BLOCK_PX, TILE_BLOCK_PX), 0, stream>>>(c, depth, s.depth_tiles, s.ctr, s.depth_m);
     const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
     k_bricks<<<(nbt + BRICK_THREADS - 1) / BRICK_THREADS, BRICK_THREADS, 0, stream>>>(c, v.summ, s.depth_tiles, s.ctr,
                                                                                      s.geo_list, s.vis_list);
-    launch_k_geometry(c, v, s, depth, g.geo, stream);
+    launch_k_geometry(c, v, s, g.geo, stream);
     unsigned gl = (nbt + LIST_THREADS - 1) / LIST_THREADS;
     if (gl > 1024u) gl = 1024u;
     k_colour_list<<<gl, LIST_THREADS, 0, stream>>>(c, v.summ, s.ctr, s.vis_list, s.col_list);

@@ -160,6 +160,7 @@ void frame_constants(const tsdf_volume* v, const float Kd[9], const float Kr[9],
     c.band = v->band;
     c.dw = dw;
     c.dh = dh;
+    c.pix_bias = 0x4B000000u * (uint32_t)(dw + 1);
     c.cw = cw;
     c.ch = ch;
     c.tiles_x = (dw + TILE_PX - 1) / TILE_PX;
@@ -255,14 +256,20 @@ tsdf_status stage_depth(tsdf_volume* v, const uint16_t* depth_mm, tsdf_image_siz
         if (e != cudaSuccess) return cuda_fail(v, e, "depth upload");
         *d_depth = v->d_depth;
     }
-    const size_t tbytes = (size_t)tiles * sizeof(uint32_t);
-    if (v->depth_tiles_cap < tbytes) {
+    return depth_scratch(v, (size_t)tiles, dsz);
+}
+
+tsdf_status depth_scratch(tsdf_volume* v, size_t tiles, tsdf_image_size dsz) {
+    const size_t tbytes = (tiles * sizeof(uint32_t) + 15) & ~(size_t)15;
+    const size_t bytes = tbytes + (size_t)dsz.width * dsz.height * sizeof(float);
+    if (v->depth_tiles_cap < bytes) {
         dev_free(v, v->depth_tiles);
-        v->depth_tiles = (uint32_t*)dev_alloc(v, tbytes);
-        v->depth_tiles_cap = v->depth_tiles ? tbytes : 0;
+        v->depth_tiles = (uint32_t*)dev_alloc(v, bytes);
+        v->depth_tiles_cap = v->depth_tiles ? bytes : 0;
         if (!v->depth_tiles) return fail(v, TSDF_ERR_OOM, "depth tile buffer");
     }
     v->scr.depth_tiles = v->depth_tiles;
+    v->scr.depth_m = reinterpret_cast<float*>(reinterpret_cast<char*>(v->depth_tiles) + tbytes);
     return TSDF_OK;
 }
 
@@ -685,14 +692,8 @@ tsdf_status tsdf_integrate(tsdf_volume* v, const uint16_t* depth_mm, tsdf_image_
         if (e != cudaSuccess) return cuda_fail(v, e, "frame pipeline");
     }
     v->stats_pending = false;
-    const size_t tiles = (size_t)c.tiles_x * c.tiles_y * sizeof(uint32_t);
-    if (v->depth_tiles_cap < tiles) {
-        dev_free(v, v->depth_tiles);
-        v->depth_tiles = (uint32_t*)dev_alloc(v, tiles);
-        v->depth_tiles_cap = v->depth_tiles ? tiles : 0;
-        if (!v->depth_tiles) return fail(v, TSDF_ERR_OOM, "depth tile buffer");
-    }
-    v->scr.depth_tiles = v->depth_tiles;
+    const tsdf_status ds = depth_scratch(v, (size_t)c.tiles_x * c.tiles_y, dsz);
+    if (ds != TSDF_OK) return ds;
     // boundary k + 1 (after phase k, before phase k + 1) is recorded when either side is timed
     cudaEvent_t marks[TSDF_PHASE_COUNT];
     for (int k = 0; k < TSDF_PHASE_COUNT; ++k)
