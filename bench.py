@@ -52,6 +52,9 @@ def parse():
                          "(one persistent launch per frame) | raycast (640x480 casts of the scan volumes) | "
                          "mesh (mesh + texture maps of the scan volumes) | track (ICP camera tracking)")
     ap.add_argument("--dense", action="store_true", help="culling off (dense sweep of every brick)")
+    ap.add_argument("--schedule", default="kernels", choices=["kernels", "fused"],
+                    help="scan workloads: how a frame runs (tsdf_set_frame_schedule): the kernel chain or one "
+                         "fused launch for geometry, colour candidates and band gate")
     ap.add_argument("--shard", default="scans", choices=["scans", "slab"],
                     help="N > 1: an independent scan per GPU (weak scaling, the default) or one scan split into "
                          "z-slabs over the GPUs (strong scaling; each GPU holds 1/N of both volumes)")
@@ -218,6 +221,11 @@ def oracle_sample(seq, frames, n_threads):
     return nvox * len(frames) / dt, dt, desc
 
 
+def schedule_of(args):
+    import paper_1602_06645_gb300 as T
+    return T.TSDF_SCHEDULE_FUSED if args.schedule == "fused" else T.TSDF_SCHEDULE_KERNELS
+
+
 def scan_config(seq, args, world, sliced):
     """Whether the scan frames are timed one by one with L2 flushed, and the
     config of the plain-scan line; both arms print this config."""
@@ -231,7 +239,7 @@ def scan_config(seq, args, world, sliced):
     return per_step_flush, {
         "workload": seq.name, "dims_geo": list(seq.dims_geo), "dims_col": list(seq.dims_col),
         "depth": "%dx%d" % seq.depth_size, "rgb": "%dx%d" % seq.rgb_size, "frames": args.steps,
-        "culling": not args.dense, "l2": l2_note,
+        "culling": not args.dense, "schedule": args.schedule, "l2": l2_note,
         "parallelism": ("z-slabs of one scan over the GPUs" if sliced else
                         "independent scan per GPU" if world > 1 else "single GPU")}
 
@@ -297,7 +305,7 @@ def run_ours(args):
 
     def volume():
         return T.Volume(seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, seq.max_weight, culling=not args.dense,
-                        stream=stream.cuda_stream, slab=slab)
+                        stream=stream.cuda_stream, slab=slab, schedule=schedule_of(args))
 
     # Phase breakdown: the same frames through a separate volume with every
     # phase timed (eight event records per frame), before the timed run.
@@ -379,6 +387,8 @@ def run_ours(args):
     band_bytes = 5.0 * 1000 * st.total_col_bricks / K       # geometry tile (10^3 F + w) per candidate brick
     vox_bytes = 8.0 * st.total_col_updated / K              # packed RGBW, read and written
     kern_bytes = {"geometry": geo_bytes, "colour_band": band_bytes, "colour_voxels": vox_bytes}
+    if args.schedule == "fused":  # one launch does the geometry update and the band gate
+        kern_bytes["geometry"] = geo_bytes + band_bytes
     ms_launch, bytes_launch = phases[kernel_phase[dom]] / max(pframes, 1), kern_bytes[dom]
     achieved = bytes_launch / (ms_launch / 1e3) / 1e9 if ms_launch > 0 else 0.0
     # DRAM traffic from the committed ncu capture, scaled to this launch by the
@@ -390,7 +400,8 @@ def run_ours(args):
             tr = json.load(f)
         with open(os.path.join(ROOT, "paper_1602_06645_gb300", "csrc", "kernels_fusion.cu"), "rb") as f:
             same_src = hashlib.sha256(f.read()).hexdigest() == tr.get("kernels_fusion_sha256")
-        if tr.get("workload") == seq.name and tr.get("kernel") == dom == "geometry" and same_src and not args.dense:
+        if (tr.get("workload") == seq.name and tr.get("kernel") == dom == "geometry" and same_src and not args.dense
+                and args.schedule == "kernels"):
             traffic = tr["bytes_per_unit"] * st.total_geo_updated / K
             traffic_note = "ncu dram bytes per updated voxel (%s) x updated voxels per launch" % tr["source"]
     except (OSError, ValueError, KeyError):
@@ -412,12 +423,16 @@ def run_ours(args):
         "phase_ms_per_frame": {k: v / max(all_frames, 1) for k, v in all_phases.items()},
         "phase_timing": "separate pass over the same frames with every phase timed; the timed run times only "
                         "the dominant kernel",
-        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+        "roofline": {"kernel": ("k_fused (geometry update, colour candidates, band gate)"
+                               if args.schedule == "fused" and dom == "geometry" else dom),
+                     "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": traffic, "traffic_source": traffic_note,
                      "bytes_per_launch": bytes_launch,
                      "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                      else "fallback 6.8 TB/s"},
-        "gpu_launches": 6 * args.steps,  # depth tiles, bricks, geometry, colour list, colour cells, colour voxels
+        # depth tiles, bricks, geometry, colour list, colour cells, colour voxels; fused: depth tiles,
+        # bricks, neighbour counts, k_fused, colour voxels
+        "gpu_launches": (5 if args.schedule == "fused" else 6) * args.steps,
         "clocks": clocks,
         "frame_generation_s": gen_s,
     }
@@ -426,7 +441,7 @@ def run_ours(args):
     if not args.no_e2e:
         host = [(torch.from_numpy(d.view(np.int16)).pin_memory(), torch.from_numpy(c).pin_memory()) for d, c in frames]
         vol2 = T.Volume(seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, seq.max_weight, culling=not args.dense,
-                        stream=stream.cuda_stream, slab=slab)
+                        stream=stream.cuda_stream, slab=slab, schedule=schedule_of(args))
         # each step: upload and integrate frame i, queue the read of its
         # counters, then wait for frame i - 1's counters (a one-frame-deep
         # pipeline: the host queues frame i while frame i - 1 finishes); the

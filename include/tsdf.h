@@ -164,8 +164,31 @@ tsdf_status tsdf_integrate(tsdf_volume* vol, const uint16_t* depth_mm, tsdf_imag
                            tsdf_image_size csz, const float K_depth[9], const float K_rgb[9],
                            const float T_world_depth[16], const float T_depth_rgb[16]);
 
-/* Copy the volumes out, linear x-fastest (Section IV.B: "the new RGB value and
- * weight are saved in the colour voxel").  Each destination may be NULL (not
+/* How tsdf_integrate runs a frame (same results either way, bit for bit).
+ *   TSDF_SCHEDULE_KERNELS  a chain of kernels: depth tiles, brick culling,
+ *       geometry update, colour candidates, band gate, colour voxels.
+ *   TSDF_SCHEDULE_FUSED    the geometry update, colour-candidate test and band
+ *       gate in one persistent launch: the colour work of a visible brick
+ *       starts as soon as the geometry of its 27-neighbourhood is updated
+ *       (Section IV.B: the colour step reads the updated TSDF), beside the
+ *       geometry of other bricks; then the colour voxels.  A pinhole K_depth
+ *       is required (otherwise the frame runs as the kernel chain).  Its only
+ *       waits are bounded (1 s); one that gives up makes the next
+ *       synchronising call return TSDF_ERR_TIMEOUT (that frame's colour is
+ *       then incomplete; its geometry is not) and the next frame starts clean.
+ * The schedule applies from the next tsdf_integrate on.  Default: KERNELS.
+ * Errors: INVALID_ARG (NULL handle, unknown schedule). */
+enum { TSDF_SCHEDULE_KERNELS = 0, TSDF_SCHEDULE_FUSED = 1 };
+tsdf_status tsdf_set_frame_schedule(tsdf_volume* vol, int32_t schedule);
+tsdf_status tsdf_get_frame_schedule(const tsdf_volume* vol, int32_t* schedule);
+
+/* Test hook of the fused schedule's bounded waits: in the next fused frame
+ * one visible brick is never released, so the wait for it runs out (no
+ * fault, no trap); synchronous. */
+tsdf_status tsdf_fused_inject_stall(tsdf_volume* vol);
+
+/* Copy the volumes out, linear x-fastest (Section IV.B: each colour voxel
+ * stores its fused RGB value and weight).  Each destination may be NULL (not
  * read) or a host or device pointer of dims_geo product floats (tsdf), bytes
  * (w_geo) or dims_col product uint32 (rgbw); for a z-slab handle, of the held
  * ranges (dims_geo[0] * dims_geo[1] * (held_geo_z[1] - held_geo_z[0]) and

@@ -27,6 +27,7 @@ TSDF_ERR_DEVICE_FAULT = -5
 TSDF_ERR_IO = -6
 TSDF_COLOUR_COUNT, TSDF_COLOUR_PAPER_NORMAL = 0, 1
 TSDF_SAMPLE_NEAREST, TSDF_SAMPLE_BILINEAR = 0, 1
+TSDF_SCHEDULE_KERNELS, TSDF_SCHEDULE_FUSED = 0, 1
 
 # symbols include/tsdf.h declares (checked by the tests)
 EXPORTS = [
@@ -38,7 +39,8 @@ EXPORTS = [
     "tsdf_adjoint_destroy", "tsdf_batch_create", "tsdf_batch_integrate", "tsdf_batch_synchronize",
     "tsdf_batch_set_schedule", "tsdf_batch_get_schedule", "tsdf_batch_autotune", "tsdf_batch_inject_stall",
     "tsdf_batch_destroy", "tsdf_raycast", "tsdf_mesh", "tsdf_mesh_ex", "tsdf_texture_layout", "tsdf_texture_fill",
-    "tsdf_profile_phases", "tsdf_track_params_default", "tsdf_track",
+    "tsdf_profile_phases", "tsdf_track_params_default", "tsdf_track", "tsdf_set_frame_schedule",
+    "tsdf_get_frame_schedule", "tsdf_fused_inject_stall",
 ]
 PHASES = ["upload", "depth_tiles", "bricks", "geometry", "colour_list", "colour_cells", "colour"]
 
@@ -156,6 +158,9 @@ def load():
     lib.tsdf_read.argtypes = [vp, vp, vp, vp]
     lib.tsdf_write.argtypes = [vp, vp, vp, vp]
     lib.tsdf_synchronize.argtypes = [vp]
+    lib.tsdf_set_frame_schedule.argtypes = [vp, ctypes.c_int32]
+    lib.tsdf_get_frame_schedule.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
+    lib.tsdf_fused_inject_stall.argtypes = [vp]
     lib.tsdf_save.argtypes = [vp, ctypes.c_char_p]
     lib.tsdf_load.argtypes = [vp, ctypes.c_char_p]
     lib.tsdf_destroy.argtypes = [vp]
@@ -398,6 +403,20 @@ def tsdf_synchronize(h):
     _check(load().tsdf_synchronize(h), h)
 
 
+def tsdf_set_frame_schedule(h, schedule):
+    _check(load().tsdf_set_frame_schedule(h, int(schedule)), h)
+
+
+def tsdf_get_frame_schedule(h):
+    out = ctypes.c_int32()
+    _check(load().tsdf_get_frame_schedule(h, ctypes.byref(out)), h)
+    return out.value
+
+
+def tsdf_fused_inject_stall(h):
+    _check(load().tsdf_fused_inject_stall(h), h)
+
+
 def tsdf_save(h, path):
     _check(load().tsdf_save(h, str(path).encode()), h)
 
@@ -628,9 +647,11 @@ class Volume:
 
     def __init__(self, dims_geo, dims_col, voxel_size, mu, max_weight, *, origin=None, sigma=0.020, band=None,
                  colour_mode=TSDF_COLOUR_COUNT, sample_mode=TSDF_SAMPLE_NEAREST, culling=True,
-                 update_free_space=True, stream=None, torch_memory=True, slab=None):
+                 update_free_space=True, stream=None, torch_memory=True, slab=None, schedule=None):
         """slab = (z0, z1): hold the z-slab [z0, z1) of the volume (see
-        tsdf_create_ex); dims_geo / dims_col are the whole volume's."""
+        tsdf_create_ex); dims_geo / dims_col are the whole volume's.
+        schedule: TSDF_SCHEDULE_KERNELS or TSDF_SCHEDULE_FUSED (see
+        tsdf_set_frame_schedule); None keeps the library's default."""
         import torch
 
         self.dims_geo = tuple(int(v) for v in dims_geo)
@@ -657,6 +678,16 @@ class Volume:
         self.slab = (info.slab_z[0], info.slab_z[1])
         self.held_geo_z = (info.held_geo_z[0], info.held_geo_z[1])
         self.held_col_z = (info.held_col_z[0], info.held_col_z[1])
+        if schedule is not None:
+            tsdf_set_frame_schedule(self.h, schedule)
+
+    @property
+    def schedule(self):
+        return tsdf_get_frame_schedule(self.h)
+
+    @schedule.setter
+    def schedule(self, value):
+        tsdf_set_frame_schedule(self.h, value)
 
     def _held_shapes(self):
         gx, gy, _ = self.dims_geo

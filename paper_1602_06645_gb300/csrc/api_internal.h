@@ -62,6 +62,7 @@ struct tsdf_volume {
     uint8_t* d_rgb;
     size_t d_rgb_cap;
     int64_t frames;
+    int32_t schedule = TSDF_SCHEDULE_KERNELS;  // tsdf_set_frame_schedule
     int64_t device_bytes;
     std::string last_error;
     // phase timing (tsdf_profile_enable)

@@ -43,6 +43,8 @@ struct FrameConst {
     int32_t record_mode;   // 1: the band kernel only records (adjoint gate recording); no colour update
     int32_t zoff_g, zoff_c;  // z-slab: global z index of held geometry / colour z = 0 (whole volume: 0)
     uint32_t pix_bias;       // 0x4B000000 (dw + 1) mod 2^32: pixel index from the bits of u + 2^23, v + 2^23
+    uint32_t frame_tag;      // nonzero, different in consecutive frames: marks this frame's ready-queue entries
+    int32_t fused;           // 1: the frame runs as one fused launch (k_fused) instead of the kernel chain
 };
 
 // Min/max of F over observed voxels (w > 0) and min of w over the in-volume
@@ -96,6 +98,7 @@ enum : uint32_t {
     ERR_RECORD_OVERFLOW = 2u,  // gate recording: band records exceeded their buffer
     ERR_PAIR_OVERFLOW = 4u,    // gate recording: (frame, voxel) pairs exceeded their buffer
     ERR_SLOT_OVERFLOW = 8u,    // adjoint: more distinct voxels or frames per voxel than reserved
+    ERR_WAIT_TIMEOUT = 16u,    // fused frame: a bounded wait for ready colour work gave up
 };
 
 // Adjoint (photometric loss) buffers.
@@ -136,6 +139,10 @@ struct Scratch {
     uint32_t* col_list;
     uint32_t* depth_tiles;  // per 8x8 tile: min valid depth | max valid depth << 16
     float* depth_m;         // per pixel RN(D * 0.001) metres, -inf where D = 0
+    uint8_t* bstate;        // per brick, this frame: bit 0 = in the geometry list, bit 1 = visible
+    uint32_t* need;         // per visible brick: listed bricks among its 27 neighbours not yet updated
+    unsigned long long* ready;  // ready queue of the fused frame: frame_tag << 32 | brick
+    struct FuseSync* fsync;
     uint32_t* err;
     uint2* vox;           // colour voxels that passed the band gate this frame: x | y << 16, z
     uint32_t vox_cap;
@@ -173,11 +180,16 @@ cudaError_t launch_init_summaries(BrickSummary* summ, int64_t n, cudaStream_t st
 // culling, geometry, colour list, colour band and colour voxels.
 struct LaunchGrids {
     int geo, col, vox;  // persistent grid sizes (blocks) of the geometry and two colour kernels
+    int fuse;           // persistent grid size of k_fused (every block resident)
 };
 // The same frame in two parts: depth tiles and brick culling (which read only
 // the depth image, the brick summaries and the tile buffer) and the rest
 // from the geometry update on.  `list_done` (nullable) is recorded after the
 // colour list, the last reader of the brick lists and tiles of this frame.
+// With c.fused the pre part also counts each visible brick's listed
+// neighbours (k_need) and the post part runs k_fused (geometry, colour
+// candidates and band gate in one launch) and then the colour voxels;
+// `list_done` is then recorded after k_fused.
 cudaError_t launch_frame_pre(const FrameConst& c, const Volumes& v, const Scratch& s, const uint16_t* depth,
                              cudaStream_t stream, cudaEvent_t* ev);
 cudaError_t launch_frame_post(const FrameConst& c, const Volumes& v, const Scratch& s, const uint16_t* depth,
@@ -189,6 +201,7 @@ int geometry_blocks_per_sm();
 int geometry_linear_blocks_per_sm();  // k_geometry_linear (the allocation-free entry point)
 int colour_blocks_per_sm();
 int voxel_blocks_per_sm();
+int fused_blocks_per_sm();
 
 // Layout conversion between brick-major storage and linear x-fastest arrays,
 // for z in [z0, z1).  `dst`/`src` point at the slab's first element.
@@ -229,6 +242,15 @@ struct ScanDesc {
     Scratch scr;
     const uint16_t* depth;
     const uint8_t* rgb;
+};
+// Ready-queue counters of the fused frame (k_fused).
+struct FuseSync {
+    unsigned int head;   // queue entries taken
+    unsigned int tail;   // queue entries pushed
+    unsigned int stall;  // test injection: the next frame's count pass withholds one ready brick
+    unsigned int claim;  // frame tag of the block that resets this frame's colour-side counters
+    unsigned int open;   // frame tag once those counters are reset (colour work may start)
+    unsigned int pad[3];
 };
 // Grid barrier and work counters of the batched persistent kernel.
 struct BatchSync {

@@ -322,14 +322,24 @@ __device__ __forceinline__ BrickAt geo_brick(const FrameConst& c, uint32_t e) {
 
 constexpr int BRICK_THREADS = 64;  // small blocks: they fit beside the band kernel's blocks on an SM
 
+// Brick culling: the geometry work list and the visible list; for the fused
+// frame also each brick's state byte (listed, visible) and a fresh ready queue.
 __global__ void __launch_bounds__(BRICK_THREADS) k_bricks(FrameConst c, const BrickSummary* __restrict__ summ,
                                                 const uint32_t* __restrict__ tiles, Counters* __restrict__ ctr,
-                                                uint32_t* __restrict__ geo_list, uint32_t* __restrict__ vis_list) {
+                                                uint32_t* __restrict__ geo_list, uint32_t* __restrict__ vis_list,
+                                                uint8_t* __restrict__ bstate, FuseSync* __restrict__ fsync) {
     chain_enter();
     const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
     uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
     bool geo, vis, inner;
     brick_flags(c, summ, tiles, b, b < nbt, geo, vis, inner);
+    if (c.fused) {
+        if (b < nbt) bstate[b] = (uint8_t)((geo ? 1u : 0u) | (vis ? 2u : 0u));
+        if (b == 0) {
+            fsync->head = 0u;
+            fsync->tail = 0u;
+        }
+    }
     // geometry list entries carry the interior flag in bit 31
     block_append2<BRICK_THREADS>(geo, vis, geo_entry(c, b, inner), b, &ctr->n_geo, geo_list, &ctr->n_vis,
                                  vis_list);
@@ -1235,6 +1245,238 @@ __global__ void __launch_bounds__(256) k_colour_voxels(FrameConst c, Volumes vol
     if ((threadIdx.x & 31) == 0 && count) atomicAdd(&ctr->col_updated, (unsigned long long)count);
 }
 
+// ------------------------------------------------------- fused frame ----
+// The frame's geometry update, colour-candidate test and band gate in one
+// persistent launch (the colour voxels follow in k_colour_voxels).  A visible
+// brick's colour work reads the updated geometry of its 27-neighbourhood, so
+// it may start once every listed brick there has been updated: k_need counts
+// those per visible brick; each warp that finishes a brick's geometry
+// decrements its visible neighbours' counts, and the warp that brings a count
+// to zero pushes that brick on a ready queue.  Warps take at most one ready
+// brick after each of their own geometry bricks (so the colour work runs
+// beside the geometry), then, with their geometry done, the remaining ones.
+// Only that last part waits, and only for bricks that the geometry still
+// running will release; each wait is bounded (FUSE_WAIT_NS of %globaltimer or
+// FUSE_WAIT_SPINS polls), after which the warp records ERR_WAIT_TIMEOUT in the
+// handle's error word and stops.  Every block is resident (the grid is the
+// occupancy times the SM count).
+constexpr unsigned long long FUSE_WAIT_NS = 1000000000ull;  // 1 s
+constexpr unsigned FUSE_WAIT_SPINS = 1u << 26;
+
+__device__ __forceinline__ unsigned long long fuse_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Push brick b on this frame's ready queue (entries are tagged with the frame).
+__device__ __forceinline__ void fuse_push(const FrameConst& c, const Scratch& scr, uint32_t b) {
+    const uint32_t slot = atomicAdd(&scr.fsync->tail, 1u);
+    const unsigned long long v = (unsigned long long)c.frame_tag << 32 | b;
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(scr.ready + slot), "l"(v) : "memory");
+}
+
+// Wait (bounded) until this frame's colour-side counters are reset and queue
+// entry `slot` is written; b = its brick (all lanes).  Lane 0 polls with
+// plain loads and a growing sleep, then one fence orders the warp's later
+// reads after what it saw (acquire); false when the wait gave up.
+__device__ __forceinline__ bool fuse_take(const FrameConst& c, const Scratch& scr, uint32_t slot, uint32_t& b,
+                                          int lane) {
+    uint32_t got = 0, v_lo = 0;
+    if (lane == 0) {
+        const volatile unsigned long long* p = scr.ready + slot;
+        const volatile unsigned int* open = &scr.fsync->open;
+        const unsigned long long t0 = fuse_ns();
+        unsigned sleep = 32;
+        for (unsigned spins = 0;; ++spins) {
+            const unsigned long long v = *p;
+            if ((uint32_t)(v >> 32) == c.frame_tag && *open == c.frame_tag) {
+                v_lo = (uint32_t)v;
+                got = 1;
+                break;
+            }
+            if ((spins & 15u) == 15u && (fuse_ns() - t0 > FUSE_WAIT_NS || spins > FUSE_WAIT_SPINS)) break;
+            __nanosleep(sleep);
+            if (sleep < 1024) sleep *= 2;
+        }
+        if (got) __threadfence();
+    }
+    __syncwarp();
+    got = __shfl_sync(0xffffffffu, got, 0);
+    b = __shfl_sync(0xffffffffu, v_lo, 0);
+    return got != 0;
+}
+
+// Visible bricks: count the listed bricks among the 27 neighbours (itself
+// included); a brick with none is ready at once.  Test injection
+// (FuseSync::stall): the first visible brick gets one count that no warp
+// will release, so a wait for it runs out.
+__global__ void __launch_bounds__(256) k_need(FrameConst c, Scratch scr) {
+    chain_enter();
+    const uint32_t n = scr.ctr->n_vis;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t b = scr.vis_list[i];
+        const int bx = (int)(b % (uint32_t)c.nb[0]), by = (int)((b / (uint32_t)c.nb[0]) % (uint32_t)c.nb[1]),
+                  bz = (int)(b / ((uint32_t)c.nb[0] * (uint32_t)c.nb[1]));
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int k = 0; k < 27; ++k) {
+            const int x = bx + k % 3 - 1, y = by + (k / 3) % 3 - 1, z = bz + k / 9 - 1;
+            if (x >= 0 && y >= 0 && z >= 0 && x < c.nb[0] && y < c.nb[1] && z < c.nb[2])
+                cnt += scr.bstate[((size_t)z * c.nb[1] + y) * c.nb[0] + x] & 1u;
+        }
+        if (i == 0 && *(volatile unsigned*)&scr.fsync->stall) {
+            scr.fsync->stall = 0u;
+            ++cnt;
+        }
+        scr.need[b] = cnt;
+        if (cnt == 0u) fuse_push(c, scr, b);
+    }
+}
+
+// colour_candidate with one lane per neighbour (lane 13: the brick itself).
+__device__ __forceinline__ bool colour_candidate_warp(const FrameConst& c, const BrickSummary* __restrict__ summ,
+                                                      uint32_t b, int lane) {
+    if (!c.culling) return true;
+    const int bx = (int)(b % (uint32_t)c.nb[0]), by = (int)((b / (uint32_t)c.nb[0]) % (uint32_t)c.nb[1]),
+              bz = (int)(b / ((uint32_t)c.nb[0] * (uint32_t)c.nb[1]));
+    uint32_t m = 0;
+    if (lane < 27) {
+        const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+        const int x = bx + dx, y = by + dy, z = bz + dz;
+        if (x >= 0 && y >= 0 && z >= 0 && x < c.nb[0] && y < c.nb[1] && z < c.nb[2]) {
+            const uint32_t f = summ[((size_t)z * c.nb[1] + y) * c.nb[0] + x].flags;
+            if (dx == 0 && dy == 0 && dz == 0) {
+                m = f & 3u;
+            } else {
+                // the neighbour at -x touches with its +x face (bits 4-5), etc.
+                m = 3u;
+                if (dx) m &= f >> (dx < 0 ? 4 : 2);
+                if (dy) m &= f >> (dy < 0 ? 8 : 6);
+                if (dz) m &= f >> (dz < 0 ? 12 : 10);
+                m &= 3u;
+            }
+        }
+    }
+    return __reduce_or_sync(0xffffffffu, m) == 3u;
+}
+
+// After a warp's geometry update of brick `at`: release its visible
+// neighbours.  Each lane with one first fences (its F, w and summary stores,
+// and through the warp barrier the other lanes', before its decrement).
+__device__ __forceinline__ void fuse_release(const FrameConst& c, const Scratch& scr, const BrickAt& at, int lane) {
+    __syncwarp();
+    if (lane < 27) {
+        const int x = at.bx + lane % 3 - 1, y = at.by + (lane / 3) % 3 - 1, z = at.bz + lane / 9 - 1;
+        if (x >= 0 && y >= 0 && z >= 0 && x < c.nb[0] && y < c.nb[1] && z < c.nb[2]) {
+            const uint32_t nb = (uint32_t)(((size_t)z * c.nb[1] + y) * c.nb[0] + x);
+            if (scr.bstate[nb] & 2u) {
+                __threadfence();
+                if (atomicSub(&scr.need[nb], 1u) == 1u) {
+                    __threadfence();  // the other releases of nb happened before this one
+                    fuse_push(c, scr, nb);
+                }
+            }
+        }
+    }
+}
+
+// The colour work of one ready visible brick.
+__device__ __forceinline__ void fuse_colour(const FrameConst& c, const Volumes& vol, const uint16_t* __restrict__ depth,
+                                            const uint8_t* __restrict__ rgb, const Scratch& scr, ColourSlot& S,
+                                            uint32_t b, int lane, uint32_t& count, uint32_t& n_active,
+                                            uint32_t& n_cells, uint32_t& n_cand) {
+    if (!colour_candidate_warp(c, vol.summ, b, lane)) return;
+    ++n_cand;
+    band_brick(c, vol, depth, rgb, scr, S, b, lane, count, n_active, n_cells);
+    __syncwarp();
+}
+
+template <bool FREE_SPACE, bool ALIGNED>
+__global__ void __launch_bounds__(COL_THREADS, 5) k_fused(FrameConst c, Volumes vol, const uint16_t* __restrict__ depth,
+                                                         const uint8_t* __restrict__ rgb, Scratch scr) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ColourSlot& S = reinterpret_cast<ColourSlot*>(smem_raw)[threadIdx.x >> 5];
+    __shared__ float rcp[256];
+    fill_weight_reciprocals(rcp);
+    __syncthreads();
+    chain_enter();
+    const unsigned full = 0xffffffffu;
+    Counters* __restrict__ ctr = scr.ctr;
+    FuseSync* __restrict__ fs = scr.fsync;
+    if (threadIdx.x == 0 && atomicExch(&fs->claim, c.frame_tag) != c.frame_tag) {
+        // the first block: fold the previous frame's colour-side counters into
+        // the running totals, then let the colour work start
+        ctr->tot_col_updated += ctr->col_updated;
+        ctr->tot_col_bricks += ctr->n_col;
+        ctr->tot_cells += ctr->n_cells;
+        ctr->tot_col_active += ctr->n_col_active;
+        ctr->n_col = ctr->col_next = 0;
+        ctr->n_cells = ctr->n_vox = ctr->n_col_active = 0;
+        ctr->col_updated = 0ull;
+        __threadfence();
+        asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&fs->open), "r"(c.frame_tag) : "memory");
+    }
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t n = ctr->n_geo, nv = ctr->n_vis;
+    const DepthM dm{scr.depth_m};
+    uint32_t gcount = 0, changed = 0, count = 0, n_active = 0, n_cells = 0, n_cand = 0;
+    bool ok = true;
+    // own geometry bricks, in list order (about z order: the bricks whose
+    // neighbourhoods are complete follow the front), one ready colour brick
+    // after each when the queue holds one
+    for (uint32_t item = warp; item < n; item += nwarps) {
+        const uint32_t e = scr.geo_list[item];
+        const BrickAt at = geo_brick(c, e);
+        if (e & GEO_INNER)
+            geometry_brick<true, FREE_SPACE, ALIGNED, true>(c, vol, dm, rcp, at, lane, gcount, changed);
+        else
+            geometry_brick<true, FREE_SPACE, ALIGNED, false>(c, vol, dm, rcp, at, lane, gcount, changed);
+        fuse_release(c, scr, at, lane);
+        uint32_t slot = 0xFFFFFFFFu;
+        if (lane == 0) {
+            const uint32_t h = *(volatile unsigned*)&fs->head, t = *(volatile unsigned*)&fs->tail;
+            if (h < t && *(volatile unsigned*)&fs->open == c.frame_tag && atomicCAS(&fs->head, h, h + 1u) == h)
+                slot = h;
+        }
+        slot = __shfl_sync(full, slot, 0);
+        if (slot != 0xFFFFFFFFu) {
+            uint32_t b;
+            if (!fuse_take(c, scr, slot, b, lane)) {
+                ok = false;
+                break;
+            }
+            fuse_colour(c, vol, depth, rgb, scr, S, b, lane, count, n_active, n_cells, n_cand);
+        }
+    }
+    // the remaining ready bricks
+    while (ok) {
+        uint32_t slot = 0;
+        if (lane == 0) slot = atomicAdd(&fs->head, 1u);
+        slot = __shfl_sync(full, slot, 0);
+        if (slot >= nv) break;
+        uint32_t b;
+        if (!fuse_take(c, scr, slot, b, lane)) {
+            ok = false;
+            break;
+        }
+        fuse_colour(c, vol, depth, rgb, scr, S, b, lane, count, n_active, n_cells, n_cand);
+    }
+    if (!ok && lane == 0) atomicOr(scr.err, ERR_WAIT_TIMEOUT);
+    gcount = __reduce_add_sync(full, gcount);
+    count = __reduce_add_sync(full, count);
+    if (lane == 0) {  // changed, n_active, n_cells and n_cand are the same in every lane
+        if (gcount) atomicAdd(&ctr->geo_updated, (unsigned long long)gcount);
+        if (changed) atomicAdd(&ctr->n_geo_changed, changed);
+        if (count) atomicAdd(&ctr->col_updated, (unsigned long long)count);
+        if (n_active) atomicAdd(&ctr->n_col_active, n_active);
+        if (n_cells) atomicAdd(&ctr->n_cells, n_cells);
+        if (n_cand) atomicAdd(&ctr->n_col, n_cand);
+    }
+}
+
 // ------------------------------------------ caller-owned geometry volume ----
 // Culling for the allocation-free geometry entry point: the frustum, empty
 // footprint and hidden-behind tests of k_bricks, without the saturated
@@ -1662,6 +1904,12 @@ int colour_blocks_per_sm() {
     return n > 0 ? n : 1;
 }
 
+int fused_blocks_per_sm() {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<true, true>, COL_THREADS, colour_smem_bytes());
+    return n > 0 ? n : 1;
+}
+
 int voxel_blocks_per_sm() {
     int n = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_colour_voxels, 256, 0);
@@ -1681,7 +1929,12 @@ cudaError_t launch_frame_pre(const FrameConst& c, const Volumes& v, const Scratc
     const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
     if (e == cudaSuccess)
         e = launch_chained(k_bricks, dim3((nbt + BRICK_THREADS - 1) / BRICK_THREADS), dim3(BRICK_THREADS), 0, stream,
-                           c, v.summ, s.depth_tiles, s.ctr, s.geo_list, s.vis_list);
+                           c, v.summ, s.depth_tiles, s.ctr, s.geo_list, s.vis_list, s.bstate, s.fsync);
+    if (e == cudaSuccess && c.fused) {
+        unsigned gn = (nbt + 255) / 256;
+        if (gn > 1024u) gn = 1024u;
+        e = launch_chained(k_need, dim3(gn), dim3(256), 0, stream, c, s);
+    }
     mark(2);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -1693,19 +1946,33 @@ cudaError_t launch_frame_post(const FrameConst& c, const Volumes& v, const Scrat
         if (ev && ev[i]) cudaEventRecord(ev[i], stream);
     };
     const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
-    cudaError_t e = launch_k_geometry(c, v, s, g.geo, stream);
-    mark(3);
-    unsigned gl = (nbt + LIST_THREADS - 1) / LIST_THREADS;
-    if (gl > 1024u) gl = 1024u;
-    if (e == cudaSuccess)
-        e = launch_chained(k_colour_list, dim3(gl), dim3(LIST_THREADS), 0, stream, c, v.summ, s.ctr, s.vis_list,
-                           s.col_list);
-    if (list_done) cudaEventRecord(list_done, stream);
-    mark(4);
-    if (e == cudaSuccess)
-        e = launch_chained(k_colour_band, dim3(g.col), dim3(COL_THREADS), colour_smem_bytes(), stream, c, v, depth,
-                           rgb, s);
-    mark(5);
+    cudaError_t e = cudaSuccess;
+    if (c.fused) {
+        // geometry, colour candidates and band gate in one launch: its time
+        // is the geometry phase's; the colour-list and band phases are empty
+        const bool aligned = c.ng[0] % BRICK == 0 && c.ng[1] % BRICK == 0 && c.ng[2] % BRICK == 0;
+        auto k = c.free_space ? (aligned ? k_fused<true, true> : k_fused<true, false>)
+                              : (aligned ? k_fused<false, true> : k_fused<false, false>);
+        e = launch_chained(k, dim3(g.fuse), dim3(COL_THREADS), colour_smem_bytes(), stream, c, v, depth, rgb, s);
+        mark(3);
+        if (list_done) cudaEventRecord(list_done, stream);
+        mark(4);
+        mark(5);
+    } else {
+        e = launch_k_geometry(c, v, s, g.geo, stream);
+        mark(3);
+        unsigned gl = (nbt + LIST_THREADS - 1) / LIST_THREADS;
+        if (gl > 1024u) gl = 1024u;
+        if (e == cudaSuccess)
+            e = launch_chained(k_colour_list, dim3(gl), dim3(LIST_THREADS), 0, stream, c, v.summ, s.ctr, s.vis_list,
+                               s.col_list);
+        if (list_done) cudaEventRecord(list_done, stream);
+        mark(4);
+        if (e == cudaSuccess)
+            e = launch_chained(k_colour_band, dim3(g.col), dim3(COL_THREADS), colour_smem_bytes(), stream, c, v, depth,
+                               rgb, s);
+        mark(5);
+    }
     if (e == cudaSuccess)
         e = launch_chained(k_colour_voxels, dim3(g.vox), dim3(256), 0, stream, c, v, depth, rgb, s);
     mark(6);
@@ -1742,7 +2009,8 @@ cudaError_t launch_frame_record(const FrameConst& c, const Volumes& v, const Scr
     k_depth_tiles<<<tg, dim3(TILE_BLOCK_PX, TILE_BLOCK_PX), 0, stream>>>(c, depth, s.depth_tiles, s.ctr, s.depth_m);
     const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
     k_bricks<<<(nbt + BRICK_THREADS - 1) / BRICK_THREADS, BRICK_THREADS, 0, stream>>>(c, v.summ, s.depth_tiles, s.ctr,
-                                                                                     s.geo_list, s.vis_list);
+                                                                                     s.geo_list, s.vis_list, s.bstate,
+                                                                                     s.fsync);
     launch_k_geometry(c, v, s, g.geo, stream);
     unsigned gl = (nbt + LIST_THREADS - 1) / LIST_THREADS;
     if (gl > 1024u) gl = 1024u;

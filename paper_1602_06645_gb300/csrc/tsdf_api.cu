@@ -186,6 +186,8 @@ tsdf_status check_device_error(tsdf_volume* v) {
     if (ce != cudaSuccess) return cuda_fail(v, ce, "device status read");
     if (e) {
         cudaMemsetAsync(v->scr.err, 0, sizeof(uint32_t), v->stream);
+        if (e == ERR_WAIT_TIMEOUT)
+            return fail(v, TSDF_ERR_TIMEOUT, "fused frame: a bounded wait for ready colour work gave up");
         return fail(v, TSDF_ERR_DEVICE_FAULT, "device status word 0x" + std::to_string(e));
     }
     return TSDF_OK;
@@ -515,10 +517,11 @@ tsdf_status tsdf_create_ex(const int32_t dims_geo[3], const int32_t dims_col[3],
     v->grids.geo = sms * geometry_blocks_per_sm();
     v->grids.col = sms * colour_blocks_per_sm();
     v->grids.vox = sms * voxel_blocks_per_sm();
+    v->grids.fuse = sms * fused_blocks_per_sm();
 
     const int64_t nbt = (int64_t)v->nb[0] * v->nb[1] * v->nb[2];
     const int64_t ncbt = (int64_t)v->ncb[0] * v->ncb[1] * v->ncb[2];
-    const size_t need = (size_t)nbt * BRICK_VOX * 5 + (size_t)ncbt * BRICK_VOX * 4 + (size_t)nbt * (sizeof(BrickSummary) + 12) +
+    const size_t need = (size_t)nbt * BRICK_VOX * 5 + (size_t)ncbt * BRICK_VOX * 4 + (size_t)nbt * (sizeof(BrickSummary) + 25) +
                         (size_t)vox_capacity(nbt) * sizeof(uint2);
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && need > free_b) {
@@ -535,6 +538,11 @@ tsdf_status tsdf_create_ex(const int32_t dims_geo[3], const int32_t dims_col[3],
     v->scr.vis_list = (uint32_t*)dev_alloc(v, (size_t)nbt * sizeof(uint32_t));
     v->scr.col_list = (uint32_t*)dev_alloc(v, (size_t)nbt * sizeof(uint32_t));
     v->scr.err = (uint32_t*)dev_alloc(v, sizeof(uint32_t));
+    // fused frame: per-brick state bytes and neighbour counts, the ready queue and its counters
+    v->scr.bstate = (uint8_t*)dev_alloc(v, (size_t)nbt);
+    v->scr.need = (uint32_t*)dev_alloc(v, (size_t)nbt * sizeof(uint32_t));
+    v->scr.ready = (unsigned long long*)dev_alloc(v, (size_t)nbt * sizeof(unsigned long long));
+    v->scr.fsync = (FuseSync*)dev_alloc(v, sizeof(FuseSync));
     // band-gate voxel records of one frame; records that do not fit are
     // finished by the band kernel itself, so the capacity only bounds memory
     v->scr.vox_cap = (uint32_t)vox_capacity(nbt);
@@ -544,7 +552,8 @@ tsdf_status tsdf_create_ex(const int32_t dims_geo[3], const int32_t dims_col[3],
     }
     v->scr.vox = (uint2*)dev_alloc(v, (size_t)v->scr.vox_cap * sizeof(uint2));
     if (!v->vol.F || !v->vol.W || !v->vol.C || !v->vol.summ || !v->scr.ctr || !v->scr.geo_list || !v->scr.vis_list ||
-        !v->scr.col_list || !v->scr.err || !v->scr.vox) {
+        !v->scr.col_list || !v->scr.err || !v->scr.vox || !v->scr.bstate || !v->scr.need || !v->scr.ready ||
+        !v->scr.fsync) {
         tsdf_destroy(v);
         return TSDF_ERR_OOM;
     }
@@ -560,6 +569,8 @@ tsdf_status tsdf_create_ex(const int32_t dims_geo[3], const int32_t dims_col[3],
     if (e == cudaSuccess) e = cudaMemsetAsync(v->vol.C, 0, (size_t)ncbt * BRICK_VOX * sizeof(uint32_t), v->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->scr.ctr, 0, sizeof(Counters), v->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->scr.err, 0, sizeof(uint32_t), v->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v->scr.ready, 0, (size_t)nbt * sizeof(unsigned long long), v->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v->scr.fsync, 0, sizeof(FuseSync), v->stream);
     if (e == cudaSuccess) e = launch_init_summaries(v->vol.summ, nbt, v->stream);
     if (e != cudaSuccess) {
         tsdf_destroy(v);
@@ -620,6 +631,8 @@ tsdf_status tsdf_integrate(tsdf_volume* v, const uint16_t* depth_mm, tsdf_image_
 
     FrameConst c;
     frame_constants(v, K_depth, K_rgb, T_world_depth, T_depth_rgb, dsz.width, dsz.height, csz.width, csz.height, c);
+    c.frame_tag = (uint32_t)(v->frames % 0xFFFFFFFFll) + 1u;  // never 0 (the queue's initial value)
+    c.fused = v->schedule == TSDF_SCHEDULE_FUSED && c.kd_pinhole ? 1 : 0;
 
     const size_t dbytes = (size_t)dsz.width * dsz.height * sizeof(uint16_t);
     const size_t cbytes = (size_t)csz.width * csz.height * 3;
@@ -712,6 +725,28 @@ tsdf_status tsdf_integrate(tsdf_volume* v, const uint16_t* depth_mm, tsdf_image_
     v->chain_ok = pipe;
     ++v->frames;
     return TSDF_OK;
+}
+
+tsdf_status tsdf_set_frame_schedule(tsdf_volume* v, int32_t schedule) {
+    if (!v) return TSDF_ERR_INVALID_ARG;
+    if (schedule != TSDF_SCHEDULE_KERNELS && schedule != TSDF_SCHEDULE_FUSED)
+        return fail(v, TSDF_ERR_INVALID_ARG, "frame schedule: TSDF_SCHEDULE_KERNELS or TSDF_SCHEDULE_FUSED");
+    v->schedule = schedule;
+    return TSDF_OK;
+}
+
+tsdf_status tsdf_get_frame_schedule(const tsdf_volume* v, int32_t* schedule) {
+    if (!v || !schedule) return TSDF_ERR_INVALID_ARG;
+    *schedule = v->schedule;
+    return TSDF_OK;
+}
+
+tsdf_status tsdf_fused_inject_stall(tsdf_volume* v) {
+    if (!v) return TSDF_ERR_INVALID_ARG;
+    const unsigned one = 1u;
+    cudaError_t e = cudaMemcpyAsync(&v->scr.fsync->stall, &one, sizeof one, cudaMemcpyHostToDevice, v->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(v->stream);
+    return e == cudaSuccess ? TSDF_OK : cuda_fail(v, e, "stall injection");
 }
 
 tsdf_status tsdf_synchronize(tsdf_volume* v) {
