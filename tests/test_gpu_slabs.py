@@ -31,13 +31,18 @@ def _seq(dims_geo, dims_col):
     return seq
 
 
-@pytest.mark.parametrize("dims_geo,dims_col,n", [(48, 96, 2), (48, 96, 3), (64, 64, 2), (48, 80, 2), (40, 80, 3)])
-def test_slabs_equal_the_whole_volume(dims_geo, dims_col, n):
+@pytest.mark.parametrize("dims_geo,dims_col,n,schedule", [
+    (48, 96, 2, "kernels"), (48, 96, 3, "kernels"), (64, 64, 2, "kernels"), (48, 80, 2, "kernels"),
+    (40, 80, 3, "kernels"), (48, 96, 3, "fused"), (40, 80, 2, "fused")])
+def test_slabs_equal_the_whole_volume(dims_geo, dims_col, n, schedule):
+    """Slab handles (either frame schedule) against a whole-volume handle run
+    as the kernel chain."""
     seq = _seq(dims_geo, dims_col)
     frames = _frames(seq, 4)
     args = (seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, seq.max_weight)
     whole = T.Volume(*args)
-    slabs = [T.Volume(*args, slab=r) for r in T.slab_ranges(seq.dims_geo, seq.dims_col, n)]
+    sched = T.TSDF_SCHEDULE_FUSED if schedule == "fused" else T.TSDF_SCHEDULE_KERNELS
+    slabs = [T.Volume(*args, slab=r, schedule=sched) for r in T.slab_ranges(seq.dims_geo, seq.dims_col, n)]
     for fr in frames:
         whole.integrate(*fr)
         for v in slabs:

@@ -1,13 +1,17 @@
-"""The allocation-free geometry entry point against the regular one.
+"""The allocation-free geometry entry point against the regular one and the
+oracle.
 
 tsdf_integrate_geometry_static is for callers that cannot allocate device
 memory (another framework owns the allocator, or the device-memory budget is
 fixed in advance): they pass their own TSDF and weight arrays and the library
 uses a fixed scratch array compiled into it.  Its results must equal the
-geometry volume that tsdf_integrate produces, call after call.
+geometry volume that tsdf_integrate produces, call after call, and the
+oracle's geometry update.
 """
 import numpy as np
 import pytest
+
+import oracle
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -46,6 +50,32 @@ def test_static_entry_matches_regular_entry_two_calls(dims):
         assert float(np.abs(F.cpu().numpy() - Fr).max()) <= F_TOL
         assert (Wr > 0).sum() > 10000
     vol.close()
+
+
+def test_static_entry_equals_the_oracle():
+    """Four frames through the static entry against the oracle's geometry
+    update (Section III): weights bit for bit, TSDF within 1e-5 (exact)."""
+    dims = (88, 72, 64)
+    seq = synth.sequence_small(n_frames=4, dims_geo=dims[0], seed=23)
+    s = float(np.float32(1.0 / dims[0]))
+    mu = float(np.float32(3 * s))
+    mw = seq.max_weight
+    origin = _origin(dims, s)
+    o = oracle.Oracle(dims, dims, s, mu, mw, origin=origin)
+    F = torch.zeros((dims[2], dims[1], dims[0]), dtype=torch.float32, device="cuda")
+    W = torch.zeros((dims[2], dims[1], dims[0]), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    for f in range(4):
+        d, _ = seq.frame(f)
+        o.integrate_geometry(d, seq.K_depth, seq.poses[f])
+        T.tsdf_integrate_geometry_static(dims, s, mu, mw, origin, F, W, torch.from_numpy(d.view(np.int16)).cuda(),
+                                         seq.K_depth, seq.poses[f], stream)
+    torch.cuda.synchronize()
+    Fg, Wg = F.cpu().numpy(), W.cpu().numpy()
+    np.testing.assert_array_equal(Wg, o.W)
+    assert float(np.abs(Fg - o.F).max()) <= F_TOL
+    assert np.array_equal(Fg, o.F)
+    assert (Wg > 0).sum() > 10000
 
 
 def test_static_entry_allocates_no_device_memory():
