@@ -384,7 +384,7 @@ def run_ours(args):
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     K = max(args.steps, 1)
     geo_bytes = 10.0 * st.total_geo_updated / K            # F (4 B) + w (1 B), read and written
-    band_bytes = 5.0 * 1000 * st.total_col_bricks / K       # geometry tile (10^3 F + w) per candidate brick
+    band_bytes = 5.0 * 729 * st.total_col_bricks / K        # geometry tile (9^3 F + w) per candidate brick
     vox_bytes = 8.0 * st.total_col_updated / K              # packed RGBW, read and written
     kern_bytes = {"geometry": geo_bytes, "colour_band": band_bytes, "colour_voxels": vox_bytes}
     if args.schedule == "fused":  # one launch does the geometry update and the band gate
@@ -583,9 +583,9 @@ def run_batched(args):
     geo_upd, col_upd, col_bricks = per_step("total_geo_updated"), per_step("total_col_updated"), \
         per_step("total_col_bricks")
     # algorithmic bytes of the step: F and w read and written per updated
-    # geometry voxel, the 10^3 geometry tile (F and w) per colour-candidate
+    # geometry voxel, the 9^3 geometry tile (F and w) per colour-candidate
     # brick, the packed colour read and written per updated colour voxel
-    step_bytes = 10.0 * geo_upd + 5.0 * 1000 * col_bricks + 8.0 * col_upd
+    step_bytes = 10.0 * geo_upd + 5.0 * 729 * col_bricks + 8.0 * col_upd
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
     achieved = step_bytes / (ms_batched / max(args.steps, 1) / 1e3) / 1e9

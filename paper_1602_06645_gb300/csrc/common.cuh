@@ -151,11 +151,13 @@ struct Scratch {
 // Per-axis tables of the colour grid, built once on the host with the band
 // kernel's binary32 operations: for colour index k on axis a, the trilinear
 // fraction of its centre (frac) and its geometry cell relative to the owning
-// brick's 10-voxel tile (cell, 0..8); for brick coordinate bb, the first owned
-// colour index (k0[bb], owned range k0[bb] .. k0[bb + 1] - 1) and, per tile
-// cell, the owned indices that fall in it (span[bb * 9 + cell] = first | end << 8,
-// relative to k0[bb]); info[bb] = mask of the tile cells that own indices
-// (9 bits) | most indices of one cell << 9.
+// brick (cell, 0..7: the cell between brick voxels cell and cell + 1, voxel 8
+// being the next brick's voxel 0); a brick owns the colour indices whose
+// cell's lower corner lies in it.  For brick coordinate bb, the first owned
+// colour index (k0[bb], owned range k0[bb] .. k0[bb + 1] - 1) and, per cell,
+// the owned indices that fall in it (span[bb * 8 + cell] = first | end << 8,
+// relative to k0[bb]); info[bb] = mask of the cells that own indices
+// (8 bits) | most indices of one cell << 9.
 struct AxisTables {
     const float* frac[3];
     const int8_t* cell[3];

@@ -25,9 +25,9 @@ namespace {
 
 constexpr int GEO_THREADS = 128;  // 4 voxels per thread, one brick per block iteration
 constexpr int COL_THREADS = 128;  // 4 warps, one colour work item per warp
-constexpr int TILE_G = BRICK + 2;          // geometry tile edge: brick + 1-voxel halo each side
+constexpr int TILE_G = BRICK + 1;          // geometry tile edge: the brick + the next bricks' first voxel layer
 constexpr int TILE_G3 = TILE_G * TILE_G * TILE_G;
-constexpr int CELLS = BRICK + 1;           // trilinear cells whose corners lie in the tile
+constexpr int CELLS = BRICK;               // trilinear cells a brick owns: lower corner in the brick
 constexpr int CELLS3 = CELLS * CELLS * CELLS;
 
 // ------------------------------------------------------- depth tiles ----
@@ -697,12 +697,14 @@ cudaError_t launch_k_geometry(const FrameConst& c, const Volumes& v, const Scrat
 // ------------------------------------------------------- colour list ----
 // A visible geometry brick goes to the colour list when some trilinear cell
 // of the colour voxels it owns can have corners on both sides of the band:
-// the cells' corners lie in the brick and in the one-voxel layers of its 26
-// neighbours that touch it, so the brick needs an observed voxel with
-// F <= band + eps and one with F >= -band - eps among its own voxels and
-// those layers.  A face neighbour contributes its touching face layer; an
-// edge or corner neighbour contributes only voxels on all of its touching
-// faces, so the AND of those faces' flags is still a necessary condition.
+// a brick owns the cells whose lower corner lies in it, so their corners lie
+// in the brick and in the first voxel layers of its seven + neighbours
+// (+x, +y, +z, the three edges and the corner between them), and the brick
+// needs an observed voxel with F <= band + eps and one with F >= -band - eps
+// among its own voxels and those layers.  A face neighbour contributes its
+// touching face layer (its -x, -y or -z face); an edge or corner neighbour
+// contributes only voxels on all of its touching faces, so the AND of those
+// faces' flags is still a necessary condition.
 // Colour-candidate test of a visible geometry brick (see above).
 __device__ __forceinline__ bool colour_candidate(const FrameConst& c, const BrickSummary* __restrict__ summ,
                                                  uint32_t b) {
@@ -710,24 +712,17 @@ __device__ __forceinline__ bool colour_candidate(const FrameConst& c, const Bric
     const int bx = b % c.nb[0], by = (b / c.nb[0]) % c.nb[1], bz = b / (c.nb[0] * c.nb[1]);
     uint32_t acc = summ[b].flags & 3u;
 #pragma unroll
-    for (int dz = -1; dz <= 1; ++dz) {  // no early exit: the 27 reads are independent
-        const int z = bz + dz;
-        if (z < 0 || z >= c.nb[2]) continue;
-        for (int dy = -1; dy <= 1; ++dy) {
-            const int y = by + dy;
-            if (y < 0 || y >= c.nb[1]) continue;
-            for (int dx = -1; dx <= 1; ++dx) {
-                const int x = bx + dx;
-                if (x < 0 || x >= c.nb[0] || (dx == 0 && dy == 0 && dz == 0)) continue;
-                const uint32_t f = summ[((size_t)z * c.nb[1] + y) * c.nb[0] + x].flags;
-                // the neighbour at -x touches with its +x face (bits 4-5), etc.
-                uint32_t m = 3u;
-                if (dx) m &= f >> (dx < 0 ? 4 : 2);
-                if (dy) m &= f >> (dy < 0 ? 8 : 6);
-                if (dz) m &= f >> (dz < 0 ? 12 : 10);
-                acc |= m & 3u;
-            }
-        }
+    for (int k = 1; k < 8; ++k) {  // no early exit: the reads are independent
+        const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+        const int x = bx + dx, y = by + dy, z = bz + dz;
+        if (x >= c.nb[0] || y >= c.nb[1] || z >= c.nb[2]) continue;
+        const uint32_t f = summ[((size_t)z * c.nb[1] + y) * c.nb[0] + x].flags;
+        // the neighbour at +x touches with its -x face (bits 2-3), +y with -y (6-7), +z with -z (10-11)
+        uint32_t m = 3u;
+        if (dx) m &= f >> 2;
+        if (dy) m &= f >> 6;
+        if (dz) m &= f >> 10;
+        acc |= m & 3u;
     }
     return acc == 3u;
 }
@@ -897,22 +892,22 @@ __device__ __forceinline__ bool colour_after_band(const FrameConst& c, uint32_t*
 constexpr int MAXK = 66;    // owned colour indices per axis (colour/geometry ratio <= 8)
 constexpr int STAGE = 256;  // per-warp record staging entries
 
-struct ColourSlot {  // one warp's shared-memory working set (~9 KB)
+struct ColourSlot {  // one warp's shared-memory working set (~7 KB)
     float F[TILE_G3];
-    // per tile row (z * 10 + y): bit x = observed, bit 10 + x = F <= band + eps,
-    // bit 20 + x = F >= -band - eps
+    // per tile row (z * 9 + y): bit x = observed, bit 9 + x = F <= band + eps,
+    // bit 18 + x = F >= -band - eps
     uint32_t row[TILE_G * TILE_G];
     uint16_t cells[CELLS3];
     float frac[3][MAXK];
     uint8_t start[3][CELLS], end[3][CELLS];
-    int32_t nbr[27];  // neighbour brick indices, -1 outside the volume
+    int32_t nbr[8];  // the brick and its + neighbours, (sz * 2 + sy) * 2 + sx; -1 outside the volume
     uint2 out[STAGE];
 };
 
 // Store one staged geometry voxel with its flags.
 // Row-mask bits of one voxel (see ColourSlot::row), at x = 0.
 __device__ __forceinline__ uint32_t voxel_bits(float f, uint32_t w, float lo_thr, float hi_thr) {
-    return (w != 0u ? 1u : 0u) | (f <= lo_thr ? 1u << 10 : 0u) | (f >= hi_thr ? 1u << 20 : 0u);
+    return (w != 0u ? 1u : 0u) | (f <= lo_thr ? 1u << 9 : 0u) | (f >= hi_thr ? 1u << 18 : 0u);
 }
 
 // Store one staged geometry voxel and its row-mask bits.
@@ -925,16 +920,12 @@ __device__ __forceinline__ void stage(ColourSlot& S, int tx, int ty, int tz, flo
 }
 
 // Offset of tile voxel (tx, ty, tz) in the brick-major volume, or -1.  Tile
-// coordinate 0 is local 7 of the previous brick, 1..8 are locals 0..7 of the
-// centre brick, 9 is local 0 of the next brick.
+// coordinates 0..7 are the brick's locals 0..7, 8 is local 0 of the next brick.
 __device__ __forceinline__ int64_t tile_offset(const ColourSlot& S, int tx, int ty, int tz) {
-    const int sx = tx == 0 ? 0 : (tx == TILE_G - 1 ? 2 : 1);
-    const int sy = ty == 0 ? 0 : (ty == TILE_G - 1 ? 2 : 1);
-    const int sz = tz == 0 ? 0 : (tz == TILE_G - 1 ? 2 : 1);
-    const int nb = S.nbr[(sz * 3 + sy) * 3 + sx];
+    const int sx = tx >> 3, sy = ty >> 3, sz = tz >> 3;
+    const int nb = S.nbr[(sz * 2 + sy) * 2 + sx];
     if (nb < 0) return -1;
-    const int lx = (tx + 7) & 7, ly = (ty + 7) & 7, lz = (tz + 7) & 7;
-    return (int64_t)nb * BRICK_VOX + (lz * BRICK + ly) * BRICK + lx;
+    return (int64_t)nb * BRICK_VOX + ((tz & 7) * BRICK + (ty & 7)) * BRICK + (tx & 7);
 }
 
 // The band kernel's overflow path, kept out of line: inlined, its registers
@@ -994,12 +985,14 @@ __device__ __forceinline__ void band_brick(const FrameConst& c, const Volumes& v
     int k0[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) k0[a] = __ldg(vol.tab.k0[a] + bb[a]);
-    if (lane < 27) {
-        const int x = bb[0] + lane % 3 - 1, y = bb[1] + (lane / 3) % 3 - 1, z = bb[2] + lane / 9 - 1;
-        S.nbr[lane] = (x >= 0 && y >= 0 && z >= 0 && x < c.nb[0] && y < c.nb[1] && z < c.nb[2])
+    if (lane < 8) {
+        const int x = bb[0] + (lane & 1), y = bb[1] + ((lane >> 1) & 1), z = bb[2] + (lane >> 2);
+        S.nbr[lane] = (x < c.nb[0] && y < c.nb[1] && z < c.nb[2])
                           ? (int32_t)(((int64_t)z * c.nb[1] + y) * c.nb[0] + x)
                           : -1;
-        const int a = lane / 9, cell = lane % 9;
+    }
+    if (lane < 3 * CELLS) {
+        const int a = lane / CELLS, cell = lane % CELLS;
         const int ba = a == 0 ? bb[0] : (a == 1 ? bb[1] : bb[2]);  // no dynamic indexing of bb
         const uint16_t* span = a == 0 ? vol.tab.span[0] : (a == 1 ? vol.tab.span[1] : vol.tab.span[2]);
         const uint16_t sp = __ldg(span + ba * CELLS + cell);
@@ -1023,7 +1016,7 @@ __device__ __forceinline__ void band_brick(const FrameConst& c, const Volumes& v
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int q = lane + 32 * j;
-            const int x0 = (q & 1) * 4 + 1, y = ((q >> 1) & 7) + 1, z = (q >> 4) + 1;
+            const int x0 = (q & 1) * 4, y = (q >> 1) & 7, z = q >> 4;
             const int r = z * TILE_G + y, i = r * TILE_G + x0;
             S.F[i] = f[j].x;
             S.F[i + 1] = f[j].y;
@@ -1037,40 +1030,34 @@ __device__ __forceinline__ void band_brick(const FrameConst& c, const Volumes& v
             if (bits) atomicOr(&S.row[r], bits);
         }
     }
-    // 1b. halo: 6 faces x 64, 12 edges x 8, 8 corners = 488 voxels
+    // 1b. halo, the next bricks' first layers: 3 faces x 64, 3 edges x 8, 1 corner = 217 voxels
     {
-        int txs[16], tys[16], tzs[16];
+        int txs[7], tys[7], tzs[7];
 #pragma unroll
-        for (int i = 0; i < 12; ++i) {  // faces: i = 2 * face + half
-            const int face = i >> 1, q = lane + 32 * (i & 1);
-            const int axis = face >> 1, side = (face & 1) ? TILE_G - 1 : 0;
-            const int a = (q & 7) + 1, bq = (q >> 3) + 1;
-            txs[i] = axis == 0 ? side : a;
-            tys[i] = axis == 1 ? side : (axis == 0 ? a : bq);
-            tzs[i] = axis == 2 ? side : bq;
+        for (int i = 0; i < 6; ++i) {  // faces: i = 2 * axis + half
+            const int axis = i >> 1, q = lane + 32 * (i & 1);
+            const int a = q & 7, bq = q >> 3;
+            txs[i] = axis == 0 ? BRICK : a;
+            tys[i] = axis == 1 ? BRICK : (axis == 0 ? a : bq);
+            tzs[i] = axis == 2 ? BRICK : bq;
         }
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {  // edges
-            const int q = lane + 32 * i, e = q >> 3, m = (q & 7) + 1;
-            const int axis = e >> 2, s1 = (e & 1) ? TILE_G - 1 : 0, s2 = (e & 2) ? TILE_G - 1 : 0;
-            txs[12 + i] = axis == 0 ? m : s1;
-            tys[12 + i] = axis == 1 ? m : (axis == 0 ? s1 : s2);
-            tzs[12 + i] = axis == 2 ? m : s2;
+        {  // edges (lanes 0..23, along axis lane / 8) and the corner (lane 24)
+            const int e = lane >> 3, m = lane & 7;
+            txs[6] = e == 0 ? m : BRICK;
+            tys[6] = e == 1 ? m : BRICK;
+            tzs[6] = e == 2 ? m : BRICK;
         }
-        txs[15] = (lane & 1) ? TILE_G - 1 : 0;  // corners (lanes 0..7)
-        tys[15] = (lane & 2) ? TILE_G - 1 : 0;
-        tzs[15] = (lane & 4) ? TILE_G - 1 : 0;
-        float hf[16];
-        uint32_t hw[16];
+        float hf[7];
+        uint32_t hw[7];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const int64_t off = (i < 15 || lane < 8) ? tile_offset(S, txs[i], tys[i], tzs[i]) : -1;
+        for (int i = 0; i < 7; ++i) {
+            const int64_t off = (i < 6 || lane < 25) ? tile_offset(S, txs[i], tys[i], tzs[i]) : -1;
             hf[i] = off >= 0 ? vol.F[off] : 0.0f;
             hw[i] = off >= 0 ? (uint32_t)vol.W[off] : 0u;
         }
 #pragma unroll
-        for (int i = 0; i < 16; ++i)
-            if (i < 15 || lane < 8) stage(S, txs[i], tys[i], tzs[i], hf[i], hw[i], lo_thr, hi_thr);
+        for (int i = 0; i < 7; ++i)
+            if (i < 6 || lane < 25) stage(S, txs[i], tys[i], tzs[i], hf[i], hw[i], lo_thr, hi_thr);
     }
     // 1c. trilinear fraction of each owned colour index, from the per-axis tables
 #pragma unroll
@@ -1083,13 +1070,13 @@ __device__ __forceinline__ void band_brick(const FrameConst& c, const Volumes& v
     // 3. active cells, compacted
     // cells along x that own colour indices, and the most indices of one cell per axis
     const uint32_t xinfo = __ldg(vol.tab.info[0] + bb[0]);
-    const uint32_t xmask = xinfo & 0x1FFu;
+    const uint32_t xmask = xinfo & 0xFFu;
     const int mx = (int)(xinfo >> 9), my = (int)(__ldg(vol.tab.info[1] + bb[1]) >> 9),
               mz = (int)(__ldg(vol.tab.info[2] + bb[2]) >> 9);
-    uint32_t act[3];
+    uint32_t act[2];
     uint32_t total = 0;
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
+    for (int r = 0; r < 2; ++r) {
         const int yz = lane + 32 * r;
         act[r] = 0;
         if (yz < CELLS * CELLS) {
@@ -1098,15 +1085,15 @@ __device__ __forceinline__ void band_brick(const FrameConst& c, const Volumes& v
                 const int r00 = cz * TILE_G + cy;
                 const uint32_t w00 = S.row[r00], w10 = S.row[r00 + 1], w01 = S.row[r00 + TILE_G],
                                w11 = S.row[r00 + TILE_G + 1];
-                uint32_t o = w00 & w10 & w01 & w11 & 0x3FFu;
+                uint32_t o = w00 & w10 & w01 & w11 & 0x1FFu;
                 o &= o >> 1;
                 uint32_t a = o & xmask;
                 if (c.culling) {
                     const uint32_t any = w00 | w10 | w01 | w11;
-                    const uint32_t l = (any >> 10) & 0x3FFu, h = (any >> 20) & 0x3FFu;
+                    const uint32_t l = (any >> 9) & 0x1FFu, h = (any >> 18) & 0x1FFu;
                     a &= (l | (l >> 1)) & (h | (h >> 1));
                 }
-                act[r] = a & 0x1FFu;
+                act[r] = a & 0xFFu;
             }
         }
         total += __popc(act[r]);
@@ -1123,7 +1110,7 @@ __device__ __forceinline__ void band_brick(const FrameConst& c, const Volumes& v
     n_cells += nact;
     uint32_t pos = incl - total;
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
+    for (int r = 0; r < 2; ++r) {
         uint32_t a = act[r];
         const int yz = lane + 32 * r;
         while (a) {
@@ -1248,11 +1235,12 @@ __global__ void __launch_bounds__(256) k_colour_voxels(FrameConst c, Volumes vol
 // ------------------------------------------------------- fused frame ----
 // The frame's geometry update, colour-candidate test and band gate in one
 // persistent launch (the colour voxels follow in k_colour_voxels).  A visible
-// brick's colour work reads the updated geometry of its 27-neighbourhood, so
-// it may start once every listed brick there has been updated: k_need counts
-// those per visible brick; each warp that finishes a brick's geometry
-// decrements its visible neighbours' counts, and the warp that brings a count
-// to zero pushes that brick on a ready queue.  Warps take at most one ready
+// brick's colour work reads the updated geometry of itself and its seven +
+// neighbours, so it may start once every listed brick there has been updated:
+// k_need counts those per visible brick; each warp that finishes a brick's
+// geometry decrements the counts of the visible bricks that read it (itself
+// and its seven - neighbours), and the warp that brings a count to zero
+// pushes that brick on a ready queue.  Warps take at most one ready
 // brick after each of their own geometry bricks (so the colour work runs
 // beside the geometry), then, with their geometry done, the remaining ones.
 // Only that last part waits, and only for bricks that the geometry still
@@ -1307,8 +1295,8 @@ __device__ __forceinline__ bool fuse_take(const FrameConst& c, const Scratch& sc
     return got != 0;
 }
 
-// Visible bricks: count the listed bricks among the 27 neighbours (itself
-// included); a brick with none is ready at once.  Test injection
+// Visible bricks: count the listed bricks among themselves and their seven +
+// neighbours; a brick with none is ready at once.  Test injection
 // (FuseSync::stall): the first visible brick gets one count that no warp
 // will release, so a wait for it runs out.
 __global__ void __launch_bounds__(256) k_need(FrameConst c, Scratch scr) {
@@ -1320,9 +1308,9 @@ __global__ void __launch_bounds__(256) k_need(FrameConst c, Scratch scr) {
                   bz = (int)(b / ((uint32_t)c.nb[0] * (uint32_t)c.nb[1]));
         uint32_t cnt = 0;
 #pragma unroll
-        for (int k = 0; k < 27; ++k) {
-            const int x = bx + k % 3 - 1, y = by + (k / 3) % 3 - 1, z = bz + k / 9 - 1;
-            if (x >= 0 && y >= 0 && z >= 0 && x < c.nb[0] && y < c.nb[1] && z < c.nb[2])
+        for (int k = 0; k < 8; ++k) {  // itself and its + neighbours: the geometry its colour work reads
+            const int x = bx + (k & 1), y = by + ((k >> 1) & 1), z = bz + (k >> 2);
+            if (x < c.nb[0] && y < c.nb[1] && z < c.nb[2])
                 cnt += scr.bstate[((size_t)z * c.nb[1] + y) * c.nb[0] + x] & 1u;
         }
         if (i == 0 && *(volatile unsigned*)&scr.fsync->stall) {
@@ -1334,28 +1322,24 @@ __global__ void __launch_bounds__(256) k_need(FrameConst c, Scratch scr) {
     }
 }
 
-// colour_candidate with one lane per neighbour (lane 13: the brick itself).
+// colour_candidate with one lane per neighbour (lane 0: the brick itself).
 __device__ __forceinline__ bool colour_candidate_warp(const FrameConst& c, const BrickSummary* __restrict__ summ,
                                                       uint32_t b, int lane) {
     if (!c.culling) return true;
     const int bx = (int)(b % (uint32_t)c.nb[0]), by = (int)((b / (uint32_t)c.nb[0]) % (uint32_t)c.nb[1]),
               bz = (int)(b / ((uint32_t)c.nb[0] * (uint32_t)c.nb[1]));
     uint32_t m = 0;
-    if (lane < 27) {
-        const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+    if (lane < 8) {
+        const int dx = lane & 1, dy = (lane >> 1) & 1, dz = lane >> 2;
         const int x = bx + dx, y = by + dy, z = bz + dz;
-        if (x >= 0 && y >= 0 && z >= 0 && x < c.nb[0] && y < c.nb[1] && z < c.nb[2]) {
+        if (x < c.nb[0] && y < c.nb[1] && z < c.nb[2]) {
             const uint32_t f = summ[((size_t)z * c.nb[1] + y) * c.nb[0] + x].flags;
-            if (dx == 0 && dy == 0 && dz == 0) {
-                m = f & 3u;
-            } else {
-                // the neighbour at -x touches with its +x face (bits 4-5), etc.
-                m = 3u;
-                if (dx) m &= f >> (dx < 0 ? 4 : 2);
-                if (dy) m &= f >> (dy < 0 ? 8 : 6);
-                if (dz) m &= f >> (dz < 0 ? 12 : 10);
-                m &= 3u;
-            }
+            m = 3u;
+            if (lane == 0) m &= f;
+            if (dx) m &= f >> 2;
+            if (dy) m &= f >> 6;
+            if (dz) m &= f >> 10;
+            m &= 3u;
         }
     }
     return __reduce_or_sync(0xffffffffu, m) == 3u;
@@ -1366,9 +1350,9 @@ __device__ __forceinline__ bool colour_candidate_warp(const FrameConst& c, const
 // and through the warp barrier the other lanes', before its decrement).
 __device__ __forceinline__ void fuse_release(const FrameConst& c, const Scratch& scr, const BrickAt& at, int lane) {
     __syncwarp();
-    if (lane < 27) {
-        const int x = at.bx + lane % 3 - 1, y = at.by + (lane / 3) % 3 - 1, z = at.bz + lane / 9 - 1;
-        if (x >= 0 && y >= 0 && z >= 0 && x < c.nb[0] && y < c.nb[1] && z < c.nb[2]) {
+    if (lane < 8) {  // the bricks whose colour work reads this one: itself and its - neighbours
+        const int x = at.bx - (lane & 1), y = at.by - ((lane >> 1) & 1), z = at.bz - (lane >> 2);
+        if (x >= 0 && y >= 0 && z >= 0) {
             const uint32_t nb = (uint32_t)(((size_t)z * c.nb[1] + y) * c.nb[0] + x);
             if (scr.bstate[nb] & 2u) {
                 __threadfence();

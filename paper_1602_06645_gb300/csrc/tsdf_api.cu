@@ -344,38 +344,41 @@ const char* tsdf_last_error(const tsdf_volume* v) { return v ? v->last_error.c_s
 // Per-axis colour tables (see AxisTables): the trilinear cell and fraction of
 // each colour index, computed with the same binary32 operations as the band
 // kernel (centre p = fmaf(k + 1/2, s_c, origin), g = fmaf(p - origin, 1/s_g,
-// -1/2), i0 = floor(g), fraction g - i0), the owned index range of each brick
-// coordinate (16 bb Nc <= (2k + 1) Ng < 16 (bb + 1) Nc) and the per-cell spans.
+// -1/2), i0 = floor(g), fraction g - i0); a brick owns the colour indices
+// whose cell's lower corner i0 lies in it (i0 is non-decreasing in k, so the
+// owned indices are a contiguous range), and the per-cell spans.
 static tsdf_status build_axis_tables(tsdf_volume* v) {
     const float inv_sg = 1.0f / v->s_g;
     for (int a = 0; a < 3; ++a) {
         const int nc = v->nc[a], nb = v->nb[a];
-        // the ratio is the whole volume's; on a z-slab handle the z indices are
-        // offset by the slab's global index of held voxel 0
-        const long long NG = a == 2 ? v->ngz_all : v->ng[a], NC = a == 2 ? v->ncz_all : v->nc[a];
+        // on a z-slab handle the z indices are offset by the slab's global
+        // index of held voxel 0 (colour zc, geometry zg)
         const long long zg = a == 2 ? v->zoff_g : 0, zc = a == 2 ? v->zoff_c : 0;
         std::vector<float> frac(nc);
         std::vector<int8_t> cell(nc);
-        std::vector<int32_t> k0(nb + 1);
-        std::vector<uint16_t> span((size_t)nb * 9, 0);
-        for (int bb = 0; bb <= nb; ++bb) {
-            // smallest global K with (2K + 1) NG >= 2 (8 bb + zg) NC, as a held index
-            const long long num = 2ll * (8ll * bb + zg) * NC - NG;
-            const long long K = num <= 0 ? 0 : (num + 2ll * NG - 1) / (2ll * NG);
-            k0[bb] = (int32_t)std::min<long long>(nc, std::max<long long>(0, K - zc));
+        std::vector<long long> low(nc);  // held geometry index of each colour index's lower cell corner
+        for (int k = 0; k < nc; ++k) {
+            const float p = std::fmaf((float)(k + zc) + 0.5f, v->s_c, v->origin[a]);
+            const float g = std::fmaf(p - v->origin[a], inv_sg, -0.5f);
+            const float i0 = std::floor(g);
+            frac[k] = g - i0;
+            low[k] = (long long)i0 - zg;
+            if (k > 0 && low[k] < low[k - 1])
+                return fail(v, TSDF_ERR_INVALID_ARG, "colour grid does not fit the bricks");
         }
+        std::vector<int32_t> k0(nb + 1);
+        for (int bb = 0, k = 0; bb <= nb; ++bb) {  // first index whose lower corner is in brick bb or later
+            while (k < nc && low[k] < 8ll * bb) ++k;
+            k0[bb] = k;
+        }
+        std::vector<uint16_t> span((size_t)nb * BRICK, 0);
         for (int bb = 0; bb < nb; ++bb) {
-            const int ta = bb * BRICK - 1;
             for (int k = k0[bb]; k < k0[bb + 1]; ++k) {
-                const float p = std::fmaf((float)(k + zc) + 0.5f, v->s_c, v->origin[a]);
-                const float g = std::fmaf(p - v->origin[a], inv_sg, -0.5f);
-                const float i0 = std::floor(g);
-                const int rel = (int)i0 - (int)zg - ta;
-                if (rel < 0 || rel > BRICK) return fail(v, TSDF_ERR_INVALID_ARG, "colour grid does not fit the bricks");
-                frac[k] = g - i0;
+                const int rel = (int)(low[k] - 8ll * bb);  // 0..7 by the ownership above
                 cell[k] = (int8_t)rel;
                 const int j = k - k0[bb];
-                uint16_t& sp = span[(size_t)bb * 9 + rel];
+                if (j > 255) return fail(v, TSDF_ERR_INVALID_ARG, "colour grid does not fit the bricks");
+                uint16_t& sp = span[(size_t)bb * BRICK + rel];
                 if ((sp >> 8) == 0) sp = (uint16_t)(j | ((j + 1) << 8));
                 else sp = (uint16_t)((sp & 0xFFu) | ((j + 1) << 8));
             }
@@ -383,8 +386,8 @@ static tsdf_status build_axis_tables(tsdf_volume* v) {
         std::vector<uint16_t> info(nb, 0);
         for (int bb = 0; bb < nb; ++bb) {
             uint32_t mask = 0, most = 0;
-            for (int cl = 0; cl < 9; ++cl) {
-                const uint16_t sp = span[(size_t)bb * 9 + cl];
+            for (int cl = 0; cl < BRICK; ++cl) {
+                const uint16_t sp = span[(size_t)bb * BRICK + cl];
                 const uint32_t n = (sp >> 8) - (sp & 0xFFu);
                 if (sp >> 8) mask |= 1u << cl;
                 most = std::max(most, (sp >> 8) ? n : 0u);
@@ -395,12 +398,12 @@ static tsdf_status build_axis_tables(tsdf_volume* v) {
         float* d_frac = (float*)dev_alloc(v, nc * sizeof(float));
         int8_t* d_cell = (int8_t*)dev_alloc(v, nc);
         int32_t* d_k0 = (int32_t*)dev_alloc(v, (nb + 1) * sizeof(int32_t));
-        uint16_t* d_span = (uint16_t*)dev_alloc(v, (size_t)nb * 9 * sizeof(uint16_t));
+        uint16_t* d_span = (uint16_t*)dev_alloc(v, (size_t)nb * BRICK * sizeof(uint16_t));
         if (!d_frac || !d_cell || !d_k0 || !d_span || !d_info) return fail(v, TSDF_ERR_OOM, "colour axis tables");
         cudaError_t e = cudaMemcpy(d_frac, frac.data(), nc * sizeof(float), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(d_cell, cell.data(), nc, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(d_k0, k0.data(), (nb + 1) * sizeof(int32_t), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMemcpy(d_span, span.data(), (size_t)nb * 9 * sizeof(uint16_t), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d_span, span.data(), (size_t)nb * BRICK * sizeof(uint16_t), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(d_info, info.data(), nb * sizeof(uint16_t), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_fail(v, e, "colour axis tables");
         v->vol.tab.frac[a] = d_frac;
