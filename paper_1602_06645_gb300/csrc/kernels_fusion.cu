@@ -890,7 +890,7 @@ __device__ __forceinline__ bool colour_after_band(const FrameConst& c, uint32_t*
 // The cell marks are conservative (eps bounds the trilinear rounding); the
 // band gate itself is evaluated exactly as written.
 constexpr int MAXK = 66;    // owned colour indices per axis (colour/geometry ratio <= 8)
-constexpr int STAGE = 256;  // per-warp record staging entries
+constexpr int STAGE = 512;  // per-warp record staging entries (kept across a warp's bricks)
 
 struct ColourSlot {  // one warp's shared-memory working set (~7 KB)
     float F[TILE_G3];
@@ -974,10 +974,12 @@ __device__ uint32_t flush_records(const FrameConst& c, const Volumes& vol, const
 
 // Band gate of the colour voxels owned by geometry brick b, by one warp with
 // shared-memory slot S (steps 1-4 above).
+// Records stay in S.out (nstage of them) across the warp's bricks: the caller
+// flushes what is left (band_flush) when its bricks are done.
 __device__ __forceinline__ void band_brick(const FrameConst& c, const Volumes& vol, const uint16_t* __restrict__ depth,
                                            const uint8_t* __restrict__ rgb, const Scratch& scr, ColourSlot& S,
                                            uint32_t b, int lane, uint32_t& count, uint32_t& n_active,
-                                           uint32_t& n_cells) {
+                                           uint32_t& n_cells, uint32_t& nstage) {
     const unsigned full = 0xffffffffu;
     const float lo_thr = c.band + CELL_EPS, hi_thr = -c.band - CELL_EPS;
     const int bb[3] = {(int)(b % c.nb[0]), (int)((b / c.nb[0]) % c.nb[1]), (int)(b / (c.nb[0] * c.nb[1]))};
@@ -1127,7 +1129,6 @@ __device__ __forceinline__ void band_brick(const FrameConst& c, const Volumes& v
     // per voxel).  Loops run to the warp-wide most indices per axis so the
     // record ballots stay uniform.
     const uint32_t lanemask_lt = (1u << lane) - 1u;
-    uint32_t nstage = 0;
     for (uint32_t cb = 0; cb < nact; cb += 32) {
         const bool live = cb + lane < nact;
         int sx = 0, ex = 0, sy = 0, ey = 0, sz = 0, ez = 0;
@@ -1182,8 +1183,15 @@ __device__ __forceinline__ void band_brick(const FrameConst& c, const Volumes& v
             }
         }
     }
+}
+
+// The records a warp still holds in S.out.
+__device__ __forceinline__ void band_flush(const FrameConst& c, const Volumes& vol, const uint16_t* __restrict__ depth,
+                                           const uint8_t* __restrict__ rgb, const Scratch& scr, const ColourSlot& S,
+                                           int lane, uint32_t& count, uint32_t& nstage) {
     __syncwarp();
     if (nstage) count += flush_records(c, vol, depth, rgb, scr, S, nstage, lane);
+    nstage = 0;
 }
 
 __global__ void __launch_bounds__(COL_THREADS, 5) k_colour_band(FrameConst c, Volumes vol,
@@ -1196,7 +1204,7 @@ __global__ void __launch_bounds__(COL_THREADS, 5) k_colour_band(FrameConst c, Vo
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
     const uint32_t n = ctr->n_col;
-    uint32_t count = 0, n_active = 0, n_cells = 0;
+    uint32_t count = 0, n_active = 0, n_cells = 0, nstage = 0;
     // the next item's index is claimed while the current one is processed
     uint32_t next = 0;
     if (lane == 0) next = atomicAdd(&ctr->col_next, 1u);
@@ -1204,9 +1212,10 @@ __global__ void __launch_bounds__(COL_THREADS, 5) k_colour_band(FrameConst c, Vo
         const uint32_t item = __shfl_sync(full, next, 0);
         if (item >= n) break;
         if (lane == 0) next = atomicAdd(&ctr->col_next, 1u);
-        band_brick(c, vol, depth, rgb, scr, S, scr.col_list[item], lane, count, n_active, n_cells);
+        band_brick(c, vol, depth, rgb, scr, S, scr.col_list[item], lane, count, n_active, n_cells, nstage);
         __syncwarp();
     }
+    band_flush(c, vol, depth, rgb, scr, S, lane, count, nstage);
     count = __reduce_add_sync(full, count);
     if (lane == 0) {  // n_active and n_cells are the same in every lane
         if (count) atomicAdd(&ctr->col_updated, (unsigned long long)count);
@@ -1369,10 +1378,10 @@ __device__ __forceinline__ void fuse_release(const FrameConst& c, const Scratch&
 __device__ __forceinline__ void fuse_colour(const FrameConst& c, const Volumes& vol, const uint16_t* __restrict__ depth,
                                             const uint8_t* __restrict__ rgb, const Scratch& scr, ColourSlot& S,
                                             uint32_t b, int lane, uint32_t& count, uint32_t& n_active,
-                                            uint32_t& n_cells, uint32_t& n_cand) {
+                                            uint32_t& n_cells, uint32_t& n_cand, uint32_t& nstage) {
     if (!colour_candidate_warp(c, vol.summ, b, lane)) return;
     ++n_cand;
-    band_brick(c, vol, depth, rgb, scr, S, b, lane, count, n_active, n_cells);
+    band_brick(c, vol, depth, rgb, scr, S, b, lane, count, n_active, n_cells, nstage);
     __syncwarp();
 }
 
@@ -1406,7 +1415,7 @@ __global__ void __launch_bounds__(COL_THREADS, 5) k_fused(FrameConst c, Volumes 
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     const uint32_t n = ctr->n_geo, nv = ctr->n_vis;
     const DepthM dm{scr.depth_m};
-    uint32_t gcount = 0, changed = 0, count = 0, n_active = 0, n_cells = 0, n_cand = 0;
+    uint32_t gcount = 0, changed = 0, count = 0, n_active = 0, n_cells = 0, n_cand = 0, nstage = 0;
     bool ok = true;
     // own geometry bricks, in list order (about z order: the bricks whose
     // neighbourhoods are complete follow the front), one ready colour brick
@@ -1432,7 +1441,7 @@ __global__ void __launch_bounds__(COL_THREADS, 5) k_fused(FrameConst c, Volumes 
                 ok = false;
                 break;
             }
-            fuse_colour(c, vol, depth, rgb, scr, S, b, lane, count, n_active, n_cells, n_cand);
+            fuse_colour(c, vol, depth, rgb, scr, S, b, lane, count, n_active, n_cells, n_cand, nstage);
         }
     }
     // the remaining ready bricks
@@ -1446,8 +1455,9 @@ __global__ void __launch_bounds__(COL_THREADS, 5) k_fused(FrameConst c, Volumes 
             ok = false;
             break;
         }
-        fuse_colour(c, vol, depth, rgb, scr, S, b, lane, count, n_active, n_cells, n_cand);
+        fuse_colour(c, vol, depth, rgb, scr, S, b, lane, count, n_active, n_cells, n_cand, nstage);
     }
+    band_flush(c, vol, depth, rgb, scr, S, lane, count, nstage);
     if (!ok && lane == 0) atomicOr(scr.err, ERR_WAIT_TIMEOUT);
     gcount = __reduce_add_sync(full, gcount);
     count = __reduce_add_sync(full, count);
@@ -1816,12 +1826,14 @@ __global__ void __launch_bounds__(COL_THREADS, 4) k_batch_step(const ScanDesc* _
         if (item >= pre[n]) break;
         const int s = find_scan(pre, n, item);
         const ScanDesc& d = descs[s];
-        uint32_t count = 0, n_active = 0, n_cells = 0;
+        uint32_t count = 0, n_active = 0, n_cells = 0, nstage = 0;
         const uint32_t k0 = (item - pre[s]) * tile, k1 = min(k0 + (uint32_t)tile, d.scr.ctr->n_col);
         for (uint32_t k = k0; k < k1; ++k) {
-            band_brick(d.c, d.vol, d.depth, d.rgb, d.scr, S, d.scr.col_list[k], lane, count, n_active, n_cells);
+            band_brick(d.c, d.vol, d.depth, d.rgb, d.scr, S, d.scr.col_list[k], lane, count, n_active, n_cells,
+                       nstage);
             __syncwarp();
         }
+        band_flush(d.c, d.vol, d.depth, d.rgb, d.scr, S, lane, count, nstage);  // the records are this scan's
         count = __reduce_add_sync(full, count);
         if (lane == 0) {
             if (count) atomicAdd(&d.scr.ctr->col_updated, (unsigned long long)count);
