@@ -304,8 +304,9 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
     def volume():
+        # the device frames are uploaded and synchronised before any step
         return T.Volume(seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, seq.max_weight, culling=not args.dense,
-                        stream=stream.cuda_stream, slab=slab, schedule=schedule_of(args))
+                        stream=stream.cuda_stream, slab=slab, schedule=schedule_of(args), device_inputs_ready=True)
 
     # Phase breakdown: the same frames through a separate volume with every
     # phase timed (eight event records per frame), before the timed run.
@@ -663,9 +664,9 @@ def run_fused(args):
         torch.cuda.synchronize()
         return float(sum(a.elapsed_time(b) for a, b in ev))
 
-    def volume():
+    def volume():  # the device frames are uploaded and synchronised before any step
         return T.Volume(seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, seq.max_weight,
-                        stream=stream.cuda_stream)
+                        stream=stream.cuda_stream, device_inputs_ready=True)
 
     vf = volume()
     batch = T.Batch([vf])

@@ -154,9 +154,12 @@ tsdf_status tsdf_create_ex(const int32_t dims_geo[3], const int32_t dims_col[3],
  * for before the frame's geometry update): pageable memory is consumed before
  * the call returns, page-locked memory by the time the handle's stream
  * reaches the frame's geometry update.  Device images are read in place by
- * kernels queued on the streams.  In both asynchronous cases the caller must
- * not overwrite the buffer until the handle's stream has passed the frame's
- * last kernel.  The call is asynchronous with respect to the host.
+ * kernels queued on the streams, after all work queued on the handle's
+ * stream before the call (a device depth image then waits for the previous
+ * frame's colour kernels too; see tsdf_set_device_inputs_ready).  In both
+ * asynchronous cases the caller must not overwrite the buffer until the
+ * handle's stream has passed the frame's last kernel.  The call is
+ * asynchronous with respect to the host.
  * Errors: INVALID_ARG (NULL pointers, sizes outside 1..16384, non-finite or
  * singular K, non-finite or non-rigid T with |R^T R - I| > 1e-4, a
  * translation beyond 10^6 m), OOM, CUDA. */
@@ -181,6 +184,17 @@ tsdf_status tsdf_integrate(tsdf_volume* vol, const uint16_t* depth_mm, tsdf_imag
 enum { TSDF_SCHEDULE_KERNELS = 0, TSDF_SCHEDULE_FUSED = 1 };
 tsdf_status tsdf_set_frame_schedule(tsdf_volume* vol, int32_t schedule);
 tsdf_status tsdf_get_frame_schedule(const tsdf_volume* vol, int32_t* schedule);
+
+/* ready = 1: the caller guarantees that the device images it passes to
+ * tsdf_integrate are complete when the call is made (written before an
+ * earlier tsdf_integrate call on this handle, or by work the caller has
+ * synchronised with).  A device depth image is then read by the frame's
+ * depth tiles and brick culling on the second stream as soon as the previous
+ * frame's colour list is done, beside its band and colour kernels, instead
+ * of after all work on the handle's stream.  Default 0.  Host images are
+ * unaffected (they are copied at the call).
+ * Errors: INVALID_ARG (NULL handle, ready not 0 or 1). */
+tsdf_status tsdf_set_device_inputs_ready(tsdf_volume* vol, int32_t ready);
 
 /* Test hook of the fused schedule's bounded waits: in the next fused frame
  * one visible brick is never released, so the wait for it runs out (no

@@ -40,7 +40,7 @@ EXPORTS = [
     "tsdf_batch_set_schedule", "tsdf_batch_get_schedule", "tsdf_batch_autotune", "tsdf_batch_inject_stall",
     "tsdf_batch_destroy", "tsdf_raycast", "tsdf_mesh", "tsdf_mesh_ex", "tsdf_texture_layout", "tsdf_texture_fill",
     "tsdf_profile_phases", "tsdf_track_params_default", "tsdf_track", "tsdf_set_frame_schedule",
-    "tsdf_get_frame_schedule", "tsdf_fused_inject_stall",
+    "tsdf_get_frame_schedule", "tsdf_fused_inject_stall", "tsdf_set_device_inputs_ready",
 ]
 PHASES = ["upload", "depth_tiles", "bricks", "geometry", "colour_list", "colour_cells", "colour"]
 
@@ -161,6 +161,7 @@ def load():
     lib.tsdf_set_frame_schedule.argtypes = [vp, ctypes.c_int32]
     lib.tsdf_get_frame_schedule.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
     lib.tsdf_fused_inject_stall.argtypes = [vp]
+    lib.tsdf_set_device_inputs_ready.argtypes = [vp, ctypes.c_int32]
     lib.tsdf_save.argtypes = [vp, ctypes.c_char_p]
     lib.tsdf_load.argtypes = [vp, ctypes.c_char_p]
     lib.tsdf_destroy.argtypes = [vp]
@@ -417,6 +418,10 @@ def tsdf_fused_inject_stall(h):
     _check(load().tsdf_fused_inject_stall(h), h)
 
 
+def tsdf_set_device_inputs_ready(h, ready):
+    _check(load().tsdf_set_device_inputs_ready(h, int(ready)), h)
+
+
 def tsdf_save(h, path):
     _check(load().tsdf_save(h, str(path).encode()), h)
 
@@ -647,11 +652,13 @@ class Volume:
 
     def __init__(self, dims_geo, dims_col, voxel_size, mu, max_weight, *, origin=None, sigma=0.020, band=None,
                  colour_mode=TSDF_COLOUR_COUNT, sample_mode=TSDF_SAMPLE_NEAREST, culling=True,
-                 update_free_space=True, stream=None, torch_memory=True, slab=None, schedule=None):
+                 update_free_space=True, stream=None, torch_memory=True, slab=None, schedule=None,
+                 device_inputs_ready=False):
         """slab = (z0, z1): hold the z-slab [z0, z1) of the volume (see
         tsdf_create_ex); dims_geo / dims_col are the whole volume's.
         schedule: TSDF_SCHEDULE_KERNELS or TSDF_SCHEDULE_FUSED (see
-        tsdf_set_frame_schedule); None keeps the library's default."""
+        tsdf_set_frame_schedule); None keeps the library's default.
+        device_inputs_ready: see tsdf_set_device_inputs_ready."""
         import torch
 
         self.dims_geo = tuple(int(v) for v in dims_geo)
@@ -680,6 +687,8 @@ class Volume:
         self.held_col_z = (info.held_col_z[0], info.held_col_z[1])
         if schedule is not None:
             tsdf_set_frame_schedule(self.h, schedule)
+        if device_inputs_ready:
+            tsdf_set_device_inputs_ready(self.h, 1)
 
     @property
     def schedule(self):

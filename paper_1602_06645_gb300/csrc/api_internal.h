@@ -63,6 +63,7 @@ struct tsdf_volume {
     size_t d_rgb_cap;
     int64_t frames;
     int32_t schedule = TSDF_SCHEDULE_KERNELS;  // tsdf_set_frame_schedule
+    bool inputs_ready = false;                 // tsdf_set_device_inputs_ready
     int64_t device_bytes;
     std::string last_error;
     // phase timing (tsdf_profile_enable)

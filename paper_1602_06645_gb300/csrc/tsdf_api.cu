@@ -662,7 +662,11 @@ tsdf_status tsdf_integrate(tsdf_volume* v, const uint16_t* depth_mm, tsdf_image_
     const bool pipe = !(v->profiling && (v->prof_mask & 0x7u));
     cudaStream_t pre = pipe ? v->side : v->stream;
     if (pipe) {
-        if (v->chain_ok) {
+        // a device depth image is read by the side stream: unless the caller
+        // declared its device images complete at the call, wait for all the
+        // work queued on the handle's stream before it
+        const bool wait_caller = is_device_ptr(depth_mm) && !v->inputs_ready;
+        if (v->chain_ok && !wait_caller) {
             e = cudaStreamWaitEvent(v->side, v->list_done, 0);
         } else {
             e = cudaEventRecord(v->main_tail, v->stream);
@@ -735,6 +739,12 @@ tsdf_status tsdf_set_frame_schedule(tsdf_volume* v, int32_t schedule) {
     if (schedule != TSDF_SCHEDULE_KERNELS && schedule != TSDF_SCHEDULE_FUSED)
         return fail(v, TSDF_ERR_INVALID_ARG, "frame schedule: TSDF_SCHEDULE_KERNELS or TSDF_SCHEDULE_FUSED");
     v->schedule = schedule;
+    return TSDF_OK;
+}
+
+tsdf_status tsdf_set_device_inputs_ready(tsdf_volume* v, int32_t ready) {
+    if (!v || (ready != 0 && ready != 1)) return TSDF_ERR_INVALID_ARG;
+    v->inputs_ready = ready != 0;
     return TSDF_OK;
 }
 

@@ -316,3 +316,35 @@ def test_async_stats_equal_synchronous_reads(device_inputs, profiled):
     a.close()
     b.close()
     assert np.array_equal(Fa, Fb) and np.array_equal(Wa, Wb) and np.array_equal(Ca, Cb)
+
+
+def test_device_depth_written_on_the_handle_stream_just_before_the_call():
+    """A device depth image written by work queued on the handle's stream
+    right before tsdf_integrate (behind a GPU sleep, so the write is late) is
+    read only after that work: the volumes equal those of the same frames
+    passed as ready device images.  With the inputs declared ready the
+    second stream may start early, so such a caller must not declare it."""
+    seq = synth.sequence_small(n_frames=4, dims_geo=48, seed=31)
+    args = (seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, seq.max_weight)
+    frames = [seq.frame(f) for f in range(4)]
+    ref = T.Volume(*args)
+    for f, (d, c) in enumerate(frames):
+        ref.integrate(torch.from_numpy(d.view(np.int16)).cuda(), torch.from_numpy(c).cuda(), seq.K_depth,
+                      seq.K_rgb, seq.poses[f], seq.T_depth_rgb)
+    expected = ref.read()
+    ref.close()
+    v = T.Volume(*args)
+    depth = torch.zeros(frames[0][0].shape, dtype=torch.int16, device="cuda")
+    for f, (d, c) in enumerate(frames):
+        # both uploads before the sleep: a pageable upload after it would make
+        # the host wait for the stream, and the write would no longer be late
+        src = torch.from_numpy(d.view(np.int16)).cuda()
+        rgb = torch.from_numpy(c).cuda()
+        torch.cuda.synchronize()
+        torch.cuda._sleep(20_000_000)  # ~10 ms on the handle's stream before the write
+        depth.copy_(src)
+        v.integrate(depth, rgb, seq.K_depth, seq.K_rgb, seq.poses[f], seq.T_depth_rgb)
+    got = v.read()
+    v.close()
+    for a, b in zip(got, expected):
+        np.testing.assert_array_equal(a, b)
