@@ -593,9 +593,11 @@ def run_batched(args):
     batch.close()
     for v in vols:
         v.close()
-    # sequential per-scan launches on fresh volumes, same frames
-    vols = [T.Volume(s.dims_geo, s.dims_col, s.voxel_size, s.mu, s.max_weight, stream=stream.cuda_stream)
-            for s, _ in data]
+    # sequential per-scan launches on fresh volumes, same frames (resident
+    # and synchronised, so each volume may overlap its frames)
+    torch.cuda.synchronize()
+    vols = [T.Volume(s.dims_geo, s.dims_col, s.voxel_size, s.mu, s.max_weight, stream=stream.cuda_stream,
+                     device_inputs_ready=True) for s, _ in data]
 
     def seq_step(f):
         for v, (_, fr) in zip(vols, data):
@@ -648,6 +650,7 @@ def run_fused(args):
     frames = [(torch.from_numpy(d.view(np.int16)).cuda(), torch.from_numpy(c).cuda(), seq.K_depth, seq.K_rgb,
                seq.poses[f], seq.T_depth_rgb) for f, (d, c) in enumerate(render_frames(seq, n))]
     gen_s = time.perf_counter() - t0
+    torch.cuda.synchronize()  # the frames are complete before any step
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
@@ -897,9 +900,13 @@ def run_adjoint(args):
         torch.cuda.synchronize()
         return a.elapsed_time(b) / reps
 
-    # plain fusion of the 20 frames (fresh volume each repetition)
+    # plain fusion of the 20 frames (fresh volume each repetition; the frames
+    # are resident and synchronised)
+    torch.cuda.synchronize()
+
     def plain():
-        v = T.Volume(seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, seq.max_weight, stream=stream.cuda_stream)
+        v = T.Volume(seq.dims_geo, seq.dims_col, seq.voxel_size, seq.mu, seq.max_weight, stream=stream.cuda_stream,
+                     device_inputs_ready=True)
         for f in range(n_frames):
             v.integrate(depth[f], rgb8[f], seq.K_depth, seq.K_rgb, seq.poses[f], seq.T_depth_rgb)
         v.synchronize()

@@ -140,7 +140,7 @@ struct Scratch {
     uint32_t* depth_tiles;  // per 8x8 tile: min valid depth | max valid depth << 16
     float* depth_m;         // per pixel RN(D * 0.001) metres, -inf where D = 0
     uint8_t* bstate;        // per brick, this frame: bit 0 = in the geometry list, bit 1 = visible
-    uint32_t* need;         // per visible brick: listed bricks among its 27 neighbours not yet updated
+    uint32_t* need;         // per visible brick: listed bricks among it and its + neighbours not yet updated
     unsigned long long* ready;  // ready queue of the fused frame: frame_tag << 32 | brick
     struct FuseSync* fsync;
     uint32_t* err;

@@ -5,7 +5,8 @@
 //   k_depth_tiles   min / max valid depth of each 8x8 depth tile; zeroes counters
 //   k_bricks        conservative per-brick visibility -> geometry and visible lists
 //   k_geometry      persistent: TSDF update of each listed brick, brick summaries
-//   k_colour_list   visible bricks whose 3x3x3 neighbourhood can hold |F| <= band
+//   k_colour_list   visible bricks whose owned cells (the brick and the first layers
+//                   of its + neighbours) can hold |F| <= band
 //   k_colour_band   one warp per listed brick: stages its geometry tile, finds
 //                   the trilinear cells that can pass the band gate and records
 //                   the colour voxels whose trilinear TSDF passes it
@@ -871,28 +872,30 @@ __device__ __forceinline__ bool colour_after_band(const FrameConst& c, uint32_t*
 }
 
 // Band gate of the colour voxels a geometry brick owns (first colour
-// kernel).  One warp per listed brick, taken with an atomic counter.  The warp
-//   1. stages the brick's post-update geometry plus a one-voxel halo (10^3 F
-//      and w: the centre brick as float4, the halo as its 6 faces, 12 edges
-//      and 8 corners) in its shared-memory slot with three flag bits per
-//      voxel: observed (w > 0), F <= band + eps, F >= -band - eps; and
-//      tabulates, per axis, the owned colour indices' centres, trilinear
-//      cell and cell fraction;
-//   2. packs the flags into 10-bit row masks;
-//   3. marks the 9^3 trilinear cells that can pass the band gate (all eight
-//      corners observed, the corner range meets [-band, band]) as 9-bit masks
+// kernel): those whose trilinear cell has its lower corner in the brick, so
+// every owned cell lies between the brick's voxels 0..8 on each axis.  One
+// warp per listed brick, taken with an atomic counter.  The warp
+//   1. stages the brick's post-update geometry plus the first voxel layers of
+//      its + neighbours (9^3 F and w: the brick as float4, the halo as 3
+//      faces, 3 edges and 1 corner) in its shared-memory slot with three flag
+//      bits per voxel: observed (w > 0), F <= band + eps, F >= -band - eps;
+//      and tabulates, per axis, the owned colour indices' cells and fractions;
+//   2. packs the flags into 9-bit row masks;
+//   3. marks the 8^3 trilinear cells that can pass the band gate (all eight
+//      corners observed, the corner range meets [-band, band]) as 8-bit masks
 //      (AND / OR of four rows, then of neighbouring bits) and compacts them;
 //   4. evaluates the trilinear TSDF (lerp along x, then y, then z) of every
 //      colour voxel of a marked cell and records those with |F| <= band for
-//      the colour-voxel kernel, through a shared staging buffer (one atomic
-//      per 256 records).  Records that do not fit the global buffer are
-//      finished by the warp itself (same arithmetic).
+//      the colour-voxel kernel, through a shared staging buffer kept across
+//      the warp's bricks (one atomic per flush of up to STAGE records).
+//      Records that do not fit the global buffer are finished by the warp
+//      itself (same arithmetic).
 // The cell marks are conservative (eps bounds the trilinear rounding); the
 // band gate itself is evaluated exactly as written.
 constexpr int MAXK = 66;    // owned colour indices per axis (colour/geometry ratio <= 8)
 constexpr int STAGE = 512;  // per-warp record staging entries (kept across a warp's bricks)
 
-struct ColourSlot {  // one warp's shared-memory working set (~7 KB)
+struct ColourSlot {  // one warp's shared-memory working set (~9 KB)
     float F[TILE_G3];
     // per tile row (z * 9 + y): bit x = observed, bit 9 + x = F <= band + eps,
     // bit 18 + x = F >= -band - eps
