@@ -1235,10 +1235,14 @@ __global__ void __launch_bounds__(256) k_colour_voxels(FrameConst c, Volumes vol
     chain_enter();
     Counters* __restrict__ ctr = scr.ctr;
     const uint32_t nv = min(ctr->n_vox, scr.vox_cap);
+    const uint32_t stride = gridDim.x * blockDim.x;
     uint32_t count = 0;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += gridDim.x * blockDim.x) {
-        const uint2 r = scr.vox[i];
+    uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    uint2 r = i < nv ? scr.vox[i] : make_uint2(0u, 0u);
+    for (; i < nv; i += stride) {  // the next record is read while this one is updated
+        const uint2 rn = i + stride < nv ? scr.vox[i + stride] : make_uint2(0u, 0u);
         if (colour_after_band(c, vol.C, depth, rgb, (int)(r.x & 0xFFFFu), (int)(r.x >> 16), (int)r.y)) ++count;
+        r = rn;
     }
     count = __reduce_add_sync(0xffffffffu, count);
     if ((threadIdx.x & 31) == 0 && count) atomicAdd(&ctr->col_updated, (unsigned long long)count);
