@@ -37,7 +37,9 @@ struct tsdf_volume {
     // after frame k + 1's culling.  chain_ok: the last call that touched the
     // volume on `stream` was a pipelined tsdf_integrate (else `side` waits for
     // all of `stream` first).  Host depth frames alternate between two
-    // staging buffers.
+    // staging buffers.  `side` has the device's highest stream priority, so
+    // its small blocks are dispatched ahead of the colour kernel queued
+    // (programmatic launch) behind frame k's band kernel.
     cudaStream_t side;
     cudaEvent_t list_done, bricks_done, main_tail;
     bool chain_ok;

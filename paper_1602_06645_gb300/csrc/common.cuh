@@ -19,7 +19,6 @@ namespace tsdf {
 constexpr int BRICK = 8;
 constexpr int BRICK_VOX = BRICK * BRICK * BRICK;
 constexpr int TILE_PX = 8;         // depth-culling tiles are 8x8 pixels
-constexpr int TILE_BLOCK_PX = 16;  // k_depth_tiles: one 16x16-pixel block makes 2x2 tiles
 
 // Per-frame constants, passed by value as a kernel parameter.
 struct FrameConst {

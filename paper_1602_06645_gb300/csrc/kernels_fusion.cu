@@ -34,62 +34,72 @@ constexpr int CELLS3 = CELLS * CELLS * CELLS;
 // ------------------------------------------------------- depth tiles ----
 // Per 8x8-pixel tile the min / max valid depth (mm); with depth_m, also the
 // depth in metres per pixel as the geometry update reads it: RN(D * 0.001),
-// -inf where D = 0.
-__global__ void __launch_bounds__(256) k_depth_tiles(FrameConst c, const uint16_t* __restrict__ depth,
-                                                     uint32_t* __restrict__ tiles, Counters* __restrict__ ctr,
-                                                     float* __restrict__ depth_m) {
+// -inf where D = 0.  One warp per strip of four tiles (32 x 8 pixels): lane
+// x reads column x of the strip row by row (64 contiguous bytes per row),
+// and lanes 8t .. 8t + 7 reduce tile t.  Blocks are two warps: the next
+// frame's tiles run beside the current frame's colour kernels, whose blocks
+// leave only a few thousand registers of an SM free.
+constexpr int TILES_THREADS = 64;
+constexpr int STRIP_PX = 32;  // strip width: four tiles
+
+__host__ __device__ inline uint32_t depth_strips(const FrameConst& c) {
+    return (uint32_t)((c.dw + STRIP_PX - 1) / STRIP_PX) * (uint32_t)c.tiles_y;
+}
+
+__global__ void __launch_bounds__(TILES_THREADS) k_depth_tiles(FrameConst c, const uint16_t* __restrict__ depth,
+                                                               uint32_t* __restrict__ tiles,
+                                                               Counters* __restrict__ ctr,
+                                                               float* __restrict__ depth_m) {
     chain_enter();
-    static_assert(TILE_BLOCK_PX == 2 * TILE_PX && TILE_PX == 8, "the lane layout below assumes 8x8 tiles");
-    // a 16x16-pixel block; warp w holds pixel rows 2w and 2w + 1, lane bit 3
-    // selects the left or right 8-pixel half: tile (hx, hy) of the block is
-    // half hx of warps 4 hy .. 4 hy + 3
-    __shared__ uint32_t s_min[8][2], s_max[8][2];
-    const int px = blockIdx.x * TILE_BLOCK_PX + threadIdx.x, py = blockIdx.y * TILE_BLOCK_PX + threadIdx.y;
-    const bool in = px < c.dw && py < c.dh;
-    const uint32_t D = in ? depth[(size_t)py * c.dw + px] : 0u;
-    if (depth_m) {
-        const float ninf = __int_as_float(0xff800000);
-        if (in) depth_m[(size_t)py * c.dw + px] = D ? (float)D * 0.001f : ninf;
-    }
-    uint32_t mn = D ? D : 0xFFFFu, mx = D;
+    static_assert(TILE_PX == 8 && STRIP_PX == 4 * TILE_PX, "the lane layout below assumes 8x8 tiles");
+    const int lane = threadIdx.x & 31;
+    const uint32_t strip = blockIdx.x * (TILES_THREADS / 32) + (threadIdx.x >> 5);
+    const uint32_t sx_n = (uint32_t)((c.dw + STRIP_PX - 1) / STRIP_PX);
+    if (strip < depth_strips(c)) {
+        const int ty = (int)(strip / sx_n), sx = (int)(strip % sx_n);
+        const int px = sx * STRIP_PX + lane;
+        const bool xin = px < c.dw;
+        uint32_t D[TILE_PX];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        if (o == 8) continue;  // keep the two halves apart
-        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    }
-    const int tid = threadIdx.y * TILE_BLOCK_PX + threadIdx.x, lane = tid & 31, w = tid >> 5;
-    if ((lane & 23) == 0) {  // lanes 0 and 8
-        s_min[w][lane >> 3] = mn;
-        s_max[w][lane >> 3] = mx;
-    }
-    __syncthreads();
-    if (tid < 4) {
-        const int hx = tid & 1, hy = tid >> 1;
-        uint32_t a = 0xFFFFu, b = 0u;
-        for (int k = 0; k < 4; ++k) {
-            a = min(a, s_min[4 * hy + k][hx]);
-            b = max(b, s_max[4 * hy + k][hx]);
+        for (int r = 0; r < TILE_PX; ++r) {  // the eight row reads are independent
+            const int py = ty * TILE_PX + r;
+            D[r] = xin && py < c.dh ? depth[(size_t)py * c.dw + px] : 0u;
         }
-        const int tx = blockIdx.x * 2 + hx, ty = blockIdx.y * 2 + hy;
-        if (tx < c.tiles_x && ty < c.tiles_y) tiles[ty * c.tiles_x + tx] = a | (b << 16);
-    }
-    if (tid == 0) {
-        if (blockIdx.x == 0 && blockIdx.y == 0) {
-            // fold the previous frame's geometry-side counters into the running
-            // totals (the colour side is folded by the geometry kernel, so this
-            // kernel may run while the previous frame's colour work finishes)
-            ctr->tot_geo_updated += ctr->geo_updated;
-            ctr->tot_geo_bricks += ctr->n_geo;
-            ctr->tot_vis_bricks += ctr->n_vis;
-            ctr->tot_geo_changed += ctr->n_geo_changed;
-            ctr->n_geo_changed = 0;
-            ctr->frames += 1ull;
-            ctr->n_geo = ctr->n_vis = 0;
-            ctr->geo_next = 0;
-            ctr->geo_updated = 0ull;
+        uint32_t mn = 0xFFFFu, mx = 0u;
+        const float ninf = __int_as_float(0xff800000);
+#pragma unroll
+        for (int r = 0; r < TILE_PX; ++r) {
+            const int py = ty * TILE_PX + r;
+            if (depth_m && xin && py < c.dh) depth_m[(size_t)py * c.dw + px] = D[r] ? (float)D[r] * 0.001f : ninf;
+            mn = min(mn, D[r] ? D[r] : 0xFFFFu);
+            mx = max(mx, D[r]);
         }
+#pragma unroll
+        for (int o = 1; o < TILE_PX; o <<= 1) {  // within each group of eight lanes
+            mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        }
+        const int tx = sx * 4 + (lane >> 3);
+        if ((lane & 7) == 0 && tx < c.tiles_x) tiles[ty * c.tiles_x + tx] = mn | (mx << 16);
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        // fold the previous frame's geometry-side counters into the running
+        // totals (the colour side is folded by the geometry kernel, so this
+        // kernel may run while the previous frame's colour work finishes)
+        ctr->tot_geo_updated += ctr->geo_updated;
+        ctr->tot_geo_bricks += ctr->n_geo;
+        ctr->tot_vis_bricks += ctr->n_vis;
+        ctr->tot_geo_changed += ctr->n_geo_changed;
+        ctr->n_geo_changed = 0;
+        ctr->frames += 1ull;
+        ctr->n_geo = ctr->n_vis = 0;
+        ctr->geo_next = 0;
+        ctr->geo_updated = 0ull;
+    }
+}
+
+dim3 depth_tiles_grid(const FrameConst& c) {
+    return dim3((depth_strips(c) + TILES_THREADS / 32 - 1) / (TILES_THREADS / 32));
 }
 
 // ------------------------------------------------------------ bricks ----
@@ -297,6 +307,33 @@ __device__ __forceinline__ void block_append2(bool p0, bool p1, uint32_t value0,
     if (p0) list0[off[0][NW] + off[0][wid] + __popc(m0 & lt)] = value0;
     if (p1) list1[off[1][NW] + off[1][wid] + __popc(m1 & lt)] = value1;
     __syncthreads();  // off is reused by the block's next call
+}
+
+// Add per-warp counts (the same value in every lane of a warp) to up to three
+// global counters with one atomic per counter per block (all threads of the
+// block call it): the warps of a balanced kernel end together, and one atomic
+// per warp on one address would queue behind each other.
+template <int NT, typename T0, typename T1 = uint32_t, typename T2 = uint32_t>
+__device__ __forceinline__ void block_add(uint32_t v0, T0* d0, uint32_t v1 = 0u, T1* d1 = nullptr, uint32_t v2 = 0u,
+                                          T2* d2 = nullptr) {
+    constexpr int NW = NT / 32;
+    __shared__ uint32_t part[3][NW];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        part[0][wid] = v0;
+        part[1][wid] = v1;
+        part[2][wid] = v2;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        uint32_t sum = 0;
+        for (int w = 0; w < NW; ++w) sum += part[threadIdx.x][w];
+        if (sum) {
+            if (threadIdx.x == 0) atomicAdd(d0, (T0)sum);
+            else if (threadIdx.x == 1 && d1) atomicAdd(d1, (T1)sum);
+            else if (threadIdx.x == 2 && d2) atomicAdd(d2, (T2)sum);
+        }
+    }
 }
 
 // Geometry work-list entry: the brick's coordinates (10 bits per axis; the
@@ -649,9 +686,7 @@ __global__ void __launch_bounds__(GEO_THREADS, 8) k_geometry(FrameConst c, Volum
         else
             geometry_brick<PINHOLE, FREE_SPACE, ALIGNED, false>(c, vol, depth, rcp, at, lane, count, changed);
     }
-    count = __reduce_add_sync(0xffffffffu, count);
-    if (lane == 0 && count) atomicAdd(&ctr->geo_updated, (unsigned long long)count);
-    if (lane == 0 && changed) atomicAdd(&ctr->n_geo_changed, changed);
+    block_add<GEO_THREADS>(__reduce_add_sync(0xffffffffu, count), &ctr->geo_updated, changed, &ctr->n_geo_changed);
 }
 
 // Launch with programmatic stream serialization (the kernel begins with
@@ -1208,23 +1243,22 @@ __global__ void __launch_bounds__(COL_THREADS, 5) k_colour_band(FrameConst c, Vo
     const unsigned full = 0xffffffffu;
     const uint32_t n = ctr->n_col;
     uint32_t count = 0, n_active = 0, n_cells = 0, nstage = 0;
-    // the next item's index is claimed while the current one is processed
-    uint32_t next = 0;
-    if (lane == 0) next = atomicAdd(&ctr->col_next, 1u);
+    // a warp's first item is its index in the grid, the later ones are
+    // claimed from the counter (offset by the warp count), each while the
+    // previous item is processed
+    const uint32_t nwarps = gridDim.x * (COL_THREADS / 32);
+    uint32_t next = blockIdx.x * (COL_THREADS / 32) + (threadIdx.x >> 5);
     for (;;) {
         const uint32_t item = __shfl_sync(full, next, 0);
         if (item >= n) break;
-        if (lane == 0) next = atomicAdd(&ctr->col_next, 1u);
+        if (lane == 0) next = nwarps + atomicAdd(&ctr->col_next, 1u);
         band_brick(c, vol, depth, rgb, scr, S, scr.col_list[item], lane, count, n_active, n_cells, nstage);
         __syncwarp();
     }
     band_flush(c, vol, depth, rgb, scr, S, lane, count, nstage);
-    count = __reduce_add_sync(full, count);
-    if (lane == 0) {  // n_active and n_cells are the same in every lane
-        if (count) atomicAdd(&ctr->col_updated, (unsigned long long)count);
-        if (n_active) atomicAdd(&ctr->n_col_active, n_active);
-        if (n_cells) atomicAdd(&ctr->n_cells, n_cells);
-    }
+    // n_active and n_cells are the same in every lane
+    block_add<COL_THREADS>(__reduce_add_sync(full, count), &ctr->col_updated, n_active, &ctr->n_col_active, n_cells,
+                           &ctr->n_cells);
 }
 
 // Colour voxels that passed the band gate (second colour kernel): one thread
@@ -1244,8 +1278,7 @@ __global__ void __launch_bounds__(256) k_colour_voxels(FrameConst c, Volumes vol
         if (colour_after_band(c, vol.C, depth, rgb, (int)(r.x & 0xFFFFu), (int)(r.x >> 16), (int)r.y)) ++count;
         r = rn;
     }
-    count = __reduce_add_sync(0xffffffffu, count);
-    if ((threadIdx.x & 31) == 0 && count) atomicAdd(&ctr->col_updated, (unsigned long long)count);
+    block_add<256>(__reduce_add_sync(0xffffffffu, count), &ctr->col_updated);
 }
 
 // ------------------------------------------------------- fused frame ----
@@ -1925,9 +1958,8 @@ cudaError_t launch_frame_pre(const FrameConst& c, const Volumes& v, const Scratc
         if (ev && ev[i]) cudaEventRecord(ev[i], stream);
     };
     mark(0);
-    const dim3 tg((c.tiles_x + 1) / 2, (c.tiles_y + 1) / 2);
-    cudaError_t e = launch_chained(k_depth_tiles, tg, dim3(TILE_BLOCK_PX, TILE_BLOCK_PX), 0, stream, c, depth, s.depth_tiles,
-                                   s.ctr, s.depth_m);
+    cudaError_t e = launch_chained(k_depth_tiles, depth_tiles_grid(c), dim3(TILES_THREADS), 0, stream, c, depth,
+                                   s.depth_tiles, s.ctr, s.depth_m);
     mark(1);
     const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
     if (e == cudaSuccess)
@@ -1991,8 +2023,7 @@ cudaError_t launch_frame(const FrameConst& c, const Volumes& v, const Scratch& s
 
 cudaError_t launch_geometry_static(const FrameConst& c, float* F, uint8_t* W, const uint16_t* depth, Counters* ctr,
                                    uint32_t* tiles, uint32_t* geo_list, int grid_geo, cudaStream_t stream) {
-    const dim3 tg((c.tiles_x + 1) / 2, (c.tiles_y + 1) / 2);
-    k_depth_tiles<<<tg, dim3(TILE_BLOCK_PX, TILE_BLOCK_PX), 0, stream>>>(c, depth, tiles, ctr, nullptr);
+    k_depth_tiles<<<depth_tiles_grid(c), TILES_THREADS, 0, stream>>>(c, depth, tiles, ctr, nullptr);
     const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
     k_bricks_static<<<(nbt + 255) / 256, 256, 0, stream>>>(c, tiles, ctr, geo_list);
     if (c.kd_pinhole && c.free_space)
@@ -2008,8 +2039,7 @@ cudaError_t launch_geometry_static(const FrameConst& c, float* F, uint8_t* W, co
 
 cudaError_t launch_frame_record(const FrameConst& c, const Volumes& v, const Scratch& s, const uint16_t* depth,
                                 const LaunchGrids& g, const AdjBuffers& a, int frame, cudaStream_t stream) {
-    const dim3 tg((c.tiles_x + 1) / 2, (c.tiles_y + 1) / 2);
-    k_depth_tiles<<<tg, dim3(TILE_BLOCK_PX, TILE_BLOCK_PX), 0, stream>>>(c, depth, s.depth_tiles, s.ctr, s.depth_m);
+    k_depth_tiles<<<depth_tiles_grid(c), TILES_THREADS, 0, stream>>>(c, depth, s.depth_tiles, s.ctr, s.depth_m);
     const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
     k_bricks<<<(nbt + BRICK_THREADS - 1) / BRICK_THREADS, BRICK_THREADS, 0, stream>>>(c, v.summ, s.depth_tiles, s.ctr,
                                                                                      s.geo_list, s.vis_list, s.bstate,

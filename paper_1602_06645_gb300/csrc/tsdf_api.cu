@@ -503,7 +503,13 @@ tsdf_status tsdf_create_ex(const int32_t dims_geo[3], const int32_t dims_col[3],
         delete v;
         return TSDF_ERR_CUDA;
     }
-    if (cudaStreamCreateWithFlags(&v->side, cudaStreamNonBlocking) != cudaSuccess ||
+    // the side stream takes the device's highest priority: the next frame's
+    // depth tiles and brick culling then get the SM room that the current
+    // frame's band kernel leaves, ahead of the colour-voxel kernel queued
+    // behind it, and finish before that kernel does instead of after it
+    int prio_least = 0, prio_greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess) prio_greatest = 0;
+    if (cudaStreamCreateWithPriority(&v->side, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
         cudaEventCreateWithFlags(&v->list_done, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&v->bricks_done, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&v->main_tail, cudaEventDisableTiming) != cudaSuccess ||
