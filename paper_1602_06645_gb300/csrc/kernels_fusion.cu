@@ -1164,8 +1164,74 @@ __device__ __forceinline__ void band_brick(const FrameConst& c, const Volumes& v
     // 4. band gate of the colour voxels of the active cells, one lane per
     // cell: the x-lerps of an index jx serve every (jy, jz) of the cell and
     // the y-lerps of (jx, jy) every jz (the same operations as one lerp chain
-    // per voxel).  Loops run to the warp-wide most indices per axis so the
-    // record ballots stay uniform.
+    // per voxel).
+    if (mx <= 2 && my <= 2 && mz <= 2) {
+        // At most two owned indices per axis (colour/geometry ratio up to 2):
+        // a lane evaluates its cell's (at most eight) colour voxels into a
+        // pass mask, bit 4 ix + 2 iy + iz, and one prefix sum over the warp
+        // places the batch's records.
+        for (uint32_t cb = 0; cb < nact; cb += 32) {
+            uint32_t mask = 0;
+            uint32_t jx0 = 0, jy0 = 0, jz0 = 0;
+            if (cb + lane < nact) {
+                const uint32_t cellid = S.cells[cb + lane];
+                const int cx = cellid % CELLS, cy = (cellid / CELLS) % CELLS, cz = cellid / (CELLS * CELLS);
+                const int sx = S.start[0][cx], sy = S.start[1][cy], sz = S.start[2][cz];
+                const int nx = S.end[0][cx] - sx, ny = S.end[1][cy] - sy, nz = S.end[2][cz] - sz;
+                const int o = (cz * TILE_G + cy) * TILE_G + cx;
+                const float q000 = S.F[o], q100 = S.F[o + 1], q010 = S.F[o + TILE_G], q110 = S.F[o + TILE_G + 1];
+                const float q001 = S.F[o + TILE_G * TILE_G], q101 = S.F[o + TILE_G * TILE_G + 1];
+                const float q011 = S.F[o + TILE_G * TILE_G + TILE_G], q111 = S.F[o + TILE_G * TILE_G + TILE_G + 1];
+                const float fx[2] = {S.frac[0][sx], S.frac[0][nx > 1 ? sx + 1 : sx]};
+                const float fy[2] = {S.frac[1][sy], S.frac[1][ny > 1 ? sy + 1 : sy]};
+                const float fz[2] = {S.frac[2][sz], S.frac[2][nz > 1 ? sz + 1 : sz]};
+#pragma unroll
+                for (int ix = 0; ix < 2; ++ix) {
+                    const float c00 = lerp(q000, q100, fx[ix]), c10 = lerp(q010, q110, fx[ix]);
+                    const float c01 = lerp(q001, q101, fx[ix]), c11 = lerp(q011, q111, fx[ix]);
+#pragma unroll
+                    for (int iy = 0; iy < 2; ++iy) {
+                        const float c0 = lerp(c00, c10, fy[iy]), c1 = lerp(c01, c11, fy[iy]);
+#pragma unroll
+                        for (int iz = 0; iz < 2; ++iz)
+                            if (fabsf(lerp(c0, c1, fz[iz])) <= c.band) mask |= 1u << (4 * ix + 2 * iy + iz);
+                    }
+                }
+                // only the indices the cell owns
+                const uint32_t own = nx > 0 && ny > 0 && nz > 0
+                                         ? (nx > 1 ? 0xFFu : 0x0Fu) & (ny > 1 ? 0xFFu : 0x33u) & (nz > 1 ? 0xFFu : 0x55u)
+                                         : 0u;
+                mask &= own;
+                jx0 = (uint32_t)(k0[0] + sx);
+                jy0 = (uint32_t)(k0[1] + sy);
+                jz0 = (uint32_t)(k0[2] + sz);
+            }
+            const uint32_t cnt = __popc(mask);
+            uint32_t incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(full, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const uint32_t total = __shfl_sync(full, incl, 31);
+            if (nstage + total > STAGE) {  // a batch holds at most 256 records
+                __syncwarp();
+                count += flush_records(c, vol, depth, rgb, scr, S, nstage, lane);
+                nstage = 0;
+            }
+            uint32_t pos = nstage + incl - cnt;
+            while (mask) {
+                const int bit = __ffs(mask) - 1;
+                mask &= mask - 1u;
+                S.out[pos++] = make_uint2((jx0 + (uint32_t)(bit >> 2)) | ((jy0 + (uint32_t)((bit >> 1) & 1)) << 16),
+                                          jz0 + (uint32_t)(bit & 1));
+            }
+            nstage += total;
+        }
+        return;
+    }
+    // The general case: loops run to the warp-wide most indices per axis so
+    // the record ballots stay uniform.
     const uint32_t lanemask_lt = (1u << lane) - 1u;
     for (uint32_t cb = 0; cb < nact; cb += 32) {
         const bool live = cb + lane < nact;
