@@ -512,96 +512,126 @@ __device__ __forceinline__ void geometry_update(const FrameConst& c, const Volum
     float fmn = FLT_MAX, fmx = -FLT_MAX, mn_xf = FLT_MAX, mx_xf = -FLT_MAX, mn_zf = FLT_MAX, mx_zf = -FLT_MAX;
     bool unobserved = false, below_cap = false;  // after the update, over this lane's in-volume voxels
     uint32_t upd = 0;                            // updated voxels of this lane, bit 4 j + i
+    // The groups in two halves of two: first the pixels and depth reads of a
+    // half's eight voxels, then their updates, so that the eight reads are in
+    // flight together (a depth the update may not use reads as -inf, which
+    // the sdf gate rejects).  All sixteen at once need more than the 64
+    // registers that eight blocks per SM allow.
+    constexpr int GS = 2;  // groups per half
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int gz = at.bz * BRICK + lz + 2 * j;
-        const bool zin = yin && gz < c.ng[2];
-        const float pz = fmaf(gzf + (float)(2 * j), c.s_g, c.origin[2]);
-        const float2 B0 = f2(fmaf(c.R[1], py, fmaf(c.R[2], pz, c.t[0])));
-        const float2 B1 = f2(fmaf(c.R[4], py, fmaf(c.R[5], pz, c.t[1])));
-        const float2 B2 = f2(fmaf(c.R[7], py, fmaf(c.R[8], pz, c.t[2])));
-        const float fin[4] = {f[j].x, f[j].y, f[j].z, f[j].w};
-        float fv[4], fo[4];
-        const uint32_t w_old = wv[j];
-        uint32_t upm = 0, inside = 0xFFFFFFFFu;
+    for (int j0 = 0; j0 < 4; j0 += GS) {
+        float2 dd[GS][2];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {  // voxel pair i = 2h, 2h + 1
-            const float2 X = __ffma2_rn(f2(c.R[0]), pxp[h], B0);
-            const float2 Y = __ffma2_rn(f2(c.R[3]), pxp[h], B1);
-            const float2 Z = __ffma2_rn(f2(c.R[6]), pxp[h], B2);
-            uint32_t pix[2];
-            bool ok[2], valid[2];
-            depth_pixels<PINHOLE, INNER>(c, X, Y, Z, pix, ok);
+        for (int jj = 0; jj < GS; ++jj) {
+            const int j = j0 + jj;
+            const int gz = at.bz * BRICK + lz + 2 * j;
+            const bool zin = yin && gz < c.ng[2];
+            const float pz = fmaf(gzf + (float)(2 * j), c.s_g, c.origin[2]);
+            const float2 B0 = f2(fmaf(c.R[1], py, fmaf(c.R[2], pz, c.t[0])));
+            const float2 B1 = f2(fmaf(c.R[4], py, fmaf(c.R[5], pz, c.t[1])));
+            const float2 B2 = f2(fmaf(c.R[7], py, fmaf(c.R[8], pz, c.t[2])));
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const int i = 2 * h + k;
-                valid[k] = ALIGNED || (zin && gx0 + i < c.ng[0]);  // ALIGNED: dims are multiples of 8
-                if (!valid[k]) inside &= ~(0xFFu << (8 * i));
-            }
-            float2 d;
-            bool has[2];  // a depth the update may use (the metres image holds -inf where D = 0)
-            if constexpr (METRES) {
-                d = make_float2(__ldg(depth.p + pix[0]), __ldg(depth.p + pix[1]));
-                has[0] = ok[0] && valid[0];
-                has[1] = ok[1] && valid[1];
-            } else {
-                // RN(D * 0.001) as fmaf(2^23 + D, 0.001, -2^23 * 0.001): the product is exact
-                // inside the fma and 2^23 * 0.001f is a power-of-two scaling, so one rounding
-                const uint32_t D0 = __ldg(depth.p + pix[0]), D1 = __ldg(depth.p + pix[1]);
-                d = __ffma2_rn(make_float2(__uint_as_float(0x4B000000u | D0), __uint_as_float(0x4B000000u | D1)),
-                               f2(0.001f), f2(-8388608.0f * 0.001f));
-                has[0] = ok[0] && valid[0] && D0 != 0u;
-                has[1] = ok[1] && valid[1] && D1 != 0u;
-            }
-            const float2 sdf = __ffma2_rn(Z, f2(-1.0f), d);  // d - Z, rounded once
-            const float2 tq = __fmul2_rn(sdf, f2(c.inv_mu));
-            const float2 t = make_float2(fminf(1.0f, tq.x), fminf(1.0f, tq.y));
-            // w as binary32 from its byte: the bits 0x4B0000ww are 2^23 + w
-            const uint32_t wb0 = __byte_perm(w_old, 0x4B000000u, 0x7440u + 2 * h);
-            const uint32_t wb1 = __byte_perm(w_old, 0x4B000000u, 0x7441u + 2 * h);
-            const float2 wbf = make_float2(__uint_as_float(wb0), __uint_as_float(wb1));
-            const float2 wf = __fadd2_rn(wbf, f2(-8388608.0f));               // w, exact
-            const float2 nb = __ffma2_rn(wbf, f2(-1.0f), f2(8388607.0f));     // -(w + 1), exact
-            const float2 y = make_float2(rcp[wb0 & 0xFFu], rcp[wb1 & 0xFFu]);  // RN(1 / (w + 1))
-            // F <- fmaf(F, w, t) / (w + 1), the quotient by div_by_weight's steps
-            const float2 a = __ffma2_rn(make_float2(fin[2 * h], fin[2 * h + 1]), wf, t);
-            const float2 q = __fmul2_rn(a, y);
-            const float2 r = __ffma2_rn(nb, q, a);
-            const float2 fn = __ffma2_rn(r, y, q);
-            const float sd[2] = {sdf.x, sdf.y}, fnew[2] = {fn.x, fn.y};
-            const uint32_t wb[2] = {wb0, wb1};
+            for (int h = 0; h < 2; ++h) {
+                const float2 X = __ffma2_rn(f2(c.R[0]), pxp[h], B0);
+                const float2 Y = __ffma2_rn(f2(c.R[3]), pxp[h], B1);
+                const float2 Z = __ffma2_rn(f2(c.R[6]), pxp[h], B2);
+                uint32_t pix[2];
+                bool ok[2], has[2];  // has: a depth the update may use
+                depth_pixels<PINHOLE, INNER>(c, X, Y, Z, pix, ok);
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const int i = 2 * h + k;
-                const bool up = has[k] && !(sd[k] < -c.mu) && (FREE_SPACE || !(sd[k] > c.mu));
-                fv[i] = up ? fnew[k] : fin[i];
-                upm |= up ? 1u << i : 0u;
-                fo[i] = (up || wb[k] != 0x4B000000u) && valid[k] ? fv[i] : qnan;  // observed after the update
+                for (int k = 0; k < 2; ++k)  // ALIGNED: dims are multiples of 8
+                    has[k] = ok[k] && (ALIGNED || (zin && gx0 + 2 * h + k < c.ng[0]));
+                float2 d;
+                if constexpr (METRES) {  // the metres image holds -inf where D = 0
+                    d = make_float2(__ldg(depth.p + pix[0]), __ldg(depth.p + pix[1]));
+                } else {
+                    // RN(D * 0.001) as fmaf(2^23 + D, 0.001, -2^23 * 0.001): the product is exact
+                    // inside the fma and 2^23 * 0.001f is a power-of-two scaling, so one rounding
+                    const uint32_t D0 = __ldg(depth.p + pix[0]), D1 = __ldg(depth.p + pix[1]);
+                    d = __ffma2_rn(make_float2(__uint_as_float(0x4B000000u | D0), __uint_as_float(0x4B000000u | D1)),
+                                   f2(0.001f), f2(-8388608.0f * 0.001f));
+                    has[0] = has[0] && D0 != 0u;
+                    has[1] = has[1] && D1 != 0u;
+                }
+                if (!(INNER && ALIGNED && METRES)) {
+                    d.x = has[0] ? d.x : -INFINITY;
+                    d.y = has[1] ? d.y : -INFINITY;
+                }
+                dd[jj][h] = d;
             }
         }
-        // w <- min(w + 1, max_weight): +1 in the updated bytes that are below the cap
-        const uint32_t upb = (upm * 0x00204081u) & 0x01010101u;  // bit i of upm -> byte i
-        const uint32_t wn = w_old + (upb & ~zero_bytes(w_old ^ maxw4));
-        // in-volume voxels only: a byte outside the volume reads as observed and at the cap
-        const uint32_t wq = ALIGNED ? wn : (wn & inside) | (maxw4 & ~inside);
-        unobserved = unobserved || any_zero_byte(wq);
-        below_cap = below_cap || wq != maxw4;
-        const float gmn = fminf(fminf(fo[0], fo[1]), fminf(fo[2], fo[3]));
-        const float gmx = fmaxf(fmaxf(fo[0], fo[1]), fmaxf(fo[2], fo[3]));
-        fmn = fminf(fmn, gmn);
-        fmx = fmaxf(fmx, gmx);
-        // this lane's x-face voxel of the group, and its z-face group
-        const float fx = lx == 0 ? fo[0] : fo[3];
-        mn_xf = fminf(mn_xf, fx);
-        mx_xf = fmaxf(mx_xf, fx);
-        if ((j == 0 && lz == 0) || (j == 3 && lz == 1)) {
-            mn_zf = gmn;
-            mx_zf = gmx;
-        }
-        upd |= upm << (4 * j);
-        if (upm) {
-            *reinterpret_cast<float4*>(Fb + 128 * j) = make_float4(fv[0], fv[1], fv[2], fv[3]);
-            *reinterpret_cast<uint32_t*>(Wb + 128 * j) = wn;
+#pragma unroll
+        for (int jj = 0; jj < GS; ++jj) {
+            const int j = j0 + jj;
+            const int gz = at.bz * BRICK + lz + 2 * j;
+            const bool zin = yin && gz < c.ng[2];
+            const float pz = fmaf(gzf + (float)(2 * j), c.s_g, c.origin[2]);
+            const float2 B2 = f2(fmaf(c.R[7], py, fmaf(c.R[8], pz, c.t[2])));
+            const float fin[4] = {f[j].x, f[j].y, f[j].z, f[j].w};
+            float fv[4], fo[4];
+            const uint32_t w_old = wv[j];
+            uint32_t upm = 0, inside = 0xFFFFFFFFu;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {  // voxel pair i = 2h, 2h + 1
+                const float2 Z = __ffma2_rn(f2(c.R[6]), pxp[h], B2);  // as in the first pass
+                bool valid[2];
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int i = 2 * h + k;
+                    valid[k] = ALIGNED || (zin && gx0 + i < c.ng[0]);
+                    if (!valid[k]) inside &= ~(0xFFu << (8 * i));
+                }
+                const float2 d = dd[jj][h];
+                const float2 sdf = __ffma2_rn(Z, f2(-1.0f), d);  // d - Z, rounded once
+                const float2 tq = __fmul2_rn(sdf, f2(c.inv_mu));
+                const float2 t = make_float2(fminf(1.0f, tq.x), fminf(1.0f, tq.y));
+                // w as binary32 from its byte: the bits 0x4B0000ww are 2^23 + w
+                const uint32_t wb0 = __byte_perm(w_old, 0x4B000000u, 0x7440u + 2 * h);
+                const uint32_t wb1 = __byte_perm(w_old, 0x4B000000u, 0x7441u + 2 * h);
+                const float2 wbf = make_float2(__uint_as_float(wb0), __uint_as_float(wb1));
+                const float2 wf = __fadd2_rn(wbf, f2(-8388608.0f));               // w, exact
+                const float2 nb = __ffma2_rn(wbf, f2(-1.0f), f2(8388607.0f));     // -(w + 1), exact
+                const float2 y = make_float2(rcp[wb0 & 0xFFu], rcp[wb1 & 0xFFu]);  // RN(1 / (w + 1))
+                // F <- fmaf(F, w, t) / (w + 1), the quotient by div_by_weight's steps
+                const float2 a = __ffma2_rn(make_float2(fin[2 * h], fin[2 * h + 1]), wf, t);
+                const float2 q = __fmul2_rn(a, y);
+                const float2 r = __ffma2_rn(nb, q, a);
+                const float2 fn = __ffma2_rn(r, y, q);
+                const float sd[2] = {sdf.x, sdf.y}, fnew[2] = {fn.x, fn.y};
+                const uint32_t wb[2] = {wb0, wb1};
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    const int i = 2 * h + k;
+                    const bool up = !(sd[k] < -c.mu) && (FREE_SPACE || !(sd[k] > c.mu));
+                    fv[i] = up ? fnew[k] : fin[i];
+                    upm |= up ? 1u << i : 0u;
+                    fo[i] = (up || wb[k] != 0x4B000000u) && valid[k] ? fv[i] : qnan;  // observed after the update
+                }
+            }
+            // w <- min(w + 1, max_weight): +1 in the updated bytes that are below the cap
+            const uint32_t upb = (upm * 0x00204081u) & 0x01010101u;  // bit i of upm -> byte i
+            const uint32_t wn = w_old + (upb & ~zero_bytes(w_old ^ maxw4));
+            // in-volume voxels only: a byte outside the volume reads as observed and at the cap
+            const uint32_t wq = ALIGNED ? wn : (wn & inside) | (maxw4 & ~inside);
+            unobserved = unobserved || any_zero_byte(wq);
+            below_cap = below_cap || wq != maxw4;
+            const float gmn = fminf(fminf(fo[0], fo[1]), fminf(fo[2], fo[3]));
+            const float gmx = fmaxf(fmaxf(fo[0], fo[1]), fmaxf(fo[2], fo[3]));
+            fmn = fminf(fmn, gmn);
+            fmx = fmaxf(fmx, gmx);
+            // this lane's x-face voxel of the group, and its z-face group
+            const float fx = lx == 0 ? fo[0] : fo[3];
+            mn_xf = fminf(mn_xf, fx);
+            mx_xf = fmaxf(mx_xf, fx);
+            if ((j == 0 && lz == 0) || (j == 3 && lz == 1)) {
+                mn_zf = gmn;
+                mx_zf = gmx;
+            }
+            upd |= upm << (4 * j);
+            if (upm) {
+                *reinterpret_cast<float4*>(Fb + 128 * j) = make_float4(fv[0], fv[1], fv[2], fv[3]);
+                *reinterpret_cast<uint32_t*>(Wb + 128 * j) = wn;
+            }
         }
     }
     count += __popc(upd);
