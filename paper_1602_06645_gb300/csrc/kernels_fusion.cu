@@ -1055,6 +1055,18 @@ __device__ __forceinline__ void band_brick(const FrameConst& c, const Volumes& v
     int k0[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) k0[a] = __ldg(vol.tab.k0[a] + bb[a]);
+    // the first 32 owned indices' trilinear fractions per axis and the
+    // per-axis cell summaries, read now so that their latency overlaps the
+    // tile reads below (indices beyond 32, at ratios above 4: read in step 1c)
+    int nk[3];
+    float fr[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        nk[a] = __ldg(vol.tab.k0[a] + bb[a] + 1) - k0[a];
+        fr[a] = lane < nk[a] ? __ldg(vol.tab.frac[a] + k0[a] + lane) : 0.0f;
+    }
+    const uint32_t xinfo = __ldg(vol.tab.info[0] + bb[0]);
+    const uint32_t yinfo = __ldg(vol.tab.info[1] + bb[1]), zinfo = __ldg(vol.tab.info[2] + bb[2]);
     if (lane < 8) {
         const int x = bb[0] + (lane & 1), y = bb[1] + ((lane >> 1) & 1), z = bb[2] + (lane >> 2);
         S.nbr[lane] = (x < c.nb[0] && y < c.nb[1] && z < c.nb[2])
@@ -1132,17 +1144,15 @@ __device__ __forceinline__ void band_brick(const FrameConst& c, const Volumes& v
     // 1c. trilinear fraction of each owned colour index, from the per-axis tables
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const int nk = __ldg(vol.tab.k0[a] + bb[a] + 1) - k0[a];
-        for (int j = lane; j < nk; j += 32) S.frac[a][j] = __ldg(vol.tab.frac[a] + k0[a] + j);
+        if (lane < nk[a]) S.frac[a][lane] = fr[a];
+        for (int j = lane + 32; j < nk[a]; j += 32) S.frac[a][j] = __ldg(vol.tab.frac[a] + k0[a] + j);
     }
     __syncwarp();
 
     // 3. active cells, compacted
     // cells along x that own colour indices, and the most indices of one cell per axis
-    const uint32_t xinfo = __ldg(vol.tab.info[0] + bb[0]);
     const uint32_t xmask = xinfo & 0xFFu;
-    const int mx = (int)(xinfo >> 9), my = (int)(__ldg(vol.tab.info[1] + bb[1]) >> 9),
-              mz = (int)(__ldg(vol.tab.info[2] + bb[2]) >> 9);
+    const int mx = (int)(xinfo >> 9), my = (int)(yinfo >> 9), mz = (int)(zinfo >> 9);
     uint32_t act[2];
     uint32_t total = 0;
 #pragma unroll

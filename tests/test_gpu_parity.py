@@ -93,6 +93,7 @@ def test_culling_changes_nothing():
     ((36, 28, 20), (108, 84, 60)),     # ratio 3
     ((24, 24, 24), (40, 40, 40)),      # ratio 5/3 (non-integer)
     ((20, 12, 28), (40, 24, 56)),      # ratio 2, dims not multiples of 8
+    ((12, 8, 12), (96, 64, 96)),       # ratio 8, the largest supported: over 32 owned indices per axis
 ])
 def test_ratios_and_ragged_dims(dims_geo, dims_col):
     seq = synth.sequence_small(n_frames=4, seed=5)
