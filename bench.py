@@ -530,14 +530,25 @@ def run_batched(args):
     import paper_1602_06645_gb300 as T
     from paper_1602_06645_gb300 import synth
 
-    torch.cuda.set_device(0)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     T.load()
     n_scans = int(os.environ.get("BATCH_SCANS", "64"))
     nf = args.warmup + args.steps
-    edges = synth.batched_edges(n_scans)
+    all_edges = synth.batched_edges(n_scans)
+    # with N ranks the scans are split by longest processing time first on
+    # their voxel counts (n^3 + (2n)^3); each rank runs its share as one batch
+    mine = T.lpt_assign([9 * e ** 3 for e in all_edges], world)[rank] if world > 1 else list(range(n_scans))
+    edges = [all_edges[i] for i in mine]
     t0 = time.perf_counter()
     data = []
-    for i, e in enumerate(edges):
+    for i, e in zip(mine, edges):
         seq = synth.sequence_batched_scan(i, n_frames=nf, edge=e)
         frames = []
         for f in range(nf):
@@ -551,19 +562,27 @@ def run_batched(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
     def timed(step_fn, after_warmup=None):
+        """Summed event time of the K steps, the max over ranks (the ranks
+        start the timed steps together and the slowest one sets the time)."""
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         for f in range(args.warmup):
             step_fn(f)
         torch.cuda.synchronize()
         if after_warmup:
             after_warmup()
+        if dist is not None:
+            dist.barrier()
+            torch.cuda.synchronize()
         for i in range(args.steps):
             flush.zero_()
             ev[i][0].record(stream)
             step_fn(args.warmup + i)
             ev[i][1].record(stream)
         torch.cuda.synchronize()
-        return float(sum(a.elapsed_time(b) for a, b in ev))
+        if dist is not None:
+            dist.barrier()
+        (ms,), _ = reduce_over_ranks(dist, "cuda", [sum(a.elapsed_time(b) for a, b in ev)])
+        return float(ms)
 
     # batched
     vols = [T.Volume(s.dims_geo, s.dims_col, s.voxel_size, s.mu, s.max_weight, stream=stream.cuda_stream)
@@ -583,13 +602,17 @@ def run_batched(args):
 
     geo_upd, col_upd, col_bricks = per_step("total_geo_updated"), per_step("total_col_updated"), \
         per_step("total_col_bricks")
+    # the job's units over all ranks
+    _, (nominal_all, geo_upd, col_upd, col_bricks) = reduce_over_ranks(dist, "cuda", [],
+                                                                       [nominal, geo_upd, col_upd, col_bricks])
     # algorithmic bytes of the step: F and w read and written per updated
     # geometry voxel, the 9^3 geometry tile (F and w) per colour-candidate
     # brick, the packed colour read and written per updated colour voxel
     step_bytes = 10.0 * geo_upd + 5.0 * 729 * col_bricks + 8.0 * col_upd
     peaks, peak_kind = measured_peaks()
     hbm = float(peaks["hbm_gbs"])
-    achieved = step_bytes / (ms_batched / max(args.steps, 1) / 1e3) / 1e9
+    # per GPU: the job's bytes over the GPUs
+    achieved = step_bytes / world / (ms_batched / max(args.steps, 1) / 1e3) / 1e9
     batch.close()
     for v in vols:
         v.close()
@@ -607,17 +630,26 @@ def run_batched(args):
     for v in vols:
         v.close()
     K = max(args.steps, 1)
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
     line = {
-        "metric": "voxel-updates/s (nominal, geo+colour), batched scans", "value": nominal * K / (ms_batched / 1e3),
-        "unit": "voxel-updates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_batched / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "metric": "voxel-updates/s (nominal, geo+colour), batched scans",
+        "value": nominal_all * K / (ms_batched / 1e3),
+        "unit": "voxel-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_batched / K, "higher_is_better": True,
+        "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
         "dtype": "f32+u8", "data": "synthetic",
-        "config": {"workload": "batched_%d_scans" % n_scans, "edges": edges, "rgb": "1280x720", "depth": "640x480",
-                   "l2": "flushed between steps (256 MiB write)", "schedule_blocks_per_sm": sched["blocks_per_sm"],
+        "config": {"workload": "batched_%d_scans" % n_scans, "edges": all_edges, "rgb": "1280x720",
+                   "depth": "640x480", "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": ("the scans split over the GPUs by longest processing time first, one batch "
+                                   "per GPU" if world > 1 else "single GPU"),
+                   "rank0_scans": mine, "schedule_blocks_per_sm": sched["blocks_per_sm"],
                    "schedule_bricks_per_item": sched["bricks_per_item"],
                    "schedule_from_cache": cached, "cuda_graph": True},
-        "sequential": {"value": nominal * K / (ms_seq / 1e3), "ms_per_step": ms_seq / K,
-                       "launches_per_step": 6 * n_scans},
+        "sequential": {"value": nominal_all * K / (ms_seq / 1e3), "ms_per_step": ms_seq / K,
+                       "launches_per_step": 6 * len(mine)},
         "speedup_vs_sequential": ms_seq / ms_batched,
         "scan_frames_per_s": n_scans * K / (ms_batched / 1e3),
         "gpu_launches": K,
@@ -625,7 +657,7 @@ def run_batched(args):
         "updated_per_step": {"geo": geo_upd, "col": col_upd, "colour_candidate_bricks": col_bricks},
         "roofline": {"kernel": "k_batch_step (whole step, one launch)", "bound": "hbm",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-                     "bytes_per_launch": step_bytes,
+                     "bytes_per_launch": step_bytes / world,
                      "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                      else "fallback 6.8 TB/s"},
         "frame_generation_s": gen_s,

@@ -646,6 +646,29 @@ def slab_ranges(dims_geo, dims_col, n):
     raise ValueError("no cut of %d layers into %d slabs falls on whole colour voxels" % (ngz, n))
 
 
+def lpt_assign(costs, n):
+    """Distribute independent scans over n devices by longest processing time
+    first: scans in decreasing cost (ties by index) each go to the device with
+    the least cost so far (ties to the lowest device).  Returns, per device,
+    the indices of its scans in increasing order.  Deterministic, so every
+    rank computes the same split without an exchange.  The slowest device's
+    total is at most (4/3 - 1/(3n)) times the best possible (Graham's bound
+    for the greedy rule)."""
+    n = int(n)
+    if n < 1:
+        raise ValueError("need at least one device")
+    costs = [float(c) for c in costs]
+    if any(not (c >= 0.0) for c in costs):
+        raise ValueError("costs must be non-negative numbers")
+    load = [0.0] * n
+    parts = [[] for _ in range(n)]
+    for i in sorted(range(len(costs)), key=lambda k: (-costs[k], k)):
+        d = min(range(n), key=lambda r: (load[r], r))
+        parts[d].append(i)
+        load[d] += costs[i]
+    return [sorted(p) for p in parts]
+
+
 # ------------------------------------------------------------- Volume -----
 class Volume:
     """A fusion handle with PyTorch-backed device memory on the current stream."""

@@ -61,3 +61,39 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     args = type("A", (), dict(workload="small", steps=1, warmup=0, gpus=2))()
     bench.run_reference(args)
     assert capsys.readouterr().out == ""
+
+
+def _rank_batched(rank, world, port, out):
+    import bench
+    import paper_1602_06645_gb300 as T
+    from paper_1602_06645_gb300 import synth
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        edges = synth.batched_edges(64)
+        mine = T.lpt_assign([9 * e ** 3 for e in edges], world)[rank]
+        units = sum(9 * edges[i] ** 3 for i in mine)
+        (mx,), (total, count) = bench.reduce_over_ranks(dist, "cpu", [float(units)], [float(units), len(mine)])
+        out[rank] = (tuple(mine), mx, total, count)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_batched_scans_split_over_two_gloo_ranks():
+    """bench.py --workload batched with N ranks: each rank takes its longest-
+    processing-time-first share of the 64 scans (computed locally, no
+    exchange); the shares are disjoint and cover every scan, and the job's
+    units are their sum."""
+    from paper_1602_06645_gb300 import synth
+    world = 2
+    with mp.get_context("spawn").Manager() as m:
+        out = m.dict()
+        mp.spawn(_rank_batched, args=(world, _free_port(), out), nprocs=world, join=True)
+        res = dict(out)
+    edges = synth.batched_edges(64)
+    shares = [set(res[r][0]) for r in range(world)]
+    assert not (shares[0] & shares[1]) and (shares[0] | shares[1]) == set(range(64))
+    total = sum(9 * e ** 3 for e in edges)
+    for r in range(world):
+        assert res[r][2] == total and res[r][3] == 64
+        assert res[r][1] <= total / world + 9 * max(edges) ** 3
