@@ -42,6 +42,14 @@ struct tsdf_volume {
     // (programmatic launch) behind frame k's band kernel.
     cudaStream_t side;
     cudaEvent_t list_done, bricks_done, main_tail;
+    // frame_done[k & 1] is recorded on `stream` after pipelined frame k's
+    // last kernel.  Frame k + 2's host frames are uploaded on `copy` into
+    // the staging half frame k used, after frame_done[k & 1] only: the
+    // uploads overlap frame k + 1's geometry update, and no counter read or
+    // colour list queued on `side` holds them back; `side` waits for
+    // upload_done before the depth tiles.
+    cudaEvent_t frame_done[2], upload_done;
+    cudaStream_t copy;
     bool chain_ok;
     // Asynchronous counter reads (tsdf_stats_request / tsdf_stats_collect):
     // per slot, page-locked copies of the counters taken on `stream` (entry

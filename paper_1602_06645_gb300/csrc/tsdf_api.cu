@@ -513,6 +513,10 @@ tsdf_status tsdf_create_ex(const int32_t dims_geo[3], const int32_t dims_col[3],
         cudaEventCreateWithFlags(&v->list_done, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&v->bricks_done, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&v->main_tail, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&v->frame_done[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&v->frame_done[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&v->upload_done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&v->copy, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&v->stats_ev[0], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&v->stats_ev[1], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&v->stats_ev_side[0], cudaEventDisableTiming) != cudaSuccess ||
@@ -601,7 +605,12 @@ void tsdf_destroy(tsdf_volume* v) {
         cudaStreamSynchronize(v->side);
         cudaStreamDestroy(v->side);
     }
-    for (cudaEvent_t x : {v->list_done, v->bricks_done, v->main_tail, v->stats_ev[0], v->stats_ev[1],
+    if (v->copy) {
+        cudaStreamSynchronize(v->copy);
+        cudaStreamDestroy(v->copy);
+    }
+    for (cudaEvent_t x : {v->list_done, v->bricks_done, v->main_tail, v->frame_done[0], v->frame_done[1], v->upload_done,
+                          v->stats_ev[0], v->stats_ev[1],
                           v->stats_ev_side[0], v->stats_ev_side[1]})
         if (x) cudaEventDestroy(x);
     if (v->stats_host) cudaFreeHost(v->stats_host);
@@ -661,19 +670,22 @@ tsdf_status tsdf_integrate(tsdf_volume* v, const uint16_t* depth_mm, tsdf_image_
         evs = &v->ev_pending.back();
         if (v->prof_mask & 1u) cudaEventRecord(evs->e[0], v->stream);
     }
-    // Frame pipelining (see tsdf_volume::side): depth upload, depth tiles and
-    // brick culling go to the side stream, which waits only for the previous
-    // frame's colour list; the geometry update waits for them.  Timing of the
-    // first three phases needs them in stream order, so it turns this off.
+    // Frame pipelining (see tsdf_volume::side): depth tiles and brick
+    // culling go to the side stream, which waits for the previous frame's
+    // colour list; the geometry update waits for them.  Host frames are
+    // uploaded on the copy stream once the frame before the previous one (the
+    // last user of their staging half) is done.  Timing of the first three
+    // phases needs them in stream order, so it turns this off.
     const bool pipe = !(v->profiling && (v->prof_mask & 0x7u));
+    // a device depth image is read by the side stream: unless the caller
+    // declared its device images complete at the call, the side stream waits
+    // for all the work queued on the handle's stream before it
+    const bool chained = pipe && v->chain_ok && !(is_device_ptr(depth_mm) && !v->inputs_ready);
     cudaStream_t pre = pipe ? v->side : v->stream;
+    cudaStream_t up = chained ? v->copy : pre;  // the stream of the host uploads
     if (pipe) {
-        // a device depth image is read by the side stream: unless the caller
-        // declared its device images complete at the call, wait for all the
-        // work queued on the handle's stream before it
-        const bool wait_caller = is_device_ptr(depth_mm) && !v->inputs_ready;
-        if (v->chain_ok && !wait_caller) {
-            e = cudaStreamWaitEvent(v->side, v->list_done, 0);
+        if (chained) {
+            e = cudaStreamWaitEvent(v->copy, v->frame_done[v->frames & 1], 0);
         } else {
             e = cudaEventRecord(v->main_tail, v->stream);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(v->side, v->main_tail, 0);
@@ -692,7 +704,7 @@ tsdf_status tsdf_integrate(tsdf_volume* v, const uint16_t* depth_mm, tsdf_image_
             cap = buf ? dbytes : 0;
             if (!buf) return fail(v, TSDF_ERR_OOM, "depth staging buffer");
         }
-        e = cudaMemcpyAsync(buf, depth_mm, dbytes, cudaMemcpyHostToDevice, pre);
+        e = cudaMemcpyAsync(buf, depth_mm, dbytes, cudaMemcpyHostToDevice, up);
         if (e != cudaSuccess) return cuda_fail(v, e, "depth upload");
         d_depth = buf;
     }
@@ -706,9 +718,17 @@ tsdf_status tsdf_integrate(tsdf_volume* v, const uint16_t* depth_mm, tsdf_image_
             cap = buf ? cbytes : 0;
             if (!buf) return fail(v, TSDF_ERR_OOM, "RGB staging buffer");
         }
-        e = cudaMemcpyAsync(buf, rgb_hwc, cbytes, cudaMemcpyHostToDevice, pre);
+        e = cudaMemcpyAsync(buf, rgb_hwc, cbytes, cudaMemcpyHostToDevice, up);
         if (e != cudaSuccess) return cuda_fail(v, e, "RGB upload");
         d_rgb = buf;
+    }
+    if (chained) {
+        // the depth tiles read the upload, and they and the culling overwrite
+        // what the previous frame's colour list reads
+        e = cudaEventRecord(v->upload_done, v->copy);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(v->side, v->upload_done, 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(v->side, v->list_done, 0);
+        if (e != cudaSuccess) return cuda_fail(v, e, "frame pipeline");
     }
     if (pipe && v->stats_pending) {
         // a counter read queued since the last frame must finish before the
@@ -734,6 +754,7 @@ tsdf_status tsdf_integrate(tsdf_volume* v, const uint16_t* depth_mm, tsdf_image_
     }
     e = launch_frame_post(c, v->vol, v->scr, d_depth, d_rgb, v->grids, v->stream, evs ? marks : nullptr,
                           pipe ? v->list_done : nullptr);
+    if (e == cudaSuccess && pipe) e = cudaEventRecord(v->frame_done[v->frames & 1], v->stream);
     if (e != cudaSuccess) return cuda_fail(v, e, "integrate launch");
     v->chain_ok = pipe;
     ++v->frames;
