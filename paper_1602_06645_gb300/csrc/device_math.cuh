@@ -88,21 +88,17 @@ __device__ __forceinline__ void back_project(const FrameConst& c, int iu, int iv
 __device__ __forceinline__ float lerp(float a, float b, float t) { return fmaf(t, b - a, a); }
 
 // Correctly rounded a / b for the small integer divisor b = w + 1 (1..256),
-// given y = RN(1/b) (a table entry): q = RN(a y) is within about an ulp of
-// a / b, the residual r = a - b q is exact in one fused multiply-add, and
-// RN(q + r y) is the correctly rounded quotient (Markstein's correction step;
-// checked exhaustively against the IEEE division for every divisor and every
+// given y = RN(1/b): q = RN(a y) is within about an ulp of a / b, the
+// residual r = a - b q is exact in one fused multiply-add, and RN(q + r y) is
+// the correctly rounded quotient (Markstein's correction step; checked
+// exhaustively against the IEEE division for every divisor and every
 // significand of a).  Replaces an IEEE division, which costs a range check and
-// several dependent instructions more per voxel.
+// several dependent instructions more per voxel.  The geometry kernel takes
+// y from rcp2_rn below, which equals RN(1/b) over its whole range.
 __device__ __forceinline__ float div_by_weight(float a, float b, float y) {
     const float q = a * y;
     const float r = fmaf(-b, q, a);
     return fmaf(r, y, q);
-}
-
-// The table of RN(1 / (w + 1)), w = 0..255, filled by the block.
-__device__ __forceinline__ void fill_weight_reciprocals(float* rcp) {
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) rcp[i] = __frcp_rn((float)(i + 1));
 }
 
 // Correctly rounded reciprocals of a pair, 1/z for z in [2^-126, 2^126): the

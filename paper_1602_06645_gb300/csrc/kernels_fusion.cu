@@ -487,7 +487,7 @@ struct DepthM {
 // y = (l >> 1) & 7, z = (l >> 4) + 2 j.  Each group of the warp is 512
 // contiguous bytes of F and 128 of w.
 template <bool PINHOLE, bool FREE_SPACE, bool ALIGNED, bool INNER, typename Depth>
-__device__ __forceinline__ void geometry_update(const FrameConst& c, const Volumes& vol, Depth depth, const float* rcp,
+__device__ __forceinline__ void geometry_update(const FrameConst& c, const Volumes& vol, Depth depth,
                                                 const BrickAt& at, int lane, const float4 (&f)[4],
                                                 const uint32_t (&wv)[4], uint32_t& count, uint32_t& changed) {
     constexpr bool METRES = std::is_same<Depth, DepthM>::value;
@@ -591,7 +591,7 @@ __device__ __forceinline__ void geometry_update(const FrameConst& c, const Volum
                 const float2 wbf = make_float2(__uint_as_float(wb0), __uint_as_float(wb1));
                 const float2 wf = __fadd2_rn(wbf, f2(-8388608.0f));               // w, exact
                 const float2 nb = __ffma2_rn(wbf, f2(-1.0f), f2(8388607.0f));     // -(w + 1), exact
-                const float2 y = make_float2(rcp[wb0 & 0xFFu], rcp[wb1 & 0xFFu]);  // RN(1 / (w + 1))
+                const float2 y = rcp2_rn(__fadd2_rn(wbf, f2(-8388607.0f)));  // RN(1 / (w + 1)), w + 1 exact
                 // F <- fmaf(F, w, t) / (w + 1), the quotient by div_by_weight's steps
                 const float2 a = __ffma2_rn(make_float2(fin[2 * h], fin[2 * h + 1]), wf, t);
                 const float2 q = __fmul2_rn(a, y);
@@ -667,7 +667,7 @@ __device__ __forceinline__ void geometry_update(const FrameConst& c, const Volum
 // issued before the first update (the stores of a group could otherwise hold
 // back the next group's loads).
 template <bool PINHOLE, bool FREE_SPACE, bool ALIGNED = false, bool INNER = false, typename Depth>
-__device__ __forceinline__ void geometry_brick(const FrameConst& c, const Volumes& vol, Depth depth, const float* rcp,
+__device__ __forceinline__ void geometry_brick(const FrameConst& c, const Volumes& vol, Depth depth,
                                                const BrickAt& at, int lane, uint32_t& count, uint32_t& changed) {
     const float* Fb = vol.F + (size_t)at.b * BRICK_VOX + lane * 4;
     const uint8_t* Wb = vol.W + (size_t)at.b * BRICK_VOX + lane * 4;
@@ -678,16 +678,13 @@ __device__ __forceinline__ void geometry_brick(const FrameConst& c, const Volume
         f[j] = *reinterpret_cast<const float4*>(Fb + 128 * j);
         wv[j] = *reinterpret_cast<const uint32_t*>(Wb + 128 * j);
     }
-    geometry_update<PINHOLE, FREE_SPACE, ALIGNED, INNER>(c, vol, depth, rcp, at, lane, f, wv, count, changed);
+    geometry_update<PINHOLE, FREE_SPACE, ALIGNED, INNER>(c, vol, depth, at, lane, f, wv, count, changed);
 }
 
 template <bool PINHOLE, bool FREE_SPACE, bool ALIGNED>
 __global__ void __launch_bounds__(GEO_THREADS, 8) k_geometry(FrameConst c, Volumes vol, const float* __restrict__ depth_m,
                                                           Counters* __restrict__ ctr,
                                                           const uint32_t* __restrict__ list) {
-    __shared__ float rcp[256];
-    fill_weight_reciprocals(rcp);
-    __syncthreads();
     chain_enter();
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         // fold the previous frame's colour-side counters into the running totals
@@ -712,9 +709,9 @@ __global__ void __launch_bounds__(GEO_THREADS, 8) k_geometry(FrameConst c, Volum
         const uint32_t e = list[n - 1u - item];
         const BrickAt at = geo_brick(c, e);
         if (e & GEO_INNER)  // the brick projects wholly into the image: no per-voxel image tests
-            geometry_brick<PINHOLE, FREE_SPACE, ALIGNED, true>(c, vol, depth, rcp, at, lane, count, changed);
+            geometry_brick<PINHOLE, FREE_SPACE, ALIGNED, true>(c, vol, depth, at, lane, count, changed);
         else
-            geometry_brick<PINHOLE, FREE_SPACE, ALIGNED, false>(c, vol, depth, rcp, at, lane, count, changed);
+            geometry_brick<PINHOLE, FREE_SPACE, ALIGNED, false>(c, vol, depth, at, lane, count, changed);
     }
     block_add<GEO_THREADS>(__reduce_add_sync(0xffffffffu, count), &ctr->geo_updated, changed, &ctr->n_geo_changed);
 }
@@ -1536,9 +1533,6 @@ __global__ void __launch_bounds__(COL_THREADS, 5) k_fused(FrameConst c, Volumes 
                                                          const uint8_t* __restrict__ rgb, Scratch scr) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ColourSlot& S = reinterpret_cast<ColourSlot*>(smem_raw)[threadIdx.x >> 5];
-    __shared__ float rcp[256];
-    fill_weight_reciprocals(rcp);
-    __syncthreads();
     chain_enter();
     const unsigned full = 0xffffffffu;
     Counters* __restrict__ ctr = scr.ctr;
@@ -1570,9 +1564,9 @@ __global__ void __launch_bounds__(COL_THREADS, 5) k_fused(FrameConst c, Volumes 
         const uint32_t e = scr.geo_list[item];
         const BrickAt at = geo_brick(c, e);
         if (e & GEO_INNER)
-            geometry_brick<true, FREE_SPACE, ALIGNED, true>(c, vol, dm, rcp, at, lane, gcount, changed);
+            geometry_brick<true, FREE_SPACE, ALIGNED, true>(c, vol, dm, at, lane, gcount, changed);
         else
-            geometry_brick<true, FREE_SPACE, ALIGNED, false>(c, vol, dm, rcp, at, lane, gcount, changed);
+            geometry_brick<true, FREE_SPACE, ALIGNED, false>(c, vol, dm, at, lane, gcount, changed);
         fuse_release(c, scr, at, lane);
         uint32_t slot = 0xFFFFFFFFu;
         if (lane == 0) {
@@ -1861,8 +1855,6 @@ __global__ void __launch_bounds__(COL_THREADS, 4) k_batch_step(const ScanDesc* _
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ColourSlot& S = reinterpret_cast<ColourSlot*>(smem_raw)[threadIdx.x >> 5];
     __shared__ uint32_t pre[MAX_BATCH + 1];
-    __shared__ float rcp[256];
-    fill_weight_reciprocals(rcp);  // read after the first grid barrier's __syncthreads
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1934,13 +1926,13 @@ __global__ void __launch_bounds__(COL_THREADS, 4) k_batch_step(const ScanDesc* _
             const BrickAt at = geo_brick(d.c, d.scr.geo_list[k]);  // the general form handles every brick
             const DepthMm dm{d.depth};
             if (d.c.kd_pinhole && d.c.free_space)
-                geometry_brick<true, true>(d.c, d.vol, dm, rcp, at, lane, count, changed);
+                geometry_brick<true, true>(d.c, d.vol, dm, at, lane, count, changed);
             else if (d.c.kd_pinhole)
-                geometry_brick<true, false>(d.c, d.vol, dm, rcp, at, lane, count, changed);
+                geometry_brick<true, false>(d.c, d.vol, dm, at, lane, count, changed);
             else if (d.c.free_space)
-                geometry_brick<false, true>(d.c, d.vol, dm, rcp, at, lane, count, changed);
+                geometry_brick<false, true>(d.c, d.vol, dm, at, lane, count, changed);
             else
-                geometry_brick<false, false>(d.c, d.vol, dm, rcp, at, lane, count, changed);
+                geometry_brick<false, false>(d.c, d.vol, dm, at, lane, count, changed);
         }
         count = __reduce_add_sync(full, count);
         if (lane == 0) {

@@ -1,10 +1,11 @@
-"""The geometry update divides by the small integer w + 1 with a reciprocal
-table and one residual correction instead of an IEEE division.  It must give
-the correctly rounded quotient for every weight and every numerator the update
-can form; checked exhaustively on the device against __fdiv_rn (see
-tests/gpu_checks/division_check.cu).  The geometry kernel performs the same
-three operations on voxel pairs (__fmul2_rn, __ffma2_rn), whose components
-round exactly as the scalar operations do."""
+"""The geometry update divides by the small integer w + 1 with its correctly
+rounded reciprocal and one residual correction instead of an IEEE division.
+It must give the correctly rounded quotient for every weight and every
+numerator the update can form; checked exhaustively on the device against
+__fdiv_rn (see tests/gpu_checks/division_check.cu).  The geometry kernel
+performs the same three operations on voxel pairs (__fmul2_rn, __ffma2_rn),
+whose components round exactly as the scalar operations do, with the
+reciprocal from rcp2_rn, which equals __frcp_rn (test_gpu_reciprocal.py)."""
 import os
 import subprocess
 
