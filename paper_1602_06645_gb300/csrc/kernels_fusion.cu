@@ -591,7 +591,7 @@ __device__ __forceinline__ void geometry_update(const FrameConst& c, const Volum
                 const float2 wbf = make_float2(__uint_as_float(wb0), __uint_as_float(wb1));
                 const float2 wf = __fadd2_rn(wbf, f2(-8388608.0f));               // w, exact
                 const float2 nb = __ffma2_rn(wbf, f2(-1.0f), f2(8388607.0f));     // -(w + 1), exact
-                const float2 y = rcp2_rn(__fadd2_rn(wbf, f2(-8388607.0f)));  // RN(1 / (w + 1)), w + 1 exact
+                const float2 y = rcp2_rn(__fadd2_rn(wbf, f2(-8388607.0f)), nb);  // RN(1 / (w + 1)); w + 1 exact
                 // F <- fmaf(F, w, t) / (w + 1), the quotient by div_by_weight's steps
                 const float2 a = __ffma2_rn(make_float2(fin[2 * h], fin[2 * h + 1]), wf, t);
                 const float2 q = __fmul2_rn(a, y);
@@ -1922,10 +1922,20 @@ __global__ void __launch_bounds__(COL_THREADS, 4) k_batch_step(const ScanDesc* _
         const ScanDesc& d = descs[s];
         const uint32_t k0 = (item - pre[s]) * tile, k1 = min(k0 + (uint32_t)tile, d.scr.ctr->n_geo);
         uint32_t count = 0, changed = 0;
+        const bool aligned = d.c.ng[0] % BRICK == 0 && d.c.ng[1] % BRICK == 0 && d.c.ng[2] % BRICK == 0;
         for (uint32_t k = k0; k < k1; ++k) {
-            const BrickAt at = geo_brick(d.c, d.scr.geo_list[k]);  // the general form handles every brick
+            const uint32_t e = d.scr.geo_list[k];
+            const BrickAt at = geo_brick(d.c, e);
             const DepthMm dm{d.depth};
-            if (d.c.kd_pinhole && d.c.free_space)
+            // the usual camera and mode: without the per-voxel image tests for
+            // bricks inside the image and without bounds tests for whole-brick
+            // volumes; the general form handles every other brick
+            if (d.c.kd_pinhole && d.c.free_space && aligned) {
+                if (e & GEO_INNER)
+                    geometry_brick<true, true, true, true>(d.c, d.vol, dm, at, lane, count, changed);
+                else
+                    geometry_brick<true, true, true, false>(d.c, d.vol, dm, at, lane, count, changed);
+            } else if (d.c.kd_pinhole && d.c.free_space)
                 geometry_brick<true, true>(d.c, d.vol, dm, at, lane, count, changed);
             else if (d.c.kd_pinhole)
                 geometry_brick<true, false>(d.c, d.vol, dm, at, lane, count, changed);
