@@ -46,42 +46,50 @@ __host__ __device__ inline uint32_t depth_strips(const FrameConst& c) {
     return (uint32_t)((c.dw + STRIP_PX - 1) / STRIP_PX) * (uint32_t)c.tiles_y;
 }
 
+// Depth tiles of one 32 x 8-pixel strip (four 8 x 8 tiles) by one warp: lane
+// x reads column x of the strip's eight rows (eight independent reads, each
+// row's 64 bytes coalesced); min / max over the column, then over each group
+// of eight lanes.  depth_m (optional) receives the strip's depths in metres.
+__device__ __forceinline__ void depth_strip(const FrameConst& c, const uint16_t* __restrict__ depth,
+                                            uint32_t* __restrict__ tiles, float* __restrict__ depth_m,
+                                            uint32_t strip, int lane) {
+    static_assert(TILE_PX == 8 && STRIP_PX == 4 * TILE_PX, "the lane layout below assumes 8x8 tiles");
+    const uint32_t sx_n = (uint32_t)((c.dw + STRIP_PX - 1) / STRIP_PX);
+    const int ty = (int)(strip / sx_n), sx = (int)(strip % sx_n);
+    const int px = sx * STRIP_PX + lane;
+    const bool xin = px < c.dw;
+    uint32_t D[TILE_PX];
+#pragma unroll
+    for (int r = 0; r < TILE_PX; ++r) {  // the eight row reads are independent
+        const int py = ty * TILE_PX + r;
+        D[r] = xin && py < c.dh ? depth[(size_t)py * c.dw + px] : 0u;
+    }
+    uint32_t mn = 0xFFFFu, mx = 0u;
+    const float ninf = __int_as_float(0xff800000);
+#pragma unroll
+    for (int r = 0; r < TILE_PX; ++r) {
+        const int py = ty * TILE_PX + r;
+        if (depth_m && xin && py < c.dh) depth_m[(size_t)py * c.dw + px] = D[r] ? (float)D[r] * 0.001f : ninf;
+        mn = min(mn, D[r] ? D[r] : 0xFFFFu);
+        mx = max(mx, D[r]);
+    }
+#pragma unroll
+    for (int o = 1; o < TILE_PX; o <<= 1) {  // within each group of eight lanes
+        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    const int tx = sx * 4 + (lane >> 3);
+    if ((lane & 7) == 0 && tx < c.tiles_x) tiles[ty * c.tiles_x + tx] = mn | (mx << 16);
+}
+
 __global__ void __launch_bounds__(TILES_THREADS) k_depth_tiles(FrameConst c, const uint16_t* __restrict__ depth,
                                                                uint32_t* __restrict__ tiles,
                                                                Counters* __restrict__ ctr,
                                                                float* __restrict__ depth_m) {
     chain_enter();
-    static_assert(TILE_PX == 8 && STRIP_PX == 4 * TILE_PX, "the lane layout below assumes 8x8 tiles");
     const int lane = threadIdx.x & 31;
     const uint32_t strip = blockIdx.x * (TILES_THREADS / 32) + (threadIdx.x >> 5);
-    const uint32_t sx_n = (uint32_t)((c.dw + STRIP_PX - 1) / STRIP_PX);
-    if (strip < depth_strips(c)) {
-        const int ty = (int)(strip / sx_n), sx = (int)(strip % sx_n);
-        const int px = sx * STRIP_PX + lane;
-        const bool xin = px < c.dw;
-        uint32_t D[TILE_PX];
-#pragma unroll
-        for (int r = 0; r < TILE_PX; ++r) {  // the eight row reads are independent
-            const int py = ty * TILE_PX + r;
-            D[r] = xin && py < c.dh ? depth[(size_t)py * c.dw + px] : 0u;
-        }
-        uint32_t mn = 0xFFFFu, mx = 0u;
-        const float ninf = __int_as_float(0xff800000);
-#pragma unroll
-        for (int r = 0; r < TILE_PX; ++r) {
-            const int py = ty * TILE_PX + r;
-            if (depth_m && xin && py < c.dh) depth_m[(size_t)py * c.dw + px] = D[r] ? (float)D[r] * 0.001f : ninf;
-            mn = min(mn, D[r] ? D[r] : 0xFFFFu);
-            mx = max(mx, D[r]);
-        }
-#pragma unroll
-        for (int o = 1; o < TILE_PX; o <<= 1) {  // within each group of eight lanes
-            mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        }
-        const int tx = sx * 4 + (lane >> 3);
-        if ((lane & 7) == 0 && tx < c.tiles_x) tiles[ty * c.tiles_x + tx] = mn | (mx << 16);
-    }
+    if (strip < depth_strips(c)) depth_strip(c, depth, tiles, depth_m, strip, lane);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         // fold the previous frame's geometry-side counters into the running
         // totals (the colour side is folded by the geometry kernel, so this
@@ -1881,22 +1889,10 @@ __global__ void __launch_bounds__(COL_THREADS, 4) k_batch_step(const ScanDesc* _
     }
     if (tid == 0) sync->band_next = 0;
     if (blockIdx.x == 0 && *(volatile unsigned*)&sync->stall) return;  // test injection: never arrive
-    scan_prefix(pre, n, 1, [&](int i) { return (uint32_t)(descs[i].c.tiles_x * descs[i].c.tiles_y); });
-    for (uint32_t item = warp; item < pre[n]; item += nwarps) {  // one warp per depth tile
+    scan_prefix(pre, n, 1, [&](int i) { return depth_strips(descs[i].c); });
+    for (uint32_t item = warp; item < pre[n]; item += nwarps) {  // one warp per strip of four depth tiles
         const int s = find_scan(pre, n, item);
-        const FrameConst& c = descs[s].c;
-        const uint32_t t = item - pre[s];
-        const int tx = t % c.tiles_x, ty = t / c.tiles_x;
-        uint32_t mn = 0xFFFFu, mx = 0u;
-        for (int k = lane; k < TILE_PX * TILE_PX; k += 32) {
-            const int px = tx * TILE_PX + (k & (TILE_PX - 1)), py = ty * TILE_PX + k / TILE_PX;
-            const uint32_t D = (px < c.dw && py < c.dh) ? descs[s].depth[(size_t)py * c.dw + px] : 0u;
-            if (D) mn = min(mn, D);
-            mx = max(mx, D);
-        }
-        mn = __reduce_min_sync(full, mn);
-        mx = __reduce_max_sync(full, mx);
-        if (lane == 0) descs[s].scr.depth_tiles[t] = mn | (mx << 16);
+        depth_strip(descs[s].c, descs[s].depth, descs[s].scr.depth_tiles, nullptr, item - pre[s], lane);
     }
     if (!grid_barrier(sync, gridDim.x)) return;
 
