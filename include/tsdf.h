@@ -148,12 +148,16 @@ tsdf_status tsdf_create_ex(const int32_t dims_geo[3], const int32_t dims_col[3],
  *   depth_mm  dsz.height x dsz.width uint16, host or device pointer
  *   rgb_hwc   csz.height x csz.width x 3 uint8, host or device pointer
  *   K_depth, K_rgb, T_world_depth, T_depth_rgb: host pointers, read before return
- * Host images are copied with cudaMemcpyAsync on the volume's internal
- * second stream (which runs the frame's depth tiles and brick culling beside
- * the previous frame's colour kernels, and which the handle's stream waits
- * for before the frame's geometry update): pageable memory is consumed before
- * the call returns, page-locked memory by the time the handle's stream
- * reaches the frame's geometry update.  Device images are read in place by
+ * Host images are copied with cudaMemcpyAsync into one of two device staging
+ * buffers, on an internal copy stream as soon as the frame before the
+ * previous one has finished with that buffer (so the copy runs beside the
+ * previous frame's geometry update), or, for the first frame after anything
+ * that broke the frame sequence, on the volume's internal second stream
+ * (which runs the frame's depth tiles and brick culling beside the previous
+ * frame's colour kernels, and which the handle's stream waits for before the
+ * frame's geometry update): pageable memory is consumed before the call
+ * returns, page-locked memory by the time the handle's stream reaches the
+ * frame's geometry update.  Device images are read in place by
  * kernels queued on the streams, after all work queued on the handle's
  * stream before the call (a device depth image then waits for the previous
  * frame's colour kernels too; see tsdf_set_device_inputs_ready).  In both
