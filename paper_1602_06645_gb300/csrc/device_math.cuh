@@ -105,15 +105,13 @@ __device__ __forceinline__ float div_by_weight(float a, float b, float y) {
 // hardware's approximate reciprocal (within an ulp) refined by one Newton
 // step with a fused residual, y = y0 + y0 (1 - z y0), whose rounding gives
 // RN(1/z) over that whole range (checked exhaustively against __frcp_rn).
-// The same given neg_z = -z as well (a caller that has it saves the negation).
-__device__ __forceinline__ float2 rcp2_rn(float2 z, float2 neg_z) {
+__device__ __forceinline__ float2 rcp2_rn(float2 z) {
     float2 y0;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0.x) : "f"(z.x));
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0.y) : "f"(z.y));
-    const float2 e = __ffma2_rn(neg_z, y0, make_float2(1.0f, 1.0f));
+    const float2 e = __ffma2_rn(make_float2(-z.x, -z.y), y0, make_float2(1.0f, 1.0f));
     return __ffma2_rn(e, y0, y0);
 }
-__device__ __forceinline__ float2 rcp2_rn(float2 z) { return rcp2_rn(z, make_float2(-z.x, -z.y)); }
 
 // Entry of a kernel of the per-frame chain.  Launched with programmatic
 // stream serialization, a kernel may start while its predecessor drains:

@@ -599,7 +599,7 @@ __device__ __forceinline__ void geometry_update(const FrameConst& c, const Volum
                 const float2 wbf = make_float2(__uint_as_float(wb0), __uint_as_float(wb1));
                 const float2 wf = __fadd2_rn(wbf, f2(-8388608.0f));               // w, exact
                 const float2 nb = __ffma2_rn(wbf, f2(-1.0f), f2(8388607.0f));     // -(w + 1), exact
-                const float2 y = rcp2_rn(__fadd2_rn(wbf, f2(-8388607.0f)), nb);  // RN(1 / (w + 1)); w + 1 exact
+                const float2 y = rcp2_rn(__fadd2_rn(wbf, f2(-8388607.0f)));  // RN(1 / (w + 1)), w + 1 exact
                 // F <- fmaf(F, w, t) / (w + 1), the quotient by div_by_weight's steps
                 const float2 a = __ffma2_rn(make_float2(fin[2 * h], fin[2 * h + 1]), wf, t);
                 const float2 q = __fmul2_rn(a, y);
