@@ -249,10 +249,13 @@ def _i32x3(v):
 
 
 def _mat(a, n):
-    arr = np.ascontiguousarray(np.asarray(a, dtype=np.float32).reshape(-1))
+    """(binary32 copy of a matrix, a ctypes float array over it).  The array
+    converts to the float* of the C signatures; built from the buffer it costs
+    a third of a numpy ctypes pointer, which counts at one call per frame."""
+    arr = np.array(a, dtype=np.float32, copy=True).reshape(-1)
     if arr.size != n:
         raise ValueError("expected %d values, got %d" % (n, arr.size))
-    return arr, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    return arr, (ctypes.c_float * n).from_buffer(arr)
 
 
 def _ptr(x, dtype, keep):
