@@ -167,39 +167,56 @@ __global__ void __launch_bounds__(TRACK_THREADS) k_icp_terms(TrackLevel L, const
 }
 
 // ------------------------------------------------------ solve and update --
-// One warp: the block partials summed in block order (lane k < NSUM owns sum
-// k), then lane 0 solves A xi = -g by Cholesky (binary64) and applies
+// One block of eight warps: the blocks' partials summed per sum in a fixed order,
+// then thread 0 solves A xi = -g by Cholesky (binary64) and applies
 // T <- exp(xi^) T; a matrix that is not positive definite leaves T as it is.
 // The step's sums, its starting pose and its xi are recorded at record.
-__global__ void k_icp_solve(const double* __restrict__ partials, int blocks, double* __restrict__ pose,
-                            double* __restrict__ record) {
+constexpr int SOLVE_THREADS = 256;
+__global__ void __launch_bounds__(SOLVE_THREADS) k_icp_solve(const double* __restrict__ partials, int blocks,
+                                                              double* __restrict__ pose, double* __restrict__ record) {
     __shared__ double s[NSUM];
-    const int lane = threadIdx.x;
-    if (lane < NSUM) {
+    // warp w sums partials w, w + 8, ...: lane l the blocks l, l + 32, ... in
+    // order, then the lanes in a fixed shuffle pattern (deterministic)
+    const int lane = threadIdx.x & 31;
+    for (int k = threadIdx.x >> 5; k < NSUM; k += SOLVE_THREADS / 32) {
         double v = 0.0;
-        for (int b = 0; b < blocks; ++b) v += partials[(size_t)b * NSUM + lane];
-        s[lane] = v;
+        for (int b = lane; b < blocks; b += 32) v += partials[(size_t)b * NSUM + k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) s[k] = v;
     }
-    __syncwarp();
-    if (lane != 0) return;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
     double A[36], g[6];
     int k = 0;
+#pragma unroll
     for (int a = 0; a < 6; ++a)
+#pragma unroll
         for (int b = a; b < 6; ++b, ++k) A[a * 6 + b] = A[b * 6 + a] = s[k];
+#pragma unroll
     for (int a = 0; a < 6; ++a) g[a] = s[21 + a];
     // record: sums (29), pose before the step (16), xi (6), solved flag (1)
+#pragma unroll
     for (int i = 0; i < NSUM; ++i) record[i] = s[i];
+#pragma unroll
     for (int i = 0; i < 16; ++i) record[NSUM + i] = pose[i];
+    // fully unrolled (the arrays then live in registers, not in local
+    // memory); a pivot that is not positive marks the step unsolved and is
+    // replaced by 1 so the remaining arithmetic stays finite (its result is
+    // not used)
     double Lc[36] = {0.0};
     bool ok = true;
-    for (int i = 0; i < 6 && ok; ++i)
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
         for (int j = 0; j <= i; ++j) {
             double v = A[i * 6 + j];
+#pragma unroll
             for (int q = 0; q < j; ++q) v -= Lc[i * 6 + q] * Lc[j * 6 + q];
             if (i == j) {
                 if (!(v > 0.0)) {
                     ok = false;
-                    break;
+                    v = 1.0;
                 }
                 Lc[i * 6 + i] = sqrt(v);
             } else {
@@ -209,13 +226,17 @@ __global__ void k_icp_solve(const double* __restrict__ partials, int blocks, dou
     double xi[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (ok) {
         double y[6];
+#pragma unroll
         for (int i = 0; i < 6; ++i) {
             double v = -g[i];
+#pragma unroll
             for (int q = 0; q < i; ++q) v -= Lc[i * 6 + q] * y[q];
             y[i] = v / Lc[i * 6 + i];
         }
+#pragma unroll
         for (int i = 5; i >= 0; --i) {
             double v = y[i];
+#pragma unroll
             for (int q = i + 1; q < 6; ++q) v -= Lc[q * 6 + i] * xi[q];
             xi[i] = v / Lc[i * 6 + i];
         }
@@ -235,26 +256,36 @@ __global__ void k_icp_solve(const double* __restrict__ partials, int blocks, dou
         }
         const double W[9] = {0, -phi[2], phi[1], phi[2], 0, -phi[0], -phi[1], phi[0], 0};
         double W2[9], Rm[9], Vm[9], tv[3], out[12];
+#pragma unroll
         for (int i = 0; i < 3; ++i)
+#pragma unroll
             for (int j = 0; j < 3; ++j) {
                 double v = 0.0;
+#pragma unroll
                 for (int q = 0; q < 3; ++q) v += W[i * 3 + q] * W[q * 3 + j];
                 W2[i * 3 + j] = v;
             }
+#pragma unroll
         for (int i = 0; i < 9; ++i) {
             const double I = (i % 4 == 0) ? 1.0 : 0.0;
             Rm[i] = I + cA * W[i] + cB * W2[i];
             Vm[i] = I + cB * W[i] + cC * W2[i];
         }
+#pragma unroll
         for (int i = 0; i < 3; ++i) tv[i] = Vm[i * 3] * rho[0] + Vm[i * 3 + 1] * rho[1] + Vm[i * 3 + 2] * rho[2];
+#pragma unroll
         for (int i = 0; i < 3; ++i)
+#pragma unroll
             for (int j = 0; j < 4; ++j) {
                 double v = 0.0;
+#pragma unroll
                 for (int q = 0; q < 3; ++q) v += Rm[i * 3 + q] * pose[q * 4 + j];
                 out[i * 4 + j] = v + (j == 3 ? tv[i] : 0.0);
             }
+#pragma unroll
         for (int i = 0; i < 12; ++i) pose[i] = out[i];
     }
+#pragma unroll
     for (int i = 0; i < 6; ++i) record[NSUM + 16 + i] = xi[i];
     record[NSUM + 22] = ok ? 1.0 : 0.0;
 }
@@ -282,9 +313,16 @@ cudaError_t launch_track_maps(const float* d, int w, int h, const float Kinv4[4]
     return cudaGetLastError();
 }
 
+// Blocks of a terms launch: one thread per pixel up to TRACK_MAX_BLOCKS
+// blocks, then each thread takes several pixels.  Each block reduces its 29
+// binary64 sums across its threads; with more blocks that reduction, not the
+// pixels, became the kernel's main cost (measured per tracked frame: 1024
+// blocks 4.34 ms, 608 and 320 4.35-4.38 ms, 152 3.88 ms, 114 3.96 ms, 76
+// 4.05 ms).
+constexpr int TRACK_MAX_BLOCKS = 152;  // one per SM of a GB300
 int track_blocks(int npx) {
     const int want = (npx + TRACK_THREADS - 1) / TRACK_THREADS;
-    return want < 1024 ? (want > 0 ? want : 1) : 1024;
+    return want < TRACK_MAX_BLOCKS ? (want > 0 ? want : 1) : TRACK_MAX_BLOCKS;
 }
 
 size_t track_record_doubles() { return NSUM + 16 + 6 + 1; }
@@ -293,7 +331,7 @@ cudaError_t launch_track_step(const TrackLevel& L, double* pose, double* partial
                               cudaStream_t stream) {
     const int blocks = track_blocks(L.w * L.h);
     k_icp_terms<<<blocks, TRACK_THREADS, 0, stream>>>(L, pose, partials);
-    k_icp_solve<<<1, 32, 0, stream>>>(partials, blocks, pose, record);
+    k_icp_solve<<<1, SOLVE_THREADS, 0, stream>>>(partials, blocks, pose, record);
     return cudaGetLastError();
 }
 
