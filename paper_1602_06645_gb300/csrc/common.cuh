@@ -81,7 +81,7 @@ struct Counters {
     uint32_t n_cells;    // trilinear cells that can pass the band gate
     uint32_t n_col_active;   // colour candidates with at least one such cell
     uint32_t n_geo_changed;  // geometry bricks with at least one updated voxel
-    uint32_t pad;
+    uint32_t n_col_light;    // colour work list entries filled from the buffer's end (taken last)
     unsigned long long geo_updated;
     unsigned long long col_updated;
     // running totals over frames, folded in by the first kernel of each frame
@@ -136,6 +136,7 @@ struct Scratch {
     uint32_t* geo_list;
     uint32_t* vis_list;
     uint32_t* col_list;
+    uint8_t* col_act;       // per geometry brick: active cells at its last band gate (capped at 255)
     uint32_t* depth_tiles;  // per 8x8 tile: min valid depth | max valid depth << 16
     float* depth_m;         // per pixel RN(D * 0.001) metres, -inf where D = 0
     uint8_t* bstate;        // per brick, this frame: bit 0 = in the geometry list, bit 1 = visible

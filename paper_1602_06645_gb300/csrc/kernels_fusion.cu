@@ -317,6 +317,41 @@ __device__ __forceinline__ void block_append2(bool p0, bool p1, uint32_t value0,
     __syncthreads();  // off is reused by the block's next call
 }
 
+// The same for three lists, the third filled from its end down: its k-th
+// value goes to list2_end[-1 - k].
+template <int NT>
+__device__ __forceinline__ void block_append3(bool p0, bool p1, bool p2, uint32_t value0, uint32_t value1,
+                                              uint32_t value2, uint32_t* ctr0, uint32_t* list0, uint32_t* ctr1,
+                                              uint32_t* list1, uint32_t* ctr2, uint32_t* list2_end) {
+    constexpr int NW = NT / 32;
+    __shared__ uint32_t off[3][NW + 1];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned m[3] = {__ballot_sync(0xffffffffu, p0), __ballot_sync(0xffffffffu, p1),
+                           __ballot_sync(0xffffffffu, p2)};
+    if (lane == 0) {
+        off[0][wid] = __popc(m[0]);
+        off[1][wid] = __popc(m[1]);
+        off[2][wid] = __popc(m[2]);
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        uint32_t tot = 0;
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t n = off[threadIdx.x][w];
+            off[threadIdx.x][w] = tot;
+            tot += n;
+        }
+        uint32_t* ctr = threadIdx.x == 0 ? ctr0 : (threadIdx.x == 1 ? ctr1 : ctr2);
+        off[threadIdx.x][NW] = tot ? atomicAdd(ctr, tot) : 0u;
+    }
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    if (p0) list0[off[0][NW] + off[0][wid] + __popc(m[0] & lt)] = value0;
+    if (p1) list1[off[1][NW] + off[1][wid] + __popc(m[1] & lt)] = value1;
+    if (p2) list2_end[-1 - (int64_t)(off[2][NW] + off[2][wid] + __popc(m[2] & lt))] = value2;
+    __syncthreads();  // off is reused by the block's next call
+}
+
 // Add per-warp counts (the same value in every lane of a warp) to up to three
 // global counters with one atomic per counter per block (all threads of the
 // block call it): the warps of a balanced kernel end together, and one atomic
@@ -697,10 +732,10 @@ __global__ void __launch_bounds__(GEO_THREADS, 8) k_geometry(FrameConst c, Volum
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         // fold the previous frame's colour-side counters into the running totals
         ctr->tot_col_updated += ctr->col_updated;
-        ctr->tot_col_bricks += ctr->n_col;
+        ctr->tot_col_bricks += ctr->n_col + ctr->n_col_light;
         ctr->tot_cells += ctr->n_cells;
         ctr->tot_col_active += ctr->n_col_active;
-        ctr->n_col = ctr->col_next = 0;
+        ctr->n_col = ctr->col_next = ctr->n_col_light = 0;
         ctr->n_cells = ctr->n_vox = ctr->n_col_active = 0;
         ctr->col_updated = 0ull;
     }
@@ -799,10 +834,13 @@ __device__ __forceinline__ bool colour_candidate(const FrameConst& c, const Bric
 }
 
 constexpr int LIST_THREADS = 256;
+constexpr uint8_t BUSY_CELLS = 32;  // active cells from which a candidate goes to the list's front
 
 __global__ void __launch_bounds__(LIST_THREADS) k_colour_list(FrameConst c, const BrickSummary* __restrict__ summ,
                                                      Counters* __restrict__ ctr, const uint32_t* __restrict__ vis_list,
-                                                     uint32_t* __restrict__ col_list) {
+                                                     uint32_t* __restrict__ col_list,
+                                                     const uint8_t* __restrict__ col_act) {
+    const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
     // The visible list and its length come from the brick culling, which had
     // finished before the geometry kernel this one follows could start, so
     // they are read before waiting for the geometry kernel (the summaries it
@@ -817,7 +855,11 @@ __global__ void __launch_bounds__(LIST_THREADS) k_colour_list(FrameConst c, cons
         const uint32_t in = i + gridDim.x * blockDim.x;
         b_next = in < n ? vis_list[in] : 0u;
         const bool act = i < n && colour_candidate(c, summ, b);
-        block_append2<LIST_THREADS>(act, false, b, b, &ctr->n_col, col_list, nullptr, nullptr);
+        // bricks with many active cells at their last band gate take the
+        // longest: they go first, the others to the list's end
+        const bool busy = act && col_act[b] >= BUSY_CELLS;
+        block_append3<LIST_THREADS>(busy, false, act && !busy, b, b, b, &ctr->n_col, col_list, nullptr, nullptr,
+                                    &ctr->n_col_light, col_list + nbt);
     }
 }
 
@@ -1190,6 +1232,7 @@ __device__ __forceinline__ void band_brick(const FrameConst& c, const Volumes& v
         if (lane >= o) incl += v;
     }
     const uint32_t nact = __shfl_sync(full, incl, 31);
+    if (lane == 0 && scr.col_act) scr.col_act[b] = (uint8_t)min(nact, 255u);  // orders the next frame's list
     if (nact == 0) return;  // no colour voxel of this brick can pass the band gate
     ++n_active;
     n_cells += nact;
@@ -1352,7 +1395,10 @@ __global__ void __launch_bounds__(COL_THREADS, 5) k_colour_band(FrameConst c, Vo
     Counters* __restrict__ ctr = scr.ctr;
     const int lane = threadIdx.x & 31;
     const unsigned full = 0xffffffffu;
-    const uint32_t n = ctr->n_col;
+    // the list's front part (bricks busy at their last band gate), then its
+    // part filled from the buffer's end
+    const uint32_t nh = ctr->n_col, n = nh + ctr->n_col_light;
+    const uint32_t nbt = (uint32_t)c.nb[0] * c.nb[1] * c.nb[2];
     uint32_t count = 0, n_active = 0, n_cells = 0, nstage = 0;
     // a warp's first item is its index in the grid, the later ones are
     // claimed from the counter (offset by the warp count), each while the
@@ -1363,7 +1409,8 @@ __global__ void __launch_bounds__(COL_THREADS, 5) k_colour_band(FrameConst c, Vo
         const uint32_t item = __shfl_sync(full, next, 0);
         if (item >= n) break;
         if (lane == 0) next = nwarps + atomicAdd(&ctr->col_next, 1u);
-        band_brick(c, vol, depth, rgb, scr, S, scr.col_list[item], lane, count, n_active, n_cells, nstage);
+        const uint32_t b = item < nh ? scr.col_list[item] : scr.col_list[nbt - 1u - (item - nh)];
+        band_brick(c, vol, depth, rgb, scr, S, b, lane, count, n_active, n_cells, nstage);
         __syncwarp();
     }
     band_flush(c, vol, depth, rgb, scr, S, lane, count, nstage);
@@ -1549,10 +1596,10 @@ __global__ void __launch_bounds__(COL_THREADS, 5) k_fused(FrameConst c, Volumes 
         // the first block: fold the previous frame's colour-side counters into
         // the running totals, then let the colour work start
         ctr->tot_col_updated += ctr->col_updated;
-        ctr->tot_col_bricks += ctr->n_col;
+        ctr->tot_col_bricks += ctr->n_col + ctr->n_col_light;
         ctr->tot_cells += ctr->n_cells;
         ctr->tot_col_active += ctr->n_col_active;
-        ctr->n_col = ctr->col_next = 0;
+        ctr->n_col = ctr->col_next = ctr->n_col_light = 0;
         ctr->n_cells = ctr->n_vox = ctr->n_col_active = 0;
         ctr->col_updated = 0ull;
         __threadfence();
@@ -1875,13 +1922,13 @@ __global__ void __launch_bounds__(COL_THREADS, 4) k_batch_step(const ScanDesc* _
         ctr->tot_geo_updated += ctr->geo_updated;
         ctr->tot_col_updated += ctr->col_updated;
         ctr->tot_geo_bricks += ctr->n_geo;
-        ctr->tot_col_bricks += ctr->n_col;
+        ctr->tot_col_bricks += ctr->n_col + ctr->n_col_light;
         ctr->tot_vis_bricks += ctr->n_vis;
         ctr->tot_cells += ctr->n_cells;
         ctr->tot_col_active += ctr->n_col_active;
         ctr->tot_geo_changed += ctr->n_geo_changed;
         ctr->frames += 1ull;
-        ctr->n_geo = ctr->n_vis = ctr->n_col = 0;
+        ctr->n_geo = ctr->n_vis = ctr->n_col = ctr->n_col_light = 0;
         ctr->geo_next = ctr->col_next = 0;
         ctr->n_cells = ctr->n_vox = 0;
         ctr->n_col_active = ctr->n_geo_changed = 0;
@@ -2104,7 +2151,7 @@ cudaError_t launch_frame_post(const FrameConst& c, const Volumes& v, const Scrat
         if (gl > 1024u) gl = 1024u;
         if (e == cudaSuccess)
             e = launch_chained(k_colour_list, dim3(gl), dim3(LIST_THREADS), 0, stream, c, v.summ, s.ctr, s.vis_list,
-                               s.col_list);
+                               s.col_list, s.col_act);
         if (list_done) cudaEventRecord(list_done, stream);
         mark(4);
         if (e == cudaSuccess)
@@ -2151,7 +2198,7 @@ cudaError_t launch_frame_record(const FrameConst& c, const Volumes& v, const Scr
     launch_k_geometry(c, v, s, g.geo, stream);
     unsigned gl = (nbt + LIST_THREADS - 1) / LIST_THREADS;
     if (gl > 1024u) gl = 1024u;
-    k_colour_list<<<gl, LIST_THREADS, 0, stream>>>(c, v.summ, s.ctr, s.vis_list, s.col_list);
+    k_colour_list<<<gl, LIST_THREADS, 0, stream>>>(c, v.summ, s.ctr, s.vis_list, s.col_list, s.col_act);
     k_colour_band<<<g.col, COL_THREADS, colour_smem_bytes(), stream>>>(c, v, depth, nullptr, s);
     k_colour_gates<<<g.vox, 256, 0, stream>>>(c, depth, s, a, frame);
     return cudaGetLastError();

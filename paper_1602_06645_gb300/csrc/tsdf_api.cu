@@ -550,6 +550,7 @@ tsdf_status tsdf_create_ex(const int32_t dims_geo[3], const int32_t dims_col[3],
     v->scr.geo_list = (uint32_t*)dev_alloc(v, (size_t)nbt * sizeof(uint32_t));
     v->scr.vis_list = (uint32_t*)dev_alloc(v, (size_t)nbt * sizeof(uint32_t));
     v->scr.col_list = (uint32_t*)dev_alloc(v, (size_t)nbt * sizeof(uint32_t));
+    v->scr.col_act = (uint8_t*)dev_alloc(v, (size_t)nbt);
     v->scr.err = (uint32_t*)dev_alloc(v, sizeof(uint32_t));
     // fused frame: per-brick state bytes and neighbour counts, the ready queue and its counters
     v->scr.bstate = (uint8_t*)dev_alloc(v, (size_t)nbt);
@@ -565,7 +566,7 @@ tsdf_status tsdf_create_ex(const int32_t dims_geo[3], const int32_t dims_col[3],
     }
     v->scr.vox = (uint2*)dev_alloc(v, (size_t)v->scr.vox_cap * sizeof(uint2));
     if (!v->vol.F || !v->vol.W || !v->vol.C || !v->vol.summ || !v->scr.ctr || !v->scr.geo_list || !v->scr.vis_list ||
-        !v->scr.col_list || !v->scr.err || !v->scr.vox || !v->scr.bstate || !v->scr.need || !v->scr.ready ||
+        !v->scr.col_list || !v->scr.col_act || !v->scr.err || !v->scr.vox || !v->scr.bstate || !v->scr.need || !v->scr.ready ||
         !v->scr.fsync) {
         tsdf_destroy(v);
         return TSDF_ERR_OOM;
@@ -584,6 +585,7 @@ tsdf_status tsdf_create_ex(const int32_t dims_geo[3], const int32_t dims_col[3],
     if (e == cudaSuccess) e = cudaMemsetAsync(v->scr.err, 0, sizeof(uint32_t), v->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->scr.ready, 0, (size_t)nbt * sizeof(unsigned long long), v->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(v->scr.fsync, 0, sizeof(FuseSync), v->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(v->scr.col_act, 0, (size_t)nbt, v->stream);
     if (e == cudaSuccess) e = launch_init_summaries(v->vol.summ, nbt, v->stream);
     if (e != cudaSuccess) {
         tsdf_destroy(v);
@@ -852,14 +854,14 @@ static void fill_stats(const tsdf_volume* v, const Counters& h, tsdf_stats* o) {
     o->geo_updated = (int64_t)h.geo_updated;
     o->col_updated = (int64_t)h.col_updated;
     o->geo_bricks = h.n_geo;
-    o->col_bricks = h.n_col;
+    o->col_bricks = h.n_col + h.n_col_light;
     o->visible_bricks = h.n_vis;
     o->total_bricks = (int64_t)v->nb[0] * v->nb[1] * v->nb[2];
     o->frames_counted = (int64_t)h.frames;
     o->total_geo_updated = (int64_t)(h.tot_geo_updated + h.geo_updated);
     o->total_col_updated = (int64_t)(h.tot_col_updated + h.col_updated);
     o->total_geo_bricks = (int64_t)(h.tot_geo_bricks + h.n_geo);
-    o->total_col_bricks = (int64_t)(h.tot_col_bricks + h.n_col);
+    o->total_col_bricks = (int64_t)(h.tot_col_bricks + h.n_col + h.n_col_light);
     o->total_visible_bricks = (int64_t)(h.tot_vis_bricks + h.n_vis);
     o->total_col_active_bricks = (int64_t)(h.tot_col_active + h.n_col_active);
     o->total_cells = (int64_t)(h.tot_cells + h.n_cells);
